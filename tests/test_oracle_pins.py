@@ -1,0 +1,360 @@
+"""Pins of the FP64 oracle to things other than itself.
+
+Each test checks the oracle against mathematics the paper fixes: a direct
+DFT (Sect. 4, exact unitarity on the torus), the dense Gaussian-elimination
+solve (Sect. 6.5), the block-inverse identity (Sect. 2.3), the Hoffman-Ribak
+covariance (eq. starH), a closed-form Laplace-type strip solution
+(Sect. 6.1), known-answer vectors of the random generator, and finite
+differences of the loss.  A dropped term, a flipped sign, a transposed index
+or a wrong normalisation in the oracle fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from workloads import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _small_case(ny=16, nx=16, seed=0, band=3, discs=2, r=2.0, spectrum="lorentz"):
+    if spectrum == "lorentz":
+        P = synth.spectrum_lorentz_beam(ny, nx, k0=2 * math.pi / 8, sb=0.8)
+    else:
+        P = synth.spectrum_cmb_like(ny, nx, 2 * math.pi / max(ny, nx), sb=0.6,
+                                    k_peak=2 * math.pi / 6, k_d=2 * math.pi / 3)
+    obs = synth.mask_band_discs(ny, nx, band, discs, r, r, seed)
+    return P, obs
+
+
+# ----------------------------------------------------------------- generator
+
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    for row in rows:
+        v = [int(t, 16) for t in row]
+        out = O.philox4x32_10(*[np.uint64(a) for a in v[:6]])
+        assert [int(o) for o in out] == v[6:10]
+
+
+def test_uniform52_range_and_exactness():
+    lo = O.uniform52(np.uint64(0), np.uint64(0))
+    hi = O.uniform52(np.uint64(0xFFFFFFFF), np.uint64(0xFFFFFFFF))
+    assert lo == 0.5 * 2.0 ** -52
+    assert hi == (2.0 ** 52 - 0.5) * 2.0 ** -52 and hi < 1.0
+
+
+def test_white_noise_moments():
+    xi = O.white_noise(512, 512, 12345).ravel()
+    n = xi.size
+    assert abs(xi.mean()) < 5 / math.sqrt(n)
+    assert abs(xi.var() - 1.0) < 5 * math.sqrt(2.0 / n)
+    # Gaussian shape: P(|xi| < 1) = erf(1/sqrt 2)
+    frac = np.mean(np.abs(xi) < 1.0)
+    p = math.erf(1 / math.sqrt(2))
+    assert abs(frac - p) < 5 * math.sqrt(p * (1 - p) / n)
+    # seed determines everything, different seeds differ
+    assert np.array_equal(O.white_noise(8, 8, 7), O.white_noise(8, 8, 7))
+    assert not np.array_equal(O.white_noise(8, 8, 7), O.white_noise(8, 8, 8))
+
+
+# ----------------------------------------------------------------- transforms
+
+def test_fft_matches_direct_dft():
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((8, 16))
+    assert np.allclose(np.fft.fft2(x), O.dft2_direct(x), rtol=0, atol=1e-12)
+
+
+def test_apply_power_is_dense_circulant():
+    """C x through the FFT equals the dense circulant matrix built from the
+    definition c(D) = (1/n) sum_k P(k) cos(k.D) (no FFT involved)."""
+    ny, nx = 8, 16
+    P = synth.spectrum_lorentz_beam(ny, nx, k0=1.0, sb=0.5)
+    Pf = O.hermitian_full(P, nx)
+    x = np.random.default_rng(1).standard_normal((ny, nx))
+    idx = np.arange(ny * nx)
+    for s in (1.0, -1.0, 0.5):
+        C = O.dense_matrix(O.circulant_corr(Pf, s), idx, idx)
+        assert np.allclose(O.apply_power(x, Pf, s).ravel(), C @ x.ravel(), rtol=1e-12, atol=1e-12)
+        assert np.allclose(C, C.T, atol=1e-13)
+
+
+def test_hermitian_full_matches_full_plane_formula():
+    ny, nx = 8, 12
+    P = synth.spectrum_lorentz_beam(ny, nx, k0=0.7, sb=0.9)
+    Pf = O.hermitian_full(P, nx)
+    ky = 2 * math.pi * np.fft.fftfreq(ny)
+    kx = 2 * math.pi * np.fft.fftfreq(nx)
+    k2 = ky[:, None] ** 2 + kx[None, :] ** 2
+    k0, sb = 0.7, 0.9
+    ref = np.exp(-k2 * sb * sb) / (k2 + k0 * k0) + 1e-4 * math.exp(-(k0 * sb) ** 2) / (2 * k0 * k0)
+    assert np.allclose(Pf, ref, rtol=1e-14)
+
+
+def test_unitary_round_trip():
+    """F^dagger F = I on the torus (Sect. 4): C^{1/2} C^{1/2} C^-1 x = x."""
+    P, _ = _small_case(32, 32)
+    Pf = O.hermitian_full(P, 32)
+    x = np.random.default_rng(2).standard_normal((32, 32))
+    y = O.apply_power(O.apply_power(O.apply_power(x, Pf, 0.5), Pf, 0.5), Pf, -1.0)
+    assert np.max(np.abs(y - x)) < 1e-12 * np.max(np.abs(x)) * 1e3
+
+
+def test_validate_spectrum_rejects():
+    P, _ = _small_case(8, 8)
+    with pytest.raises(ValueError):
+        O.validate_spectrum(-P, 8)
+    bad = P.copy()
+    bad[1, 0] *= 1.1          # breaks P(0,ky) = P(0,-ky)
+    with pytest.raises(ValueError):
+        O.validate_spectrum(bad, 8)
+    bad = P.copy()
+    bad[2, 0] = np.nan
+    with pytest.raises(ValueError):
+        O.validate_spectrum(bad, 8)
+
+
+# ----------------------------------------------------------------- solver
+
+def test_pcg_on_dense_spd_system():
+    """PCG against a direct solve on a random SPD system (no FFT)."""
+    rng = np.random.default_rng(3)
+    G = rng.standard_normal((60, 60))
+    A = G @ G.T + 60 * np.eye(60)
+    Binv = np.diag(1.0 / np.diag(A))
+    b = rng.standard_normal(60)
+    for pre in (None, lambda v: Binv @ v):
+        res = O.pcg(lambda v: A @ v, b, pre, tol=1e-13)
+        assert res.status == "converged"
+        assert np.allclose(res.u, np.linalg.solve(A, b), rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("n", [16, 32])
+def test_dense_ml_two_forms_agree(n):
+    """Block-inverse identity of Sect. 2.3: C_MU C_UU^-1 = -(Q_MM)^-1 Q_MU,
+    fixing the sign of x_ML (written without the minus in Sect. 1)."""
+    P, obs = _small_case(n, n, seed=n)
+    Pf = O.hermitian_full(P, n)
+    dU = np.random.default_rng(4).standard_normal(int(obs.sum()))
+    a = O.ml_dense_cov(Pf, obs, dU)
+    b = O.ml_dense_prec(Pf, obs, dU)
+    assert np.linalg.norm(a - b) <= 1e-9 * np.linalg.norm(a)
+
+
+@pytest.mark.parametrize("n,precond", [(16, True), (32, True), (32, False)])
+def test_realization_matches_dense_solve(n, precond):
+    """x_M = y_M + C_MU C_UU^-1 (d - y)_U by Cholesky, vs the PCG pipeline."""
+    P, obs = _small_case(n, n, seed=n + 1)
+    Pf = O.hermitian_full(P, n)
+    d = O.draw(Pf, 99)
+    r = O.realize(P, obs, d, seed=5, tol=1e-13, precond=precond)
+    m = obs.ravel() == 0
+    ref = r.y.ravel()[m] + O.ml_dense_cov(Pf, obs, (d - r.y).ravel()[~m])
+    assert r.pcg.status == "converged"
+    assert np.linalg.norm(r.x.ravel()[m] - ref) <= 1e-9 * np.linalg.norm(ref)
+    # unmasked pixels are the data, bit for bit
+    assert np.array_equal(r.x.ravel()[~m], d.ravel()[~m])
+
+
+def test_plain64_dense():
+    """The 64x64 plain-method workload against the dense solve."""
+    from workloads import workload
+    P, obs, spec = workload("plain64")
+    Pf = O.hermitian_full(P, 64)
+    d = O.draw(Pf, spec["data_seed"])
+    r = O.realize(P, obs, d, seed=spec["seeds"][0], tol=1e-12)
+    m = obs.ravel() == 0
+    ref = r.y.ravel()[m] + O.ml_dense_prec(Pf, obs, (d - r.y).ravel()[~m])
+    assert np.linalg.norm(r.x.ravel()[m] - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+def _stencil_spectrum(ny, nx, m2):
+    ky = 2 * math.pi * np.fft.fftfreq(ny)
+    kx = 2 * math.pi * np.arange(nx // 2 + 1) / nx
+    lam = 4 * np.sin(ky[:, None] / 2) ** 2 + 4 * np.sin(kx[None, :] / 2) ** 2
+    return 1.0 / (lam + m2)
+
+
+def test_stencil_residual_any_mask():
+    """P = 1/(lambda(k) + m^2) makes C^-1 the 5-point operator -Lap + m^2;
+    the ML fill then satisfies (4+m^2) x_i = sum of its 4 neighbours on M."""
+    ny, nx, m2 = 32, 32, 0.05
+    P = _stencil_spectrum(ny, nx, m2)
+    obs = synth.mask_band_discs(ny, nx, 4, 3, 3.0, 3.0, 21)
+    d = np.random.default_rng(6).standard_normal((ny, nx))
+    Pf = O.hermitian_full(P, nx)
+    b = O.rhs(Pf, obs, d, np.zeros_like(d))
+    masked = obs == 0
+    u = O.pcg(lambda v: O.apply_A(v, Pf, masked), b, tol=1e-13).u
+    x = np.where(masked, u, d)
+    nb = np.roll(x, 1, 0) + np.roll(x, -1, 0) + np.roll(x, 1, 1) + np.roll(x, -1, 1)
+    res = (4 + m2) * x - nb
+    assert np.max(np.abs(res[masked])) < 1e-9 * np.max(np.abs(d))
+
+
+def test_strip_closed_form():
+    """Full-width band of rows j0..j1 with the 5-point operator: each x-mode
+    interpolates the two boundary rows as sinh(theta(j1+1-j)) and
+    sinh(theta(j-j0+1)) over sinh(theta(j1-j0+2)), 2cosh(theta) = 2+lam_x+m^2
+    (the discrete analogue of the periodic-strip formula of Sect. 6.1)."""
+    ny, nx, m2 = 32, 16, 0.02
+    P = _stencil_spectrum(ny, nx, m2)
+    obs = (~synth.band_mask_rows(ny, nx, 10)).astype(np.uint8)
+    rows = np.nonzero(obs[:, 0] == 0)[0]
+    j0, j1 = rows[0], rows[-1]
+    d = np.random.default_rng(7).standard_normal((ny, nx))
+    Pf = O.hermitian_full(P, nx)
+    masked = obs == 0
+    b = O.rhs(Pf, obs, d, np.zeros_like(d))
+    u = O.pcg(lambda v: O.apply_A(v, Pf, masked), b, tol=1e-13).u
+    top, bot = np.fft.fft(d[j0 - 1]), np.fft.fft(d[j1 + 1])
+    kx = 2 * math.pi * np.fft.fftfreq(nx)
+    theta = np.arccosh((2 + 4 * np.sin(kx / 2) ** 2 + m2) / 2)
+    span = j1 - j0 + 2
+    for j in range(j0, j1 + 1):
+        row_hat = (top * np.sinh(theta * (j1 + 1 - j)) + bot * np.sinh(theta * (j - j0 + 1))) / np.sinh(theta * span)
+        assert np.allclose(u[j], np.real(np.fft.ifft(row_hat)), atol=1e-9)
+
+
+def test_white_spectrum_no_fill_needed():
+    """P = const: C^-1 is diagonal, (C^-1)_MU = 0, so b = 0 and x_M = y_M."""
+    ny = nx = 16
+    P = np.full((ny, nx // 2 + 1), 2.5)
+    obs = synth.mask_band_discs(ny, nx, 3, 1, 2.0, 2.0, 3)
+    d = np.random.default_rng(8).standard_normal((ny, nx))
+    r = O.realize(P, obs, d, seed=9, tol=1e-8)
+    m = obs == 0
+    assert np.max(np.abs(r.b)) < 1e-13 * np.max(np.abs(d))
+    assert np.max(np.abs(r.x[m] - r.y[m])) < 1e-12
+    assert np.array_equal(r.x[~m], d[~m])
+
+
+def test_trivial_masks():
+    ny = nx = 16
+    P, _ = _small_case(ny, nx)
+    d = np.random.default_rng(10).standard_normal((ny, nx))
+    r = O.realize(P, np.ones((ny, nx), np.uint8), d, seed=1)
+    assert np.array_equal(r.x, d) and r.pcg.iters == 0
+    r = O.realize(P, np.zeros((ny, nx), np.uint8), d, seed=1)
+    assert np.array_equal(r.x, r.y) and r.pcg.iters == 0
+
+
+def test_operator_symmetry():
+    """<a, A b> = <A a, b> and the same for S (the Hermiticity whose loss
+    stalls CG on the sphere, Sect. 3)."""
+    P, obs = _small_case(32, 32, seed=5)
+    Pf = O.hermitian_full(P, 32)
+    masked = obs == 0
+    rng = np.random.default_rng(11)
+    a = np.where(masked, rng.standard_normal((32, 32)), 0)
+    b = np.where(masked, rng.standard_normal((32, 32)), 0)
+    for op in (O.apply_A, O.apply_S):
+        lhs = np.sum(a * op(b, Pf, masked))
+        rhs = np.sum(op(a, Pf, masked) * b)
+        assert abs(lhs - rhs) <= 1e-13 * np.linalg.norm(a) * np.linalg.norm(op(b, Pf, masked))
+
+
+# ----------------------------------------------------------------- statistics
+
+def test_hoffman_ribak_covariance():
+    """Sample mean and covariance of x_M over seeds match x_ML and
+    C_MM - C_MU C_UU^-1 C_UM (eq. starH)."""
+    ny = nx = 8
+    P = synth.spectrum_lorentz_beam(ny, nx, k0=1.0, sb=0.6)
+    Pf = O.hermitian_full(P, nx)
+    obs = np.ones((ny, nx), np.uint8)
+    obs[3:5, 2:5] = 0
+    d = O.draw(Pf, 1234)
+    m = obs.ravel() == 0
+    ns = 3000
+    xs = np.array([O.realize(P, obs, d, seed=s, tol=1e-12).x.ravel()[m] for s in range(ns)])
+    cov = O.constrained_cov_dense(Pf, obs)
+    mean = O.ml_dense_cov(Pf, obs, d.ravel()[~m])
+    se_mean = np.sqrt(np.diag(cov) / ns)
+    assert np.all(np.abs(xs.mean(0) - mean) < 5 * se_mean)
+    S = np.cov(xs.T)
+    se = np.sqrt((np.outer(np.diag(cov), np.diag(cov)) + cov ** 2) / ns)
+    assert np.all(np.abs(S - cov) < 5 * se)
+
+
+def test_ensemble_power_spectrum():
+    """With d itself drawn from C, every filled map is a draw from C: the
+    band-averaged |F x|^2 / (n P) has mean 1 within sampling error."""
+    ny = nx = 32
+    P, obs = _small_case(ny, nx, seed=3, band=6, discs=3, r=3.0)
+    Pf = O.hermitian_full(P, nx)
+    k = np.sqrt((2 * math.pi * np.fft.fftfreq(ny))[:, None] ** 2 +
+                (2 * math.pi * np.fft.fftfreq(nx))[None, :] ** 2)
+    edges = np.array([0.0, 0.4, 0.8, 1.4, 2.0, 2.6, 4.5])
+    band = np.clip(np.searchsorted(edges, k, side="right") - 1, 0, len(edges) - 2)
+    nreal = 150
+    acc = np.zeros(len(edges) - 1)
+    for s in range(nreal):
+        d = O.draw(Pf, 10_000 + s)
+        x = O.realize(P, obs, d, seed=s, tol=1e-10).x
+        ratio = np.abs(np.fft.fft2(x)) ** 2 / (ny * nx * Pf)
+        acc += np.bincount(band.ravel(), weights=ratio.ravel(), minlength=len(acc))
+    counts = np.bincount(band.ravel(), minlength=len(acc))
+    mean = acc / (counts * nreal)
+    sigma = 1.0 / np.sqrt(counts * nreal / 2.0)     # Hermitian pairs are not independent
+    assert np.all(np.abs(mean - 1.0) < 5 * sigma), (mean, sigma)
+
+
+# ----------------------------------------------------------------- gradient
+
+def test_gradient_finite_differences():
+    """Adjoint gradients of L = sum_M x^2 vs central differences of the
+    oracle at tol 1e-13 (noise draw fixed by the seed)."""
+    ny = nx = 16
+    k_lo = 2 * math.pi / 16
+    nb = 6
+    bidx, sig, noise = synth.band_templates_half(ny, nx, k_lo, nb, sb=0.6)
+    obs = synth.mask_band_discs(ny, nx, 3, 2, 2.0, 2.0, 17)
+    amps = 1.0 + 0.1 * np.arange(nb)
+    P_of = lambda a: a[bidx] * sig + noise          # noqa: E731
+    d = O.draw(O.hermitian_full(P_of(amps), nx), 77)
+    seed = 5
+
+    def L(a, dd):
+        return O.loss_masked_sq(O.realize(P_of(a), obs, dd, seed, tol=1e-13).x, obs)
+
+    real = O.realize(P_of(amps), obs, d, seed, tol=1e-13)
+    gd, gb, _ = O.backward(P_of(amps), obs, d, seed, real, bidx, sig, tol=1e-13)
+    assert np.all(gd[obs == 0] == 0)
+    h = 1e-4
+    for b in range(nb):
+        e = np.zeros(nb)
+        e[b] = h
+        fd = (L(amps + e, d) - L(amps - e, d)) / (2 * h)
+        assert abs(fd - gb[b]) <= 1e-6 * max(1.0, abs(fd)), (b, fd, gb[b])
+    rng = np.random.default_rng(3)
+    for _ in range(4):
+        v = rng.standard_normal((ny, nx))
+        fd = (L(amps, d + h * v) - L(amps, d - h * v)) / (2 * h)
+        assert abs(fd - np.sum(gd * v)) <= 1e-6 * max(1.0, abs(fd))
+
+
+# ----------------------------------------------------------------- Lanczos
+
+def test_lanczos_extremes_from_cg():
+    """The CG coefficients give a Lanczos tridiagonal whose extreme Ritz
+    values approach the extreme eigenvalues of the preconditioned operator."""
+    P, obs = _small_case(16, 16, seed=4)
+    Pf = O.hermitian_full(P, 16)
+    m = obs.ravel() == 0
+    idx = np.nonzero(m)[0]
+    Q = O.dense_matrix(O.circulant_corr(Pf, -1.0), idx, idx)
+    Sh = O.dense_matrix(O.circulant_corr(Pf, 0.5), idx, idx)
+    ev = np.linalg.eigvalsh(Sh @ Q @ Sh)
+    b = O.rhs(Pf, obs, O.draw(Pf, 1), np.zeros((16, 16)))
+    masked = obs == 0
+    res = O.pcg(lambda v: O.apply_A(v, Pf, masked), b,
+                lambda v: O.apply_S(O.apply_S(v, Pf, masked), Pf, masked), tol=1e-14)
+    ritz = np.linalg.eigvalsh(O.lanczos_tridiag(res.alphas, res.betas))
+    assert ritz.min() >= ev.min() * (1 - 1e-6) and ritz.max() <= ev.max() * (1 + 1e-6)
+    assert abs(ritz.max() - ev.max()) < 1e-3 * ev.max()
