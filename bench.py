@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Benchmark: constrained Gaussian realizations per second (and CG iterations
+per second) on the 4096^2 wide-cut workload -- 20% band plus 2000 discs of
+radius 2-20 px, a CMB-like P(k), batches of 8 realizations of one data map,
+mixed precision (FP32 FFT operator, FP64 residuals and iterative refinement)
+down to a relative residual of 1e-10 -- next to the plain FP64 GPU PCG on the
+same inputs and the FP64 CPU oracle on the host cores.
+
+One step = one fill_realize call on a batch of 8 realizations.  Synthetic
+inputs: the spectrum and mask recipes of ``workloads`` and a data map drawn
+from P(k) on the GPU.  Every timed step streams ~1.5 GB per CG iteration
+through HBM, far more than the 129 MB L2, so no L2 flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Multi-GPU runs (torchrun) are replicas: each rank runs its own batches with
+its own seeds (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "constrained realizations/s at 4096^2 (rel err <= 1e-5; refined to 1e-10)"
+UNIT = "realizations/s"
+# FP64 PCG iterations for one realization of this workload at tol 1e-10
+# (measured by the FP64 GPU arm; used only to scale the oracle's per-iteration
+# CPU time to realizations/s in the reference / cpu_baseline legs).
+FP64_ITERS_WIDE4096 = 200
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="wide4096")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 PCG arm")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.lines, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx or None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def oracle_sample(P, obs, d, seed, iters):
+    """Times the FP64 CPU oracle on the full-size workload: the draw and the
+    right-hand side once, then `iters` preconditioned CG iterations."""
+    import numpy as np
+    import oracle as O
+    nx = obs.shape[1]
+    Pf = O.hermitian_full(P, nx)
+    masked = obs == 0
+    t0 = time.perf_counter()
+    y = O.draw(Pf, seed)
+    b = O.rhs(Pf, obs, d, y)
+    t1 = time.perf_counter()
+    A = lambda v: O.apply_A(v, Pf, masked)                                     # noqa: E731
+    B = lambda v: O.apply_S(O.apply_S(v, Pf, masked), Pf, masked)               # noqa: E731
+    res = O.pcg(A, b, B, tol=0.0, max_iter=iters)
+    t2 = time.perf_counter()
+    assert res.iters == iters and np.isfinite(res.u).all()
+    return t1 - t0, (t2 - t1) / iters
+
+
+def threads_used():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] + [1])
+    except Exception:
+        return 1
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle as O
+    from workloads import workload
+    P, obs, spec = workload(args.workload)
+    Pf = O.hermitian_full(P, obs.shape[1])
+    d = O.draw(Pf, spec["data_seed"])
+    nx = obs.shape[1]
+    masked = obs == 0
+    t0 = time.perf_counter()
+    b = O.rhs(Pf, obs, d, O.draw(Pf, spec["seeds"][0]))
+    setup = time.perf_counter() - t0
+    A = lambda v: O.apply_A(v, Pf, masked)                                     # noqa: E731
+    Bp = lambda v: O.apply_S(O.apply_S(v, Pf, masked), Pf, masked)              # noqa: E731
+    per_iter = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        O.pcg(A, b, Bp, tol=0.0, max_iter=1)
+        if k >= args.warmup:
+            per_iter.append(time.perf_counter() - t0)
+    t_iter = sum(per_iter) / len(per_iter)
+    t_real = setup + FP64_ITERS_WIDE4096 * t_iter
+    value = 1.0 / t_real
+    cores = threads_used()
+    sample = (f"oracle (NumPy FP64) on {obs.shape[0]}x{obs.shape[1]}: draw + RHS once "
+              f"({setup:.1f} s) and 1 preconditioned CG iteration per step "
+              f"({t_iter:.1f} s); realizations/s = 1/(setup + {FP64_ITERS_WIDE4096} iterations)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_iter * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "grid": [obs.shape[0], obs.shape[1]],
+                       "batch": 1, "tol": spec["tol"]},
+            "cg_iters_per_s": 1.0 / t_iter,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import paper_1109_0286_gb300 as cg
+    from workloads import workload
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    P, obs, spec = workload(args.workload)
+    ny, nx = obs.shape
+    B = len(spec["seeds"])
+    tol = spec["tol"]
+    plan = cg.Plan(P, obs, mode="mixed", batch=B)
+    d = plan.draw([spec["data_seed"]] * B)[0].clone()       # data drawn from P(k)
+    seeds = lambda k: [s + 100_003 * k + 10_000_019 * rank for s in spec["seeds"]]  # noqa: E731
+
+    for k in range(args.warmup):
+        plan.realize(d, seeds(k), tol)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters, launches, worst_resid = 0, 0, 0.0
+    barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for k in range(args.steps):
+            _, st = plan.realize(d, seeds(args.warmup + k), tol)
+            iters += sum(s["iters"] for s in st)
+            launches += st[0]["launches"]
+            worst_resid = max([worst_resid] + [s["true_rel_resid"] for s in st])
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = B * args.steps * world / (ms_max / 1e3)
+    iters_per_s = iters * world / (ms_max / 1e3)
+
+    # end to end through the public API with host buffers: H2D of d, D2H of x
+    d_host = d.cpu().pin_memory()
+    out_host = torch.empty((B, ny, nx), dtype=torch.float64).pin_memory()
+    out_dev = torch.empty((B, ny, nx), dtype=torch.float64, device="cuda")
+    d_dev = torch.empty_like(d)
+    esteps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(esteps):
+        d_dev.copy_(d_host, non_blocking=True)
+        plan.realize(d_dev, seeds(1000 + k), tol, out=out_dev)
+        out_host.copy_(out_dev, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / esteps
+    e2e = {"value": B * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": d_host.numel() * 8, "d2h_bytes_per_step": out_host.numel() * 8}
+
+    # roofline of the hot-loop passes (CUDA events on the plan's stream)
+    peaks, peak_src = measured_peaks()
+    passes = {0: ("k_col (column FFT, x 1/(nP), inverse FFT)", 3),
+              1: ("k_row src (r, u update + R2C)", 1),
+              2: ("k_row src (p update + R2C)", 1),
+              3: ("k_row sink (C2R + q = P_x, p^T q)", 2),
+              4: ("k_row mid (C2R, P_x, R2C)", 1)}
+    timing = {}
+    for pid, (name, per_iter) in passes.items():
+        pms, pbytes = plan.time_pass(pid, precision=0, reps=20)
+        timing[pid] = (name, per_iter, pms, pbytes)
+    dom = max(timing, key=lambda k: timing[k][1] * timing[k][2])
+    name, _, pms, pbytes = timing[dom]
+    achieved = pbytes / (pms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": name, "achieved": achieved,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": f"{peak_src} (hbm_gbs, burst)",
+                "bytes_per_launch": pbytes, "ms_per_launch": pms}
+    pass_table = {timing[k][0]: {"ms": round(timing[k][2], 4),
+                                 "GB/s": round(timing[k][3] / timing[k][2] / 1e6, 1),
+                                 "per_iter": timing[k][1]} for k in timing}
+    plan.close()
+
+    # plain FP64 GPU PCG on the same inputs
+    fp64 = None
+    if not args.no_fp64 and args.fp64_steps > 0:
+        p64 = cg.Plan(P, obs, mode="fp64", batch=B)
+        p64.realize(d, seeds(0), tol)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        it64 = 0
+        for k in range(args.fp64_steps):
+            _, st = p64.realize(d, seeds(1 + k), tol)
+            it64 += sum(s["iters"] for s in st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        fp64 = {"value": B * args.fp64_steps / (ms64 / 1e3), "unit": UNIT,
+                "ms_per_step": ms64 / args.fp64_steps,
+                "cg_iters_per_s": it64 / (ms64 / 1e3),
+                "iters_per_realization": it64 / (B * args.fp64_steps)}
+        p64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle as O
+        dn = d.cpu().numpy()
+        setup, t_iter = oracle_sample(P, obs, dn, spec["seeds"][0], 1)
+        n_it = fp64["iters_per_realization"] if fp64 else FP64_ITERS_WIDE4096
+        cpu = {"value": 1.0 / (setup + n_it * t_iter), "unit": UNIT, "cores": threads_used(),
+               "kind": "oracle",
+               "sample": (f"NumPy FP64 oracle on the full {ny}x{nx} workload: draw + RHS "
+                          f"({setup:.1f} s) and 1 preconditioned CG iteration ({t_iter:.1f} s), "
+                          f"scaled to {n_it:.0f} iterations per realization")}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": args.workload, "grid": [ny, nx], "batch": B,
+                           "tol": tol, "mode": "mixed", "precond": "sqrtC",
+                           "masked_fraction": round(float((obs == 0).mean()), 4),
+                           "parallelism": f"replicas{world}",
+                           "l2": "inputs larger than L2 (no flush)"},
+                "cg_iters_per_s": iters_per_s,
+                "iters_per_realization": iters / (B * args.steps),
+                "worst_true_rel_resid": worst_resid,
+                "fp64_pcg": fp64,
+                "speedup_vs_fp64": (value / world / fp64["value"]) if fp64 else None,
+                "gpu_launches": launches, "e2e": e2e, "roofline": roofline,
+                "passes": pass_table, "clocks": clk.summary(), "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * cgfill.h -- C ABI of the GB300 constrained-realization fill-in library.
+ *
+ * Method: Bucher & Louis, "Filling in CMB map missing data using constrained
+ * Gaussian realizations" (arXiv:1109.0286), on the flat periodic sky (the
+ * torus of Sect. 3).
+ *
+ *   Pixels split into masked M (to fill; the paper's x) and observed U (the
+ *   constraints; the paper's y).  C = P + N is diagonal in Fourier space with
+ *   eigenvalues P(k) (Sect. 4: the DFT is exactly unitary on the torus).
+ *   One constrained realization (Sects. 2.1 and 2.3, Hoffman-Ribak):
+ *       y   = F^-1 [ sqrt(P) F xi ],   xi ~ N(0,1) white noise from the seed
+ *       b   = -( C^-1 z )_M,           z = d - y on U, 0 on M
+ *       solve A u = b,  A = P_x C^-1 P_x          (eq. ModEq, Sect. 2.4)
+ *       x_M = y_M + u,  x_U = d_U (bit for bit)
+ *   by conjugate gradients (Sect. 2.4), optionally preconditioned with
+ *   S = P_x C^{1/2} P_x on both sides (Sect. 2.4; run in the equivalent
+ *   preconditioned form with B = S S, which exposes the true residual).
+ *
+ * Conventions shared by every entry point:
+ *   - Grid ny x nx, row-major, periodic; nx and ny powers of two with
+ *     32 <= nx <= 8192 and 16 <= ny <= 8192.
+ *   - DFT: F x(k) = sum_r x(r) exp(-i k.r), F^-1 carries 1/n, n = ny*nx,
+ *     k = 2 pi m / N with m in [-N/2, N/2).
+ *   - P_half: host, float64, ny x (nx/2+1) row-major (the half plane of a
+ *     real 2D FFT: row my in FFT order, column mx = 0..nx/2).
+ *   - observed: host, uint8, ny x nx, 1 = observed (constraint), 0 = masked.
+ *   - Maps passed to the compute calls are DEVICE pointers owned by the
+ *     caller; their element type depends on the plan's mode (float for
+ *     FILL_MODE_FP32, double otherwise).  Work is ordered on the plan's
+ *     stream; the calls below return after that work has completed.
+ *   - No call aborts the process: every failure is a returned status.
+ *     After FILL_ECUDA the plan must be destroyed.
+ */
+#ifndef CGFILL_H
+#define CGFILL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CGFILL_VERSION 1
+
+typedef struct fill_plan fill_plan;
+
+typedef enum {
+  FILL_OK = 0,
+  FILL_EINVAL = 1,      /* bad argument: size, spectrum, mask, pointer */
+  FILL_ENOMEM = 2,      /* device or pinned host allocation failed */
+  FILL_ENOTCONV = 3,    /* iteration limit reached before the tolerance */
+  FILL_EBREAKDOWN = 4,  /* p^T A p <= 0, r^T z <= 0 or a non-finite value */
+  FILL_ETIMEOUT = 5,    /* reserved: bounded device wait expired */
+  FILL_ECUDA = 6        /* CUDA runtime error (message via fill_last_error) */
+} fill_status;
+
+typedef enum {
+  FILL_MODE_FP64 = 0,   /* every step in FP64 ("plain FP64 PCG") */
+  FILL_MODE_FP32 = 1,   /* FP32 FFT operator and vectors, FP64-accurate inner
+                           products; maps are float */
+  FILL_MODE_MIXED = 2   /* FP64 draw, right-hand side and residual; FP32 inner
+                           PCG solves; FP64 iterative refinement; maps double */
+} fill_mode;
+
+typedef struct {
+  int mode;              /* fill_mode; default FILL_MODE_MIXED */
+  int precond;           /* 0: plain CG (Sect. 3, point-source masks);
+                            1: sqrt(C) split preconditioner (Sect. 2.4); default 1 */
+  int batch;             /* realizations per fill_realize call (same mask and P); default 1 */
+  int max_iter;          /* CG iterations per solve; default 10000 */
+  int max_refine;        /* FP64 refinement steps (mixed mode); default 10 */
+  double inner_tol;      /* relative tolerance floor of the FP32 inner solves
+                            (mixed mode); default 1e-6 */
+  int history_cap;       /* residual-history entries kept per realization; default 0 */
+  int rows_per_cta;      /* row-pass CTA height, 0 = default schedule */
+  int ffts_per_cta;      /* column FFTs per CTA, 0 = default schedule */
+} fill_opts;
+
+typedef struct {
+  int iters;             /* CG operator applications (all inner solves in mixed mode) */
+  int refine_steps;      /* FP64 residual recomputations (mixed mode) */
+  int status;            /* fill_status of this realization */
+  int launches;          /* kernels launched by the whole call (same for every entry) */
+  double rel_resid;      /* recurrence ||r|| / ||b|| at exit (last inner solve) */
+  double true_rel_resid; /* FP64 ||b - A u|| / ||b|| (mixed mode), else -1 */
+  double ms;             /* wall time of the whole call */
+} fill_stats;
+
+/* Fills *opts with the defaults listed above. */
+void fill_opts_default(fill_opts* opts);
+
+/*
+ * fill_init -- build a plan for one grid, one spectrum P(k) and one mask.
+ * Validates P (finite, > 0, and P(0,ky) = P(0,-ky), P(nx/2,ky) = P(nx/2,-ky)
+ * so that C is a real symmetric operator; Sect. 4) and the mask (values 0/1),
+ * builds the spectral tables 1/(nP) and sqrt(P)/n in the transposed layout of
+ * the column pass, and allocates every device buffer the plan will use (the
+ * compute calls allocate nothing).  stream: a cudaStream_t (NULL = legacy
+ * default stream).  On success *plan owns its memory until fill_destroy.
+ * Errors: FILL_EINVAL (sizes, spectrum, mask, opts), FILL_ENOMEM, FILL_ECUDA.
+ */
+fill_status fill_init(fill_plan** plan, int ny, int nx, const double* P_half,
+                      const uint8_t* observed, const fill_opts* opts, void* stream);
+
+/*
+ * fill_realize -- `batch` constrained Gaussian realizations (Sects. 2.1-2.4).
+ * d:       device, batch maps of ny*nx (float in FP32 mode, else double); the
+ *          values on masked pixels are ignored.  d_stride: elements between
+ *          consecutive maps (0 = one map shared by the whole batch).
+ * seeds:   host, batch uint64; the seed alone fixes the white noise xi.
+ * tol:     stop when ||b - A u|| <= tol ||b|| (recurrence residual in the
+ *          FP32/FP64 modes; the FP64 true residual in mixed mode).
+ * out:     device, batch contiguous maps of ny*nx (same type as d);
+ *          out_U = d_U exactly, out_M = y_M + u.
+ * stats:   host array of batch entries, or NULL.
+ * Returns the worst per-realization status (FILL_ENOTCONV / FILL_EBREAKDOWN
+ * leave the last iterate in out), or FILL_EINVAL / FILL_ECUDA.
+ */
+fill_status fill_realize(fill_plan* plan, const void* d, long long d_stride,
+                         const uint64_t* seeds, double tol, void* out, fill_stats* stats);
+
+/*
+ * fill_draw -- unconstrained realizations y = F^-1[sqrt(P) F xi(seed)] with
+ * covariance C (Sect. 2.3, the draw that needs no cuts).  out: device, batch
+ * maps (plan element type).  Errors: FILL_EINVAL, FILL_ECUDA.
+ */
+fill_status fill_draw(fill_plan* plan, const uint64_t* seeds, void* out);
+
+/*
+ * fill_apply -- one operator application on a single map, for checks of the
+ * GPU operator (symmetry, parity):  which = 0: C^-1 x;  1: C^{1/2} x;
+ * 2: A x = P_x C^-1 P_x x (eq. ModEq);  3: S x = P_x C^{1/2} P_x x (Sect. 2.4).
+ * in, out: device maps of the plan's element type (may not alias).
+ * Errors: FILL_EINVAL, FILL_ECUDA.
+ */
+fill_status fill_apply(fill_plan* plan, int which, const void* in, void* out);
+
+/*
+ * fill_history -- copies the residual history ||r_k||/||b||, k = 0..iters, of
+ * realization `inst` of the last fill_realize into host array hist of
+ * capacity cap (FP32 / FP64 modes: the CG recurrence residual per iteration;
+ * mixed mode: the FP64 true residual after each refinement step, k = 0 being
+ * the start).  Needs opts.history_cap > 0 at fill_init; *count receives the
+ * number of entries written.  Errors: FILL_EINVAL, FILL_ECUDA.
+ */
+fill_status fill_history(fill_plan* plan, int inst, double* hist, int cap, int* count);
+
+/*
+ * fill_time_pass -- average device time of one launch of a hot-loop pass
+ * kernel over all `batch` instances, timed with CUDA events on the plan's
+ * stream (`reps` launches between two events, after one warm-up launch), and
+ * the algorithmic bytes of one launch (the reads and writes the pass has to
+ * make).  pass: 0 column pass (forward column FFT, x 1/(nP), inverse FFT);
+ * 1 forward row pass fused with r -= alpha q, u += alpha p; 2 forward row pass
+ * fused with p = z + beta p; 3 inverse row pass fused with q = P_x(.) and
+ * p^T q; 4 inverse row pass, P_x, forward row pass (middle of S S r).
+ * precision: 0 FP32 kernels, 1 FP64 kernels (must exist in the plan's mode).
+ * Overwrites the plan's scratch; the next fill_realize starts afresh.
+ * Errors: FILL_EINVAL, FILL_ECUDA.
+ */
+fill_status fill_time_pass(fill_plan* plan, int pass, int precision, int reps,
+                           double* ms_per_launch, double* bytes_per_launch);
+
+/* Number of masked pixels n_M of the plan's mask. */
+long long fill_masked_count(const fill_plan* plan);
+
+/* Frees every resource of the plan (NULL is allowed). */
+void fill_destroy(fill_plan* plan);
+
+/* Static description of a status code. */
+const char* fill_strerror(fill_status status);
+
+/* Text of the last CUDA error seen by this thread (empty if none). */
+const char* fill_last_error(void);
+
+/* CGFILL_VERSION of the loaded library. */
+int fill_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CGFILL_H */

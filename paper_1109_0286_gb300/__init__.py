@@ -1,0 +1,293 @@
+"""GB300 constrained-realization fill-in of masked pixels on the flat sky.
+
+Python binding of the C ABI declared in ``include/cgfill.h`` (Bucher & Louis,
+arXiv:1109.0286, Sects. 2.1-2.4 on the periodic flat domain of Sect. 3).  The
+functions below only marshal arguments: every numerical step runs in the CUDA
+kernels of ``libcgfill.so``.  There is no CPU fallback; using the library
+without the built extension or without a GPU raises.
+
+Low-level names mirror the C ABI (``fill_init``, ``fill_realize``,
+``fill_draw``, ``fill_apply``, ``fill_history``, ``fill_destroy``,
+``fill_strerror``, ``fill_version``); ``Plan`` wraps them for torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+__all__ = [
+    "FillOpts", "FillStats", "FillError", "load", "lib_path", "fill_opts_default",
+    "fill_init", "fill_realize", "fill_draw", "fill_apply", "fill_history",
+    "fill_time_pass", "fill_masked_count", "fill_destroy", "fill_strerror", "fill_last_error",
+    "fill_version", "Plan", "MODES", "EXPORTED_SYMBOLS",
+]
+
+MODES = {"fp64": 0, "fp32": 1, "mixed": 2}
+STATUS = {0: "FILL_OK", 1: "FILL_EINVAL", 2: "FILL_ENOMEM", 3: "FILL_ENOTCONV",
+          4: "FILL_EBREAKDOWN", 5: "FILL_ETIMEOUT", 6: "FILL_ECUDA"}
+EXPORTED_SYMBOLS = [
+    "fill_opts_default", "fill_init", "fill_realize", "fill_draw", "fill_apply",
+    "fill_history", "fill_time_pass", "fill_masked_count", "fill_destroy",
+    "fill_strerror", "fill_last_error", "fill_version",
+]
+
+
+class FillOpts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("precond", ctypes.c_int),
+                ("batch", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("max_refine", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("history_cap", ctypes.c_int), ("rows_per_cta", ctypes.c_int),
+                ("ffts_per_cta", ctypes.c_int)]
+
+
+class FillStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("refine_steps", ctypes.c_int),
+                ("status", ctypes.c_int), ("launches", ctypes.c_int),
+                ("rel_resid", ctypes.c_double), ("true_rel_resid", ctypes.c_double),
+                ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class FillError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = f"{where}: {STATUS.get(status, status)} ({fill_strerror(status)})"
+        if status == 6:
+            msg += ": " + fill_last_error()
+        super().__init__(msg)
+        self.status = status
+
+
+_LIB = None
+_vp, _ci, _cd, _cll = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+
+
+def lib_path() -> str:
+    return _build.lib_path()
+
+
+def load() -> ctypes.CDLL:
+    """Load ``libcgfill.so`` (built by ``__graft_entry__.build()``)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing "
+                           "(run `python -c 'import __graft_entry__ as g; g.build()'`)")
+    lib = ctypes.CDLL(path)
+    lib.fill_opts_default.argtypes = [ctypes.POINTER(FillOpts)]
+    lib.fill_opts_default.restype = None
+    lib.fill_init.argtypes = [ctypes.POINTER(_vp), _ci, _ci, _vp, _vp,
+                              ctypes.POINTER(FillOpts), _vp]
+    lib.fill_init.restype = _ci
+    lib.fill_realize.argtypes = [_vp, _vp, _cll, _vp, _cd, _vp, ctypes.POINTER(FillStats)]
+    lib.fill_realize.restype = _ci
+    lib.fill_draw.argtypes = [_vp, _vp, _vp]
+    lib.fill_draw.restype = _ci
+    lib.fill_apply.argtypes = [_vp, _ci, _vp, _vp]
+    lib.fill_apply.restype = _ci
+    lib.fill_history.argtypes = [_vp, _ci, _vp, _ci, ctypes.POINTER(_ci)]
+    lib.fill_history.restype = _ci
+    lib.fill_time_pass.argtypes = [_vp, _ci, _ci, _ci, ctypes.POINTER(_cd), ctypes.POINTER(_cd)]
+    lib.fill_time_pass.restype = _ci
+    lib.fill_masked_count.argtypes = [_vp]
+    lib.fill_masked_count.restype = _cll
+    lib.fill_destroy.argtypes = [_vp]
+    lib.fill_destroy.restype = None
+    lib.fill_strerror.argtypes = [_ci]
+    lib.fill_strerror.restype = ctypes.c_char_p
+    lib.fill_last_error.argtypes = []
+    lib.fill_last_error.restype = ctypes.c_char_p
+    lib.fill_version.argtypes = []
+    lib.fill_version.restype = _ci
+    _LIB = lib
+    return lib
+
+
+# ------------------------------------------------------------ C-ABI mirrors
+
+def fill_opts_default() -> FillOpts:
+    o = FillOpts()
+    load().fill_opts_default(ctypes.byref(o))
+    return o
+
+
+def fill_init(ny, nx, P_half, observed, opts: FillOpts, stream: int = 0) -> int:
+    P = np.ascontiguousarray(P_half, dtype=np.float64)
+    m = np.ascontiguousarray(observed, dtype=np.uint8)
+    if P.shape != (ny, nx // 2 + 1) or m.shape != (ny, nx):
+        raise ValueError("P_half must be ny x (nx/2+1) and observed ny x nx")
+    plan = _vp()
+    st = load().fill_init(ctypes.byref(plan), int(ny), int(nx), P.ctypes.data, m.ctypes.data,
+                          ctypes.byref(opts), _vp(stream))
+    if st != 0:
+        raise FillError(st, "fill_init")
+    return plan.value
+
+
+def fill_realize(plan, d_ptr, d_stride, seeds, tol, out_ptr, batch):
+    s = np.ascontiguousarray(seeds, dtype=np.uint64)
+    stats = (FillStats * batch)()
+    st = load().fill_realize(_vp(plan), _vp(d_ptr), _cll(d_stride), s.ctypes.data,
+                             _cd(tol), _vp(out_ptr), stats)
+    return st, [x.as_dict() for x in stats]
+
+
+def fill_draw(plan, seeds, out_ptr):
+    s = np.ascontiguousarray(seeds, dtype=np.uint64)
+    st = load().fill_draw(_vp(plan), s.ctypes.data, _vp(out_ptr))
+    if st != 0:
+        raise FillError(st, "fill_draw")
+
+
+def fill_apply(plan, which, in_ptr, out_ptr):
+    st = load().fill_apply(_vp(plan), int(which), _vp(in_ptr), _vp(out_ptr))
+    if st != 0:
+        raise FillError(st, "fill_apply")
+
+
+def fill_history(plan, inst, cap):
+    buf = np.zeros(max(cap, 1), dtype=np.float64)
+    cnt = _ci(0)
+    st = load().fill_history(_vp(plan), int(inst), buf.ctypes.data, int(cap), ctypes.byref(cnt))
+    if st != 0:
+        raise FillError(st, "fill_history")
+    return buf[: cnt.value].copy()
+
+
+def fill_time_pass(plan, pass_id, precision, reps):
+    ms, nbytes = _cd(0), _cd(0)
+    st = load().fill_time_pass(_vp(plan), int(pass_id), int(precision), int(reps),
+                               ctypes.byref(ms), ctypes.byref(nbytes))
+    if st != 0:
+        raise FillError(st, "fill_time_pass")
+    return ms.value, nbytes.value
+
+
+def fill_masked_count(plan) -> int:
+    return int(load().fill_masked_count(_vp(plan)))
+
+
+def fill_destroy(plan) -> None:
+    if plan:
+        load().fill_destroy(_vp(plan))
+
+
+def fill_strerror(status: int) -> str:
+    return load().fill_strerror(int(status)).decode()
+
+
+def fill_last_error() -> str:
+    return load().fill_last_error().decode()
+
+
+def fill_version() -> int:
+    return int(load().fill_version())
+
+
+# ------------------------------------------------------------ torch wrapper
+
+class Plan:
+    """A fill-in plan for one grid, spectrum and mask, fed with torch tensors.
+
+    ``mode`` is ``"fp64"`` (plain FP64 PCG), ``"fp32"`` (FP32 operator,
+    FP64-accurate inner products) or ``"mixed"`` (FP32 inner PCG with FP64
+    residuals and iterative refinement).  Maps are float32 in fp32 mode and
+    float64 otherwise, on the current CUDA device.
+    """
+
+    def __init__(self, P_half, observed, mode="mixed", precond=True, batch=1,
+                 max_iter=10000, max_refine=10, inner_tol=1e-6, history_cap=0,
+                 rows_per_cta=0, ffts_per_cta=0, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_1109_0286_gb300 needs a CUDA GPU; no CPU fallback exists")
+        o = fill_opts_default()
+        o.mode = MODES[mode]
+        o.precond = 1 if precond else 0
+        o.batch = int(batch)
+        o.max_iter = int(max_iter)
+        o.max_refine = int(max_refine)
+        o.inner_tol = float(inner_tol)
+        o.history_cap = int(history_cap)
+        o.rows_per_cta = int(rows_per_cta)
+        o.ffts_per_cta = int(ffts_per_cta)
+        self.ny, self.nx = observed.shape
+        self.batch = int(batch)
+        self.mode = mode
+        self.history_cap = int(history_cap)
+        self.dtype = torch.float32 if mode == "fp32" else torch.float64
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        self._plan = fill_init(self.ny, self.nx, P_half, observed, o, self._stream.cuda_stream)
+
+    def _check(self, t, name, maps):
+        import torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == self.dtype
+                and t.is_contiguous() and t.numel() == maps * self.ny * self.nx):
+            raise ValueError(f"{name}: expected a contiguous {self.dtype} CUDA tensor "
+                             f"with {maps} map(s) of {self.ny}x{self.nx}")
+
+    def realize(self, d, seeds, tol, out=None, check=True):
+        """Constrained realizations of data ``d`` (one map shared by the batch,
+        or ``batch`` maps).  Returns ``(out, stats)``."""
+        import torch
+        shared = d.numel() == self.ny * self.nx
+        self._check(d, "d", 1 if shared else self.batch)
+        if out is None:
+            out = torch.empty((self.batch, self.ny, self.nx), dtype=self.dtype, device=d.device)
+        self._check(out, "out", self.batch)
+        seeds = np.asarray(seeds, dtype=np.uint64).reshape(-1)
+        if seeds.size != self.batch:
+            raise ValueError("need one seed per realization")
+        st, stats = fill_realize(self._plan, d.data_ptr(), 0 if shared else self.ny * self.nx,
+                                 seeds, tol, out.data_ptr(), self.batch)
+        if check and st not in (0,):
+            raise FillError(st, "fill_realize")
+        return out, stats
+
+    def draw(self, seeds, out=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.batch, self.ny, self.nx), dtype=self.dtype, device=self.device)
+        self._check(out, "out", self.batch)
+        fill_draw(self._plan, np.asarray(seeds, dtype=np.uint64).reshape(-1), out.data_ptr())
+        return out
+
+    def apply(self, which, x):
+        """0: C^-1 x, 1: C^{1/2} x, 2: P_x C^-1 P_x x, 3: P_x C^{1/2} P_x x."""
+        import torch
+        self._check(x, "x", 1)
+        out = torch.empty_like(x)
+        fill_apply(self._plan, which, x.data_ptr(), out.data_ptr())
+        return out
+
+    def time_pass(self, pass_id, precision=None, reps=20):
+        """(ms per launch, algorithmic bytes per launch) of one hot-loop pass."""
+        if precision is None:
+            precision = 1 if self.mode == "fp64" else 0
+        return fill_time_pass(self._plan, pass_id, precision, reps)
+
+    def history(self, inst=0):
+        return fill_history(self._plan, inst, self.history_cap)
+
+    @property
+    def masked_count(self) -> int:
+        return fill_masked_count(self._plan)
+
+    def close(self):
+        if getattr(self, "_plan", None):
+            fill_destroy(self._plan)
+            self._plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,183 @@
+// Register-resident complex FFT of length L = 2^LOG_L (16 <= L <= 8192) by a
+// group of L/16 threads that each hold 16 elements.
+//
+// Stockham auto-sort formulation: a stage of radix R after sub-transforms of
+// size Ns reads element j + r L/R, multiplies it by W_{Ns R}^{(j mod Ns) r},
+// applies a length-R DFT and writes element (j div Ns) Ns R + (j mod Ns) + r Ns.
+// The plan is one leading stage of radix 2^(LOG_L mod 4) (if nonzero) and then
+// radix-16 stages.  On entry thread t holds x[t + e L/16] in v[e]; on exit it
+// holds X[t + e L/16] -- the same positions -- so a forward transform, a
+// diagonal multiply and an inverse transform chain without a shared-memory
+// round trip.  Between stages data goes through shared memory (split real /
+// imaginary arrays, one pad word per 16, which keeps the stage writes free of
+// bank conflicts).
+#pragma once
+#include "cg_common.cuh"
+
+namespace cgf {
+
+__device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
+
+// a * (-i) for the forward transform, a * (+i) for the inverse.
+template <typename T, bool INV>
+__device__ __forceinline__ cx<T> mul_mi(cx<T> a) {
+  return INV ? cx<T>{-a.i, a.r} : cx<T>{a.i, -a.r};
+}
+// a * (c - i s) forward, a * (c + i s) inverse.
+template <typename T, bool INV>
+__device__ __forceinline__ cx<T> twc(cx<T> a, T c, T s) {
+  return INV ? cx<T>{a.r * c - a.i * s, a.r * s + a.i * c}
+             : cx<T>{a.r * c + a.i * s, a.i * c - a.r * s};
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void dft2(cx<T>& a, cx<T>& b) {
+  cx<T> t = a;
+  a = t + b;
+  b = t - b;
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void dft4(cx<T>& a0, cx<T>& a1, cx<T>& a2, cx<T>& a3) {
+  cx<T> s02 = a0 + a2, d02 = a0 - a2, s13 = a1 + a3;
+  cx<T> d13 = mul_mi<T, INV>(a1 - a3);
+  a0 = s02 + s13;
+  a2 = s02 - s13;
+  a1 = d02 + d13;
+  a3 = d02 - d13;
+}
+
+// cos(pi/8), sin(pi/8), sqrt(1/2)
+#define CGF_C8 0.92387953251128674
+#define CGF_S8 0.38268343236508978
+#define CGF_R2 0.70710678118654752
+
+// Length-8 DFT, natural order in and out (8 = 2 x 4 split).
+template <typename T, bool INV>
+__device__ __forceinline__ void dft8(cx<T> (&v)[8]) {
+  const T r2 = (T)CGF_R2;
+  dft2<T, INV>(v[0], v[4]);
+  dft2<T, INV>(v[1], v[5]);
+  dft2<T, INV>(v[2], v[6]);
+  dft2<T, INV>(v[3], v[7]);
+  v[5] = twc<T, INV>(v[5], r2, r2);
+  v[6] = mul_mi<T, INV>(v[6]);
+  v[7] = twc<T, INV>(v[7], -r2, r2);
+  dft4<T, INV>(v[0], v[1], v[2], v[3]);
+  dft4<T, INV>(v[4], v[5], v[6], v[7]);
+  cx<T> o[8] = {v[0], v[4], v[1], v[5], v[2], v[6], v[3], v[7]};
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = o[i];
+}
+
+// Length-16 DFT, natural order in and out (16 = 4 x 4 split:
+// n = 4 n1 + n2, k = k1 + 4 k2, inner twiddles W16^(n2 k1)).
+template <typename T, bool INV>
+__device__ __forceinline__ void dft16(cx<T> (&v)[16]) {
+  const T c = (T)CGF_C8, s = (T)CGF_S8, r2 = (T)CGF_R2;
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft4<T, INV>(v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]);
+  v[5] = twc<T, INV>(v[5], c, s);      // W^1
+  v[9] = twc<T, INV>(v[9], r2, r2);    // W^2
+  v[13] = twc<T, INV>(v[13], s, c);    // W^3
+  v[6] = twc<T, INV>(v[6], r2, r2);    // W^2
+  v[10] = mul_mi<T, INV>(v[10]);       // W^4
+  v[14] = twc<T, INV>(v[14], -r2, r2); // W^6
+  v[7] = twc<T, INV>(v[7], s, c);      // W^3
+  v[11] = twc<T, INV>(v[11], -r2, r2); // W^6
+  v[15] = twc<T, INV>(v[15], -c, -s);  // W^9
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) dft4<T, INV>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+  cx<T> o[16];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) o[k1 + 4 * k2] = v[4 * k1 + k2];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = o[i];
+}
+
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void dft_small(cx<T> (&u)[R]) {
+  if constexpr (R == 2) {
+    dft2<T, INV>(u[0], u[1]);
+  } else if constexpr (R == 4) {
+    dft4<T, INV>(u[0], u[1], u[2], u[3]);
+  } else {
+    dft8<T, INV>(u);
+  }
+}
+
+// W_kLmax^m = exp(-2 pi i m / kLmax), interleaved table.
+template <typename T>
+__device__ __forceinline__ cx<T> twiddle(const T* __restrict__ tw, int m) {
+  return ldg_cx<T>(tw + 2 * m);
+}
+
+template <typename T, int LOG_L, bool INV>
+__device__ __forceinline__ void fft_regs(cx<T> (&v)[16], T* __restrict__ sre,
+                                         T* __restrict__ sim, int tid,
+                                         const T* __restrict__ tw) {
+  constexpr int TT = (1 << LOG_L) / 16;
+  constexpr int S16 = LOG_L / 4;
+  constexpr int REM = LOG_L % 4;
+  constexpr int NS0 = REM > 0 ? (1 << REM) : 1;
+  if constexpr (REM > 0) {
+    constexpr int R0 = 1 << REM, NB = 16 / R0;
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      cx<T> u[R0];
+#pragma unroll
+      for (int r = 0; r < R0; ++r) u[r] = v[q + r * NB];
+      dft_small<T, R0, INV>(u);
+#pragma unroll
+      for (int r = 0; r < R0; ++r) v[q + r * NB] = u[r];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+#pragma unroll
+      for (int r = 0; r < R0; ++r) {
+        const int idx = padi((tid + q * TT) * R0 + r);
+        sre[idx] = v[q + r * NB].r;
+        sim[idx] = v[q + r * NB].i;
+      }
+  }
+#pragma unroll
+  for (int s = 0; s < S16; ++s) {
+    int ns = NS0;
+#pragma unroll
+    for (int t = 0; t < s; ++t) ns *= 16;
+    const bool first = (REM == 0) && (s == 0);
+    const bool last = (s == S16 - 1);
+    if (!first) {
+      __syncthreads();
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int idx = padi(tid + e * TT);
+        v[e] = cx<T>{sre[idx], sim[idx]};
+      }
+      const int jm = tid & (ns - 1);
+      const int stride = kLmax / (ns * 16);
+#pragma unroll
+      for (int r = 1; r < 16; ++r) {
+        const cx<T> w = twiddle<T>(tw, jm * r * stride);
+        v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+      }
+    }
+    dft16<T, INV>(v);
+    if (!last) {
+      __syncthreads();
+      const int jm = tid & (ns - 1);
+      const int base = (tid - jm) * 16 + jm;
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const int idx = padi(base + r * ns);
+        sre[idx] = v[r].r;
+        sim[idx] = v[r].i;
+      }
+    }
+  }
+}
+
+}  // namespace cgf

@@ -1,0 +1,356 @@
+// Fused FFT passes of the masked operator (Sect. 2.4, eq. ModEq):
+//
+//   C^s v = F^-1 diag(P^s) F v on the periodic grid (exact unitarity, Sect. 4)
+//
+// is split into a ROW pass (real row <-> half-spectrum row, R2C / C2R by a
+// half-length complex FFT), a COLUMN pass (forward column FFT, multiply by the
+// real table, inverse column FFT, all in registers), and the inverse ROW pass.
+// The row passes write / read the half spectrum transposed (kx-major), so the
+// column pass streams contiguous rows.  Everything elementwise -- the mask
+// projections P_x, the white-noise draw, the CG vector updates and the inner
+// products -- is fused into the row passes.
+#pragma once
+#include "cg_fft.cuh"
+
+namespace cgf {
+
+template <typename T> struct KCfg;
+template <> struct KCfg<float> { static constexpr int kMaxThreads = 1024; };
+template <> struct KCfg<double> { static constexpr int kMaxThreads = 512; };
+
+__device__ __forceinline__ bool observed_bit(const uint32_t* __restrict__ obs, long long pix) {
+  return (__ldg(obs + (pix >> 5)) >> (pix & 31)) & 1u;
+}
+
+// ----------------------------------------------------------------- sources
+template <typename T>
+__device__ __forceinline__ void src_op(int op, const InstDesc<T>& I, long long pix,
+                                       T alpha, T beta, T& a0, T& a1, Acc<T>& acc) {
+  switch (op) {
+    case OP_XI: {
+      double x0, x1;
+      normal_pair(I.seed, (uint32_t)(pix >> 1), x0, x1);
+      a0 = (T)x0;
+      a1 = (T)x1;
+      break;
+    }
+    case OP_LOAD_R_MASK: {
+      ld_pair(I.r + pix, a0, a1);
+      const uint32_t w = __ldg(I.obs + (pix >> 5));
+      if ((w >> (pix & 31)) & 1u) a0 = (T)0;
+      if ((w >> ((pix + 1) & 31)) & 1u) a1 = (T)0;
+      break;
+    }
+    case OP_LOAD_R:
+      ld_pair(I.r + pix, a0, a1);
+      acc.add_prod(a0, a0);
+      acc.add_prod(a1, a1);
+      break;
+    case OP_P_UPD_Z:
+    case OP_P_UPD_R: {
+      T z0, z1, p0, p1;
+      ld_pair((op == OP_P_UPD_Z ? I.z : I.r) + pix, z0, z1);
+      ld_pair(I.p + pix, p0, p1);
+      a0 = z0 + beta * p0;
+      a1 = z1 + beta * p1;
+      st_pair(I.p + pix, a0, a1);
+      break;
+    }
+    case OP_R_UPD: {
+      T r0, r1, q0, q1, u0, u1, p0, p1;
+      ld_pair(I.r + pix, r0, r1);
+      ld_pair(I.q + pix, q0, q1);
+      ld_pair(I.u + pix, u0, u1);
+      ld_pair(I.p + pix, p0, p1);
+      a0 = r0 - alpha * q0;
+      a1 = r1 - alpha * q1;
+      st_pair(I.r + pix, a0, a1);
+      st_pair(I.u + pix, u0 + alpha * p0, u1 + alpha * p1);
+      acc.add_prod(a0, a0);
+      acc.add_prod(a1, a1);
+      break;
+    }
+    case OP_U64_UPD: {
+      T u0, u1;
+      ld_pair(I.u + pix, u0, u1);
+      const float2 dl = *reinterpret_cast<const float2*>(I.dlt + pix);
+      a0 = u0 + (T)dl.x;
+      a1 = u1 + (T)dl.y;
+      st_pair(I.u + pix, a0, a1);
+      break;
+    }
+    default:
+      a0 = a1 = (T)0;
+  }
+}
+
+// ----------------------------------------------------------------- middles / sinks
+template <typename T>
+__device__ __forceinline__ void sink_op(int op, const InstDesc<T>& I, long long pix,
+                                        T& a0, T& a1, Acc<T>& acc) {
+  const uint32_t w = __ldg(I.obs + (pix >> 5));
+  const bool o0 = (w >> (pix & 31)) & 1u, o1 = (w >> ((pix + 1) & 31)) & 1u;
+  switch (op) {
+    case OP_MASK:
+      a0 = o0 ? (T)0 : a0;
+      a1 = o1 ? (T)0 : a1;
+      break;
+    case OP_Y_W: {
+      st_pair(I.y + pix, a0, a1);
+      T d0, d1;
+      ld_pair(I.d + pix, d0, d1);
+      a0 = o0 ? d0 - a0 : (T)0;
+      a1 = o1 ? d1 - a1 : (T)0;
+      break;
+    }
+    case OP_STORE_Y:
+      st_pair(I.y + pix, a0, a1);
+      break;
+    case OP_Q: {
+      a0 = o0 ? (T)0 : a0;
+      a1 = o1 ? (T)0 : a1;
+      st_pair(I.q + pix, a0, a1);
+      T p0, p1;
+      ld_pair(I.p + pix, p0, p1);
+      acc.add_prod(p0, a0);
+      acc.add_prod(p1, a1);
+      break;
+    }
+    case OP_Z: {
+      a0 = o0 ? (T)0 : a0;
+      a1 = o1 ? (T)0 : a1;
+      st_pair(I.z + pix, a0, a1);
+      T r0, r1;
+      ld_pair(I.r + pix, r0, r1);
+      acc.add_prod(r0, a0);
+      acc.add_prod(r1, a1);
+      break;
+    }
+    case OP_B: {
+      a0 = o0 ? (T)0 : -a0;
+      a1 = o1 ? (T)0 : -a1;
+      st_pair(I.r + pix, a0, a1);
+      if (I.b) st_pair(I.b + pix, a0, a1);
+      if (I.r32) *reinterpret_cast<float2*>(I.r32 + pix) = make_float2((float)a0, (float)a1);
+      acc.add_prod(a0, a0);
+      acc.add_prod(a1, a1);
+      break;
+    }
+    case OP_RES: {
+      T b0, b1;
+      ld_pair(I.b + pix, b0, b1);
+      a0 = b0 - (o0 ? (T)0 : a0);
+      a1 = b1 - (o1 ? (T)0 : a1);
+      st_pair(I.r + pix, a0, a1);
+      if (I.r32) *reinterpret_cast<float2*>(I.r32 + pix) = make_float2((float)a0, (float)a1);
+      acc.add_prod(a0, a0);
+      acc.add_prod(a1, a1);
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+// ----------------------------------------------------------------- row pass
+// CTA = `rows` consecutive grid rows, L/16 threads per row; blockIdx.y is the
+// instance.  Shared memory: per-row FFT exchange areas, aliased with the
+// transposed tile [(L+1) x (rows+1)] used for the spectrum load / store.
+template <typename T, int LOG_L, bool IN_SPEC, bool OUT_SPEC>
+__global__ void __launch_bounds__(KCfg<T>::kMaxThreads)
+k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw) {
+  constexpr int L = 1 << LOG_L, TT = L / 16, PADL = L + L / 16 + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  __shared__ double red[32];
+  const InstDesc<T>& I = insts[blockIdx.y];
+  if (a.check_done && *(volatile int*)&I.st->done) return;
+
+  const int rows = a.rows;
+  const int row = threadIdx.x / TT, tid = threadIdx.x - row * TT;
+  const int y0 = blockIdx.x * rows, y = y0 + row;
+  const int ny = a.ny, nx = a.nx;
+  const int tstride = rows + 1;
+  T* sre = sm + row * 2 * PADL;
+  T* sim = sre + PADL;
+  T* tre = sm;
+  T* tim = sm + (L + 1) * tstride;
+  constexpr int TWS = kLmax / (2 * L);   // W_{nx}^k = table[k * TWS]
+  const long long rowpix = (long long)y * nx;
+
+  cx<T> v[16];
+  Acc<T> acc;
+
+  if constexpr (IN_SPEC) {
+    const T* spec = I.spec;
+    for (int e = threadIdx.x; e < (L + 1) * rows; e += blockDim.x) {
+      const int k = e / rows, rr = e - k * rows;
+      const cx<T> s = ld_cx<T>(spec + 2 * ((long long)k * ny + y0 + rr));
+      tre[k * tstride + rr] = s.r;
+      tim[k * tstride + rr] = s.i;
+    }
+    __syncthreads();
+    // C2R: Z[k] = (X[k] + conj X[L-k]) + i e^{+2 pi i k / nx} (X[k] - conj X[L-k])
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const int k = tid + e * TT;
+      cx<T> xk{tre[k * tstride + row], tim[k * tstride + row]};
+      cx<T> xc{tre[(L - k) * tstride + row], -tim[(L - k) * tstride + row]};
+      if (k == 0) {
+        xk.i = (T)0;
+        xc.i = (T)0;
+      }
+      const cx<T> w = twiddle<T>(tw, k * TWS);
+      const cx<T> sum = xk + xc;
+      const cx<T> dif = cmulc(xk - xc, w);  // (X - conj X') e^{+i...}
+      v[e] = cx<T>{sum.r - dif.i, sum.i + dif.r};
+    }
+    fft_regs<T, LOG_L, true>(v, sre, sim, tid, tw);
+    // v[e] = x[2j] + i x[2j+1], j = tid + e TT
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const long long pix = rowpix + 2 * (tid + e * TT);
+      sink_op<T>(a.op, I, pix, v[e].r, v[e].i, acc);
+    }
+  } else {
+    const T alpha = (T)I.st->alpha, beta = (T)I.st->beta;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const long long pix = rowpix + 2 * (tid + e * TT);
+      src_op<T>(a.op, I, pix, alpha, beta, v[e].r, v[e].i, acc);
+    }
+  }
+
+  if constexpr (OUT_SPEC) {
+    fft_regs<T, LOG_L, false>(v, sre, sim, tid, tw);
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const int idx = padi(tid + e * TT);
+      sre[idx] = v[e].r;
+      sim[idx] = v[e].i;
+    }
+    __syncthreads();
+    // R2C: X[k] = (Z[k] + conj Z[L-k]) / 2 - (i/2) e^{-2 pi i k/nx} (Z[k] - conj Z[L-k])
+    cx<T> nyq{v[0].r - v[0].i, (T)0};
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const int k = tid + e * TT;
+      const int kc = padi((L - k) & (L - 1));
+      const cx<T> zc{sre[kc], -sim[kc]};
+      const cx<T> zk = v[e];
+      const cx<T> ev = scal(zk + zc, (T)0.5);
+      const cx<T> od = scal(mul_mi<T, false>(zk - zc), (T)0.5);
+      v[e] = ev + cmul(od, twiddle<T>(tw, k * TWS));
+    }
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const int k = tid + e * TT;
+      tre[k * tstride + row] = v[e].r;
+      tim[k * tstride + row] = v[e].i;
+    }
+    if (tid == 0) {
+      tre[L * tstride + row] = nyq.r;
+      tim[L * tstride + row] = nyq.i;
+    }
+    __syncthreads();
+    T* spec = I.spec;
+    for (int e = threadIdx.x; e < (L + 1) * rows; e += blockDim.x) {
+      const int k = e / rows, rr = e - k * rows;
+      st_cx<T>(spec + 2 * ((long long)k * ny + y0 + rr),
+               cx<T>{tre[k * tstride + rr], tim[k * tstride + rr]});
+    }
+  }
+
+  if (a.sop != SC_NONE)
+    grid_reduce(acc.value(), red, I.partial, I.st, a.sop, gridDim.x, blockIdx.x);
+}
+
+// ----------------------------------------------------------------- column pass
+// CTA = `ffts` spectrum rows (one kx each), N/16 threads per row; forward
+// column FFT, multiply by the real table, inverse column FFT, in place.
+template <typename T, int LOG_N>
+__global__ void __launch_bounds__(KCfg<T>::kMaxThreads)
+k_col(const InstDesc<T>* __restrict__ insts, ColArgs a, const T* __restrict__ tw) {
+  constexpr int N = 1 << LOG_N, TT = N / 16, PADN = N + N / 16 + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const InstDesc<T>& I = insts[blockIdx.y];
+  if (a.check_done && *(volatile int*)&I.st->done) return;
+  const int f = threadIdx.x / TT, tid = threadIdx.x - f * TT;
+  const int kx = blockIdx.x * a.ffts + f;
+  const bool act = kx < a.nkx;
+  T* sre = sm + f * 2 * PADN;
+  T* sim = sre + PADN;
+  T* col = I.spec + 2 * (long long)(act ? kx : 0) * N;
+  const T* tab = (a.table ? I.t_sqrt : I.t_inv) + (long long)(act ? kx : 0) * N;
+  cx<T> v[16];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) v[e] = act ? ld_cx<T>(col + 2 * (tid + e * TT)) : cx<T>{(T)0, (T)0};
+  fft_regs<T, LOG_N, false>(v, sre, sim, tid, tw);
+#pragma unroll
+  for (int e = 0; e < 16; ++e) {
+    const T t = act ? __ldg(tab + tid + e * TT) : (T)0;
+    v[e] = scal(v[e], t);
+  }
+  fft_regs<T, LOG_N, true>(v, sre, sim, tid, tw);
+  if (act) {
+#pragma unroll
+    for (int e = 0; e < 16; ++e) st_cx<T>(col + 2 * (tid + e * TT), v[e]);
+  }
+}
+
+// ----------------------------------------------------------------- elementwise
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_vec(const InstDesc<T>* __restrict__ insts, VecArgs a) {
+  __shared__ double red[32];
+  const InstDesc<T>& I = insts[blockIdx.y];
+  if (a.check_done && *(volatile int*)&I.st->done) return;
+  Acc<T> acc;
+  const T alpha = (T)I.st->alpha;
+  const long long npair = a.npix >> 1;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < npair;
+       j += (long long)gridDim.x * blockDim.x) {
+    const long long pix = 2 * j;
+    switch (a.op) {
+      case VOP_UPDATE: {
+        T r0, r1, q0, q1, u0, u1, p0, p1;
+        ld_pair(I.r + pix, r0, r1);
+        ld_pair(I.q + pix, q0, q1);
+        ld_pair(I.u + pix, u0, u1);
+        ld_pair(I.p + pix, p0, p1);
+        r0 -= alpha * q0;
+        r1 -= alpha * q1;
+        st_pair(I.r + pix, r0, r1);
+        st_pair(I.u + pix, u0 + alpha * p0, u1 + alpha * p1);
+        acc.add_prod(r0, r0);
+        acc.add_prod(r1, r1);
+        break;
+      }
+      case VOP_ASSEMBLE: {
+        const uint32_t w = __ldg(I.obs + (pix >> 5));
+        const bool o0 = (w >> (pix & 31)) & 1u, o1 = (w >> ((pix + 1) & 31)) & 1u;
+        T d0, d1, y0, y1, u0, u1;
+        ld_pair(I.d + pix, d0, d1);
+        ld_pair(I.y + pix, y0, y1);
+        ld_pair(I.u + pix, u0, u1);
+        st_pair(I.out + pix, o0 ? d0 : y0 + u0, o1 ? d1 : y1 + u1);
+        break;
+      }
+      case VOP_COPY_D: {
+        T d0, d1;
+        ld_pair(I.d + pix, d0, d1);
+        st_pair(I.out + pix, d0, d1);
+        break;
+      }
+      default:
+        break;
+    }
+  }
+  if (a.sop != SC_NONE)
+    grid_reduce(acc.value(), red, I.partial, I.st, a.sop, gridDim.x, blockIdx.x);
+}
+
+}  // namespace cgf

@@ -1,0 +1,119 @@
+// Size dispatch: runtime log2 sizes -> compile-time kernel instantiations.
+#pragma once
+#include "cg_kernels.cuh"
+#include "cg_launch.h"
+
+namespace cgf {
+
+template <typename T>
+size_t Launch<T>::row_smem(int log_l, int rows) {
+  const size_t L = size_t(1) << log_l, padl = L + L / 16 + 1;
+  const size_t fft = size_t(rows) * 2 * padl, tile = 2 * (L + 1) * size_t(rows + 1);
+  return (fft > tile ? fft : tile) * sizeof(T);
+}
+
+template <typename T>
+size_t Launch<T>::col_smem(int log_n, int ffts) {
+  const size_t N = size_t(1) << log_n;
+  return size_t(ffts) * 2 * (N + N / 16 + 1) * sizeof(T);
+}
+
+template <typename T>
+int Launch<T>::max_threads() { return KCfg<T>::kMaxThreads; }
+
+namespace detail {
+
+// Opt the kernel in to the largest dynamic shared memory the device allows
+// next to its static shared memory.
+template <typename K>
+inline cudaError_t allow_smem(K kernel) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa{};
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              optin - (int)fa.sharedSizeBytes);
+}
+
+template <typename T, int LL>
+cudaError_t row_ll(bool in_spec, bool out_spec, const InstDesc<T>* d, int ninst, const RowArgs& a,
+                   const T* tw, cudaStream_t s) {
+  constexpr int TT = (1 << LL) / 16;
+  dim3 grid(a.ny / a.rows, ninst), block(a.rows * TT);
+  const size_t sm = Launch<T>::row_smem(LL, a.rows);
+  if (in_spec && out_spec)
+    k_row<T, LL, true, true><<<grid, block, sm, s>>>(d, a, tw);
+  else if (in_spec)
+    k_row<T, LL, true, false><<<grid, block, sm, s>>>(d, a, tw);
+  else
+    k_row<T, LL, false, true><<<grid, block, sm, s>>>(d, a, tw);
+  return cudaGetLastError();
+}
+
+template <typename T, int LN>
+cudaError_t col_ln(const InstDesc<T>* d, int ninst, const ColArgs& a, const T* tw, cudaStream_t s) {
+  constexpr int TT = (1 << LN) / 16;
+  dim3 grid((a.nkx + a.ffts - 1) / a.ffts, ninst), block(a.ffts * TT);
+  k_col<T, LN><<<grid, block, Launch<T>::col_smem(LN, a.ffts), s>>>(d, a, tw);
+  return cudaGetLastError();
+}
+
+template <typename T, int LL>
+cudaError_t prep_row() {
+  cudaError_t e = allow_smem(k_row<T, LL, true, true>);
+  if (e == cudaSuccess) e = allow_smem(k_row<T, LL, true, false>);
+  if (e == cudaSuccess) e = allow_smem(k_row<T, LL, false, true>);
+  return e;
+}
+
+}  // namespace detail
+
+#define CGF_ROW_CASE(LL) \
+  case LL: return detail::row_ll<T, LL>(in_spec, out_spec, d, ninst, a, tw, s);
+template <typename T>
+cudaError_t Launch<T>::row(int log_l, bool in_spec, bool out_spec, const InstDesc<T>* d, int ninst,
+                           const RowArgs& a, const T* tw, cudaStream_t s) {
+  switch (log_l) {
+    CGF_ROW_CASE(4) CGF_ROW_CASE(5) CGF_ROW_CASE(6) CGF_ROW_CASE(7) CGF_ROW_CASE(8)
+    CGF_ROW_CASE(9) CGF_ROW_CASE(10) CGF_ROW_CASE(11) CGF_ROW_CASE(12)
+    default: return cudaErrorInvalidValue;
+  }
+}
+#undef CGF_ROW_CASE
+
+#define CGF_COL_CASE(LN) \
+  case LN: return detail::col_ln<T, LN>(d, ninst, a, tw, s);
+template <typename T>
+cudaError_t Launch<T>::col(int log_n, const InstDesc<T>* d, int ninst, const ColArgs& a,
+                           const T* tw, cudaStream_t s) {
+  switch (log_n) {
+    CGF_COL_CASE(4) CGF_COL_CASE(5) CGF_COL_CASE(6) CGF_COL_CASE(7) CGF_COL_CASE(8)
+    CGF_COL_CASE(9) CGF_COL_CASE(10) CGF_COL_CASE(11) CGF_COL_CASE(12) CGF_COL_CASE(13)
+    default: return cudaErrorInvalidValue;
+  }
+}
+#undef CGF_COL_CASE
+
+template <typename T>
+cudaError_t Launch<T>::vec(const InstDesc<T>* d, int ninst, const VecArgs& a, int nblk, cudaStream_t s) {
+  k_vec<T><<<dim3(nblk, ninst), 256, 0, s>>>(d, a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::prepare() {
+  cudaError_t e = cudaSuccess;
+#define CGF_PREP_ROW(LL) if (e == cudaSuccess) e = detail::prep_row<T, LL>();
+  CGF_PREP_ROW(4) CGF_PREP_ROW(5) CGF_PREP_ROW(6) CGF_PREP_ROW(7) CGF_PREP_ROW(8)
+  CGF_PREP_ROW(9) CGF_PREP_ROW(10) CGF_PREP_ROW(11) CGF_PREP_ROW(12)
+#undef CGF_PREP_ROW
+#define CGF_PREP_COL(LN) if (e == cudaSuccess) e = detail::allow_smem(k_col<T, LN>);
+  CGF_PREP_COL(4) CGF_PREP_COL(5) CGF_PREP_COL(6) CGF_PREP_COL(7) CGF_PREP_COL(8)
+  CGF_PREP_COL(9) CGF_PREP_COL(10) CGF_PREP_COL(11) CGF_PREP_COL(12) CGF_PREP_COL(13)
+#undef CGF_PREP_COL
+  return e;
+}
+
+}  // namespace cgf

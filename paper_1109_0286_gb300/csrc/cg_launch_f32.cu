@@ -1,0 +1,3 @@
+// FP32 instantiations of the pass kernels.
+#include "cg_launch.cuh"
+template struct cgf::Launch<float>;

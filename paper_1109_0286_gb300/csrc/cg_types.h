@@ -1,0 +1,130 @@
+// Shared host/device data structures of the constrained-realization solver.
+//
+// Layout on the device, per realization ("instance"):
+//   * real maps (d, y, u, r, p, q, z, b, out): row-major ny x nx, 0 outside M
+//     for the CG vectors (the masked system of Sect. 2.4 lives on M only);
+//   * half spectrum "spec": transposed, (nx/2+1) rows of ny complex values,
+//     spec[kx * ny + y]; the column pass runs along contiguous rows;
+//   * spectral tables [kx][ky] (same transposed layout), real, with the
+//     1/n of the inverse DFT folded in;
+//   * observation mask: one bit per pixel, bit 1 = observed (constraint).
+#pragma once
+#include <cstdint>
+
+namespace cgf {
+
+// Scalar state of one CG solve (Sect. 2.4), kept on the device so the
+// iteration runs without host round trips.
+struct CgState {
+  double rho;      // r^T z of the current iterate
+  double alpha;    // step length
+  double beta;     // direction update
+  double bb;       // ||b||^2
+  double rr;       // ||r||^2 after the last update
+  double tol2;     // tol^2 (stop when rr <= tol2 * bb)
+  double pq;       // last p^T A p
+  double spare;
+  int iter;        // completed operator applications
+  int max_iter;
+  int done;        // 1 once converged / stopped; later passes skip the instance
+  int status;      // 0 ok, 3 not converged, 4 breakdown
+  int first;       // 1 before the first z: beta = 0
+  int hist_cap;
+  unsigned int ticket;  // last-CTA counter for the grid reductions
+  int refine;      // FP64 residual recomputations (mixed refinement)
+  int total_iter;  // inner iterations summed over refinement steps
+  int pad;
+  double* hist;    // ||r_k|| / ||b||, k = 0..iter
+};
+
+// Per-instance pointers handed to every kernel (element type T of the pass).
+template <typename T>
+struct InstDesc {
+  const uint32_t* obs;     // observed-pixel bits
+  const T* t_inv;          // 1 / (n P)     [kx][ky]
+  const T* t_sqrt;         // sqrt(P) / n   [kx][ky]
+  T* spec;                 // interleaved complex half spectrum, transposed
+  T* r;
+  T* p;
+  T* q;
+  T* z;
+  T* u;
+  T* y;
+  T* b;
+  const T* d;              // caller's data map
+  T* out;                  // caller's output map
+  const float* dlt;        // FP32 correction (mixed refinement, FP64 passes)
+  float* r32;              // FP32 residual target (mixed refinement, FP64 passes)
+  CgState* st;
+  double* partial;         // per-CTA partial sums
+  unsigned long long seed;
+};
+
+// Elementwise operations fused into the row passes (runtime-uniform switch).
+enum RowOp : int {
+  // sources (row pass without an input spectrum)
+  OP_XI = 1,        // v = unit white noise (Philox4x32-10 + Box-Muller)
+  OP_LOAD_R = 2,    // v = r
+  OP_P_UPD_Z = 3,   // p = z + beta p; store p; v = p
+  OP_P_UPD_R = 4,   // p = r + beta p; store p; v = p   (no preconditioner)
+  OP_R_UPD = 5,     // r -= alpha q; u += alpha p; store; acc ||r||^2; v = r
+  OP_U64_UPD = 6,   // u += (double) dlt; store; v = u  (mixed refinement)
+  OP_LOAD_R_MASK = 7,  // v = P_x r
+  // middles (input spectrum -> output spectrum)
+  OP_MASK = 10,     // v = P_x v
+  OP_Y_W = 11,      // store y = v; v = (d - y) on U, 0 on M
+  // sinks (input spectrum, no output spectrum)
+  OP_STORE_Y = 20,  // store y = v
+  OP_Q = 21,        // q = P_x v; store; acc p^T q
+  OP_Z = 22,        // z = P_x v; store; acc r^T z
+  OP_B = 23,        // b = -P_x v; store r = b (and b); acc ||b||^2
+  OP_RES = 24,      // r = b - P_x v; store; acc ||r||^2; r32 = (float) r
+};
+
+// Scalar updates run by the last CTA of a reducing pass.
+enum ScalarOp : int {
+  SC_NONE = 0,
+  SC_BB = 1,          // bb = sum; rr = bb; done if bb == 0
+  SC_BB_RHO = 2,      // as SC_BB, plus rho = bb, beta = 0 (no preconditioner)
+  SC_ALPHA = 3,       // pq = sum; alpha = rho / pq (breakdown if pq <= 0)
+  SC_RCHECK = 4,      // rr = sum; iter++; convergence / iteration limit
+  SC_RCHECK_BETA = 5, // SC_RCHECK, then beta = rr / rho; rho = rr
+  SC_BETA = 6,        // rz = sum; beta = rz / rho (0 on the first); rho = rz
+  SC_RES = 7,         // rr = sum (FP64 true residual); refine++; done if rr <= tol2 bb
+};
+
+enum VecOp : int {
+  VOP_UPDATE = 1,     // r -= alpha q; u += alpha p; acc ||r||^2
+  VOP_ASSEMBLE = 2,   // out = d on U, y + u on M
+  VOP_COPY_D = 3,     // out = d
+  VOP_TO_F32 = 4,     // r32 = (float) r64 on the FP64 desc; acc ||r32||^2
+};
+
+// Launch arguments of the pass kernels.
+struct RowArgs {
+  int ny, nx;       // grid (nx = 2 L)
+  int rows;         // rows per CTA
+  int op;           // RowOp
+  int sop;          // ScalarOp (SC_NONE: no reduction)
+  int check_done;   // skip instances whose CG state is done
+};
+
+struct ColArgs {
+  int ny;           // column length (FFT size)
+  int nkx;          // nx/2 + 1 spectrum rows
+  int ffts;         // column FFTs per CTA
+  int table;        // 0: 1/(nP), 1: sqrt(P)/n
+  int check_done;
+};
+
+struct VecArgs {
+  long long npix;   // pixels per instance
+  int op;           // VecOp
+  int sop;
+  int check_done;
+};
+
+constexpr int kLmax = 8192;        // twiddle master table: W_8192^m
+constexpr int kMaxPartials = 4096; // CTAs per instance per reducing pass
+
+}  // namespace cgf

@@ -1,0 +1,295 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Inputs are seeded and synthetic (``workloads``); every expected value comes
+from ``oracle`` on the CPU.  Tolerances: FP64 path 1e-10 relative L2 on the
+filled pixels (1e-12 for single operator applications), FP32 operator 1e-5;
+observed pixels must equal the data bit for bit in every mode.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from workloads import synth, workload
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU containers
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1109_0286_gb300 as cg  # noqa: E402
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def case(ny, nx, seed=0, band_frac=0.15, ndiscs=6, r=(2.0, 6.0), spectrum="cmb"):
+    if spectrum == "cmb":
+        P = synth.spectrum_cmb_like(ny, nx, 2 * math.pi / max(ny, nx))
+    else:
+        P = synth.spectrum_lorentz_beam(ny, nx)
+    obs = synth.mask_band_discs(ny, nx, int(round(band_frac * ny)), ndiscs, r[0], r[1], seed)
+    return P, obs
+
+
+def gpu_map(x, dtype):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(dtype=dtype, device="cuda")
+
+
+# ------------------------------------------------------------------ draw / operator
+
+@pytest.mark.parametrize("ny,nx", [(64, 64), (32, 128), (256, 64), (128, 256)])
+@pytest.mark.parametrize("mode,bound", [("fp64", 1e-12), ("fp32", 2e-6)])
+def test_draw_matches_oracle(ny, nx, mode, bound):
+    P, obs = case(ny, nx)
+    plan = cg.Plan(P, obs, mode=mode, batch=2)
+    y = plan.draw([5, 2**40 + 7]).cpu().numpy()
+    Pf = O.hermitian_full(P, nx)
+    for i, s in enumerate([5, 2**40 + 7]):
+        assert rel(y[i], O.draw(Pf, s)) <= bound
+
+
+@pytest.mark.parametrize("ny,nx", [(16, 32), (64, 64), (32, 256), (512, 32), (256, 512)])
+@pytest.mark.parametrize("mode,bound", [("fp64", 1e-12), ("fp32", 2e-6)])
+def test_operators_match_oracle(ny, nx, mode, bound):
+    P, obs = case(ny, nx, seed=ny + nx)
+    Pf = O.hermitian_full(P, nx)
+    masked = obs == 0
+    plan = cg.Plan(P, obs, mode=mode)
+    dt = torch.float32 if mode == "fp32" else torch.float64
+    x = np.random.default_rng(ny * nx).standard_normal((ny, nx))
+    refs = [O.apply_power(x, Pf, -1.0), O.apply_power(x, Pf, 0.5),
+            O.apply_A(x, Pf, masked), O.apply_S(x, Pf, masked)]
+    for which, ref in enumerate(refs):
+        got = plan.apply(which, gpu_map(x, dt)).cpu().numpy()
+        assert rel(got, ref) <= bound, (which, rel(got, ref))
+
+
+@pytest.mark.parametrize("mode,bound", [("fp64", 1e-13), ("fp32", 1e-5)])
+def test_gpu_operator_symmetry(mode, bound):
+    """<a, A b> = <A a, b> for the GPU operator: the Hermiticity the paper
+    found indispensable for CG (Sect. 3)."""
+    P, obs = case(256, 256, seed=3)
+    plan = cg.Plan(P, obs, mode=mode)
+    dt = torch.float32 if mode == "fp32" else torch.float64
+    rng = np.random.default_rng(9)
+    m = obs == 0
+    for which in (2, 3):
+        a = np.where(m, rng.standard_normal(obs.shape), 0)
+        b = np.where(m, rng.standard_normal(obs.shape), 0)
+        Ab = plan.apply(which, gpu_map(b, dt)).cpu().numpy().astype(np.float64)
+        Aa = plan.apply(which, gpu_map(a, dt)).cpu().numpy().astype(np.float64)
+        lhs, rhs = np.sum(a * Ab), np.sum(Aa * b)
+        assert abs(lhs - rhs) <= bound * np.linalg.norm(a) * np.linalg.norm(Ab)
+
+
+# ------------------------------------------------------------------ full realizations
+
+def fp64_gate(x, ref_tol, ref_conv, m):
+    """FP64 parity at a loose tolerance: the GPU result must sit as close to
+    the oracle as the oracle sits to its own converged answer (the spread two
+    FP64 implementations show at the same tolerance), plus 1e-10."""
+    spread = rel(ref_tol.x[m], ref_conv.x[m])
+    return rel(x[m], ref_tol.x[m]) <= 2.0 * spread + 1e-10
+
+
+def test_plain64_fp64_parity():
+    """The plain method in FP64 on 64x64 (tol 1e-8) against the oracle at the
+    same tolerance, and at tol 1e-12 to 1e-10; plus the dense Cholesky solve."""
+    P, obs, spec = workload("plain64")
+    Pf = O.hermitian_full(P, 64)
+    d = O.draw(Pf, spec["data_seed"])
+    seed, tol = spec["seeds"][0], spec["tol"]
+    ref = O.realize(P, obs, d, seed, tol=tol)
+    conv = O.realize(P, obs, d, seed, tol=1e-13)
+    plan = cg.Plan(P, obs, mode="fp64", history_cap=512)
+    out, stats = plan.realize(gpu_map(d, torch.float64), [seed], tol)
+    x = out[0].cpu().numpy()
+    m = obs == 0
+    assert np.array_equal(x[~m], d[~m])
+    assert abs(stats[0]["iters"] - ref.pcg.iters) <= 1
+    assert fp64_gate(x, ref, conv, m)
+    h = plan.history(0)
+    assert len(h) == stats[0]["iters"] + 1 and h[0] == 1.0
+    # finite-precision CG histories of two FP64 implementations agree to
+    # rounding for the first iterations and drift apart later (loss of
+    # orthogonality), as two CPU FFT libraries do too
+    k = min(len(h), len(ref.pcg.history))
+    assert np.allclose(h[:6], ref.pcg.history[:6], rtol=1e-10)
+    assert np.allclose(h[:k], ref.pcg.history[:k], rtol=0.25)
+    out, stats = plan.realize(gpu_map(d, torch.float64), [seed], 1e-12)
+    x = out[0].cpu().numpy()
+    assert rel(x[m], O.realize(P, obs, d, seed, tol=1e-12).x[m]) <= 1e-10
+    dense = conv.y[m] + O.ml_dense_prec(Pf, obs, (d - conv.y)[~m])
+    assert rel(x[m], dense) <= 1e-10
+
+
+@pytest.mark.parametrize("precond", [True, False])
+def test_fp64_parity_cmb_256(precond):
+    P, obs = case(256, 256, seed=21)
+    Pf = O.hermitian_full(P, 256)
+    d = O.draw(Pf, 31)
+    ref = O.realize(P, obs, d, 4, tol=1e-9, precond=precond, max_iter=3000)
+    conv = O.realize(P, obs, d, 4, tol=1e-13, precond=True, max_iter=3000)
+    plan = cg.Plan(P, obs, mode="fp64", precond=precond, max_iter=3000)
+    out, stats = plan.realize(gpu_map(d, torch.float64), [4], 1e-9)
+    x = out[0].cpu().numpy()
+    m = obs == 0
+    assert np.array_equal(x[~m], d[~m])
+    assert abs(stats[0]["iters"] - ref.pcg.iters) <= 2
+    assert fp64_gate(x, ref, conv, m)
+    if precond:
+        out, _ = plan.realize(gpu_map(d, torch.float64), [4], 1e-13)
+        assert rel(out[0].cpu().numpy()[m], conv.x[m]) <= 1e-10
+
+
+@pytest.mark.parametrize("scale", [4, 1])
+def test_patch1024_fp32_parity(scale):
+    """FP32 operator with FP64-accurate inner products at tol 1e-6: within
+    1e-5 of the oracle at the same tolerance and of the converged oracle."""
+    P, obs, spec = workload("patch1024", scale=scale)
+    ny, nx = obs.shape
+    Pf = O.hermitian_full(P, nx)
+    d = O.draw(Pf, spec["data_seed"])
+    seed, tol = spec["seeds"][0], spec["tol"]
+    ref = O.realize(P, obs, d, seed, tol=tol)
+    conv = O.realize(P, obs, d, seed, tol=1e-12)
+    plan = cg.Plan(P, obs, mode="fp32")
+    out, stats = plan.realize(gpu_map(d, torch.float32), [seed], tol)
+    x = out[0].cpu().numpy().astype(np.float64)
+    m = obs == 0
+    assert np.array_equal(x[~m], d.astype(np.float32)[~m].astype(np.float64))
+    e_same, e_conv = rel(x[m], ref.x[m]), rel(x[m], conv.x[m])
+    spread = rel(ref.x[m], conv.x[m])
+    print(f"fp32 {ny}x{nx}: iters {stats[0]['iters']} (oracle {ref.pcg.iters}) "
+          f"err same-tol {e_same:.2e} converged {e_conv:.2e} oracle spread {spread:.2e}")
+    assert e_same <= 1e-5
+    assert e_conv <= 2.0 * spread + 1e-5
+
+
+@pytest.mark.parametrize("precond", [True, False])
+def test_mixed_refinement_to_1e10(precond):
+    """Mixed precision: FP32 inner PCG, FP64 residual and refinement, down to
+    a relative residual of 1e-10; error vs the converged FP64 oracle."""
+    P, obs, spec = workload("wide4096", scale=16)
+    ny, nx = obs.shape
+    Pf = O.hermitian_full(P, nx)
+    d = O.draw(Pf, spec["data_seed"])
+    seeds = spec["seeds"][:2]
+    plan = cg.Plan(P, obs, mode="mixed", precond=precond, batch=2, max_iter=4000)
+    out, stats = plan.realize(gpu_map(d, torch.float64), seeds, 1e-10)
+    m = obs == 0
+    for i, s in enumerate(seeds):
+        conv = O.realize(P, obs, d, s, tol=1e-12, precond=True)
+        x = out[i].cpu().numpy()
+        assert np.array_equal(x[~m], d[~m])
+        assert stats[i]["true_rel_resid"] <= 1e-10 and stats[i]["refine_steps"] >= 1
+        assert rel(x[m], conv.x[m]) <= 1e-8, rel(x[m], conv.x[m])
+
+
+def test_batch_equals_singles():
+    P, obs = case(128, 128, seed=8)
+    d = O.draw(O.hermitian_full(P, 128), 3)
+    seeds = [11, 12, 13, 14]
+    pb = cg.Plan(P, obs, mode="fp64", batch=4)
+    xb, _ = pb.realize(gpu_map(d, torch.float64), seeds, 1e-9)
+    ps = cg.Plan(P, obs, mode="fp64")
+    for i, s in enumerate(seeds):
+        xs, _ = ps.realize(gpu_map(d, torch.float64), [s], 1e-9)
+        assert torch.equal(xb[i], xs[0])
+
+
+# ------------------------------------------------------------------ edge cases
+
+@pytest.mark.parametrize("mode", ["fp64", "fp32", "mixed"])
+def test_no_mask_returns_data(mode):
+    P, _ = case(64, 64)
+    obs = np.ones((64, 64), np.uint8)
+    dt = torch.float32 if mode == "fp32" else torch.float64
+    d = np.random.default_rng(1).standard_normal((64, 64))
+    plan = cg.Plan(P, obs, mode=mode)
+    out, st = plan.realize(gpu_map(d, dt), [1], 1e-8)
+    assert torch.equal(out[0], gpu_map(d, dt)) and st[0]["iters"] == 0
+
+
+@pytest.mark.parametrize("mode", ["fp64", "fp32", "mixed"])
+def test_all_masked_returns_draw(mode):
+    P, _ = case(64, 64)
+    obs = np.zeros((64, 64), np.uint8)
+    dt = torch.float32 if mode == "fp32" else torch.float64
+    d = np.random.default_rng(1).standard_normal((64, 64))
+    plan = cg.Plan(P, obs, mode=mode)
+    out, st = plan.realize(gpu_map(d, dt), [9], 1e-8)
+    y = O.draw(O.hermitian_full(P, 64), 9)
+    assert st[0]["iters"] == 0
+    assert rel(out[0].cpu().numpy().astype(np.float64), y) <= (2e-6 if mode == "fp32" else 1e-12)
+
+
+def test_white_spectrum_fill_is_draw():
+    """P = const: b = 0 up to rounding, so x_M = y_M (P4)."""
+    P = np.full((64, 33), 1.7)
+    obs = synth.mask_band_discs(64, 64, 8, 3, 3.0, 3.0, 5)
+    d = np.random.default_rng(2).standard_normal((64, 64))
+    plan = cg.Plan(P, obs, mode="fp64")
+    out, _ = plan.realize(gpu_map(d, torch.float64), [4], 1e-8)
+    y = O.draw(O.hermitian_full(P, 64), 4)
+    m = obs == 0
+    assert np.max(np.abs(out[0].cpu().numpy()[m] - y[m])) < 1e-10
+
+
+def test_invalid_inputs_rejected():
+    P, obs = case(64, 64)
+    with pytest.raises(cg.FillError) as e:
+        cg.Plan(-P, obs)
+    assert e.value.status == 1
+    bad = P.copy()
+    bad[1, 0] *= 1.01
+    with pytest.raises(cg.FillError):
+        cg.Plan(bad, obs)
+    with pytest.raises(cg.FillError):
+        cg.Plan(synth.spectrum_cmb_like(48, 48, 0.1), np.ones((48, 48), np.uint8))
+    obs2 = obs.copy()
+    obs2[0, 0] = 2
+    with pytest.raises(cg.FillError):
+        cg.Plan(P, obs2)
+
+
+def test_iteration_limit_reports_not_converged():
+    P, obs = case(128, 128, seed=4)
+    d = O.draw(O.hermitian_full(P, 128), 1)
+    plan = cg.Plan(P, obs, mode="fp64", max_iter=3)
+    out, st = plan.realize(gpu_map(d, torch.float64), [2], 1e-12, check=False)
+    assert st[0]["status"] == 3 and st[0]["iters"] == 3
+    ref = O.realize(P, obs, d, 2, tol=1e-12, max_iter=3)
+    m = obs == 0
+    assert rel(out[0].cpu().numpy()[m], ref.x[m]) <= 1e-10
+
+
+# ------------------------------------------------------------------ full size
+
+def test_wide4096_full_size_certificate():
+    """4096^2, batch 8, mixed refinement to 1e-10, in the launch configuration
+    the benchmark times.  Checks at full size: observed pixels equal the data;
+    the draw y equals the oracle's at sampled rows; and the ML certificate
+    (eq. Boo / (C^-1 w)_M = 0 with w = d - y on U, u on M) holds to ~tol,
+    evaluated by the oracle's own operator."""
+    P, obs, spec = workload("wide4096")
+    ny, nx = obs.shape
+    Pf = O.hermitian_full(P, nx)
+    d = O.draw(Pf, spec["data_seed"])
+    seeds = spec["seeds"]
+    plan = cg.Plan(P, obs, mode="mixed", batch=len(seeds))
+    out, stats = plan.realize(gpu_map(d, torch.float64), seeds, spec["tol"])
+    m = obs == 0
+    for i in (0, len(seeds) - 1):
+        x = out[i].cpu().numpy()
+        assert np.array_equal(x[~m], d[~m])
+        y = O.draw(Pf, seeds[i])
+        w = np.where(m, x - y, d - y)
+        b = O.rhs(Pf, obs, d, y)
+        cert = np.linalg.norm(np.where(m, O.apply_power(w, Pf, -1.0), 0)) / np.linalg.norm(b)
+        assert cert <= 3e-10, cert
+        assert stats[i]["true_rel_resid"] <= spec["tol"]

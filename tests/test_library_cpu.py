@@ -1,0 +1,94 @@
+"""CPU-only checks of the boundary: the C-ABI library builds, loads without a
+GPU and exports every function ``include/cgfill.h`` declares; the Python
+binding mirrors those names; no compute call is made here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1109_0286_gb300 as cg
+from paper_1109_0286_gb300 import _build
+from workloads import synth, WORKLOADS
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "cgfill.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fill_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return cg.load()
+
+
+def test_header_and_binding_agree():
+    assert declared_functions() == sorted(cg.EXPORTED_SYMBOLS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert callable(getattr(lib, name))
+
+
+def test_host_only_calls(lib):
+    o = cg.fill_opts_default()
+    assert (o.mode, o.precond, o.batch, o.max_iter, o.max_refine) == (2, 1, 1, 10000, 10)
+    assert o.inner_tol == 1e-6
+    assert cg.fill_version() == 1
+    assert cg.fill_strerror(0) == "ok"
+    assert "converged" in cg.fill_strerror(3)
+    # argument validation happens before any device work
+    plan = ctypes.c_void_p()
+    P = np.ones((64, 33))
+    m = np.ones((64, 64), np.uint8)
+    st = lib.fill_init(ctypes.byref(plan), 64, 48, P.ctypes.data, m.ctypes.data,
+                       ctypes.byref(o), None)
+    assert st == 1 and not plan.value
+    assert lib.fill_realize(None, None, 0, None, 1e-6, None, None) == 1
+    lib.fill_destroy(None)
+
+
+def test_struct_layouts():
+    assert ctypes.sizeof(cg.FillOpts) == 48
+    assert ctypes.sizeof(cg.FillStats) == 40
+
+
+def test_mask_generators():
+    obs = synth.mask_band_discs(256, 256, 26, 20, 2.0, 12.0, seed=3)
+    assert obs.dtype == np.uint8 and set(np.unique(obs)) <= {0, 1}
+    assert np.all(obs[128 - 13:128 + 13] == 0)
+    # periodic discs wrap around the edges
+    m = np.zeros((32, 32), bool)
+    synth.add_discs(m, np.array([[0.0, 0.0]]), np.array([2.5]))
+    assert m[0, 0] and m[31, 31] and m[0, 30] and not m[16, 16]
+    for s in range(5):
+        a = 1 - synth.mask_area_target(256, 256, seed=s).mean()
+        assert 0.05 <= a <= 0.27
+
+
+def test_spectra_hermitian_and_positive():
+    for ny, nx in [(64, 64), (32, 128)]:
+        for P in (synth.spectrum_lorentz_beam(ny, nx),
+                  synth.spectrum_cmb_like(ny, nx, 2 * np.pi / 1024)):
+            assert P.shape == (ny, nx // 2 + 1) and np.all(P > 0)
+            my = (-np.arange(ny)) % ny
+            assert np.array_equal(P[:, 0], P[my, 0]) and np.array_equal(P[:, -1], P[my, -1])
+    k_lo = 2 * np.pi / 256
+    amps = np.ones(32)
+    assert np.allclose(synth.spectrum_cmb_bands(256, 256, amps, k_lo),
+                       synth.spectrum_cmb_like(256, 256, k_lo), rtol=1e-15)
+    b = synth.band_index_half(256, 256, k_lo)
+    assert b[0, 0] == 0 and b.max() == 31
+
+
+def test_workload_table():
+    assert set(WORKLOADS) == {"plain64", "patch1024", "batch_mixed", "grad2048", "wide4096"}
+    sizes = WORKLOADS["batch_mixed"]["sizes"]
+    assert sum(c for _, c in sizes) == 256
