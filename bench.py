@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 PCG arm")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--mode", default="mixed", choices=["mixed", "fp32", "fp64"],
+                    help="precision mode of the timed arm (profiling cases)")
+    ap.add_argument("--batch", type=int, default=0, help="realizations per step (0: workload's)")
+    ap.add_argument("--tol", type=float, default=0.0, help="CG tolerance (0: workload's)")
     return ap.parse_args()
 
 
@@ -221,11 +225,15 @@ def run_gpu(args):
 
     P, obs, spec = workload(args.workload)
     ny, nx = obs.shape
-    B = len(spec["seeds"])
-    tol = spec["tol"]
-    plan = cg.Plan(P, obs, mode="mixed", batch=B)
+    B = args.batch or len(spec["seeds"])
+    tol = args.tol or spec["tol"]
+    mode = args.mode
+    fdt = torch.float32 if mode == "fp32" else torch.float64
+    esz = 4 if mode == "fp32" else 8
+    plan = cg.Plan(P, obs, mode=mode, batch=B)
     d = plan.draw([spec["data_seed"]] * B)[0].clone()       # data drawn from P(k)
-    seeds = lambda k: [s + 100_003 * k + 10_000_019 * rank for s in spec["seeds"]]  # noqa: E731
+    seeds = lambda k: [spec["seeds"][0] + i + 100_003 * k + 10_000_019 * rank  # noqa: E731
+                       for i in range(B)]
 
     for k in range(args.warmup):
         plan.realize(d, seeds(k), tol)
@@ -241,7 +249,8 @@ def run_gpu(args):
             _, st = plan.realize(d, seeds(args.warmup + k), tol)
             iters += sum(s["iters"] for s in st)
             launches += st[0]["launches"]
-            worst_resid = max([worst_resid] + [s["true_rel_resid"] for s in st])
+            worst_resid = max([worst_resid] + [s["true_rel_resid"] if s["true_rel_resid"] >= 0
+                                               else s["rel_resid"] for s in st])
         e1.record(stream)
         torch.cuda.synchronize()
     barrier()
@@ -255,8 +264,8 @@ def run_gpu(args):
 
     # end to end through the public API with host buffers: H2D of d, D2H of x
     d_host = d.cpu().pin_memory()
-    out_host = torch.empty((B, ny, nx), dtype=torch.float64).pin_memory()
-    out_dev = torch.empty((B, ny, nx), dtype=torch.float64, device="cuda")
+    out_host = torch.empty((B, ny, nx), dtype=fdt).pin_memory()
+    out_dev = torch.empty((B, ny, nx), dtype=fdt, device="cuda")
     d_dev = torch.empty_like(d)
     esteps = max(1, min(args.steps, 3))
     torch.cuda.synchronize()
@@ -269,7 +278,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / esteps
     e2e = {"value": B * world / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": d_host.numel() * 8, "d2h_bytes_per_step": out_host.numel() * 8}
+           "h2d_bytes_per_step": d_host.numel() * esz, "d2h_bytes_per_step": out_host.numel() * esz}
 
     # roofline of the hot-loop passes (CUDA events on the plan's stream)
     peaks, peak_src = measured_peaks()
@@ -280,7 +289,7 @@ def run_gpu(args):
               4: ("k_row mid (C2R, P_x, R2C)", 1)}
     timing = {}
     for pid, (name, per_iter) in passes.items():
-        pms, pbytes = plan.time_pass(pid, precision=0, reps=20)
+        pms, pbytes = plan.time_pass(pid, reps=20)
         timing[pid] = (name, per_iter, pms, pbytes)
     dom = max(timing, key=lambda k: timing[k][1] * timing[k][2])
     name, _, pms, pbytes = timing[dom]
@@ -297,14 +306,15 @@ def run_gpu(args):
 
     # plain FP64 GPU PCG on the same inputs
     fp64 = None
-    if not args.no_fp64 and args.fp64_steps > 0:
+    if not args.no_fp64 and args.fp64_steps > 0 and mode != "fp64":
         p64 = cg.Plan(P, obs, mode="fp64", batch=B)
-        p64.realize(d, seeds(0), tol)
+        d64 = d.to(torch.float64)
+        p64.realize(d64, seeds(0), tol)
         torch.cuda.synchronize()
         e0.record(stream)
         it64 = 0
         for k in range(args.fp64_steps):
-            _, st = p64.realize(d, seeds(1 + k), tol)
+            _, st = p64.realize(d64, seeds(1 + k), tol)
             it64 += sum(s["iters"] for s in st)
         e1.record(stream)
         torch.cuda.synchronize()
@@ -318,7 +328,7 @@ def run_gpu(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle as O
-        dn = d.cpu().numpy()
+        dn = d.cpu().numpy().astype("float64")
         setup, t_iter = oracle_sample(P, obs, dn, spec["seeds"][0], 1)
         n_it = fp64["iters_per_realization"] if fp64 else FP64_ITERS_WIDE4096
         cpu = {"value": 1.0 / (setup + n_it * t_iter), "unit": UNIT, "cores": threads_used(),
@@ -331,9 +341,10 @@ def run_gpu(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32+f64", "data": "synthetic",
+                "dtype": {"mixed": "f32+f64", "fp32": "f32", "fp64": "f64"}[mode],
+                "data": "synthetic",
                 "config": {"workload": args.workload, "grid": [ny, nx], "batch": B,
-                           "tol": tol, "mode": "mixed", "precond": "sqrtC",
+                           "tol": tol, "mode": mode, "precond": "sqrtC",
                            "masked_fraction": round(float((obs == 0).mean()), 4),
                            "parallelism": f"replicas{world}",
                            "l2": "inputs larger than L2 (no flush)"},

@@ -76,6 +76,7 @@ typedef struct {
   int history_cap;       /* residual-history entries kept per realization; default 0 */
   int rows_per_cta;      /* row-pass CTA height, 0 = default schedule */
   int ffts_per_cta;      /* column FFTs per CTA, 0 = default schedule */
+  int backward;          /* 1: allocate the buffers fill_backward needs; default 0 */
 } fill_opts;
 
 typedef struct {
@@ -162,6 +163,76 @@ fill_status fill_history(fill_plan* plan, int inst, double* hist, int cap, int* 
  */
 fill_status fill_time_pass(fill_plan* plan, int pass, int precision, int reps,
                            double* ms_per_launch, double* bytes_per_launch);
+
+/*
+ * fill_set_bands -- band-power parameterisation for fill_backward:
+ * P(k) = sum_b a_b T_b(k) + N with T_b(k) = 1[band(k) = b] S(k).
+ * band_of_k: host int32, ny x (nx/2+1) (layout of P_half), values in
+ * [0, nbands), nbands <= 64; sig_half: host float64 S(k), same layout.  The
+ * derivative is taken at the plan's P.  Allocates the plan's gradient tables
+ * (on the first call).  Errors: FILL_EINVAL, FILL_ENOMEM, FILL_ECUDA.
+ */
+fill_status fill_set_bands(fill_plan* plan, int nbands, const int32_t* band_of_k,
+                           const double* sig_half);
+
+/*
+ * fill_backward -- adjoint gradients of a scalar loss L(x) through the
+ * realizations of the LAST fill_realize on this plan (no other compute call
+ * in between; d must be the same data).  The paper does not differentiate its
+ * method; with g = dL/dx the adjoint is one more solve with the same
+ * symmetric operator and preconditioner, lam = A^-1 g_M (Sect. 2.4), and
+ *   dL/dd = g_U - (C^-1 lam)_U on U, 0 on M;
+ *   dL/da_b = sum_k T_b(k) [ Re(conj(F h) F xi)/(2 n sqrt P)
+ *                            + Re(conj(F lam) F w)/(n P^2) ]   (full k plane)
+ * with h = g on M, (C^-1 lam)_U on U, w = d - y on U, u on M, and xi the
+ * seed's white noise held fixed (reparameterised draw).
+ * grad_x, grad_d: device, batch maps (plan element type); grad_bands: host
+ * batch x nbands doubles, or NULL to skip the band gradient.  Needs
+ * opts.backward = 1 (and fill_set_bands if grad_bands is given).
+ * Returns like fill_realize; stats describe the adjoint solve.
+ */
+fill_status fill_backward(fill_plan* plan, const void* d, long long d_stride,
+                          const void* grad_x, double tol, void* grad_d, double* grad_bands,
+                          fill_stats* stats);
+
+/*
+ * fill_autotune -- chooses the plan's launch schedule (grid rows per CTA of
+ * the row passes, column FFTs per CTA of the column pass) by timing every
+ * valid candidate on the device; results are cached as text lines in
+ * cache_path (NULL: no cache).  Call after fill_init, before fill_realize.
+ * Errors: FILL_EINVAL, FILL_ECUDA.
+ */
+fill_status fill_autotune(fill_plan* plan, const char* cache_path);
+
+/*
+ * Groups: many realizations over masks and grid sizes in one call.
+ * fill_group_init collects plans (all FILL_MODE_FP32 or all FILL_MODE_FP64,
+ * same precond and stream; each keeps its own mask, spectrum and buffers).
+ * Plans with the same grid form a size class whose instances share every pass
+ * launch; the classes run concurrently as parallel branches of one captured
+ * CUDA graph per chunk of CG iterations.  autotune != 0 tunes each class's
+ * schedule (cached in cache_path if not NULL).  The plans must outlive the
+ * group.  Errors: FILL_EINVAL, FILL_ENOMEM, FILL_ECUDA.
+ */
+typedef struct fill_group fill_group;
+fill_status fill_group_init(fill_group** group, fill_plan* const* plans, int count,
+                            int autotune, const char* cache_path);
+
+/*
+ * fill_group_realize -- constrained realizations (Sects. 2.1-2.4) for every
+ * plan of the group.  d[i]: device, one data map shared by plan i's batch;
+ * out[i]: device, plan i's batch maps; seeds: host, one per realization in
+ * plan order (plan 0's batch first); stats: host, one per realization, or
+ * NULL.  Returns the worst status.
+ */
+fill_status fill_group_realize(fill_group* group, const void* const* d, const uint64_t* seeds,
+                               double tol, void* const* out, fill_stats* stats);
+
+/* Realizations per fill_group_realize call (sum of the plans' batches). */
+int fill_group_size(const fill_group* group);
+
+/* Frees the group (not its plans; NULL is allowed). */
+void fill_group_destroy(fill_group* group);
 
 /* Number of masked pixels n_M of the plan's mask. */
 long long fill_masked_count(const fill_plan* plan);

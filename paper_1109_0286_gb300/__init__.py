@@ -22,7 +22,8 @@ from . import _build
 __all__ = [
     "FillOpts", "FillStats", "FillError", "load", "lib_path", "fill_opts_default",
     "fill_init", "fill_realize", "fill_draw", "fill_apply", "fill_history",
-    "fill_time_pass", "fill_masked_count", "fill_destroy", "fill_strerror", "fill_last_error",
+    "fill_time_pass", "fill_set_bands", "fill_backward", "fill_autotune", "fill_group_init",
+    "fill_group_realize", "fill_group_size", "fill_group_destroy", "Group", "fill_masked_count", "fill_destroy", "fill_strerror", "fill_last_error",
     "fill_version", "Plan", "MODES", "EXPORTED_SYMBOLS",
 ]
 
@@ -31,8 +32,9 @@ STATUS = {0: "FILL_OK", 1: "FILL_EINVAL", 2: "FILL_ENOMEM", 3: "FILL_ENOTCONV",
           4: "FILL_EBREAKDOWN", 5: "FILL_ETIMEOUT", 6: "FILL_ECUDA"}
 EXPORTED_SYMBOLS = [
     "fill_opts_default", "fill_init", "fill_realize", "fill_draw", "fill_apply",
-    "fill_history", "fill_time_pass", "fill_masked_count", "fill_destroy",
-    "fill_strerror", "fill_last_error", "fill_version",
+    "fill_history", "fill_time_pass", "fill_set_bands", "fill_backward", "fill_autotune",
+    "fill_group_init", "fill_group_realize", "fill_group_size", "fill_group_destroy",
+    "fill_masked_count", "fill_destroy", "fill_strerror", "fill_last_error", "fill_version",
 ]
 
 
@@ -41,7 +43,7 @@ class FillOpts(ctypes.Structure):
                 ("batch", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("max_refine", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("history_cap", ctypes.c_int), ("rows_per_cta", ctypes.c_int),
-                ("ffts_per_cta", ctypes.c_int)]
+                ("ffts_per_cta", ctypes.c_int), ("backward", ctypes.c_int)]
 
 
 class FillStats(ctypes.Structure):
@@ -96,6 +98,22 @@ def load() -> ctypes.CDLL:
     lib.fill_history.restype = _ci
     lib.fill_time_pass.argtypes = [_vp, _ci, _ci, _ci, ctypes.POINTER(_cd), ctypes.POINTER(_cd)]
     lib.fill_time_pass.restype = _ci
+    lib.fill_set_bands.argtypes = [_vp, _ci, _vp, _vp]
+    lib.fill_set_bands.restype = _ci
+    lib.fill_backward.argtypes = [_vp, _vp, _cll, _vp, _cd, _vp, _vp, ctypes.POINTER(FillStats)]
+    lib.fill_backward.restype = _ci
+    lib.fill_autotune.argtypes = [_vp, ctypes.c_char_p]
+    lib.fill_autotune.restype = _ci
+    lib.fill_group_init.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_vp), _ci, _ci,
+                                    ctypes.c_char_p]
+    lib.fill_group_init.restype = _ci
+    lib.fill_group_realize.argtypes = [_vp, ctypes.POINTER(_vp), _vp, _cd, ctypes.POINTER(_vp),
+                                       ctypes.POINTER(FillStats)]
+    lib.fill_group_realize.restype = _ci
+    lib.fill_group_size.argtypes = [_vp]
+    lib.fill_group_size.restype = _ci
+    lib.fill_group_destroy.argtypes = [_vp]
+    lib.fill_group_destroy.restype = None
     lib.fill_masked_count.argtypes = [_vp]
     lib.fill_masked_count.restype = _cll
     lib.fill_destroy.argtypes = [_vp]
@@ -170,6 +188,57 @@ def fill_time_pass(plan, pass_id, precision, reps):
     return ms.value, nbytes.value
 
 
+def fill_set_bands(plan, band_of_k, sig_half):
+    b = np.ascontiguousarray(band_of_k, dtype=np.int32)
+    sg = np.ascontiguousarray(sig_half, dtype=np.float64)
+    st = load().fill_set_bands(_vp(plan), int(b.max()) + 1, b.ctypes.data, sg.ctypes.data)
+    if st != 0:
+        raise FillError(st, "fill_set_bands")
+    return int(b.max()) + 1
+
+
+def fill_backward(plan, d_ptr, d_stride, gx_ptr, tol, gd_ptr, nbands, batch):
+    gb = np.zeros((batch, max(nbands, 1)), dtype=np.float64)
+    stats = (FillStats * batch)()
+    st = load().fill_backward(_vp(plan), _vp(d_ptr), _cll(d_stride), _vp(gx_ptr), _cd(tol),
+                              _vp(gd_ptr), gb.ctypes.data if nbands else None, stats)
+    return st, (gb if nbands else None), [x.as_dict() for x in stats]
+
+
+def fill_autotune(plan, cache_path=None):
+    st = load().fill_autotune(_vp(plan), cache_path.encode() if cache_path else None)
+    if st != 0:
+        raise FillError(st, "fill_autotune")
+
+
+def fill_group_init(plans, autotune=False, cache_path=None):
+    arr = (_vp * len(plans))(*plans)
+    g = _vp()
+    st = load().fill_group_init(ctypes.byref(g), arr, len(plans), 1 if autotune else 0,
+                                cache_path.encode() if cache_path else None)
+    if st != 0:
+        raise FillError(st, "fill_group_init")
+    return g.value
+
+
+def fill_group_realize(group, d_ptrs, seeds, tol, out_ptrs, total):
+    s = np.ascontiguousarray(seeds, dtype=np.uint64)
+    d = (_vp * len(d_ptrs))(*d_ptrs)
+    o = (_vp * len(out_ptrs))(*out_ptrs)
+    stats = (FillStats * total)()
+    st = load().fill_group_realize(_vp(group), d, s.ctypes.data, _cd(tol), o, stats)
+    return st, [x.as_dict() for x in stats]
+
+
+def fill_group_size(group) -> int:
+    return int(load().fill_group_size(_vp(group)))
+
+
+def fill_group_destroy(group) -> None:
+    if group:
+        load().fill_group_destroy(_vp(group))
+
+
 def fill_masked_count(plan) -> int:
     return int(load().fill_masked_count(_vp(plan)))
 
@@ -204,7 +273,7 @@ class Plan:
 
     def __init__(self, P_half, observed, mode="mixed", precond=True, batch=1,
                  max_iter=10000, max_refine=10, inner_tol=1e-6, history_cap=0,
-                 rows_per_cta=0, ffts_per_cta=0, stream=None):
+                 rows_per_cta=0, ffts_per_cta=0, backward=False, stream=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("paper_1109_0286_gb300 needs a CUDA GPU; no CPU fallback exists")
@@ -218,6 +287,8 @@ class Plan:
         o.history_cap = int(history_cap)
         o.rows_per_cta = int(rows_per_cta)
         o.ffts_per_cta = int(ffts_per_cta)
+        o.backward = 1 if backward else 0
+        self.nbands = 0
         self.ny, self.nx = observed.shape
         self.batch = int(batch)
         self.mode = mode
@@ -252,6 +323,27 @@ class Plan:
             raise FillError(st, "fill_realize")
         return out, stats
 
+    def set_bands(self, band_of_k, sig_half):
+        """Band-power templates T_b(k) = 1[band(k) = b] S(k) for ``backward``."""
+        self.nbands = fill_set_bands(self._plan, band_of_k, sig_half)
+
+    def backward(self, d, grad_x, tol, grad_d=None, bands=True, check=True):
+        """Adjoint gradients of L(x) through the last ``realize``: returns
+        ``(dL/dd, dL/da_b or None, stats)``."""
+        import torch
+        shared = d.numel() == self.ny * self.nx
+        self._check(d, "d", 1 if shared else self.batch)
+        self._check(grad_x, "grad_x", self.batch)
+        if grad_d is None:
+            grad_d = torch.empty((self.batch, self.ny, self.nx), dtype=self.dtype, device=d.device)
+        self._check(grad_d, "grad_d", self.batch)
+        nb = self.nbands if bands else 0
+        st, gb, stats = fill_backward(self._plan, d.data_ptr(), 0 if shared else self.ny * self.nx,
+                                      grad_x.data_ptr(), tol, grad_d.data_ptr(), nb, self.batch)
+        if check and st != 0:
+            raise FillError(st, "fill_backward")
+        return grad_d, gb, stats
+
     def draw(self, seeds, out=None):
         import torch
         if out is None:
@@ -274,6 +366,10 @@ class Plan:
             precision = 1 if self.mode == "fp64" else 0
         return fill_time_pass(self._plan, pass_id, precision, reps)
 
+    def autotune(self, cache_path=None):
+        """Time the valid launch schedules and keep the fastest."""
+        fill_autotune(self._plan, cache_path)
+
     def history(self, inst=0):
         return fill_history(self._plan, inst, self.history_cap)
 
@@ -285,6 +381,44 @@ class Plan:
         if getattr(self, "_plan", None):
             fill_destroy(self._plan)
             self._plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Group:
+    """Many plans (masks, spectra, grid sizes) realized together: plans of one
+    grid size share each pass launch, sizes run as concurrent graph branches."""
+
+    def __init__(self, plans, autotune=False, cache_path=None):
+        self.plans = list(plans)
+        self._g = fill_group_init([p._plan for p in self.plans], autotune, cache_path)
+        self.size = fill_group_size(self._g)
+
+    def realize(self, ds, seeds, tol, outs=None, check=True):
+        import torch
+        if outs is None:
+            outs = [torch.empty((p.batch, p.ny, p.nx), dtype=p.dtype, device=p.device)
+                    for p in self.plans]
+        for p, d, o in zip(self.plans, ds, outs):
+            p._check(d, "d", 1)
+            p._check(o, "out", p.batch)
+        seeds = np.asarray(seeds, dtype=np.uint64).reshape(-1)
+        if seeds.size != self.size:
+            raise ValueError("need one seed per realization")
+        st, stats = fill_group_realize(self._g, [d.data_ptr() for d in ds], seeds, tol,
+                                       [o.data_ptr() for o in outs], self.size)
+        if check and st != 0:
+            raise FillError(st, "fill_group_realize")
+        return outs, stats
+
+    def close(self):
+        if getattr(self, "_g", None):
+            fill_group_destroy(self._g)
+            self._g = None
 
     def __del__(self):
         try:

@@ -9,14 +9,27 @@
 // holds X[t + e L/16] -- the same positions -- so a forward transform, a
 // diagonal multiply and an inverse transform chain without a shared-memory
 // round trip.  Between stages data goes through shared memory (split real /
-// imaginary arrays, one pad word per 16, which keeps the stage writes free of
-// bank conflicts).
+// imaginary arrays, index map sidx<T>).  A radix-16 stage needs W^(jm r),
+// r = 1..15: three table loads and at most four complex products each.
 #pragma once
 #include "cg_common.cuh"
 
 namespace cgf {
 
-__device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
+// Shared-memory index of logical element i of an FFT exchange area.  FP32:
+// XOR swizzle of the low five bits with q ^ (q << 1), q = i / 32, which makes
+// every stage write (strides 1..16) and the strided reads free of bank
+// conflicts; FP64: one pad word per 16 elements (conflict-free for 8-byte
+// elements).  Both stay inside [0, L + L/16].
+template <typename T>
+__device__ __forceinline__ int sidx(int i) {
+  if constexpr (sizeof(T) == 4) {
+    const int q = i >> 5;
+    return i ^ ((q ^ (q << 1)) & 31);
+  } else {
+    return i + (i >> 4);
+  }
+}
 
 // a * (-i) for the forward transform, a * (+i) for the inverse.
 template <typename T, bool INV>
@@ -138,7 +151,7 @@ __device__ __forceinline__ void fft_regs(cx<T> (&v)[16], T* __restrict__ sre,
     for (int q = 0; q < NB; ++q)
 #pragma unroll
       for (int r = 0; r < R0; ++r) {
-        const int idx = padi((tid + q * TT) * R0 + r);
+        const int idx = sidx<T>((tid + q * TT) * R0 + r);
         sre[idx] = v[q + r * NB].r;
         sim[idx] = v[q + r * NB].i;
       }
@@ -154,16 +167,26 @@ __device__ __forceinline__ void fft_regs(cx<T> (&v)[16], T* __restrict__ sre,
       __syncthreads();
 #pragma unroll
       for (int e = 0; e < 16; ++e) {
-        const int idx = padi(tid + e * TT);
+        const int idx = sidx<T>(tid + e * TT);
         v[e] = cx<T>{sre[idx], sim[idx]};
       }
       const int jm = tid & (ns - 1);
       const int stride = kLmax / (ns * 16);
+      // W^(jm r) for r = 1..15 from three table entries (W^jm, W^4jm, W^8jm)
+      // and at most four complex products each (a few ulp).
+      cx<T> w[16];
+      w[1] = twiddle<T>(tw, jm * stride);
+      w[4] = twiddle<T>(tw, 4 * jm * stride);
+      w[8] = twiddle<T>(tw, 8 * jm * stride);
+      w[2] = cmul(w[1], w[1]);
+      w[3] = cmul(w[2], w[1]);
+      w[5] = cmul(w[4], w[1]);
+      w[6] = cmul(w[4], w[2]);
+      w[7] = cmul(w[4], w[3]);
 #pragma unroll
-      for (int r = 1; r < 16; ++r) {
-        const cx<T> w = twiddle<T>(tw, jm * r * stride);
-        v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
-      }
+      for (int r = 9; r < 16; ++r) w[r] = cmul(w[8], w[r - 8]);
+#pragma unroll
+      for (int r = 1; r < 16; ++r) v[r] = INV ? cmulc(v[r], w[r]) : cmul(v[r], w[r]);
     }
     dft16<T, INV>(v);
     if (!last) {
@@ -172,7 +195,7 @@ __device__ __forceinline__ void fft_regs(cx<T> (&v)[16], T* __restrict__ sre,
       const int base = (tid - jm) * 16 + jm;
 #pragma unroll
       for (int r = 0; r < 16; ++r) {
-        const int idx = padi(base + r * ns);
+        const int idx = sidx<T>(base + r * ns);
         sre[idx] = v[r].r;
         sim[idx] = v[r].i;
       }

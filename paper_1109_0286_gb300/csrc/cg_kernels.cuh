@@ -41,6 +41,15 @@ __device__ __forceinline__ void src_op(int op, const InstDesc<T>& I, long long p
       if ((w >> ((pix + 1) & 31)) & 1u) a1 = (T)0;
       break;
     }
+    case OP_LOAD_U:
+      ld_pair(I.u + pix, a0, a1);
+      break;
+    case OP_LOAD_Y:
+      ld_pair(I.y + pix, a0, a1);
+      break;
+    case OP_LOAD_W:
+      ld_pair(I.w + pix, a0, a1);
+      break;
     case OP_LOAD_R:
       ld_pair(I.r + pix, a0, a1);
       acc.add_prod(a0, a0);
@@ -147,6 +156,15 @@ __device__ __forceinline__ void sink_op(int op, const InstDesc<T>& I, long long 
       acc.add_prod(a1, a1);
       break;
     }
+    case OP_GRAD: {
+      // v = C^-1 lam.  dL/dd_U = g_U - (C^-1 lam)_U, dL/dd_M = 0;
+      // dL/dy = h = g on M, (C^-1 lam)_U on U (kept in y).
+      T g0, g1;
+      ld_pair(I.gx + pix, g0, g1);
+      st_pair(I.out + pix, o0 ? g0 - a0 : (T)0, o1 ? g1 - a1 : (T)0);
+      st_pair(I.y + pix, o0 ? a0 : g0, o1 ? a1 : g1);
+      break;
+    }
     default:
       break;
   }
@@ -163,6 +181,7 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   __shared__ double red[32];
+  __shared__ cx<T> wcol[16];   // W_nx^(e TT), e = 0..15 (warp-uniform factor)
   const InstDesc<T>& I = insts[blockIdx.y];
   if (a.check_done && *(volatile int*)&I.st->done) return;
 
@@ -182,15 +201,17 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
   Acc<T> acc;
 
   if constexpr (IN_SPEC) {
-    const T* spec = I.spec;
+    const T* spec = a.spec_sel ? I.spec2 : I.spec;
     for (int e = threadIdx.x; e < (L + 1) * rows; e += blockDim.x) {
       const int k = e / rows, rr = e - k * rows;
       const cx<T> s = ld_cx<T>(spec + 2 * ((long long)k * ny + y0 + rr));
       tre[k * tstride + rr] = s.r;
       tim[k * tstride + rr] = s.i;
     }
+    if (threadIdx.x < 16) wcol[threadIdx.x] = twiddle<T>(tw, threadIdx.x * TT * TWS);
     __syncthreads();
     // C2R: Z[k] = (X[k] + conj X[L-k]) + i e^{+2 pi i k / nx} (X[k] - conj X[L-k])
+    const cx<T> wt = twiddle<T>(tw, tid * TWS);
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       const int k = tid + e * TT;
@@ -200,7 +221,7 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
         xk.i = (T)0;
         xc.i = (T)0;
       }
-      const cx<T> w = twiddle<T>(tw, k * TWS);
+      const cx<T> w = cmul(wt, wcol[e]);   // W_nx^k, k = tid + e TT
       const cx<T> sum = xk + xc;
       const cx<T> dif = cmulc(xk - xc, w);  // (X - conj X') e^{+i...}
       v[e] = cx<T>{sum.r - dif.i, sum.i + dif.r};
@@ -222,26 +243,28 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
   }
 
   if constexpr (OUT_SPEC) {
+    if (!IN_SPEC && threadIdx.x < 16) wcol[threadIdx.x] = twiddle<T>(tw, threadIdx.x * TT * TWS);
     fft_regs<T, LOG_L, false>(v, sre, sim, tid, tw);
     __syncthreads();
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
-      const int idx = padi(tid + e * TT);
+      const int idx = sidx<T>(tid + e * TT);
       sre[idx] = v[e].r;
       sim[idx] = v[e].i;
     }
     __syncthreads();
+    const cx<T> wt = twiddle<T>(tw, tid * TWS);
     // R2C: X[k] = (Z[k] + conj Z[L-k]) / 2 - (i/2) e^{-2 pi i k/nx} (Z[k] - conj Z[L-k])
     cx<T> nyq{v[0].r - v[0].i, (T)0};
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       const int k = tid + e * TT;
-      const int kc = padi((L - k) & (L - 1));
+      const int kc = sidx<T>((L - k) & (L - 1));
       const cx<T> zc{sre[kc], -sim[kc]};
       const cx<T> zk = v[e];
       const cx<T> ev = scal(zk + zc, (T)0.5);
       const cx<T> od = scal(mul_mi<T, false>(zk - zc), (T)0.5);
-      v[e] = ev + cmul(od, twiddle<T>(tw, k * TWS));
+      v[e] = ev + cmul(od, cmul(wt, wcol[e]));
     }
     __syncthreads();
 #pragma unroll
@@ -255,7 +278,7 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
       tim[L * tstride + row] = nyq.i;
     }
     __syncthreads();
-    T* spec = I.spec;
+    T* spec = a.spec_sel ? I.spec2 : I.spec;
     for (int e = threadIdx.x; e < (L + 1) * rows; e += blockDim.x) {
       const int k = e / rows, rr = e - k * rows;
       st_cx<T>(spec + 2 * ((long long)k * ny + y0 + rr),
@@ -283,18 +306,20 @@ k_col(const InstDesc<T>* __restrict__ insts, ColArgs a, const T* __restrict__ tw
   const bool act = kx < a.nkx;
   T* sre = sm + f * 2 * PADN;
   T* sim = sre + PADN;
-  T* col = I.spec + 2 * (long long)(act ? kx : 0) * N;
-  const T* tab = (a.table ? I.t_sqrt : I.t_inv) + (long long)(act ? kx : 0) * N;
+  T* col = (a.spec_sel ? I.spec2 : I.spec) + 2 * (long long)(act ? kx : 0) * N;
   cx<T> v[16];
 #pragma unroll
   for (int e = 0; e < 16; ++e) v[e] = act ? ld_cx<T>(col + 2 * (tid + e * TT)) : cx<T>{(T)0, (T)0};
   fft_regs<T, LOG_N, false>(v, sre, sim, tid, tw);
+  if (a.table >= 0) {
+    const T* tab = (a.table ? I.t_sqrt : I.t_inv) + (long long)(act ? kx : 0) * N;
 #pragma unroll
-  for (int e = 0; e < 16; ++e) {
-    const T t = act ? __ldg(tab + tid + e * TT) : (T)0;
-    v[e] = scal(v[e], t);
+    for (int e = 0; e < 16; ++e) {
+      const T t = act ? __ldg(tab + tid + e * TT) : (T)0;
+      v[e] = scal(v[e], t);
+    }
+    fft_regs<T, LOG_N, true>(v, sre, sim, tid, tw);
   }
-  fft_regs<T, LOG_N, true>(v, sre, sim, tid, tw);
   if (act) {
 #pragma unroll
     for (int e = 0; e < 16; ++e) st_cx<T>(col + 2 * (tid + e * TT), v[e]);
@@ -339,6 +364,34 @@ k_vec(const InstDesc<T>* __restrict__ insts, VecArgs a) {
         st_pair(I.out + pix, o0 ? d0 : y0 + u0, o1 ? d1 : y1 + u1);
         break;
       }
+      case VOP_MAKE_W: {
+        const uint32_t w = __ldg(I.obs + (pix >> 5));
+        const bool o0 = (w >> (pix & 31)) & 1u, o1 = (w >> ((pix + 1) & 31)) & 1u;
+        T d0, d1, y0, y1, u0, u1;
+        ld_pair(I.d + pix, d0, d1);
+        ld_pair(I.y + pix, y0, y1);
+        ld_pair(I.u + pix, u0, u1);
+        st_pair(I.w + pix, o0 ? d0 - y0 : u0, o1 ? d1 - y1 : u1);
+        break;
+      }
+      case VOP_LOAD_G: {
+        const uint32_t w = __ldg(I.obs + (pix >> 5));
+        const bool o0 = (w >> (pix & 31)) & 1u, o1 = (w >> ((pix + 1) & 31)) & 1u;
+        T g0, g1;
+        ld_pair(I.gx + pix, g0, g1);
+        g0 = o0 ? (T)0 : g0;
+        g1 = o1 ? (T)0 : g1;
+        st_pair(I.r + pix, g0, g1);
+        st_pair(I.b + pix, g0, g1);
+        if (I.r32) *reinterpret_cast<float2*>(I.r32 + pix) = make_float2((float)g0, (float)g1);
+        acc.add_prod(g0, g0);
+        acc.add_prod(g1, g1);
+        break;
+      }
+      case VOP_ZERO_UP:
+        st_pair(I.u + pix, (T)0, (T)0);
+        st_pair(I.p + pix, (T)0, (T)0);
+        break;
       case VOP_COPY_D: {
         T d0, d1;
         ld_pair(I.d + pix, d0, d1);
@@ -351,6 +404,30 @@ k_vec(const InstDesc<T>* __restrict__ insts, VecArgs a) {
   }
   if (a.sop != SC_NONE)
     grid_reduce(acc.value(), red, I.partial, I.st, a.sop, gridDim.x, blockIdx.x);
+}
+
+// ----------------------------------------------------------------- band products
+// part[inst][cta][b] = sum over the CTA's half-plane modes k with band(k) = b
+// of coef(k) Re(conj(spec(k)) spec2(k)); both spectra are full 2D transforms
+// in the transposed layout, coef carries the Hermitian weight (1 on the two
+// self-conjugate columns, 2 elsewhere).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_band_dot(const InstDesc<T>* __restrict__ insts, DotArgs a) {
+  __shared__ double hist[kMaxBands];
+  const InstDesc<T>& I = insts[blockIdx.y];
+  for (int b = threadIdx.x; b < a.nbands; b += blockDim.x) hist[b] = 0.0;
+  __syncthreads();
+  const T* coef = reinterpret_cast<const T*>(a.coef);
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.nmodes;
+       m += (long long)gridDim.x * blockDim.x) {
+    const cx<T> x = ld_cx<T>(I.spec + 2 * m), z = ld_cx<T>(I.spec2 + 2 * m);
+    const double v = (double)((x.r * z.r + x.i * z.i) * __ldg(coef + m));
+    atomicAdd(&hist[__ldg(a.band + m)], v);
+  }
+  __syncthreads();
+  double* out = a.part + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * a.nbands;
+  for (int b = threadIdx.x; b < a.nbands; b += blockDim.x) out[b] = hist[b];
 }
 
 }  // namespace cgf

@@ -103,6 +103,12 @@ cudaError_t Launch<T>::vec(const InstDesc<T>* d, int ninst, const VecArgs& a, in
 }
 
 template <typename T>
+cudaError_t Launch<T>::band_dot(const InstDesc<T>* d, int ninst, const DotArgs& a, cudaStream_t s) {
+  k_band_dot<T><<<dim3(kDotCtas, ninst), 256, 0, s>>>(d, a);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t Launch<T>::prepare() {
   cudaError_t e = cudaSuccess;
 #define CGF_PREP_ROW(LL) if (e == cudaSuccess) e = detail::prep_row<T, LL>();

@@ -7,9 +7,6 @@
 
 namespace cgf {
 
-struct RowArgs;
-struct ColArgs;
-struct VecArgs;
 
 template <typename T>
 struct Launch {
@@ -19,6 +16,7 @@ struct Launch {
   static cudaError_t col(int log_n, const InstDesc<T>* d, int ninst, const ColArgs& a,
                          const T* tw, cudaStream_t s);
   static cudaError_t vec(const InstDesc<T>* d, int ninst, const VecArgs& a, int nblk, cudaStream_t s);
+  static cudaError_t band_dot(const InstDesc<T>* d, int ninst, const DotArgs& a, cudaStream_t s);
   static size_t row_smem(int log_l, int rows);
   static size_t col_smem(int log_n, int ffts);
   static int max_threads();

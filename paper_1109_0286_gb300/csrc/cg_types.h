@@ -44,6 +44,7 @@ struct InstDesc {
   const T* t_inv;          // 1 / (n P)     [kx][ky]
   const T* t_sqrt;         // sqrt(P) / n   [kx][ky]
   T* spec;                 // interleaved complex half spectrum, transposed
+  T* spec2;                // second spectrum (gradient products), or null
   T* r;
   T* p;
   T* q;
@@ -52,11 +53,14 @@ struct InstDesc {
   T* y;
   T* b;
   const T* d;              // caller's data map
-  T* out;                  // caller's output map
+  T* out;                  // caller's output map (dL/dd in the backward pass)
+  const T* gx;             // caller's dL/dx (backward pass)
+  T* w;                    // w = d - y on U, u on M (backward pass)
   const float* dlt;        // FP32 correction (mixed refinement, FP64 passes)
   float* r32;              // FP32 residual target (mixed refinement, FP64 passes)
   CgState* st;
   double* partial;         // per-CTA partial sums
+  double* hist;            // residual history (hist_cap entries), or null
   unsigned long long seed;
 };
 
@@ -70,6 +74,8 @@ enum RowOp : int {
   OP_R_UPD = 5,     // r -= alpha q; u += alpha p; store; acc ||r||^2; v = r
   OP_U64_UPD = 6,   // u += (double) dlt; store; v = u  (mixed refinement)
   OP_LOAD_R_MASK = 7,  // v = P_x r
+  OP_LOAD_U = 8,    // v = u
+  OP_LOAD_Y = 9,    // v = y
   // middles (input spectrum -> output spectrum)
   OP_MASK = 10,     // v = P_x v
   OP_Y_W = 11,      // store y = v; v = (d - y) on U, 0 on M
@@ -79,6 +85,8 @@ enum RowOp : int {
   OP_Z = 22,        // z = P_x v; store; acc r^T z
   OP_B = 23,        // b = -P_x v; store r = b (and b); acc ||b||^2
   OP_RES = 24,      // r = b - P_x v; store; acc ||r||^2; r32 = (float) r
+  OP_GRAD = 25,     // v = C^-1 lam: out = (g - v) on U, 0 on M; y = h = g on M, v on U
+  OP_LOAD_W = 26,   // (source) v = w
 };
 
 // Scalar updates run by the last CTA of a reducing pass.
@@ -97,7 +105,9 @@ enum VecOp : int {
   VOP_UPDATE = 1,     // r -= alpha q; u += alpha p; acc ||r||^2
   VOP_ASSEMBLE = 2,   // out = d on U, y + u on M
   VOP_COPY_D = 3,     // out = d
-  VOP_TO_F32 = 4,     // r32 = (float) r64 on the FP64 desc; acc ||r32||^2
+  VOP_MAKE_W = 5,     // w = d - y on U, u on M
+  VOP_LOAD_G = 6,     // r = b = P_x g (r32 = (float) r if set); acc ||r||^2
+  VOP_ZERO_UP = 7,    // u = 0, p = 0
 };
 
 // Launch arguments of the pass kernels.
@@ -107,14 +117,25 @@ struct RowArgs {
   int op;           // RowOp
   int sop;          // ScalarOp (SC_NONE: no reduction)
   int check_done;   // skip instances whose CG state is done
+  int spec_sel;     // 0: spec, 1: spec2
 };
 
 struct ColArgs {
   int ny;           // column length (FFT size)
   int nkx;          // nx/2 + 1 spectrum rows
   int ffts;         // column FFTs per CTA
-  int table;        // 0: 1/(nP), 1: sqrt(P)/n
+  int table;        // 0: 1/(nP), 1: sqrt(P)/n; -1: forward transform only
   int check_done;
+  int spec_sel;     // 0: spec, 1: spec2
+};
+
+// Band-binned spectral products for the band-power gradient.
+struct DotArgs {
+  long long nmodes;     // (nx/2+1) * ny half-plane modes per instance
+  int nbands;
+  const int* band;      // [kx][ky] band of every mode
+  const void* coef;     // [kx][ky] weight (element type of the pass)
+  double* part;         // [inst][cta][nbands] partial sums
 };
 
 struct VecArgs {
@@ -126,5 +147,7 @@ struct VecArgs {
 
 constexpr int kLmax = 8192;        // twiddle master table: W_8192^m
 constexpr int kMaxPartials = 4096; // CTAs per instance per reducing pass
+constexpr int kMaxBands = 64;      // band-power gradient bins
+constexpr int kDotCtas = 256;      // CTAs per instance of the band-binned product
 
 }  // namespace cgf

@@ -70,6 +70,10 @@ struct Precision {
   // device buffers (instance-major slabs of batch * npix)
   T* r = nullptr; T* p = nullptr; T* q = nullptr; T* z = nullptr;
   T* u = nullptr; T* y = nullptr; T* b = nullptr; T* spec = nullptr;
+  T* w = nullptr; T* spec2 = nullptr;              // backward buffers
+  int* band = nullptr; T* coef1 = nullptr; T* coef2 = nullptr;
+  double* bpart = nullptr; double* bsum = nullptr; // band partials, sums
+  int nbands = 0;
   T* t_inv = nullptr; T* t_sqrt = nullptr; T* tw = nullptr;
   CgState* st = nullptr;        // device, batch
   CgState* hst = nullptr;       // pinned mirror
@@ -93,6 +97,7 @@ struct fill_plan {
   cudaStream_t s = nullptr;      // caller's stream
   cudaStream_t cap = nullptr;    // plan-owned stream for graph capture
   uint32_t* obs = nullptr;
+  std::vector<double> P_half;    // host copy of the spectrum
   long long launches = 0;        // kernels issued by the current call
   Precision<float> f;
   Precision<double> g;
@@ -130,11 +135,14 @@ struct fill_plan {
 namespace {
 
 // ----------------------------------------------------------------- schedules
+// Default row-pass CTA: at least 16 rows or 256 threads, at most 512 threads
+// (two CTAs per SM) unless that would leave fewer than 4 rows per CTA.
 template <typename T>
 int default_rows(int log_l, int ny) {
   const int TT = (1 << log_l) / 16;
   int rows = std::max(16, 256 / TT);
-  rows = std::min(rows, Launch<T>::max_threads() / TT);
+  const int cap = std::min(512, Launch<T>::max_threads());
+  rows = std::min(rows, std::max(cap / TT, std::min(4, Launch<T>::max_threads() / TT)));
   while (rows > 1 && Launch<T>::row_smem(log_l, rows) > 210 * 1024) rows /= 2;
   return std::min(rows, ny);
 }
@@ -149,7 +157,8 @@ int default_ffts(int log_n, int nkx) {
 }
 
 // ----------------------------------------------------------------- small kernels
-__global__ void k_state_init(CgState* st, int n, double tol2, int max_iter, double* hist,
+template <typename T>
+__global__ void k_state_init(const InstDesc<T>* desc, int n, double tol2, int max_iter,
                              int hist_cap) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -158,8 +167,26 @@ __global__ void k_state_init(CgState* st, int n, double tol2, int max_iter, doub
   s.max_iter = max_iter;
   s.first = 1;
   s.hist_cap = hist_cap;
-  s.hist = hist ? hist + size_t(i) * hist_cap : nullptr;
-  st[i] = s;
+  s.hist = desc[i].hist;
+  *desc[i].st = s;
+}
+
+// 1 in *flag iff every instance's CG state is done (one CTA).
+template <typename T>
+__global__ void k_all_done(const InstDesc<T>* desc, int n, int* flag) {
+  __shared__ int any_running;
+  if (threadIdx.x == 0) any_running = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    if (!*(volatile int*)&desc[i].st->done) any_running = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) *flag = any_running ? 0 : 1;
+}
+
+template <typename T>
+__global__ void k_gather_states(const InstDesc<T>* desc, int n, CgState* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = *desc[i].st;
 }
 
 // Prepares the FP32 inner solve of a refinement step: accumulate the finished
@@ -203,32 +230,61 @@ Precision<float>& prec<float>(fill_plan* p) { return p->f; }
 template <>
 Precision<double>& prec<double>(fill_plan* p) { return p->g; }
 
+// Launch context: one grid size, one descriptor array (a plan's instances or
+// a size class of a group).
+template <typename T>
+struct Ctx {
+  int ny, nx, log_l, log_n, rows, ffts, ninst, precond;
+  long long npix;
+  const InstDesc<T>* desc;
+  const T* tw;
+  long long* launches;
+};
+
+template <typename T>
+Ctx<T> ctx(fill_plan* p, int ninst = -1) {
+  Precision<T>& P = prec<T>(p);
+  return Ctx<T>{p->ny, p->nx, p->log_l, p->log_n, P.rows, P.ffts,
+                ninst < 0 ? p->batch : ninst, p->o.precond, p->npix, P.desc, P.tw, &p->launches};
+}
+
+template <typename T>
+cudaError_t row(const Ctx<T>& c, cudaStream_t s, int op, int sop, bool in_spec, bool out_spec,
+                bool check_done, int spec_sel = 0) {
+  ++*c.launches;
+  RowArgs a{c.ny, c.nx, c.rows, op, sop, check_done ? 1 : 0, spec_sel};
+  return Launch<T>::row(c.log_l, in_spec, out_spec, c.desc, c.ninst, a, c.tw, s);
+}
+
+template <typename T>
+cudaError_t col(const Ctx<T>& c, cudaStream_t s, int table, bool check_done, int spec_sel = 0) {
+  ++*c.launches;
+  ColArgs a{c.ny, c.nx / 2 + 1, c.ffts, table, check_done ? 1 : 0, spec_sel};
+  return Launch<T>::col(c.log_n, c.desc, c.ninst, a, c.tw, s);
+}
+
+template <typename T>
+cudaError_t vec(const Ctx<T>& c, cudaStream_t s, int op, int sop, bool check_done) {
+  ++*c.launches;
+  VecArgs a{c.npix, op, sop, check_done ? 1 : 0};
+  const long long pairs = c.npix / 2;
+  const int nblk = (int)std::min<long long>((pairs + 255) / 256, 1024);
+  return Launch<T>::vec(c.desc, c.ninst, a, nblk, s);
+}
+
 template <typename T>
 cudaError_t row(fill_plan* p, cudaStream_t s, int op, int sop, bool in_spec, bool out_spec,
-                bool check_done, int ninst = -1) {
-  Precision<T>& P = prec<T>(p);
-  ++p->launches;
-  RowArgs a{p->ny, p->nx, P.rows, op, sop, check_done ? 1 : 0};
-  return Launch<T>::row(p->log_l, in_spec, out_spec, P.desc, ninst < 0 ? p->batch : ninst, a,
-                        P.tw, s);
+                bool check_done, int ninst = -1, int spec_sel = 0) {
+  return row<T>(ctx<T>(p, ninst), s, op, sop, in_spec, out_spec, check_done, spec_sel);
 }
-
 template <typename T>
-cudaError_t col(fill_plan* p, cudaStream_t s, int table, bool check_done, int ninst = -1) {
-  Precision<T>& P = prec<T>(p);
-  ++p->launches;
-  ColArgs a{p->ny, p->nx / 2 + 1, P.ffts, table, check_done ? 1 : 0};
-  return Launch<T>::col(p->log_n, P.desc, ninst < 0 ? p->batch : ninst, a, P.tw, s);
+cudaError_t col(fill_plan* p, cudaStream_t s, int table, bool check_done, int ninst = -1,
+                int spec_sel = 0) {
+  return col<T>(ctx<T>(p, ninst), s, table, check_done, spec_sel);
 }
-
 template <typename T>
 cudaError_t vec(fill_plan* p, cudaStream_t s, int op, int sop, bool check_done) {
-  Precision<T>& P = prec<T>(p);
-  ++p->launches;
-  VecArgs a{p->npix, op, sop, check_done ? 1 : 0};
-  long long pairs = p->npix / 2;
-  int nblk = (int)std::min<long long>((pairs + 255) / 256, 1024);
-  return Launch<T>::vec(P.desc, p->batch, a, nblk, s);
+  return vec<T>(ctx<T>(p), s, op, sop, check_done);
 }
 
 #define CE(expr)                              \
@@ -240,48 +296,61 @@ cudaError_t vec(fill_plan* p, cudaStream_t s, int op, int sop, bool check_done) 
 // Unconstrained draw and right-hand side (Sects. 2.3, 2.1):
 //   y = F^-1 sqrt(P) F xi;  b = -P_x F^-1 (1/P) F [(d - y) on U].
 template <typename T>
-cudaError_t draw_and_rhs(fill_plan* p, cudaStream_t s, bool plain_cg) {
-  CE(row<T>(p, s, OP_XI, SC_NONE, false, true, false));
-  CE(col<T>(p, s, 1, false));
-  CE(row<T>(p, s, OP_Y_W, SC_NONE, true, true, false));
-  CE(col<T>(p, s, 0, false));
-  return row<T>(p, s, OP_B, plain_cg ? SC_BB_RHO : SC_BB, true, false, false);
+cudaError_t draw_and_rhs(const Ctx<T>& c, cudaStream_t s, bool plain_cg) {
+  CE(row<T>(c, s, OP_XI, SC_NONE, false, true, false));
+  CE(col<T>(c, s, 1, false));
+  CE(row<T>(c, s, OP_Y_W, SC_NONE, true, true, false));
+  CE(col<T>(c, s, 0, false));
+  return row<T>(c, s, OP_B, plain_cg ? SC_BB_RHO : SC_BB, true, false, false);
 }
 
 // First preconditioned residual z0 = S S r0 and rho0 = r0^T z0.
 template <typename T>
-cudaError_t pcg_start(fill_plan* p, cudaStream_t s, int load_sop) {
-  if (!p->o.precond) {
+cudaError_t pcg_start(const Ctx<T>& c, cudaStream_t s, int load_sop) {
+  if (!c.precond) {
     if (load_sop == SC_NONE) return cudaSuccess;
     // plain CG inner solve: rho = bb = ||r||^2, beta = 0
-    return row<T>(p, s, OP_LOAD_R, SC_BB_RHO, false, true, true);
+    return row<T>(c, s, OP_LOAD_R, SC_BB_RHO, false, true, true);
   }
-  CE(row<T>(p, s, OP_LOAD_R, load_sop, false, true, true));
-  CE(col<T>(p, s, 1, true));
-  CE(row<T>(p, s, OP_MASK, SC_NONE, true, true, true));
-  CE(col<T>(p, s, 1, true));
-  return row<T>(p, s, OP_Z, SC_BETA, true, false, true);
+  CE(row<T>(c, s, OP_LOAD_R, load_sop, false, true, true));
+  CE(col<T>(c, s, 1, true));
+  CE(row<T>(c, s, OP_MASK, SC_NONE, true, true, true));
+  CE(col<T>(c, s, 1, true));
+  return row<T>(c, s, OP_Z, SC_BETA, true, false, true);
 }
 
 // One CG iteration (Sect. 2.4).  Preconditioned form with B = S S:
 //   p = z + beta p; q = A p; alpha = rho / p^T q; u += alpha p; r -= alpha q;
 //   z = S S r; beta = r^T z / rho.
 template <typename T>
-cudaError_t pcg_iter(fill_plan* p, cudaStream_t s) {
-  if (p->o.precond) {
-    CE(row<T>(p, s, OP_P_UPD_Z, SC_NONE, false, true, true));
-    CE(col<T>(p, s, 0, true));
-    CE(row<T>(p, s, OP_Q, SC_ALPHA, true, false, true));
-    CE(row<T>(p, s, OP_R_UPD, SC_RCHECK, false, true, true));
-    CE(col<T>(p, s, 1, true));
-    CE(row<T>(p, s, OP_MASK, SC_NONE, true, true, true));
-    CE(col<T>(p, s, 1, true));
-    return row<T>(p, s, OP_Z, SC_BETA, true, false, true);
+cudaError_t pcg_iter(const Ctx<T>& c, cudaStream_t s) {
+  if (c.precond) {
+    CE(row<T>(c, s, OP_P_UPD_Z, SC_NONE, false, true, true));
+    CE(col<T>(c, s, 0, true));
+    CE(row<T>(c, s, OP_Q, SC_ALPHA, true, false, true));
+    CE(row<T>(c, s, OP_R_UPD, SC_RCHECK, false, true, true));
+    CE(col<T>(c, s, 1, true));
+    CE(row<T>(c, s, OP_MASK, SC_NONE, true, true, true));
+    CE(col<T>(c, s, 1, true));
+    return row<T>(c, s, OP_Z, SC_BETA, true, false, true);
   }
-  CE(row<T>(p, s, OP_P_UPD_R, SC_NONE, false, true, true));
-  CE(col<T>(p, s, 0, true));
-  CE(row<T>(p, s, OP_Q, SC_ALPHA, true, false, true));
-  return vec<T>(p, s, VOP_UPDATE, SC_RCHECK_BETA, true);
+  CE(row<T>(c, s, OP_P_UPD_R, SC_NONE, false, true, true));
+  CE(col<T>(c, s, 0, true));
+  CE(row<T>(c, s, OP_Q, SC_ALPHA, true, false, true));
+  return vec<T>(c, s, VOP_UPDATE, SC_RCHECK_BETA, true);
+}
+
+template <typename T>
+cudaError_t draw_and_rhs(fill_plan* p, cudaStream_t s, bool plain_cg) {
+  return draw_and_rhs<T>(ctx<T>(p), s, plain_cg);
+}
+template <typename T>
+cudaError_t pcg_start(fill_plan* p, cudaStream_t s, int load_sop) {
+  return pcg_start<T>(ctx<T>(p), s, load_sop);
+}
+template <typename T>
+cudaError_t pcg_iter(fill_plan* p, cudaStream_t s) {
+  return pcg_iter<T>(ctx<T>(p), s);
 }
 
 template <typename T>
@@ -332,15 +401,130 @@ fill_status run_pcg(fill_plan* p) {
   return FILL_OK;
 }
 
+// Mixed-precision solve of A u = b: b, r (FP64) and r32 are set and the FP64
+// state holds ||b||^2.  Each step runs an FP32 PCG on A delta = r32 to the
+// tolerance the outer target still needs, then u += delta and the true
+// residual r = b - A u in FP64 (iterative refinement).
+fill_status mixed_refine(fill_plan* p, double tol) {
+  const int B = p->batch;
+  const size_t n = p->npix;
+  const int nb = (B + 127) / 128;
+  for (int outer = 0; outer < p->o.max_refine; ++outer) {
+    ++p->launches;
+    k_inner_reset<<<nb, 128, 0, p->s>>>(p->f.st, p->g.st, B, tol, p->o.inner_tol, p->o.max_iter);
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(p->f.u, 0, B * n * sizeof(float), p->s));
+    CK(cudaMemsetAsync(p->f.p, 0, B * n * sizeof(float), p->s));
+    CK(pcg_start<float>(p, p->s, SC_BB));
+    fill_status fs = run_pcg<float>(p);
+    if (fs != FILL_OK) return fs;
+    CK(row<double>(p, p->s, OP_U64_UPD, SC_NONE, false, true, true));
+    CK(col<double>(p, p->s, 0, true));
+    CK(row<double>(p, p->s, OP_RES, SC_RES, true, false, true));
+    CK(cudaMemcpyAsync(p->g.hst, p->g.st, sizeof(CgState) * B, cudaMemcpyDeviceToHost, p->s));
+    CK(cudaStreamSynchronize(p->s));
+    bool all = true;
+    for (int i = 0; i < B; ++i) all = all && p->g.hst[i].done;
+    if (all) break;
+  }
+  ++p->launches;
+  k_inner_collect<<<nb, 128, 0, p->s>>>(p->f.st, p->g.st, B);
+  CK(cudaGetLastError());
+  return FILL_OK;
+}
+
+// Sums the band partials of every CTA in order: out[i][b] (+)= sum_c part[i][c][b].
+__global__ void k_band_sum(const double* part, int ninst, int nctas, int nbands, double* out,
+                           int accumulate) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ninst * nbands) return;
+  const int i = t / nbands, b = t % nbands;
+  double s = 0.0;
+  for (int c = 0; c < nctas; ++c) s += part[((long long)i * nctas + c) * nbands + b];
+  out[t] = accumulate ? out[t] + s : s;
+}
+
 template <typename T>
-void fill_desc(fill_plan* p, const void* d, long long d_stride, const uint64_t* seeds, void* out) {
+cudaError_t init_states(fill_plan* p, double tol);
+template <typename T>
+void fill_desc(fill_plan* p, const void* d, long long d_stride, const uint64_t* seeds, void* out,
+               const void* gx);
+template <typename T>
+cudaError_t upload_desc(fill_plan* p);
+
+template <typename T>
+cudaError_t band_term(fill_plan* p, int src1, int src2, const T* coef, bool accumulate) {
+  Precision<T>& P = prec<T>(p);
+  CE(row<T>(p, p->s, src1, SC_NONE, false, true, false, -1, 0));
+  CE(row<T>(p, p->s, src2, SC_NONE, false, true, false, -1, 1));
+  CE(col<T>(p, p->s, -1, false, -1, 0));
+  CE(col<T>(p, p->s, -1, false, -1, 1));
+  DotArgs a{(long long)(p->nx / 2 + 1) * p->ny, P.nbands, P.band, coef, P.bpart};
+  ++p->launches;
+  CE(Launch<T>::band_dot(P.desc, p->batch, a, p->s));
+  const int tot = p->batch * P.nbands;
+  ++p->launches;
+  k_band_sum<<<(tot + 127) / 128, 128, 0, p->s>>>(P.bpart, p->batch, kDotCtas, P.nbands, P.bsum,
+                                                 accumulate ? 1 : 0);
+  return cudaGetLastError();
+}
+
+// Adjoint gradients (differentiation of the realization; the paper is silent):
+// with g = dL/dx, lam = A^-1 g_M (same operator and preconditioner),
+// dL/dd = g_U - (C^-1 lam)_U on U (0 on M), h = dL/dy = g on M, (C^-1 lam)_U
+// on U, and for P = sum_b a_b T_b + N, T_b = 1[k in b] S(k):
+//   dL/da_b = sum_k T_b [ Re(conj(F h) F xi) / (2 n sqrt P) + Re(conj(F lam) F w) / (n P^2) ]
+// with w = d - y on U and u on M, xi the seed's white noise.
+template <typename T>
+fill_status backward_t(fill_plan* p, const void* d, long long d_stride, const void* gx,
+                       double tol, void* grad_d, double* grad_bands) {
+  Precision<T>& P = prec<T>(p);
+  const int B = p->batch;
+  const size_t n = p->npix;
+  fill_desc<T>(p, d, d_stride, nullptr, grad_d, gx);
+  CK(upload_desc<T>(p));
+  CK(vec<T>(p, p->s, VOP_MAKE_W, SC_NONE, false));
+  const bool mixed = p->o.mode == FILL_MODE_MIXED;
+  CK(init_states<T>(p, tol));
+  CK(cudaMemsetAsync(P.u, 0, B * n * sizeof(T), p->s));
+  if (mixed) {
+    fill_desc<float>(p, nullptr, 0, nullptr, nullptr, nullptr);
+    CK(upload_desc<float>(p));
+    CK(init_states<float>(p, p->o.inner_tol));
+    CK(vec<T>(p, p->s, VOP_LOAD_G, SC_BB, false));
+    fill_status fs = mixed_refine(p, tol);
+    if (fs != FILL_OK) return fs;
+  } else {
+    CK(cudaMemsetAsync(P.p, 0, B * n * sizeof(T), p->s));
+    CK(vec<T>(p, p->s, VOP_LOAD_G, p->o.precond ? SC_BB : SC_BB_RHO, false));
+    CK(pcg_start<T>(p, p->s, SC_NONE));
+    fill_status fs = run_pcg<T>(p);
+    if (fs != FILL_OK) return fs;
+  }
+  // lam is in u.  C^-1 lam -> dL/dd and h (into y).
+  CK(row<T>(p, p->s, OP_LOAD_U, SC_NONE, false, true, false));
+  CK(col<T>(p, p->s, 0, false));
+  CK(row<T>(p, p->s, OP_GRAD, SC_NONE, true, false, false));
+  if (grad_bands) {
+    CK(band_term<T>(p, OP_XI, OP_LOAD_Y, P.coef1, false));
+    CK(band_term<T>(p, OP_LOAD_U, OP_LOAD_W, P.coef2, true));
+    CK(cudaMemcpyAsync(grad_bands, P.bsum, sizeof(double) * B * P.nbands,
+                       cudaMemcpyDeviceToHost, p->s));
+  }
+  return FILL_OK;
+}
+
+template <typename T>
+void fill_desc(fill_plan* p, const void* d, long long d_stride, const uint64_t* seeds, void* out,
+               const void* gx) {
   Precision<T>& P = prec<T>(p);
   for (int i = 0; i < p->batch; ++i) {
     InstDesc<T>& D = P.hdesc[i];
     const size_t off = size_t(i) * p->npix;
     D.d = d ? reinterpret_cast<const T*>(d) + size_t(d_stride) * i : nullptr;
     D.out = out ? reinterpret_cast<T*>(out) + off : nullptr;
-    D.seed = seeds ? (unsigned long long)seeds[i] : 0ull;
+    D.gx = gx ? reinterpret_cast<const T*>(gx) + off : nullptr;
+    if (seeds) D.seed = (unsigned long long)seeds[i];
   }
 }
 
@@ -362,6 +546,10 @@ fill_status setup_precision(fill_plan* p, const std::vector<double>& tinv,
   for (T** v : vecs)
     if (p->dalloc(v, B * n) != cudaSuccess) return FILL_ENOMEM;
   if (p->dalloc(&P.spec, B * nspec) != cudaSuccess) return FILL_ENOMEM;
+  if (p->o.backward) {
+    if (p->dalloc(&P.w, B * n) != cudaSuccess || p->dalloc(&P.spec2, B * nspec) != cudaSuccess)
+      return FILL_ENOMEM;
+  }
   const size_t ntab = size_t(p->nx / 2 + 1) * p->ny;
   if (p->dalloc(&P.t_inv, ntab) != cudaSuccess || p->dalloc(&P.t_sqrt, ntab) != cudaSuccess ||
       p->dalloc(&P.tw, 2 * size_t(kLmax)) != cudaSuccess)
@@ -398,6 +586,8 @@ fill_status setup_precision(fill_plan* p, const std::vector<double>& tinv,
     D.t_inv = P.t_inv;
     D.t_sqrt = P.t_sqrt;
     D.spec = P.spec + i * nspec;
+    D.spec2 = P.spec2 ? P.spec2 + i * nspec : nullptr;
+    D.w = P.w ? P.w + i * n : nullptr;
     D.r = P.r + i * n;
     D.p = P.p + i * n;
     D.q = P.q + i * n;
@@ -407,6 +597,7 @@ fill_status setup_precision(fill_plan* p, const std::vector<double>& tinv,
     D.b = P.b + i * n;
     D.st = P.st + i;
     D.partial = P.partial + i * kMaxPartials;
+    D.hist = P.hist + i * hc;
     P.hdesc[i] = D;
   }
   return FILL_OK;
@@ -417,8 +608,8 @@ cudaError_t init_states(fill_plan* p, double tol) {
   Precision<T>& P = prec<T>(p);
   const int hc = std::max(p->o.history_cap, 1);
   ++p->launches;
-  k_state_init<<<(p->batch + 127) / 128, 128, 0, p->s>>>(P.st, p->batch, tol * tol,
-                                                        p->o.max_iter, P.hist, hc);
+  k_state_init<T><<<(p->batch + 127) / 128, 128, 0, p->s>>>(P.desc, p->batch, tol * tol,
+                                                           p->o.max_iter, hc);
   return cudaGetLastError();
 }
 
@@ -478,7 +669,7 @@ fill_status fill_init(fill_plan** out, int ny, int nx, const double* P_half,
     fill_opts_default(&o);
   if (o.mode < 0 || o.mode > 2 || o.batch < 1 || o.batch > 65535 || o.max_iter < 1 ||
       o.max_refine < 1 || !(o.inner_tol > 0.0) || o.history_cap < 0 || o.rows_per_cta < 0 ||
-      o.ffts_per_cta < 0)
+      o.ffts_per_cta < 0 || o.backward < 0 || o.backward > 1)
     return FILL_EINVAL;
   const int nkx = nx / 2 + 1;
   // P: finite, positive, real-symmetric on the self-conjugate columns.
@@ -510,6 +701,7 @@ fill_status fill_init(fill_plan** out, int ny, int nx, const double* P_half,
   p->nmasked = nmasked;
   p->o = o;
   p->s = reinterpret_cast<cudaStream_t>(stream);
+  p->P_half.assign(P_half, P_half + (size_t)ny * nkx);
   fill_status fs = FILL_OK;
   auto fail = [&](fill_status st) {
     delete p;
@@ -572,7 +764,7 @@ fill_status fill_realize(fill_plan* p, const void* d, long long d_stride, const 
   if (p->o.mode == FILL_MODE_FP32 || p->o.mode == FILL_MODE_FP64) {
     const bool f32 = p->o.mode == FILL_MODE_FP32;
     if (f32) {
-      fill_desc<float>(p, d, d_stride, seeds, out);
+      fill_desc<float>(p, d, d_stride, seeds, out, nullptr);
       CK(upload_desc<float>(p));
       CK(init_states<float>(p, tol));
       CK(cudaMemsetAsync(p->f.u, 0, B * n * sizeof(float), p->s));
@@ -584,7 +776,7 @@ fill_status fill_realize(fill_plan* p, const void* d, long long d_stride, const 
       CK(vec<float>(p, p->s, VOP_ASSEMBLE, SC_NONE, false));
       CK(cudaMemcpyAsync(p->f.hst, p->f.st, sizeof(CgState) * B, cudaMemcpyDeviceToHost, p->s));
     } else {
-      fill_desc<double>(p, d, d_stride, seeds, out);
+      fill_desc<double>(p, d, d_stride, seeds, out, nullptr);
       CK(upload_desc<double>(p));
       CK(init_states<double>(p, tol));
       CK(cudaMemsetAsync(p->g.u, 0, B * n * sizeof(double), p->s));
@@ -598,37 +790,16 @@ fill_status fill_realize(fill_plan* p, const void* d, long long d_stride, const 
     }
   } else {
     // Mixed: FP64 draw / RHS / residual, FP32 inner PCG, FP64 refinement.
-    fill_desc<double>(p, d, d_stride, seeds, out);
-    fill_desc<float>(p, nullptr, 0, seeds, nullptr);
+    fill_desc<double>(p, d, d_stride, seeds, out, nullptr);
+    fill_desc<float>(p, nullptr, 0, seeds, nullptr, nullptr);
     CK(upload_desc<double>(p));
     CK(upload_desc<float>(p));
     CK(init_states<double>(p, tol));
     CK(init_states<float>(p, p->o.inner_tol));
     CK(cudaMemsetAsync(p->g.u, 0, B * n * sizeof(double), p->s));
     CK(draw_and_rhs<double>(p, p->s, false));
-    const int nb = (B + 127) / 128;
-    for (int outer = 0; outer < p->o.max_refine; ++outer) {
-      ++p->launches;
-      k_inner_reset<<<nb, 128, 0, p->s>>>(p->f.st, p->g.st, B, tol, p->o.inner_tol, p->o.max_iter);
-      CK(cudaGetLastError());
-      CK(cudaMemsetAsync(p->f.u, 0, B * n * sizeof(float), p->s));
-      CK(cudaMemsetAsync(p->f.p, 0, B * n * sizeof(float), p->s));
-      CK(pcg_start<float>(p, p->s, SC_BB));
-      fs = run_pcg<float>(p);
-      if (fs != FILL_OK) return fs;
-      // u += delta (FP64), r = b - A u (FP64 true residual), r32 = (float) r
-      CK(row<double>(p, p->s, OP_U64_UPD, SC_NONE, false, true, true));
-      CK(col<double>(p, p->s, 0, true));
-      CK(row<double>(p, p->s, OP_RES, SC_RES, true, false, true));
-      CK(cudaMemcpyAsync(p->g.hst, p->g.st, sizeof(CgState) * B, cudaMemcpyDeviceToHost, p->s));
-      CK(cudaStreamSynchronize(p->s));
-      bool all = true;
-      for (int i = 0; i < B; ++i) all = all && p->g.hst[i].done;
-      if (all) break;
-    }
-    ++p->launches;
-    k_inner_collect<<<nb, 128, 0, p->s>>>(p->f.st, p->g.st, B);
-    CK(cudaGetLastError());
+    fs = mixed_refine(p, tol);
+    if (fs != FILL_OK) return fs;
     CK(vec<double>(p, p->s, VOP_ASSEMBLE, SC_NONE, false));
     CK(cudaMemcpyAsync(p->g.hst, p->g.st, sizeof(CgState) * B, cudaMemcpyDeviceToHost, p->s));
     CK(cudaMemcpyAsync(p->f.hst, p->f.st, sizeof(CgState) * B, cudaMemcpyDeviceToHost, p->s));
@@ -643,7 +814,7 @@ fill_status fill_draw(fill_plan* p, const uint64_t* seeds, void* out) {
   if (!p || !seeds || !out) return FILL_EINVAL;
   const size_t n = p->npix;
   if (p->o.mode == FILL_MODE_FP32) {
-    fill_desc<float>(p, nullptr, 0, seeds, nullptr);
+    fill_desc<float>(p, nullptr, 0, seeds, nullptr, nullptr);
     CK(upload_desc<float>(p));
     CK(init_states<float>(p, 0.0));
     CK(row<float>(p, p->s, OP_XI, SC_NONE, false, true, false));
@@ -651,7 +822,7 @@ fill_status fill_draw(fill_plan* p, const uint64_t* seeds, void* out) {
     CK(row<float>(p, p->s, OP_STORE_Y, SC_NONE, true, false, false));
     CK(cudaMemcpyAsync(out, p->f.y, p->batch * n * sizeof(float), cudaMemcpyDeviceToDevice, p->s));
   } else {
-    fill_desc<double>(p, nullptr, 0, seeds, nullptr);
+    fill_desc<double>(p, nullptr, 0, seeds, nullptr, nullptr);
     CK(upload_desc<double>(p));
     CK(init_states<double>(p, 0.0));
     CK(row<double>(p, p->s, OP_XI, SC_NONE, false, true, false));
@@ -670,7 +841,7 @@ template <typename T>
 fill_status apply_t(fill_plan* p, int which, const void* in, void* out) {
   Precision<T>& P = prec<T>(p);
   const size_t n = p->npix;
-  fill_desc<T>(p, nullptr, 0, nullptr, nullptr);
+  fill_desc<T>(p, nullptr, 0, nullptr, nullptr, nullptr);
   CK(upload_desc<T>(p));
   CK(init_states<T>(p, 0.0));
   CK(cudaMemcpyAsync(P.r, in, n * sizeof(T), cudaMemcpyDeviceToDevice, p->s));
@@ -721,7 +892,7 @@ template <typename T>
 fill_status time_pass_t(fill_plan* p, int pass, int reps, double* ms, double* bytes) {
   Precision<T>& P = prec<T>(p);
   if (!P.used) return FILL_EINVAL;
-  fill_desc<T>(p, nullptr, 0, nullptr, nullptr);
+  fill_desc<T>(p, nullptr, 0, nullptr, nullptr, nullptr);
   CK(upload_desc<T>(p));
   CK(init_states<T>(p, 0.0));
   const double n = double(p->npix), S = double(p->nx / 2 + 1) * p->ny, t = sizeof(T);
@@ -771,6 +942,81 @@ fill_status fill_time_pass(fill_plan* p, int pass, int precision, int reps, doub
                         : time_pass_t<double>(p, pass, reps, ms, bytes);
 }
 
+}  // extern "C"
+
+namespace {
+template <typename T>
+fill_status set_bands_t(fill_plan* p, int nbands, const int32_t* band_of_k, const double* sig) {
+  Precision<T>& P = prec<T>(p);
+  if (!P.used) return FILL_OK;
+  const int nkx = p->nx / 2 + 1, ny = p->ny;
+  const size_t nt = (size_t)nkx * ny;
+  const double n = double(p->npix);
+  std::vector<int> band(nt);
+  std::vector<T> c1(nt), c2(nt);
+  for (int ky = 0; ky < ny; ++ky)
+    for (int kx = 0; kx < nkx; ++kx) {
+      const size_t h = (size_t)ky * nkx + kx, t = (size_t)kx * ny + ky;
+      const double P_ = p->P_half[h], S = sig[h];
+      const double wt = (kx == 0 || kx == p->nx / 2) ? 1.0 : 2.0;
+      band[t] = band_of_k[h];
+      c1[t] = (T)(wt * S / (2.0 * n * std::sqrt(P_)));
+      c2[t] = (T)(wt * S / (n * P_ * P_));
+    }
+  if (!P.band) {
+    if (p->dalloc(&P.band, nt) != cudaSuccess || p->dalloc(&P.coef1, nt) != cudaSuccess ||
+        p->dalloc(&P.coef2, nt) != cudaSuccess ||
+        p->dalloc(&P.bpart, (size_t)p->batch * kDotCtas * kMaxBands) != cudaSuccess ||
+        p->dalloc(&P.bsum, (size_t)p->batch * kMaxBands) != cudaSuccess)
+      return FILL_ENOMEM;
+  }
+  CK(cudaMemcpy(P.band, band.data(), nt * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(P.coef1, c1.data(), nt * sizeof(T), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(P.coef2, c2.data(), nt * sizeof(T), cudaMemcpyHostToDevice));
+  P.nbands = nbands;
+  return FILL_OK;
+}
+}  // namespace
+
+extern "C" {
+
+fill_status fill_set_bands(fill_plan* p, int nbands, const int32_t* band_of_k,
+                           const double* sig_half) {
+  if (!p || !band_of_k || !sig_half || nbands < 1 || nbands > kMaxBands) return FILL_EINVAL;
+  const size_t nh = (size_t)p->ny * (p->nx / 2 + 1);
+  for (size_t i = 0; i < nh; ++i)
+    if (band_of_k[i] < 0 || band_of_k[i] >= nbands || !std::isfinite(sig_half[i])) return FILL_EINVAL;
+  fill_status fs = set_bands_t<float>(p, nbands, band_of_k, sig_half);
+  if (fs == FILL_OK) fs = set_bands_t<double>(p, nbands, band_of_k, sig_half);
+  return fs;
+}
+
+fill_status fill_backward(fill_plan* p, const void* d, long long d_stride, const void* grad_x,
+                          double tol, void* grad_d, double* grad_bands, fill_stats* stats) {
+  if (!p || !d || !grad_x || !grad_d || !(tol >= 0.0) || d_stride < 0) return FILL_EINVAL;
+  if (!p->o.backward) return FILL_EINVAL;
+  const bool f32 = p->o.mode == FILL_MODE_FP32;
+  if (grad_bands && (f32 ? p->f.nbands : p->g.nbands) == 0) return FILL_EINVAL;
+  const auto t0 = std::chrono::steady_clock::now();
+  p->launches = 0;
+  fill_status fs = f32 ? backward_t<float>(p, d, d_stride, grad_x, tol, grad_d, grad_bands)
+                       : backward_t<double>(p, d, d_stride, grad_x, tol, grad_d, grad_bands);
+  if (fs != FILL_OK) return fs;
+  if (p->o.mode == FILL_MODE_MIXED) {
+    CK(cudaMemcpyAsync(p->g.hst, p->g.st, sizeof(CgState) * p->batch, cudaMemcpyDeviceToHost, p->s));
+    CK(cudaMemcpyAsync(p->f.hst, p->f.st, sizeof(CgState) * p->batch, cudaMemcpyDeviceToHost, p->s));
+  } else if (f32) {
+    CK(cudaMemcpyAsync(p->f.hst, p->f.st, sizeof(CgState) * p->batch, cudaMemcpyDeviceToHost, p->s));
+  } else {
+    CK(cudaMemcpyAsync(p->g.hst, p->g.st, sizeof(CgState) * p->batch, cudaMemcpyDeviceToHost, p->s));
+  }
+  CK(cudaStreamSynchronize(p->s));
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  fill_status worst = FILL_OK;
+  collect_stats(p, stats, ms, &worst);
+  return worst;
+}
+
 long long fill_masked_count(const fill_plan* p) { return p ? p->nmasked : -1; }
 
 void fill_destroy(fill_plan* p) {
@@ -795,5 +1041,438 @@ const char* fill_strerror(fill_status s) {
 const char* fill_last_error(void) { return g_last_error.c_str(); }
 
 int fill_version(void) { return CGFILL_VERSION; }
+
+}  // extern "C"
+
+// =================================================================== tuning
+namespace {
+
+// Times `reps` launches of f(stream) with CUDA events (after one warm-up).
+template <typename F>
+cudaError_t time_launches(cudaStream_t s, int reps, F f, float* ms) {
+  cudaEvent_t e0, e1;
+  CE(cudaEventCreate(&e0));
+  CE(cudaEventCreate(&e1));
+  cudaError_t e = f(s);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+  for (int i = 0; i < reps && e == cudaSuccess; ++i) e = f(s);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return e;
+}
+
+// The row and column passes of one preconditioned iteration, without scalar
+// updates or done checks (schedule timing only; vector contents are scratch).
+template <typename T>
+cudaError_t tune_rows_once(const Ctx<T>& c, cudaStream_t s) {
+  CE(row<T>(c, s, OP_P_UPD_Z, SC_NONE, false, true, false));
+  CE(row<T>(c, s, OP_Q, SC_NONE, true, false, false));
+  CE(row<T>(c, s, OP_R_UPD, SC_NONE, false, true, false));
+  CE(row<T>(c, s, OP_MASK, SC_NONE, true, true, false));
+  return row<T>(c, s, OP_Z, SC_NONE, true, false, false);
+}
+
+// Chooses rows per CTA (row passes) and FFTs per CTA (column pass) for a
+// launch context by timing every valid candidate.
+template <typename T>
+cudaError_t autotune_ctx(Ctx<T> c, cudaStream_t s, int* best_rows, int* best_ffts) {
+  int optin = 0, dev = 0;
+  CE(cudaGetDevice(&dev));
+  CE(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const size_t limit = size_t(optin) - 1024;
+  const int TT = (1 << c.log_l) / 16, TN = (1 << c.log_n) / 16, nkx = c.nx / 2 + 1;
+  float best = 1e30f;
+  for (int r = 1; r <= c.ny && r <= 256; r *= 2) {
+    if (r * TT > Launch<T>::max_threads() || r * TT < 32 || c.ny / r > kMaxPartials ||
+        Launch<T>::row_smem(c.log_l, r) > limit)
+      continue;
+    c.rows = r;
+    float ms = 0.f;
+    CE(time_launches(s, 3, [&](cudaStream_t st) { return tune_rows_once<T>(c, st); }, &ms));
+    if (ms < best) {
+      best = ms;
+      *best_rows = r;
+    }
+  }
+  best = 1e30f;
+  for (int f = 1; f <= nkx && f <= 64; f *= 2) {
+    if (f * TN > Launch<T>::max_threads() || Launch<T>::col_smem(c.log_n, f) > limit) continue;
+    c.ffts = f;
+    float ms = 0.f;
+    CE(time_launches(s, 3, [&](cudaStream_t st) { return col<T>(c, st, 0, false); }, &ms));
+    if (ms < best) {
+      best = ms;
+      *best_ffts = f;
+    }
+  }
+  return cudaSuccess;
+}
+
+// Autotune cache: lines "prec ny nx ninst rows ffts".
+bool cache_lookup(const char* path, int prec, int ny, int nx, int ninst, int* rows, int* ffts) {
+  if (!path) return false;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  int a, b, c, d, r, q;
+  bool found = false;
+  while (std::fscanf(f, "%d %d %d %d %d %d", &a, &b, &c, &d, &r, &q) == 6)
+    if (a == prec && b == ny && c == nx && d == ninst) {
+      *rows = r;
+      *ffts = q;
+      found = true;
+    }
+  std::fclose(f);
+  return found;
+}
+
+void cache_store(const char* path, int prec, int ny, int nx, int ninst, int rows, int ffts) {
+  if (!path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%d %d %d %d %d %d\n", prec, ny, nx, ninst, rows, ffts);
+  std::fclose(f);
+}
+
+template <typename T>
+fill_status tune_plan_t(fill_plan* p, const char* path) {
+  Precision<T>& P = prec<T>(p);
+  if (!P.used) return FILL_OK;
+  const int pr = sizeof(T) == 4 ? 0 : 1;
+  int rows = P.rows, ffts = P.ffts;
+  if (!cache_lookup(path, pr, p->ny, p->nx, p->batch, &rows, &ffts)) {
+    fill_desc<T>(p, nullptr, 0, nullptr, nullptr, nullptr);
+    CK(upload_desc<T>(p));
+    CK(init_states<T>(p, 0.0));
+    CK(autotune_ctx<T>(ctx<T>(p), p->s, &rows, &ffts));
+    cache_store(path, pr, p->ny, p->nx, p->batch, rows, ffts);
+  }
+  if (rows != P.rows || ffts != P.ffts) {
+    P.rows = rows;
+    P.ffts = ffts;
+    if (P.iter_graph) {
+      cudaGraphExecDestroy(P.iter_graph);
+      P.iter_graph = nullptr;
+    }
+  }
+  return FILL_OK;
+}
+
+}  // namespace
+
+// =================================================================== groups
+namespace {
+
+struct GroupClass {
+  int ny = 0, nx = 0, log_l = 0, log_n = 0, rows = 0, ffts = 0, ninst = 0;
+  long long npix = 0;
+  std::vector<int> plans;       // group indices of the plans in this class
+  void* desc = nullptr;         // device InstDesc<T>[ninst]
+  void* hdesc = nullptr;        // pinned mirror
+  CgState* st = nullptr;        // device gather buffer
+  CgState* hst = nullptr;       // pinned
+  cudaStream_t cs = nullptr;    // class stream
+  cudaEvent_t join = nullptr;
+};
+
+}  // namespace
+
+struct fill_group {
+  std::vector<fill_plan*> plans;
+  std::vector<int> first;       // first flat instance of each plan
+  std::vector<GroupClass> cls;
+  int mode = 1, precond = 1, max_iter = 10000, ntot = 0;
+  cudaStream_t s = nullptr, cap = nullptr;
+  cudaEvent_t fork = nullptr, fork_cap = nullptr;
+  int* flags = nullptr;         // device, one per class
+  int* hflags = nullptr;        // pinned
+  cudaGraphExec_t graph = nullptr;
+  long long graph_kernels = 0, launches = 0;
+  std::vector<void*> dev, host;
+  ~fill_group() {
+    if (graph) cudaGraphExecDestroy(graph);
+    for (auto& c : cls) {
+      if (c.cs) cudaStreamDestroy(c.cs);
+      if (c.join) cudaEventDestroy(c.join);
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (fork_cap) cudaEventDestroy(fork_cap);
+    if (cap) cudaStreamDestroy(cap);
+    for (void* v : dev) cudaFree(v);
+    for (void* v : host) cudaFreeHost(v);
+  }
+};
+
+namespace {
+
+template <typename T>
+Ctx<T> gctx(fill_group* g, GroupClass& c) {
+  fill_plan* p0 = g->plans[c.plans[0]];
+  return Ctx<T>{c.ny, c.nx, c.log_l, c.log_n, c.rows, c.ffts, c.ninst, g->precond, c.npix,
+                reinterpret_cast<const InstDesc<T>*>(c.desc), prec<T>(p0).tw, &g->launches};
+}
+
+template <typename T>
+fill_status group_setup(fill_group* g, int autotune, const char* path) {
+  for (auto& c : g->cls) {
+    const size_t nb = sizeof(InstDesc<T>) * c.ninst;
+    if (cudaMalloc(&c.desc, nb) != cudaSuccess) return FILL_ENOMEM;
+    g->dev.push_back(c.desc);
+    if (cudaMallocHost(&c.hdesc, nb) != cudaSuccess) return FILL_ENOMEM;
+    g->host.push_back(c.hdesc);
+    InstDesc<T>* h = reinterpret_cast<InstDesc<T>*>(c.hdesc);
+    int k = 0;
+    for (int pi : c.plans) {
+      fill_plan* p = g->plans[pi];
+      for (int i = 0; i < p->batch; ++i) h[k++] = prec<T>(p).hdesc[i];
+    }
+    fill_plan* p0 = g->plans[c.plans[0]];
+    c.rows = prec<T>(p0).rows;
+    c.ffts = prec<T>(p0).ffts;
+    CK(cudaMemcpy(c.desc, c.hdesc, nb, cudaMemcpyHostToDevice));
+    if (autotune) {
+      const int pr = sizeof(T) == 4 ? 0 : 1;
+      if (!cache_lookup(path, pr, c.ny, c.nx, c.ninst, &c.rows, &c.ffts)) {
+        Ctx<T> cx_ = gctx<T>(g, c);
+        k_state_init<T><<<(c.ninst + 127) / 128, 128, 0, g->s>>>(
+            reinterpret_cast<const InstDesc<T>*>(c.desc), c.ninst, 0.0, 1, 1);
+        CK(cudaGetLastError());
+        CK(autotune_ctx<T>(cx_, g->s, &c.rows, &c.ffts));
+        cache_store(path, pr, c.ny, c.nx, c.ninst, c.rows, c.ffts);
+      }
+    }
+  }
+  return FILL_OK;
+}
+
+template <typename T>
+fill_status group_build_graph(fill_group* g, int chunk) {
+  if (g->graph) return FILL_OK;
+  cudaGraph_t graph = nullptr;
+  const long long before = g->launches;
+  CK(cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaEventRecord(g->fork_cap, g->cap);
+  for (auto& c : g->cls) {
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c.cs, g->fork_cap, 0);
+    Ctx<T> cx_ = gctx<T>(g, c);
+    for (int k = 0; k < chunk && e == cudaSuccess; ++k) e = pcg_iter<T>(cx_, c.cs);
+    if (e == cudaSuccess) e = cudaEventRecord(c.join, c.cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(g->cap, c.join, 0);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(g->cap, &graph);
+  g->graph_kernels = g->launches - before;
+  g->launches = before;
+  if (e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(e, "capture group iteration");
+  }
+  CK(e2);
+  e = cudaGraphInstantiate(&g->graph, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  return FILL_OK;
+}
+
+// Starts every class on its own stream after `s` reaches this point, and
+// makes `s` wait for all of them at the end of the enclosed work.
+template <typename T, typename F>
+fill_status group_fork_join(fill_group* g, F body) {
+  CK(cudaEventRecord(g->fork, g->s));
+  for (auto& c : g->cls) {
+    CK(cudaStreamWaitEvent(c.cs, g->fork, 0));
+    CK(body(c));
+    CK(cudaEventRecord(c.join, c.cs));
+    CK(cudaStreamWaitEvent(g->s, c.join, 0));
+  }
+  return FILL_OK;
+}
+
+template <typename T>
+fill_status group_realize_t(fill_group* g, const void* const* d, const uint64_t* seeds,
+                            double tol, void* const* out, fill_stats* stats) {
+  // per-call descriptor fields
+  for (auto& c : g->cls) {
+    InstDesc<T>* h = reinterpret_cast<InstDesc<T>*>(c.hdesc);
+    int k = 0;
+    for (int pi : c.plans) {
+      fill_plan* p = g->plans[pi];
+      for (int i = 0; i < p->batch; ++i, ++k) {
+        h[k].d = reinterpret_cast<const T*>(d[pi]);
+        h[k].out = reinterpret_cast<T*>(out[pi]) + size_t(i) * p->npix;
+        h[k].seed = (unsigned long long)seeds[g->first[pi] + i];
+      }
+    }
+    CK(cudaMemcpyAsync(c.desc, c.hdesc, sizeof(InstDesc<T>) * c.ninst, cudaMemcpyHostToDevice, g->s));
+  }
+  const int hc = 1;
+  fill_status fs = group_fork_join<T>(g, [&](GroupClass& c) -> cudaError_t {
+    Ctx<T> cx_ = gctx<T>(g, c);
+    ++g->launches;
+    k_state_init<T><<<(c.ninst + 127) / 128, 128, 0, c.cs>>>(cx_.desc, c.ninst, tol * tol,
+                                                            g->max_iter, hc);
+    CE(cudaGetLastError());
+    CE(vec<T>(cx_, c.cs, VOP_ZERO_UP, SC_NONE, false));
+    CE(draw_and_rhs<T>(cx_, c.cs, !g->precond));
+    return pcg_start<T>(cx_, c.cs, SC_NONE);
+  });
+  if (fs != FILL_OK) return fs;
+  const int chunk = 8;
+  fs = group_build_graph<T>(g, chunk);
+  if (fs != FILL_OK) return fs;
+  const int limit = g->max_iter / chunk + 2;
+  for (int it = 0; it <= limit; ++it) {
+    for (size_t ci = 0; ci < g->cls.size(); ++ci) {
+      ++g->launches;
+      k_all_done<T><<<1, 256, 0, g->s>>>(reinterpret_cast<const InstDesc<T>*>(g->cls[ci].desc),
+                                         g->cls[ci].ninst, g->flags + ci);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(g->hflags, g->flags, sizeof(int) * g->cls.size(), cudaMemcpyDeviceToHost, g->s));
+    CK(cudaStreamSynchronize(g->s));
+    bool all = true;
+    for (size_t ci = 0; ci < g->cls.size(); ++ci) all = all && g->hflags[ci];
+    if (all) break;
+    CK(cudaGraphLaunch(g->graph, g->s));
+    g->launches += g->graph_kernels;
+  }
+  fs = group_fork_join<T>(g, [&](GroupClass& c) -> cudaError_t {
+    Ctx<T> cx_ = gctx<T>(g, c);
+    CE(vec<T>(cx_, c.cs, VOP_ASSEMBLE, SC_NONE, false));
+    ++g->launches;
+    k_gather_states<T><<<(c.ninst + 127) / 128, 128, 0, c.cs>>>(cx_.desc, c.ninst, c.st);
+    CE(cudaGetLastError());
+    return cudaMemcpyAsync(c.hst, c.st, sizeof(CgState) * c.ninst, cudaMemcpyDeviceToHost, c.cs);
+  });
+  if (fs != FILL_OK) return fs;
+  CK(cudaStreamSynchronize(g->s));
+  if (stats) {
+    for (auto& c : g->cls) {
+      int k = 0;
+      for (int pi : c.plans) {
+        fill_plan* p = g->plans[pi];
+        for (int i = 0; i < p->batch; ++i, ++k) {
+          const CgState& a = c.hst[k];
+          fill_stats st{};
+          st.iters = a.iter;
+          st.status = a.status;
+          st.rel_resid = a.bb > 0 ? std::sqrt(a.rr / a.bb) : 0.0;
+          st.true_rel_resid = -1.0;
+          stats[g->first[pi] + i] = st;
+        }
+      }
+    }
+  }
+  return FILL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fill_status fill_autotune(fill_plan* p, const char* cache_path) {
+  if (!p) return FILL_EINVAL;
+  fill_status fs = tune_plan_t<float>(p, cache_path);
+  if (fs == FILL_OK) fs = tune_plan_t<double>(p, cache_path);
+  if (fs == FILL_OK) CK(cudaStreamSynchronize(p->s));
+  return fs;
+}
+
+fill_status fill_group_init(fill_group** out, fill_plan* const* plans, int count, int autotune,
+                            const char* cache_path) {
+  if (!out || !plans || count < 1) return FILL_EINVAL;
+  *out = nullptr;
+  const int mode = plans[0] ? plans[0]->o.mode : -1;
+  if (mode != FILL_MODE_FP32 && mode != FILL_MODE_FP64) return FILL_EINVAL;
+  fill_group* g = new (std::nothrow) fill_group();
+  if (!g) return FILL_ENOMEM;
+  auto fail = [&](fill_status st) {
+    delete g;
+    return st;
+  };
+  g->mode = mode;
+  g->precond = plans[0]->o.precond;
+  g->max_iter = plans[0]->o.max_iter;
+  g->s = plans[0]->s;
+  int flat = 0;
+  for (int i = 0; i < count; ++i) {
+    fill_plan* p = plans[i];
+    if (!p || p->o.mode != mode || p->o.precond != g->precond || p->s != g->s)
+      return fail(FILL_EINVAL);
+    g->plans.push_back(p);
+    g->first.push_back(flat);
+    flat += p->batch;
+    g->max_iter = std::max(g->max_iter, p->o.max_iter);
+    size_t ci = 0;
+    for (; ci < g->cls.size(); ++ci)
+      if (g->cls[ci].ny == p->ny && g->cls[ci].nx == p->nx) break;
+    if (ci == g->cls.size()) {
+      GroupClass c;
+      c.ny = p->ny;
+      c.nx = p->nx;
+      c.log_l = p->log_l;
+      c.log_n = p->log_n;
+      c.npix = p->npix;
+      g->cls.push_back(c);
+    }
+    g->cls[ci].plans.push_back(i);
+    g->cls[ci].ninst += p->batch;
+  }
+  g->ntot = flat;
+  cudaError_t e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->fork_cap, cudaEventDisableTiming);
+  for (auto& c : g->cls) {
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c.cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&c.st, sizeof(CgState) * c.ninst);
+    if (e == cudaSuccess) g->dev.push_back(c.st);
+    if (e == cudaSuccess) e = cudaMallocHost(&c.hst, sizeof(CgState) * c.ninst);
+    if (e == cudaSuccess) g->host.push_back(c.hst);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&g->flags, sizeof(int) * g->cls.size());
+  if (e == cudaSuccess) g->dev.push_back(g->flags);
+  if (e == cudaSuccess) e = cudaMallocHost(&g->hflags, sizeof(int) * g->cls.size());
+  if (e == cudaSuccess) g->host.push_back(g->hflags);
+  if (e != cudaSuccess) return fail(cuda_fail(e, "fill_group_init"));
+  fill_status fs = mode == FILL_MODE_FP32 ? group_setup<float>(g, autotune, cache_path)
+                                          : group_setup<double>(g, autotune, cache_path);
+  if (fs != FILL_OK) return fail(fs);
+  e = cudaStreamSynchronize(g->s);
+  if (e != cudaSuccess) return fail(cuda_fail(e, "fill_group_init"));
+  *out = g;
+  return FILL_OK;
+}
+
+fill_status fill_group_realize(fill_group* g, const void* const* d, const uint64_t* seeds,
+                               double tol, void* const* out, fill_stats* stats) {
+  if (!g || !d || !seeds || !out || !(tol >= 0.0)) return FILL_EINVAL;
+  for (size_t i = 0; i < g->plans.size(); ++i)
+    if (!d[i] || !out[i]) return FILL_EINVAL;
+  const auto t0 = std::chrono::steady_clock::now();
+  g->launches = 0;
+  fill_status fs = g->mode == FILL_MODE_FP32
+                       ? group_realize_t<float>(g, d, seeds, tol, out, stats)
+                       : group_realize_t<double>(g, d, seeds, tol, out, stats);
+  if (fs != FILL_OK) return fs;
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  fill_status worst = FILL_OK;
+  if (stats)
+    for (int i = 0; i < g->ntot; ++i) {
+      stats[i].ms = ms;
+      stats[i].launches = (int)g->launches;
+      if (stats[i].status > worst) worst = (fill_status)stats[i].status;
+    }
+  return worst;
+}
+
+int fill_group_size(const fill_group* g) { return g ? g->ntot : -1; }
+
+void fill_group_destroy(fill_group* g) {
+  if (!g) return;
+  cudaStreamSynchronize(g->s);
+  delete g;
+}
 
 }  // extern "C"

@@ -1,0 +1,111 @@
+"""GPU batching: many realizations over masks and grid sizes in one call
+(fill_group_*), the mixed-size batch workload, and the autotuner."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from workloads import synth, WORKLOADS
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1109_0286_gb300 as cg  # noqa: E402
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def mixed_items(sizes, k_lo_n, seed0=13):
+    items = []
+    k_lo = 2 * math.pi / k_lo_n
+    spectra = {}
+    for n, count in sizes:
+        spectra[n] = synth.spectrum_cmb_like(n, n, k_lo)
+        for j in range(count):
+            obs = synth.mask_area_target(n, n, seed=seed0 * 100_000 + n * 1000 + j)
+            items.append((n, spectra[n], obs))
+    return items
+
+
+@pytest.mark.parametrize("mode", ["fp64", "fp32"])
+def test_group_equals_single_plans(mode):
+    """A group of mixed-size plans gives every realization the single-plan
+    path gives (same schedule, same arithmetic), and matches the oracle."""
+    items = mixed_items([(64, 3), (128, 2), (256, 2)], 256)
+    dt = torch.float32 if mode == "fp32" else torch.float64
+    plans, ds, dn = [], [], []
+    for k, (n, P, obs) in enumerate(items):
+        plans.append(cg.Plan(P, obs, mode=mode, batch=2 if k == 1 else 1))
+        d = O.draw(O.hermitian_full(P, n), 500 + k)
+        dn.append(d)
+        ds.append(torch.from_numpy(d).to(dtype=dt, device="cuda"))
+    g = cg.Group(plans)
+    seeds = list(range(7, 7 + g.size))
+    tol = 1e-9 if mode == "fp64" else 1e-6
+    outs, stats = g.realize(ds, seeds, tol)
+    flat = 0
+    for k, (p, (n, P, obs)) in enumerate(zip(plans, items)):
+        xs, _ = p.realize(ds[k], seeds[flat:flat + p.batch], tol)
+        assert torch.equal(outs[k], xs), k
+        m = obs == 0
+        if k < 3:
+            ref = O.realize(P, obs, dn[k], seeds[flat], tol=1e-12)
+            x = outs[k][0].cpu().numpy().astype(np.float64)
+            assert rel(x[m], ref.x[m]) <= (1e-8 if mode == "fp64" else 2e-5)
+        flat += p.batch
+    assert all(s["status"] == 0 for s in stats)
+
+
+def test_autotune_keeps_results_close(tmp_path):
+    n = 256
+    P = synth.spectrum_cmb_like(n, n, 2 * math.pi / n)
+    obs = synth.mask_area_target(n, n, seed=4)
+    d = torch.from_numpy(O.draw(O.hermitian_full(P, n), 1)).cuda()
+    a = cg.Plan(P, obs, mode="fp64", batch=2)
+    xa, _ = a.realize(d, [3, 4], 1e-10)
+    b = cg.Plan(P, obs, mode="fp64", batch=2)
+    cache = str(tmp_path / "tune.txt")
+    b.autotune(cache)
+    assert os.path.exists(cache) and open(cache).read().strip()
+    xb, _ = b.realize(d, [3, 4], 1e-10)
+    m = torch.from_numpy(obs == 0).cuda()
+    assert rel(xb[:, m].cpu().numpy(), xa[:, m].cpu().numpy()) <= 1e-9
+    c = cg.Plan(P, obs, mode="fp64", batch=2)
+    c.autotune(cache)                     # served from the cache
+    xc, _ = c.realize(d, [3, 4], 1e-10)
+    assert torch.equal(xb, xc)
+
+
+def test_batch_mixed_full_workload():
+    """256 realizations (128 x 256^2, 96 x 512^2, 32 x 1024^2), own masks at
+    5-25% masked area, shared CMB-like P(k), FP32 operator, tol 1e-6, in one
+    group call; sampled instances of every size against the oracle."""
+    spec = WORKLOADS["batch_mixed"]
+    items = mixed_items(spec["sizes"], spec["k_lo_n"], spec["mask_seed"])
+    plans, ds, dn = [], [], {}
+    for k, (n, P, obs) in enumerate(items):
+        plans.append(cg.Plan(P, obs, mode="fp32"))
+        if n not in dn:
+            dn[n] = O.draw(O.hermitian_full(P, n), spec["data_seed"])
+        ds.append(torch.from_numpy(dn[n]).float().cuda())
+    g = cg.Group(plans, autotune=True)
+    seeds = [spec["seed0"] + i for i in range(g.size)]
+    outs, stats = g.realize(ds, seeds, spec["tol"])
+    assert g.size == 256 and all(s["status"] == 0 for s in stats)
+    firsts = {}
+    for k, (n, _, _) in enumerate(items):
+        firsts.setdefault(n, k)
+    for n, k in firsts.items():
+        _, P, obs = items[k]
+        ref = O.realize(P, obs, dn[n], seeds[k], tol=spec["tol"])
+        x = outs[k][0].cpu().numpy().astype(np.float64)
+        m = obs == 0
+        assert np.array_equal(x[~m], dn[n].astype(np.float32)[~m].astype(np.float64))
+        assert rel(x[m], ref.x[m]) <= 1e-5, (n, rel(x[m], ref.x[m]))
