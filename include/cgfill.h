@@ -60,8 +60,8 @@ typedef enum {
   FILL_MODE_FP64 = 0,   /* every step in FP64 ("plain FP64 PCG") */
   FILL_MODE_FP32 = 1,   /* FP32 FFT operator and vectors, FP64-accurate inner
                            products; maps are float */
-  FILL_MODE_MIXED = 2   /* FP64 draw, right-hand side and residual; FP32 inner
-                           PCG solves; FP64 iterative refinement; maps double */
+  FILL_MODE_MIXED = 2   /* FP64 draw, right-hand side and residuals; FP32 PCG
+                           iterations with FP64 residual updates; maps double */
 } fill_mode;
 
 typedef struct {
@@ -77,6 +77,11 @@ typedef struct {
   int rows_per_cta;      /* row-pass CTA height, 0 = default schedule */
   int ffts_per_cta;      /* column FFTs per CTA, 0 = default schedule */
   int backward;          /* 1: allocate the buffers fill_backward needs; default 0 */
+  double update_delta;   /* mixed mode: one FP32 PCG with reliable updates -- the FP32
+                            correction is folded into the FP64 solution and the
+                            residual recomputed in FP64 whenever the FP32 residual
+                            has fallen by this factor; default 1e-2.  0: restarted
+                            iterative refinement (FP32 solves to inner_tol) */
 } fill_opts;
 
 typedef struct {

@@ -43,7 +43,8 @@ class FillOpts(ctypes.Structure):
                 ("batch", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("max_refine", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("history_cap", ctypes.c_int), ("rows_per_cta", ctypes.c_int),
-                ("ffts_per_cta", ctypes.c_int), ("backward", ctypes.c_int)]
+                ("ffts_per_cta", ctypes.c_int), ("backward", ctypes.c_int),
+                ("update_delta", ctypes.c_double)]
 
 
 class FillStats(ctypes.Structure):
@@ -273,7 +274,8 @@ class Plan:
 
     def __init__(self, P_half, observed, mode="mixed", precond=True, batch=1,
                  max_iter=10000, max_refine=10, inner_tol=1e-6, history_cap=0,
-                 rows_per_cta=0, ffts_per_cta=0, backward=False, stream=None):
+                 rows_per_cta=0, ffts_per_cta=0, backward=False, update_delta=1e-2,
+                 stream=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("paper_1109_0286_gb300 needs a CUDA GPU; no CPU fallback exists")
@@ -288,6 +290,7 @@ class Plan:
         o.rows_per_cta = int(rows_per_cta)
         o.ffts_per_cta = int(ffts_per_cta)
         o.backward = 1 if backward else 0
+        o.update_delta = float(update_delta)
         self.nbands = 0
         self.ny, self.nx = observed.shape
         self.batch = int(batch)

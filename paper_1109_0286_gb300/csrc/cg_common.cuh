@@ -170,6 +170,7 @@ __device__ __forceinline__ void scalar_update(int sop, CgState* st, double sum) 
     case SC_BB_RHO:
       st->bb = sum;
       st->rr = sum;
+      st->rrmax = sum;
       if (st->hist && st->hist_cap > 0) st->hist[0] = sum > 0.0 ? 1.0 : 0.0;
       if (!isfinite(sum)) {
         st->done = 1;
@@ -177,9 +178,10 @@ __device__ __forceinline__ void scalar_update(int sop, CgState* st, double sum) 
       } else if (sum == 0.0) {
         st->done = 1;    // nothing to solve: u = 0
       }
-      if (sop == SC_BB_RHO) {
+      if (sop == SC_BB_RHO) {   // plain CG: z = r, rho = ||r||^2, p = r
         st->rho = sum;
         st->beta = 0.0;
+        st->first = 0;
       }
       break;
     case SC_ALPHA:
@@ -223,6 +225,46 @@ __device__ __forceinline__ void scalar_update(int sop, CgState* st, double sum) 
         st->rho = sum;
       }
       break;
+    case SC_RCHECK_UPD: {
+      st->rr = sum;
+      st->iter += 1;
+      if (st->hist && st->iter < st->hist_cap) st->hist[st->iter] = sqrt(sum / st->bb);
+      if (!isfinite(sum)) {
+        st->status = 4;
+        st->done = 1;
+        st->peer->upd = 1;   // fold what was gained and report the true residual
+      } else if (sum <= st->delta2 * st->rrmax || sum <= st->tol2 * st->bb) {
+        st->peer->upd = 1;
+      } else if (st->iter >= st->max_iter) {
+        st->status = 3;
+        st->done = 1;
+        st->peer->upd = 1;
+      }
+      break;
+    }
+    case SC_RES_UPD: {
+      CgState* f = st->peer;
+      st->rr = sum;
+      st->upd = 0;
+      st->refine += 1;
+      if (st->hist && st->refine < st->hist_cap) st->hist[st->refine] = sqrt(sum / st->bb);
+      if (!isfinite(sum)) {
+        st->status = 4;
+        st->done = 1;
+        f->done = 1;
+      } else if (sum <= st->tol2 * st->bb) {
+        st->done = 1;
+        f->done = 1;
+      } else if (!f->done) {
+        f->rr = sum;
+        f->rrmax = sum;
+        f->upd = 1;
+      }
+      break;
+    }
+    case SC_CLEAR_UPD:
+      st->upd = 0;
+      break;
     case SC_RES:
       st->rr = sum;
       st->refine += 1;
@@ -237,6 +279,14 @@ __device__ __forceinline__ void scalar_update(int sop, CgState* st, double sum) 
     default:
       break;
   }
+}
+
+// Whether a pass skips this instance (SkipMode).
+__device__ __forceinline__ bool skip_instance(int mode, const CgState* st) {
+  if (mode == SKIP_NEVER) return false;
+  const int done = *(volatile const int*)&st->done;
+  if (mode == SKIP_DONE) return done != 0;
+  return done != 0 || *(volatile const int*)&st->upd == 0;
 }
 
 // Writes this CTA's partial; the last CTA of the instance sums all partials in

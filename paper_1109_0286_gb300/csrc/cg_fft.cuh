@@ -8,28 +8,46 @@
 // radix-16 stages.  On entry thread t holds x[t + e L/16] in v[e]; on exit it
 // holds X[t + e L/16] -- the same positions -- so a forward transform, a
 // diagonal multiply and an inverse transform chain without a shared-memory
-// round trip.  Between stages data goes through shared memory (split real /
-// imaginary arrays, index map sidx<T>).  A radix-16 stage needs W^(jm r),
+// round trip.  Between stages data goes through shared memory (XBuf).  A radix-16 stage needs W^(jm r),
 // r = 1..15: three table loads and at most four complex products each.
 #pragma once
 #include "cg_common.cuh"
 
 namespace cgf {
 
-// Shared-memory index of logical element i of an FFT exchange area.  FP32:
-// XOR swizzle of the low five bits with q ^ (q << 1), q = i / 32, which makes
-// every stage write (strides 1..16) and the strided reads free of bank
-// conflicts; FP64: one pad word per 16 elements (conflict-free for 8-byte
-// elements).  Both stay inside [0, L + L/16].
-template <typename T>
-__device__ __forceinline__ int sidx(int i) {
-  if constexpr (sizeof(T) == 4) {
-    const int q = i >> 5;
-    return i ^ ((q ^ (q << 1)) & 31);
-  } else {
-    return i + (i >> 4);
+// Exchange area of one FFT in shared memory (PADL = L + L/16 + 1 words per
+// component).  Element i lives at padded index i + i/16, which keeps every
+// stage write (strides 1..16) and the strided stage reads free of bank
+// conflicts for 8-byte elements.  FP32: interleaved complex (one 8-byte access
+// per element); FP64: split real / imaginary arrays (8-byte accesses).
+template <typename T> struct XBuf;
+
+template <>
+struct XBuf<float> {
+  float2* c;
+  __device__ __forceinline__ XBuf(float* base, int padl) : c(reinterpret_cast<float2*>(base)) {}
+  __device__ __forceinline__ void st(int i, cx<float> v) const {
+    c[i + (i >> 4)] = make_float2(v.r, v.i);
   }
-}
+  __device__ __forceinline__ cx<float> ld(int i) const {
+    const float2 t = c[i + (i >> 4)];
+    return {t.x, t.y};
+  }
+};
+
+template <>
+struct XBuf<double> {
+  double* re;
+  double* im;
+  __device__ __forceinline__ XBuf(double* base, int padl) : re(base), im(base + padl) {}
+  __device__ __forceinline__ void st(int i, cx<double> v) const {
+    re[i + (i >> 4)] = v.r;
+    im[i + (i >> 4)] = v.i;
+  }
+  __device__ __forceinline__ cx<double> ld(int i) const {
+    return {re[i + (i >> 4)], im[i + (i >> 4)]};
+  }
+};
 
 // a * (-i) for the forward transform, a * (+i) for the inverse.
 template <typename T, bool INV>
@@ -128,8 +146,7 @@ __device__ __forceinline__ cx<T> twiddle(const T* __restrict__ tw, int m) {
 }
 
 template <typename T, int LOG_L, bool INV>
-__device__ __forceinline__ void fft_regs(cx<T> (&v)[16], T* __restrict__ sre,
-                                         T* __restrict__ sim, int tid,
+__device__ __forceinline__ void fft_regs(cx<T> (&v)[16], const XBuf<T>& xb, int tid,
                                          const T* __restrict__ tw) {
   constexpr int TT = (1 << LOG_L) / 16;
   constexpr int S16 = LOG_L / 4;
@@ -151,9 +168,7 @@ __device__ __forceinline__ void fft_regs(cx<T> (&v)[16], T* __restrict__ sre,
     for (int q = 0; q < NB; ++q)
 #pragma unroll
       for (int r = 0; r < R0; ++r) {
-        const int idx = sidx<T>((tid + q * TT) * R0 + r);
-        sre[idx] = v[q + r * NB].r;
-        sim[idx] = v[q + r * NB].i;
+        xb.st((tid + q * TT) * R0 + r, v[q + r * NB]);
       }
   }
 #pragma unroll
@@ -166,10 +181,7 @@ __device__ __forceinline__ void fft_regs(cx<T> (&v)[16], T* __restrict__ sre,
     if (!first) {
       __syncthreads();
 #pragma unroll
-      for (int e = 0; e < 16; ++e) {
-        const int idx = sidx<T>(tid + e * TT);
-        v[e] = cx<T>{sre[idx], sim[idx]};
-      }
+      for (int e = 0; e < 16; ++e) v[e] = xb.ld(tid + e * TT);
       const int jm = tid & (ns - 1);
       const int stride = kLmax / (ns * 16);
       // W^(jm r) for r = 1..15 from three table entries (W^jm, W^4jm, W^8jm)
@@ -194,11 +206,7 @@ __device__ __forceinline__ void fft_regs(cx<T> (&v)[16], T* __restrict__ sre,
       const int jm = tid & (ns - 1);
       const int base = (tid - jm) * 16 + jm;
 #pragma unroll
-      for (int r = 0; r < 16; ++r) {
-        const int idx = sidx<T>(base + r * ns);
-        sre[idx] = v[r].r;
-        sim[idx] = v[r].i;
-      }
+      for (int r = 0; r < 16; ++r) xb.st(base + r * ns, v[r]);
     }
   }
 }

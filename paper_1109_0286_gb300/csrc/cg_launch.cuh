@@ -47,6 +47,8 @@ cudaError_t row_ll(bool in_spec, bool out_spec, const InstDesc<T>* d, int ninst,
     k_row<T, LL, true, true><<<grid, block, sm, s>>>(d, a, tw);
   else if (in_spec)
     k_row<T, LL, true, false><<<grid, block, sm, s>>>(d, a, tw);
+  else if (a.op == OP_XI)
+    k_row<T, LL, false, true, true><<<grid, block, sm, s>>>(d, a, tw);
   else
     k_row<T, LL, false, true><<<grid, block, sm, s>>>(d, a, tw);
   return cudaGetLastError();
@@ -65,6 +67,7 @@ cudaError_t prep_row() {
   cudaError_t e = allow_smem(k_row<T, LL, true, true>);
   if (e == cudaSuccess) e = allow_smem(k_row<T, LL, true, false>);
   if (e == cudaSuccess) e = allow_smem(k_row<T, LL, false, true>);
+  if (e == cudaSuccess) e = allow_smem(k_row<T, LL, false, true, true>);
   return e;
 }
 

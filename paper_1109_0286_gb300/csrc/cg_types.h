@@ -23,7 +23,8 @@ struct CgState {
   double rr;       // ||r||^2 after the last update
   double tol2;     // tol^2 (stop when rr <= tol2 * bb)
   double pq;       // last p^T A p
-  double spare;
+  double rrmax;    // ||r||^2 at the last FP64 residual update (reliable updates)
+  double delta2;   // update when rr <= delta2 * rrmax (reliable updates)
   int iter;        // completed operator applications
   int max_iter;
   int done;        // 1 once converged / stopped; later passes skip the instance
@@ -33,7 +34,8 @@ struct CgState {
   unsigned int ticket;  // last-CTA counter for the grid reductions
   int refine;      // FP64 residual recomputations (mixed refinement)
   int total_iter;  // inner iterations summed over refinement steps
-  int pad;
+  int upd;         // reliable updates: FP64 update (FP64 state) / reload (FP32 state) due
+  CgState* peer;   // the other precision's state of the same instance (mixed mode)
   double* hist;    // ||r_k|| / ||b||, k = 0..iter
 };
 
@@ -56,7 +58,7 @@ struct InstDesc {
   T* out;                  // caller's output map (dL/dd in the backward pass)
   const T* gx;             // caller's dL/dx (backward pass)
   T* w;                    // w = d - y on U, u on M (backward pass)
-  const float* dlt;        // FP32 correction (mixed refinement, FP64 passes)
+  float* dlt;              // FP32 correction (mixed refinement, FP64 passes)
   float* r32;              // FP32 residual target (mixed refinement, FP64 passes)
   CgState* st;
   double* partial;         // per-CTA partial sums
@@ -99,7 +101,16 @@ enum ScalarOp : int {
   SC_RCHECK_BETA = 5, // SC_RCHECK, then beta = rr / rho; rho = rr
   SC_BETA = 6,        // rz = sum; beta = rz / rho (0 on the first); rho = rz
   SC_RES = 7,         // rr = sum (FP64 true residual); refine++; done if rr <= tol2 bb
+  SC_RCHECK_UPD = 8,  // reliable updates, FP32 state: rr = sum; iter++; request an FP64
+                      // update when rr <= delta2 rrmax or rr <= tol2 bb or at max_iter
+  SC_RES_UPD = 9,     // reliable updates, FP64 state: true residual; converged -> both
+                      // done; else FP32 residual replaced, reload of its spectrum due
+  SC_CLEAR_UPD = 10,  // upd = 0 (after the reload)
 };
+
+// Instance skipping of a pass: 0 never; 1 once the state is done;
+// 2 unless an update is due (and the state is not done).
+enum SkipMode : int { SKIP_NEVER = 0, SKIP_DONE = 1, SKIP_UNLESS_UPD = 2 };
 
 enum VecOp : int {
   VOP_UPDATE = 1,     // r -= alpha q; u += alpha p; acc ||r||^2

@@ -99,11 +99,14 @@ struct fill_plan {
   uint32_t* obs = nullptr;
   std::vector<double> P_half;    // host copy of the spectrum
   long long launches = 0;        // kernels issued by the current call
+  cudaGraphExec_t mixed_graph = nullptr;   // reliable-update mixed iteration chunk
+  long long mixed_graph_kernels = 0;
   Precision<float> f;
   Precision<double> g;
   std::vector<void*> dev;
   std::vector<void*> host;
   ~fill_plan() {
+    if (mixed_graph) cudaGraphExecDestroy(mixed_graph);
     if (f.iter_graph) cudaGraphExecDestroy(f.iter_graph);
     if (g.iter_graph) cudaGraphExecDestroy(g.iter_graph);
     for (void* p : dev) cudaFree(p);
@@ -250,23 +253,23 @@ Ctx<T> ctx(fill_plan* p, int ninst = -1) {
 
 template <typename T>
 cudaError_t row(const Ctx<T>& c, cudaStream_t s, int op, int sop, bool in_spec, bool out_spec,
-                bool check_done, int spec_sel = 0) {
+                int skip, int spec_sel = 0) {
   ++*c.launches;
-  RowArgs a{c.ny, c.nx, c.rows, op, sop, check_done ? 1 : 0, spec_sel};
+  RowArgs a{c.ny, c.nx, c.rows, op, sop, skip, spec_sel};
   return Launch<T>::row(c.log_l, in_spec, out_spec, c.desc, c.ninst, a, c.tw, s);
 }
 
 template <typename T>
-cudaError_t col(const Ctx<T>& c, cudaStream_t s, int table, bool check_done, int spec_sel = 0) {
+cudaError_t col(const Ctx<T>& c, cudaStream_t s, int table, int skip, int spec_sel = 0) {
   ++*c.launches;
-  ColArgs a{c.ny, c.nx / 2 + 1, c.ffts, table, check_done ? 1 : 0, spec_sel};
+  ColArgs a{c.ny, c.nx / 2 + 1, c.ffts, table, skip, spec_sel};
   return Launch<T>::col(c.log_n, c.desc, c.ninst, a, c.tw, s);
 }
 
 template <typename T>
-cudaError_t vec(const Ctx<T>& c, cudaStream_t s, int op, int sop, bool check_done) {
+cudaError_t vec(const Ctx<T>& c, cudaStream_t s, int op, int sop, int skip) {
   ++*c.launches;
-  VecArgs a{c.npix, op, sop, check_done ? 1 : 0};
+  VecArgs a{c.npix, op, sop, skip};
   const long long pairs = c.npix / 2;
   const int nblk = (int)std::min<long long>((pairs + 255) / 256, 1024);
   return Launch<T>::vec(c.desc, c.ninst, a, nblk, s);
@@ -274,17 +277,17 @@ cudaError_t vec(const Ctx<T>& c, cudaStream_t s, int op, int sop, bool check_don
 
 template <typename T>
 cudaError_t row(fill_plan* p, cudaStream_t s, int op, int sop, bool in_spec, bool out_spec,
-                bool check_done, int ninst = -1, int spec_sel = 0) {
-  return row<T>(ctx<T>(p, ninst), s, op, sop, in_spec, out_spec, check_done, spec_sel);
+                int skip, int ninst = -1, int spec_sel = 0) {
+  return row<T>(ctx<T>(p, ninst), s, op, sop, in_spec, out_spec, skip, spec_sel);
 }
 template <typename T>
-cudaError_t col(fill_plan* p, cudaStream_t s, int table, bool check_done, int ninst = -1,
+cudaError_t col(fill_plan* p, cudaStream_t s, int table, int skip, int ninst = -1,
                 int spec_sel = 0) {
-  return col<T>(ctx<T>(p, ninst), s, table, check_done, spec_sel);
+  return col<T>(ctx<T>(p, ninst), s, table, skip, spec_sel);
 }
 template <typename T>
-cudaError_t vec(fill_plan* p, cudaStream_t s, int op, int sop, bool check_done) {
-  return vec<T>(ctx<T>(p), s, op, sop, check_done);
+cudaError_t vec(fill_plan* p, cudaStream_t s, int op, int sop, int skip) {
+  return vec<T>(ctx<T>(p), s, op, sop, skip);
 }
 
 #define CE(expr)                              \
@@ -433,6 +436,119 @@ fill_status mixed_refine(fill_plan* p, double tol) {
   return FILL_OK;
 }
 
+// Links the FP32 and FP64 states of each instance and sets the reliable-update
+// threshold on the FP32 state.
+__global__ void k_link_states(CgState* st32, CgState* st64, int n, double delta2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  st32[i].peer = st64 + i;
+  st64[i].peer = st32 + i;
+  st32[i].delta2 = delta2;
+  st32[i].tol2 = st64[i].tol2;
+}
+
+// One iteration of the mixed reliable-update PCG: an FP32 CG step; if the
+// FP32 residual has dropped by update_delta since the last update (or looks
+// converged), fold the FP32 correction into the FP64 solution, recompute the
+// true residual r = b - A u in FP64, restart the FP32 residual from it and
+// keep the search direction; then the preconditioned residual.  The update
+// passes skip every instance without a pending update.
+cudaError_t mixed_iter(fill_plan* p, cudaStream_t s) {
+  CE(row<float>(p, s, OP_P_UPD_Z, SC_NONE, false, true, SKIP_DONE));
+  CE(col<float>(p, s, 0, SKIP_DONE));
+  CE(row<float>(p, s, OP_Q, SC_ALPHA, true, false, SKIP_DONE));
+  CE(row<float>(p, s, OP_R_UPD, SC_RCHECK_UPD, false, true, SKIP_DONE));
+  CE(row<double>(p, s, OP_U64_UPD, SC_NONE, false, true, SKIP_UNLESS_UPD));
+  CE(col<double>(p, s, 0, SKIP_UNLESS_UPD));
+  CE(row<double>(p, s, OP_RES, SC_RES_UPD, true, false, SKIP_UNLESS_UPD));
+  CE(row<float>(p, s, OP_LOAD_R, SC_CLEAR_UPD, false, true, SKIP_UNLESS_UPD));
+  CE(col<float>(p, s, 1, SKIP_DONE));
+  CE(row<float>(p, s, OP_MASK, SC_NONE, true, true, SKIP_DONE));
+  CE(col<float>(p, s, 1, SKIP_DONE));
+  return row<float>(p, s, OP_Z, SC_BETA, true, false, SKIP_DONE);
+}
+
+cudaError_t mixed_iter_plain(fill_plan* p, cudaStream_t s) {
+  CE(row<float>(p, s, OP_P_UPD_R, SC_NONE, false, true, SKIP_DONE));
+  CE(col<float>(p, s, 0, SKIP_DONE));
+  CE(row<float>(p, s, OP_Q, SC_ALPHA, true, false, SKIP_DONE));
+  CE(vec<float>(p, s, VOP_UPDATE, SC_RCHECK_UPD, SKIP_DONE));
+  CE(row<double>(p, s, OP_U64_UPD, SC_NONE, false, true, SKIP_UNLESS_UPD));
+  CE(col<double>(p, s, 0, SKIP_UNLESS_UPD));
+  CE(row<double>(p, s, OP_RES, SC_RES_UPD, true, false, SKIP_UNLESS_UPD));
+  // plain CG: z = r, so beta = r^T r / rho (the reload pass also reduces ||r||^2)
+  return row<float>(p, s, OP_LOAD_R, SC_BETA, false, true, SKIP_DONE);
+}
+
+fill_status build_mixed_graph(fill_plan* p, int chunk) {
+  if (p->mixed_graph) return FILL_OK;
+  cudaGraph_t graph = nullptr;
+  const long long before = p->launches;
+  CK(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int c = 0; c < chunk && e == cudaSuccess; ++c)
+    e = p->o.precond ? mixed_iter(p, p->cap) : mixed_iter_plain(p, p->cap);
+  cudaError_t e2 = cudaStreamEndCapture(p->cap, &graph);
+  p->mixed_graph_kernels = p->launches - before;
+  p->launches = before;
+  if (e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(e, "capture mixed_iter");
+  }
+  CK(e2);
+  e = cudaGraphInstantiate(&p->mixed_graph, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  return FILL_OK;
+}
+
+// Mixed-precision solve with reliable updates (b, r, r32 and the FP64 state
+// with ||b||^2 are set; u64 = 0).
+fill_status mixed_reliable(fill_plan* p, double tol) {
+  const int B = p->batch;
+  const size_t n = p->npix;
+  const int nb = (B + 127) / 128;
+  const double d = p->o.update_delta;
+  ++p->launches;
+  k_link_states<<<nb, 128, 0, p->s>>>(p->f.st, p->g.st, B, d * d);
+  CK(cudaGetLastError());
+  CK(cudaMemsetAsync(p->f.u, 0, B * n * sizeof(float), p->s));
+  CK(cudaMemsetAsync(p->f.p, 0, B * n * sizeof(float), p->s));
+  // instances with b = 0 are done in the FP64 state: mirror that to FP32
+  ++p->launches;
+  k_inner_reset<<<nb, 128, 0, p->s>>>(p->f.st, p->g.st, B, tol, 0.0, p->o.max_iter);
+  CK(cudaGetLastError());
+  ++p->launches;
+  k_link_states<<<nb, 128, 0, p->s>>>(p->f.st, p->g.st, B, d * d);
+  CK(cudaGetLastError());
+  CK(pcg_start<float>(p, p->s, SC_BB));
+  const int chunk = 8;
+  fill_status fs = build_mixed_graph(p, chunk);
+  if (fs != FILL_OK) return fs;
+  const int limit = p->o.max_iter / chunk + 2;
+  for (int c = 0; c <= limit; ++c) {
+    CK(cudaMemcpyAsync(p->f.hst, p->f.st, sizeof(CgState) * B, cudaMemcpyDeviceToHost, p->s));
+    CK(cudaStreamSynchronize(p->s));
+    bool all = true;
+    for (int i = 0; i < B; ++i) all = all && p->f.hst[i].done;
+    if (all) break;
+    CK(cudaGraphLaunch(p->mixed_graph, p->s));
+    p->launches += p->mixed_graph_kernels;
+  }
+  // fold anything left (breakdown / limits) and report the true residual
+  CK(row<double>(p, p->s, OP_U64_UPD, SC_NONE, false, true, SKIP_DONE));
+  CK(col<double>(p, p->s, 0, SKIP_DONE));
+  CK(row<double>(p, p->s, OP_RES, SC_RES, true, false, SKIP_DONE));
+  ++p->launches;
+  k_inner_collect<<<nb, 128, 0, p->s>>>(p->f.st, p->g.st, B);
+  CK(cudaGetLastError());
+  return FILL_OK;
+}
+
+fill_status mixed_solve(fill_plan* p, double tol) {
+  return p->o.update_delta > 0.0 ? mixed_reliable(p, tol) : mixed_refine(p, tol);
+}
+
 // Sums the band partials of every CTA in order: out[i][b] (+)= sum_c part[i][c][b].
 __global__ void k_band_sum(const double* part, int ninst, int nctas, int nbands, double* out,
                            int accumulate) {
@@ -492,7 +608,7 @@ fill_status backward_t(fill_plan* p, const void* d, long long d_stride, const vo
     CK(upload_desc<float>(p));
     CK(init_states<float>(p, p->o.inner_tol));
     CK(vec<T>(p, p->s, VOP_LOAD_G, SC_BB, false));
-    fill_status fs = mixed_refine(p, tol);
+    fill_status fs = mixed_solve(p, tol);
     if (fs != FILL_OK) return fs;
   } else {
     CK(cudaMemsetAsync(P.p, 0, B * n * sizeof(T), p->s));
@@ -655,6 +771,7 @@ void fill_opts_default(fill_opts* o) {
   o->max_refine = 10;
   o->inner_tol = 1e-6;
   o->history_cap = 0;
+  o->update_delta = 1e-2;
 }
 
 fill_status fill_init(fill_plan** out, int ny, int nx, const double* P_half,
@@ -669,7 +786,8 @@ fill_status fill_init(fill_plan** out, int ny, int nx, const double* P_half,
     fill_opts_default(&o);
   if (o.mode < 0 || o.mode > 2 || o.batch < 1 || o.batch > 65535 || o.max_iter < 1 ||
       o.max_refine < 1 || !(o.inner_tol > 0.0) || o.history_cap < 0 || o.rows_per_cta < 0 ||
-      o.ffts_per_cta < 0 || o.backward < 0 || o.backward > 1)
+      o.ffts_per_cta < 0 || o.backward < 0 || o.backward > 1 || !(o.update_delta >= 0.0) ||
+      !(o.update_delta < 1.0))
     return FILL_EINVAL;
   const int nkx = nx / 2 + 1;
   // P: finite, positive, real-symmetric on the self-conjugate columns.
@@ -798,7 +916,7 @@ fill_status fill_realize(fill_plan* p, const void* d, long long d_stride, const 
     CK(init_states<float>(p, p->o.inner_tol));
     CK(cudaMemsetAsync(p->g.u, 0, B * n * sizeof(double), p->s));
     CK(draw_and_rhs<double>(p, p->s, false));
-    fs = mixed_refine(p, tol);
+    fs = mixed_solve(p, tol);
     if (fs != FILL_OK) return fs;
     CK(vec<double>(p, p->s, VOP_ASSEMBLE, SC_NONE, false));
     CK(cudaMemcpyAsync(p->g.hst, p->g.st, sizeof(CgState) * B, cudaMemcpyDeviceToHost, p->s));

@@ -40,7 +40,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_host_only_calls(lib):
     o = cg.fill_opts_default()
     assert (o.mode, o.precond, o.batch, o.max_iter, o.max_refine) == (2, 1, 1, 10000, 10)
-    assert o.inner_tol == 1e-6
+    assert o.inner_tol == 1e-6 and o.update_delta == 1e-2
     assert cg.fill_version() == 1
     assert cg.fill_strerror(0) == "ok"
     assert "converged" in cg.fill_strerror(3)
@@ -56,7 +56,7 @@ def test_host_only_calls(lib):
 
 
 def test_struct_layouts():
-    assert ctypes.sizeof(cg.FillOpts) == 48
+    assert ctypes.sizeof(cg.FillOpts) == 56
     assert ctypes.sizeof(cg.FillStats) == 40
 
 
