@@ -239,6 +239,29 @@ int fill_group_size(const fill_group* group);
 /* Frees the group (not its plans; NULL is allowed). */
 void fill_group_destroy(fill_group* group);
 
+/*
+ * fill_apply_static -- fill_apply without a plan and without any allocation,
+ * for callers that cannot allocate device memory (code that runs inside a
+ * memory pool or arena it does not own, or under an allocator that forbids
+ * new allocations).  The paper has no counterpart; this is a library
+ * convenience.  Applies, on one FP32 map, which = 0: C^-1 x; 1: C^{1/2} x;
+ * 2: P_x C^-1 P_x x; 3: P_x C^{1/2} P_x x, with the same kernels as
+ * fill_apply.  All pointers are DEVICE pointers: P_half float64 ny x (nx/2+1)
+ * (assumed valid as fill_init would require; not checked), observed uint8
+ * ny x nx (needed for which >= 2, else ignored), in / out float ny x nx (may
+ * not alias).  stream: a cudaStream_t; the call returns once the work is
+ * queued.  Scratch: one 8 MiB file-scope device array per device that loads
+ * the library (held until exit), which limits the grid to about 1024 x 1024
+ * pixels; larger grids return FILL_EINVAL with the reason in
+ * fill_last_error().  The first call on a device does a one-time set-up
+ * (symbol address, kernel attributes) and should come before any stream
+ * capture.  All calls share the scratch and overwrite it: calls that overlap
+ * on the GPU race, so order them on one stream.  No cudaMalloc / cudaFree
+ * and no allocating library routine is called.
+ */
+fill_status fill_apply_static(int ny, int nx, const double* P_half, const uint8_t* observed,
+                              int which, const float* in, float* out, void* stream);
+
 /* Number of masked pixels n_M of the plan's mask. */
 long long fill_masked_count(const fill_plan* plan);
 

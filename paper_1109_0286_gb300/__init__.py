@@ -23,7 +23,8 @@ __all__ = [
     "FillOpts", "FillStats", "FillError", "load", "lib_path", "fill_opts_default",
     "fill_init", "fill_realize", "fill_draw", "fill_apply", "fill_history",
     "fill_time_pass", "fill_set_bands", "fill_backward", "fill_autotune", "fill_group_init",
-    "fill_group_realize", "fill_group_size", "fill_group_destroy", "Group", "fill_masked_count", "fill_destroy", "fill_strerror", "fill_last_error",
+    "fill_group_realize", "fill_group_size", "fill_group_destroy", "Group", "fill_apply_static",
+    "fill_masked_count", "fill_destroy", "fill_strerror", "fill_last_error",
     "fill_version", "Plan", "MODES", "EXPORTED_SYMBOLS",
 ]
 
@@ -34,7 +35,8 @@ EXPORTED_SYMBOLS = [
     "fill_opts_default", "fill_init", "fill_realize", "fill_draw", "fill_apply",
     "fill_history", "fill_time_pass", "fill_set_bands", "fill_backward", "fill_autotune",
     "fill_group_init", "fill_group_realize", "fill_group_size", "fill_group_destroy",
-    "fill_masked_count", "fill_destroy", "fill_strerror", "fill_last_error", "fill_version",
+    "fill_apply_static", "fill_masked_count", "fill_destroy", "fill_strerror",
+    "fill_last_error", "fill_version",
 ]
 
 
@@ -60,7 +62,7 @@ class FillStats(ctypes.Structure):
 class FillError(RuntimeError):
     def __init__(self, status: int, where: str):
         msg = f"{where}: {STATUS.get(status, status)} ({fill_strerror(status)})"
-        if status == 6:
+        if status == 6 or (status == 1 and where == "fill_apply_static"):
             msg += ": " + fill_last_error()
         super().__init__(msg)
         self.status = status
@@ -115,6 +117,8 @@ def load() -> ctypes.CDLL:
     lib.fill_group_size.restype = _ci
     lib.fill_group_destroy.argtypes = [_vp]
     lib.fill_group_destroy.restype = None
+    lib.fill_apply_static.argtypes = [_ci, _ci, _vp, _vp, _ci, _vp, _vp, _vp]
+    lib.fill_apply_static.restype = _ci
     lib.fill_masked_count.argtypes = [_vp]
     lib.fill_masked_count.restype = _cll
     lib.fill_destroy.argtypes = [_vp]
@@ -238,6 +242,14 @@ def fill_group_size(group) -> int:
 def fill_group_destroy(group) -> None:
     if group:
         load().fill_group_destroy(_vp(group))
+
+
+def fill_apply_static(ny, nx, P_ptr, obs_ptr, which, in_ptr, out_ptr, stream=0):
+    """Operator application without a plan or any allocation (device pointers)."""
+    st = load().fill_apply_static(int(ny), int(nx), _vp(P_ptr), _vp(obs_ptr), int(which),
+                                  _vp(in_ptr), _vp(out_ptr), _vp(stream))
+    if st != 0:
+        raise FillError(st, "fill_apply_static")
 
 
 def fill_masked_count(plan) -> int:

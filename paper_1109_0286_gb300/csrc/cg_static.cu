@@ -1,0 +1,171 @@
+// fill_apply_static: the operator application of fill_apply for callers that
+// cannot allocate device memory (for example code running inside a memory
+// pool or arena owned by someone else, or a process whose allocator is locked
+// down).  Instead of a plan's buffers it uses one file-scope device array as
+// scratch, so the call itself performs no cudaMalloc / cudaFree and calls no
+// allocating library routine.
+//
+// The scratch lives in g_static_scratch (kStaticScratchBytes per device that
+// loads this library, held until the process exits).  It holds the twiddle
+// table, the spectral table, the transposed half spectrum, the mask bits and
+// one instance descriptor with its CG state.  Host code may not use the
+// array's name as a device address: the address comes from
+// cudaGetSymbolAddress, taken once per device (with that device current) on
+// the first call, which also raises the kernels' shared-memory limits; make
+// that first call before any stream capture.  Every call shares the array and
+// overwrites it, so calls that overlap on the GPU (different streams, or
+// threads without ordering) race; order them on one stream.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <mutex>
+
+#include "../../include/cgfill.h"
+#include "cg_launch.h"
+#include "cg_types.h"
+
+namespace {
+
+using namespace cgf;
+
+constexpr size_t kStaticScratchBytes = size_t(8) << 20;   // 8 MiB per device
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+void* g_scratch_addr[kMaxDevices] = {};
+std::mutex g_setup_mutex;
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+}  // namespace
+
+// Records the reason of a rejected call for fill_last_error (cgfill.cu).
+void cgf_set_last_error(const char* msg);
+
+namespace {
+
+// Scratch layout for an ny x nx FP32 problem.
+struct Layout {
+  size_t tw, tab, spec, bits, desc, st, part, total;
+};
+
+Layout layout(int ny, int nx) {
+  const size_t nkx = size_t(nx) / 2 + 1, npix = size_t(ny) * nx;
+  Layout L{};
+  size_t o = 0;
+  L.tw = o;   o = align256(o + 2 * sizeof(float) * kLmax);
+  L.tab = o;  o = align256(o + sizeof(float) * nkx * ny);
+  L.spec = o; o = align256(o + 2 * sizeof(float) * nkx * ny);
+  L.bits = o; o = align256(o + sizeof(uint32_t) * ((npix + 31) / 32));
+  L.desc = o; o = align256(o + sizeof(InstDesc<float>));
+  L.st = o;   o = align256(o + sizeof(CgState));
+  L.part = o; o = align256(o + sizeof(double) * kMaxPartials);
+  L.total = o;
+  return L;
+}
+
+// Builds everything a call needs inside the scratch: twiddles W_8192^m, the
+// table (1/(nP) or sqrt(P)/n in the transposed [kx][ky] layout), the mask
+// bits, a zeroed CG state and the instance descriptor.
+__global__ void k_static_setup(unsigned char* base, Layout L, int ny, int nx, const double* P,
+                               const uint8_t* observed, int sqrt_table, const float* in,
+                               float* out) {
+  const int nkx = nx / 2 + 1;
+  const long long npix = (long long)ny * nx;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nthr = (long long)gridDim.x * blockDim.x;
+  float* tw = reinterpret_cast<float*>(base + L.tw);
+  float* tab = reinterpret_cast<float*>(base + L.tab);
+  uint32_t* bits = reinterpret_cast<uint32_t*>(base + L.bits);
+  for (long long m = tid; m < kLmax; m += nthr) {
+    double s, c;
+    sincospi(2.0 * double(m) / double(kLmax), &s, &c);
+    tw[2 * m] = (float)c;
+    tw[2 * m + 1] = (float)-s;
+  }
+  for (long long t = tid; t < (long long)nkx * ny; t += nthr) {
+    const int kx = (int)(t / ny), ky = (int)(t % ny);
+    const double p = P[(long long)ky * nkx + kx];
+    tab[t] = (float)(sqrt_table ? sqrt(p) / double(npix) : 1.0 / (p * double(npix)));
+  }
+  for (long long w = tid; w < (npix + 31) / 32; w += nthr) {
+    uint32_t word = 0;
+    for (int b = 0; b < 32; ++b) {
+      const long long i = w * 32 + b;
+      if (i < npix && (observed == nullptr || observed[i])) word |= 1u << b;
+    }
+    bits[w] = word;
+  }
+  if (tid == 0) {
+    CgState* st = reinterpret_cast<CgState*>(base + L.st);
+    *st = CgState{};
+    InstDesc<float> D{};
+    D.obs = bits;
+    D.t_inv = tab;
+    D.t_sqrt = tab;
+    D.spec = reinterpret_cast<float*>(base + L.spec);
+    D.r = const_cast<float*>(in);   // read only (the source pass)
+    D.y = out;                      // unmasked sink
+    D.z = out;                      // masked sink
+    D.st = st;
+    D.partial = reinterpret_cast<double*>(base + L.part);
+    *reinterpret_cast<InstDesc<float>*>(base + L.desc) = D;
+  }
+}
+
+int pow2_log(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return (1 << l) == v ? l : -1;
+}
+
+}  // namespace
+
+extern "C" fill_status fill_apply_static(int ny, int nx, const double* P_half,
+                                         const uint8_t* observed, int which, const float* in,
+                                         float* out, void* stream) {
+  const int log_l = pow2_log(nx / 2), log_n = pow2_log(ny);
+  if (!P_half || !in || !out || in == out || which < 0 || which > 3 || log_l < 4 || log_l > 12 ||
+      log_n < 4 || log_n > 13 || (which >= 2 && !observed))
+    return FILL_EINVAL;
+  const Layout L = layout(ny, nx);
+  if (L.total > kStaticScratchBytes) {
+    cgf_set_last_error("fill_apply_static: grid too large for the 8 MiB static scratch "
+                       "(at most about 1024 x 1024 pixels)");
+    return FILL_EINVAL;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FILL_ECUDA;
+  {
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_scratch_addr[dev]) {
+      void* ptr = nullptr;
+      if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || !ptr) return FILL_ECUDA;
+      if (Launch<float>::prepare() != cudaSuccess) return FILL_ECUDA;
+      g_scratch_addr[dev] = ptr;
+    }
+  }
+  unsigned char* base = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const bool masked = which >= 2;
+  k_static_setup<<<256, 256, 0, s>>>(base, L, ny, nx, P_half, masked ? observed : nullptr,
+                                     (which == 1 || which == 3) ? 1 : 0, in, out);
+  if (cudaGetLastError() != cudaSuccess) return FILL_ECUDA;
+  const InstDesc<float>* desc = reinterpret_cast<const InstDesc<float>*>(base + L.desc);
+  const float* tw = reinterpret_cast<const float*>(base + L.tw);
+  // same launch schedule as a plan's default for this grid
+  const int TT = (1 << log_l) / 16, TN = (1 << log_n) / 16;
+  int rows = TT >= 256 ? 4 : (TT >= 128 ? 4 : (TT >= 64 ? 8 : 16));
+  if (rows * TT < 256) rows = 256 / TT;
+  if (rows > ny) rows = ny;
+  int ffts = TN >= 256 ? 1 : 256 / TN;
+  if (ffts > nx / 2 + 1) ffts = nx / 2 + 1;
+  RowArgs ra{ny, nx, rows, masked ? OP_LOAD_R_MASK : OP_LOAD_R, SC_NONE, SKIP_NEVER, 0};
+  if (Launch<float>::row(log_l, false, true, desc, 1, ra, tw, s) != cudaSuccess) return FILL_ECUDA;
+  ColArgs ca{ny, nx / 2 + 1, ffts, 0, SKIP_NEVER, 0};
+  if (Launch<float>::col(log_n, desc, 1, ca, tw, s) != cudaSuccess) return FILL_ECUDA;
+  RowArgs rb{ny, nx, rows, masked ? OP_Z : OP_STORE_Y, SC_NONE, SKIP_NEVER, 0};
+  if (Launch<float>::row(log_l, true, false, desc, 1, rb, tw, s) != cudaSuccess) return FILL_ECUDA;
+  return FILL_OK;
+}

@@ -27,6 +27,12 @@ namespace {
 
 thread_local std::string g_last_error;
 
+}  // namespace
+
+void cgf_set_last_error(const char* msg) { g_last_error = msg; }
+
+namespace {
+
 fill_status cuda_fail(cudaError_t e, const char* where) {
   g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
   return FILL_ECUDA;

@@ -169,16 +169,18 @@ def test_patch1024_fp32_parity(scale):
     assert e_conv <= 2.0 * spread + 1e-5
 
 
-@pytest.mark.parametrize("precond", [True, False])
-def test_mixed_refinement_to_1e10(precond):
-    """Mixed precision: FP32 inner PCG, FP64 residual and refinement, down to
-    a relative residual of 1e-10; error vs the converged FP64 oracle."""
+@pytest.mark.parametrize("precond,delta", [(True, 1e-2), (False, 1e-2), (True, 0.0), (False, 0.0)])
+def test_mixed_refinement_to_1e10(precond, delta):
+    """Mixed precision, FP32 PCG iterations with FP64 residuals, down to a
+    relative residual of 1e-10: reliable updates (delta > 0) and restarted
+    refinement (delta = 0); error vs the converged FP64 oracle."""
     P, obs, spec = workload("wide4096", scale=16)
     ny, nx = obs.shape
     Pf = O.hermitian_full(P, nx)
     d = O.draw(Pf, spec["data_seed"])
     seeds = spec["seeds"][:2]
-    plan = cg.Plan(P, obs, mode="mixed", precond=precond, batch=2, max_iter=4000)
+    plan = cg.Plan(P, obs, mode="mixed", precond=precond, batch=2, max_iter=4000,
+                   update_delta=delta)
     out, stats = plan.realize(gpu_map(d, torch.float64), seeds, 1e-10)
     m = obs == 0
     for i, s in enumerate(seeds):
@@ -187,6 +189,8 @@ def test_mixed_refinement_to_1e10(precond):
         assert np.array_equal(x[~m], d[~m])
         assert stats[i]["true_rel_resid"] <= 1e-10 and stats[i]["refine_steps"] >= 1
         assert rel(x[m], conv.x[m]) <= 1e-8, rel(x[m], conv.x[m])
+    print(f"mixed precond={precond} delta={delta}: iters {[s['iters'] for s in stats]} "
+          f"updates {[s['refine_steps'] for s in stats]}")
 
 
 def test_batch_equals_singles():
