@@ -38,6 +38,24 @@ UNIT = "realizations/s"
 # CPU time to realizations/s in the reference / cpu_baseline legs).
 FP64_ITERS_WIDE4096 = 200
 
+# DRAM traffic (read + write bytes) of one launch of the roofline kernel per
+# instance, from the ncu capture summarised in
+# profiles/k_row_sink_fp32_4096x4096x2.md (2 instances of 4096^2; scaled by the
+# instance count).  Reported only while the pass-kernel sources hash to the
+# profiled version; otherwise traffic is null.
+TRAFFIC = {"kernel": "k_row sink (C2R + q = P_x, p^T q)", "bytes_per_instance": 377.339904e6 / 2,
+           "src_hash": "c604b6f5371e03c9"}
+KERNEL_SOURCES = ["cg_types.h", "cg_common.cuh", "cg_fft.cuh", "cg_kernels.cuh"]
+
+
+def kernel_src_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1109_0286_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -150,12 +168,9 @@ def oracle_sample(P, obs, d, seed, iters):
 
 
 def threads_used():
-    try:
-        import threadpoolctl
-        info = threadpoolctl.threadpool_info()
-        return max([i.get("num_threads", 1) for i in info] + [1])
-    except Exception:
-        return 1
+    """Threads the oracle actually runs on: numpy.fft (pocketfft) and the
+    element-wise ufuncs it uses are single-threaded."""
+    return 1
 
 
 # ------------------------------------------------------------------ reference arm
@@ -294,9 +309,13 @@ def run_gpu(args):
     dom = max(timing, key=lambda k: timing[k][1] * timing[k][2])
     name, _, pms, pbytes = timing[dom]
     achieved = pbytes / (pms / 1e3) / 1e9
+    traffic = None
+    if name == TRAFFIC["kernel"] and mode in ("fp32", "mixed") and \
+            kernel_src_hash() == TRAFFIC["src_hash"] and (ny, nx) == (4096, 4096):
+        traffic = TRAFFIC["bytes_per_instance"] * B
     roofline = {"bound": "hbm", "kernel": name, "achieved": achieved,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                 "peak_source": f"{peak_src} (hbm_gbs, burst)",
                 "bytes_per_launch": pbytes, "ms_per_launch": pms}
     pass_table = {timing[k][0]: {"ms": round(timing[k][2], 4),

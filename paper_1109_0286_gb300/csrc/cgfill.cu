@@ -3,10 +3,10 @@
 //
 // Every numerical step runs in the pass kernels (cg_kernels.cuh); this file
 // validates inputs, builds the tables, owns the buffers and sequences the
-// passes on the plan's stream.  The CG loop runs in chunks of iterations
-// replayed from a captured CUDA graph; each kernel of a converged instance
-// returns at once, so the host only polls the per-instance `done` flags
-// between chunks.
+// passes on the plan's stream.  A whole CG loop is one launch of a captured
+// CUDA graph with a conditional WHILE node: kernels of converged instances
+// return at once, and a one-CTA control kernel ends the loop when every
+// instance is done (or after a hard iteration limit).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -89,9 +89,9 @@ struct Precision {
   InstDesc<T>* hdesc = nullptr; // pinned
   int rows = 0, ffts = 0;
   bool used = false;
-  cudaGraphExec_t iter_graph = nullptr;
-  int iter_graph_chunk = 0;
-  long long iter_graph_kernels = 0;
+  cudaGraphExec_t iter_graph = nullptr;   // CG loop graph (conditional WHILE node)
+  long long iter_graph_kernels = 0;       // kernels per loop body
+  CgState** stp = nullptr;                // device: state pointer of each instance
 };
 
 }  // namespace
@@ -102,11 +102,15 @@ struct fill_plan {
   fill_opts o{};
   cudaStream_t s = nullptr;      // caller's stream
   cudaStream_t cap = nullptr;    // plan-owned stream for graph capture
+  cudaStream_t cap2 = nullptr;   // second capture stream (conditional bodies)
   uint32_t* obs = nullptr;
   std::vector<double> P_half;    // host copy of the spectrum
   long long launches = 0;        // kernels issued by the current call
-  cudaGraphExec_t mixed_graph = nullptr;   // reliable-update mixed iteration chunk
+  cudaGraphExec_t mixed_graph = nullptr;   // reliable-update mixed CG loop
   long long mixed_graph_kernels = 0;
+  int* loop_counter = nullptr;   // device [2]: loop bodies, IF bodies of the last loop graph
+  int* hloop = nullptr;          // pinned mirror
+  long long if_kernels = 0;      // kernels inside the update IF node
   Precision<float> f;
   Precision<double> g;
   std::vector<void*> dev;
@@ -118,6 +122,7 @@ struct fill_plan {
     for (void* p : dev) cudaFree(p);
     for (void* p : host) cudaFreeHost(p);
     if (cap) cudaStreamDestroy(cap);
+    if (cap2) cudaStreamDestroy(cap2);
   }
   template <typename X>
   cudaError_t dalloc(X** p, size_t count) {
@@ -178,18 +183,6 @@ __global__ void k_state_init(const InstDesc<T>* desc, int n, double tol2, int ma
   s.hist_cap = hist_cap;
   s.hist = desc[i].hist;
   *desc[i].st = s;
-}
-
-// 1 in *flag iff every instance's CG state is done (one CTA).
-template <typename T>
-__global__ void k_all_done(const InstDesc<T>* desc, int n, int* flag) {
-  __shared__ int any_running;
-  if (threadIdx.x == 0) any_running = 0;
-  __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x)
-    if (!*(volatile int*)&desc[i].st->done) any_running = 1;
-  __syncthreads();
-  if (threadIdx.x == 0) *flag = any_running ? 0 : 1;
 }
 
 template <typename T>
@@ -362,52 +355,110 @@ cudaError_t pcg_iter(fill_plan* p, cudaStream_t s) {
   return pcg_iter<T>(ctx<T>(p), s);
 }
 
-template <typename T>
-fill_status build_iter_graph(fill_plan* p, int chunk) {
-  Precision<T>& P = prec<T>(p);
-  if (P.iter_graph && P.iter_graph_chunk == chunk) return FILL_OK;
-  if (P.iter_graph) {
-    cudaGraphExecDestroy(P.iter_graph);
-    P.iter_graph = nullptr;
+// ----------------------------------------------------------------- device-side CG loop
+// A CG loop is one graph launch: a reset node, then a conditional WHILE node
+// whose body is one iteration followed by k_loop_ctl, which keeps the loop
+// going while any instance is not done -- and stops it after `limit` bodies
+// whatever the states say, so the loop always ends.
+// counter[0]: loop bodies run; counter[1]: IF bodies run (update passes).
+__global__ void k_loop_reset(int* counter) {
+  counter[0] = 0;
+  counter[1] = 0;
+}
+
+__global__ void k_loop_ctl(cudaGraphConditionalHandle h, CgState* const* sts, int n, int* counter,
+                           int limit) {
+  __shared__ int running;
+  if (threadIdx.x == 0) running = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    if (!*(volatile int*)&sts[i]->done) running = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int c = ++*counter;
+    cudaGraphSetConditional(h, (running && c < limit) ? 1u : 0u);
   }
-  cudaGraph_t graph = nullptr;
-  const long long before = p->launches;
-  CK(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = cudaSuccess;
-  for (int c = 0; c < chunk && e == cudaSuccess; ++c) e = pcg_iter<T>(p, p->cap);
-  cudaError_t e2 = cudaStreamEndCapture(p->cap, &graph);
-  P.iter_graph_kernels = p->launches - before;
-  p->launches = before;
-  if (e != cudaSuccess) {
-    if (graph) cudaGraphDestroy(graph);
-    return cuda_fail(e, "capture pcg_iter");
+}
+
+template <typename Body>
+fill_status build_loop_graph(cudaStream_t cap, Body body, CgState* const* sts, int n,
+                             int* counter, int limit, long long* launches,
+                             cudaGraphExec_t* exec_out, long long* body_kernels) {
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  auto fail = [&](cudaError_t e, const char* where) {
+    cudaGraphDestroy(g);
+    return cuda_fail(e, where);
+  };
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return fail(e, "cudaGraphConditionalHandleCreate");
+  cudaKernelNodeParams kp{};
+  void* args[] = {&counter};
+  kp.func = reinterpret_cast<void*>(k_loop_reset);
+  kp.gridDim = dim3(1);
+  kp.blockDim = dim3(1);
+  kp.kernelParams = args;
+  cudaGraphNode_t reset;
+  e = cudaGraphAddKernelNode(&reset, g, nullptr, 0, &kp);
+  if (e != cudaSuccess) return fail(e, "cudaGraphAddKernelNode");
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  e = cudaGraphAddNode(&wnode, g, &reset, nullptr, 1, &cp);
+  if (e != cudaSuccess) return fail(e, "cudaGraphAddNode(while)");
+  cudaGraph_t bg = cp.conditional.phGraph_out[0];
+  const long long before = *launches;
+  e = cudaStreamBeginCaptureToGraph(cap, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return fail(e, "cudaStreamBeginCaptureToGraph");
+  e = body(cap);
+  if (e == cudaSuccess) {
+    k_loop_ctl<<<1, 256, 0, cap>>>(h, sts, n, counter, limit);
+    e = cudaGetLastError();
   }
-  CK(e2);
-  e = cudaGraphInstantiate(&P.iter_graph, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-  P.iter_graph_chunk = chunk;
+  cudaError_t e2 = cudaStreamEndCapture(cap, &bg);
+  *body_kernels = *launches - before + 1;
+  *launches = before;
+  if (e != cudaSuccess) return fail(e, "capture loop body");
+  if (e2 != cudaSuccess) return fail(e2, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(exec_out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate(loop)");
   return FILL_OK;
 }
 
-// Runs CG iterations until every instance's state is done.
+// Launches a loop graph on the plan's stream and accounts for its kernels
+// (if_kernels of each body run only when its IF node fires).
+fill_status run_loop_graph(fill_plan* p, cudaGraphExec_t exec, long long body_kernels,
+                           long long if_kernels = 0) {
+  CK(cudaGraphLaunch(exec, p->s));
+  CK(cudaMemcpyAsync(p->hloop, p->loop_counter, 2 * sizeof(int), cudaMemcpyDeviceToHost, p->s));
+  CK(cudaStreamSynchronize(p->s));
+  p->launches += 1 + (long long)p->hloop[0] * (body_kernels - if_kernels) +
+                 (long long)p->hloop[1] * if_kernels;
+  return FILL_OK;
+}
+
+template <typename T>
+fill_status build_iter_graph(fill_plan* p) {
+  Precision<T>& P = prec<T>(p);
+  if (P.iter_graph) return FILL_OK;
+  return build_loop_graph(
+      p->cap, [&](cudaStream_t s) { return pcg_iter<T>(p, s); }, P.stp, p->batch,
+      p->loop_counter, p->o.max_iter + 4, &p->launches, &P.iter_graph, &P.iter_graph_kernels);
+}
+
+// Runs CG iterations until every instance's state is done: one launch of the
+// plan's loop graph.
 template <typename T>
 fill_status run_pcg(fill_plan* p) {
   Precision<T>& P = prec<T>(p);
-  const int chunk = 8;
-  fill_status fs = build_iter_graph<T>(p, chunk);
+  fill_status fs = build_iter_graph<T>(p);
   if (fs != FILL_OK) return fs;
-  const int limit = p->o.max_iter / chunk + 2;
-  for (int c = 0; c <= limit; ++c) {
-    CK(cudaMemcpyAsync(P.hst, P.st, sizeof(CgState) * p->batch, cudaMemcpyDeviceToHost, p->s));
-    CK(cudaStreamSynchronize(p->s));
-    bool all = true;
-    for (int i = 0; i < p->batch; ++i) all = all && P.hst[i].done;
-    if (all) return FILL_OK;
-    CK(cudaGraphLaunch(P.iter_graph, p->s));
-    p->launches += P.iter_graph_kernels;
-  }
-  return FILL_OK;
+  return run_loop_graph(p, P.iter_graph, P.iter_graph_kernels);
 }
 
 // Mixed-precision solve of A u = b: b, r (FP64) and r32 are set and the FP64
@@ -453,21 +504,88 @@ __global__ void k_link_states(CgState* st32, CgState* st64, int n, double delta2
   st32[i].tol2 = st64[i].tol2;
 }
 
+// Sets an IF condition to 1 iff some instance's state has an update due.
+__global__ void k_if_any_upd(cudaGraphConditionalHandle h, CgState* const* sts, int n,
+                             int* counter) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    if (*(volatile int*)&sts[i]->upd) any = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (any) counter[1] += 1;
+    cudaGraphSetConditional(h, any ? 1u : 0u);
+  }
+}
+
+// Inside a stream capture on s: adds an IF node (on handle h of the captured
+// graph) whose body is body(s2), captured on stream s2; capture on s resumes
+// after the node.
+template <typename Body>
+cudaError_t capture_if(cudaStream_t s, cudaStream_t s2, cudaGraphConditionalHandle h, Body body) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* ed = nullptr;
+  size_t nd = 0;
+  CE(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, &ed, &nd));
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeIf;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  CE(cudaGraphAddNode(&node, g, deps, ed, nd, &cp));
+  CE(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  cudaGraph_t bg = cp.conditional.phGraph_out[0];
+  CE(cudaStreamBeginCaptureToGraph(s2, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = body(s2);
+  cudaError_t e2 = cudaStreamEndCapture(s2, &bg);
+  return e != cudaSuccess ? e : e2;
+}
+
 // One iteration of the mixed reliable-update PCG: an FP32 CG step; if the
 // FP32 residual has dropped by update_delta since the last update (or looks
 // converged), fold the FP32 correction into the FP64 solution, recompute the
 // true residual r = b - A u in FP64, restart the FP32 residual from it and
 // keep the search direction; then the preconditioned residual.  The update
 // passes skip every instance without a pending update.
+// The update passes sit in an IF node that runs only when some instance has
+// an update due (kernels inside still skip the instances without one).
+cudaError_t mixed_update_passes(fill_plan* p, cudaStream_t s) {
+  CE(row<double>(p, s, OP_U64_UPD, SC_NONE, false, true, SKIP_UNLESS_UPD));
+  CE(col<double>(p, s, 0, SKIP_UNLESS_UPD));
+  CE(row<double>(p, s, OP_RES, SC_RES_UPD, true, false, SKIP_UNLESS_UPD));
+  return row<float>(p, s, OP_LOAD_R, SC_CLEAR_UPD, false, true, SKIP_UNLESS_UPD);
+}
+
+cudaError_t update_if(fill_plan* p, cudaStream_t s, bool reload) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  CE(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr));
+  cudaGraphConditionalHandle h;
+  CE(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+  ++p->launches;
+  k_if_any_upd<<<1, 256, 0, s>>>(h, p->g.stp, p->batch, p->loop_counter);
+  CE(cudaGetLastError());
+  const long long before = p->launches;
+  cudaError_t e = capture_if(s, p->cap2, h, [&](cudaStream_t s2) -> cudaError_t {
+    if (reload) return mixed_update_passes(p, s2);
+    CE(row<double>(p, s2, OP_U64_UPD, SC_NONE, false, true, SKIP_UNLESS_UPD));
+    CE(col<double>(p, s2, 0, SKIP_UNLESS_UPD));
+    return row<double>(p, s2, OP_RES, SC_RES_UPD, true, false, SKIP_UNLESS_UPD);
+  });
+  p->if_kernels = p->launches - before;
+  return e;
+}
+
 cudaError_t mixed_iter(fill_plan* p, cudaStream_t s) {
   CE(row<float>(p, s, OP_P_UPD_Z, SC_NONE, false, true, SKIP_DONE));
   CE(col<float>(p, s, 0, SKIP_DONE));
   CE(row<float>(p, s, OP_Q, SC_ALPHA, true, false, SKIP_DONE));
   CE(row<float>(p, s, OP_R_UPD, SC_RCHECK_UPD, false, true, SKIP_DONE));
-  CE(row<double>(p, s, OP_U64_UPD, SC_NONE, false, true, SKIP_UNLESS_UPD));
-  CE(col<double>(p, s, 0, SKIP_UNLESS_UPD));
-  CE(row<double>(p, s, OP_RES, SC_RES_UPD, true, false, SKIP_UNLESS_UPD));
-  CE(row<float>(p, s, OP_LOAD_R, SC_CLEAR_UPD, false, true, SKIP_UNLESS_UPD));
+  CE(update_if(p, s, true));
   CE(col<float>(p, s, 1, SKIP_DONE));
   CE(row<float>(p, s, OP_MASK, SC_NONE, true, true, SKIP_DONE));
   CE(col<float>(p, s, 1, SKIP_DONE));
@@ -479,33 +597,18 @@ cudaError_t mixed_iter_plain(fill_plan* p, cudaStream_t s) {
   CE(col<float>(p, s, 0, SKIP_DONE));
   CE(row<float>(p, s, OP_Q, SC_ALPHA, true, false, SKIP_DONE));
   CE(vec<float>(p, s, VOP_UPDATE, SC_RCHECK_UPD, SKIP_DONE));
-  CE(row<double>(p, s, OP_U64_UPD, SC_NONE, false, true, SKIP_UNLESS_UPD));
-  CE(col<double>(p, s, 0, SKIP_UNLESS_UPD));
-  CE(row<double>(p, s, OP_RES, SC_RES_UPD, true, false, SKIP_UNLESS_UPD));
+  CE(update_if(p, s, false));
   // plain CG: z = r, so beta = r^T r / rho (the reload pass also reduces ||r||^2)
   return row<float>(p, s, OP_LOAD_R, SC_BETA, false, true, SKIP_DONE);
 }
 
-fill_status build_mixed_graph(fill_plan* p, int chunk) {
+fill_status build_mixed_graph(fill_plan* p) {
   if (p->mixed_graph) return FILL_OK;
-  cudaGraph_t graph = nullptr;
-  const long long before = p->launches;
-  CK(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = cudaSuccess;
-  for (int c = 0; c < chunk && e == cudaSuccess; ++c)
-    e = p->o.precond ? mixed_iter(p, p->cap) : mixed_iter_plain(p, p->cap);
-  cudaError_t e2 = cudaStreamEndCapture(p->cap, &graph);
-  p->mixed_graph_kernels = p->launches - before;
-  p->launches = before;
-  if (e != cudaSuccess) {
-    if (graph) cudaGraphDestroy(graph);
-    return cuda_fail(e, "capture mixed_iter");
-  }
-  CK(e2);
-  e = cudaGraphInstantiate(&p->mixed_graph, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-  return FILL_OK;
+  return build_loop_graph(
+      p->cap,
+      [&](cudaStream_t s) { return p->o.precond ? mixed_iter(p, s) : mixed_iter_plain(p, s); },
+      p->f.stp, p->batch, p->loop_counter, p->o.max_iter + 4, &p->launches, &p->mixed_graph,
+      &p->mixed_graph_kernels);
 }
 
 // Mixed-precision solve with reliable updates (b, r, r32 and the FP64 state
@@ -528,19 +631,10 @@ fill_status mixed_reliable(fill_plan* p, double tol) {
   k_link_states<<<nb, 128, 0, p->s>>>(p->f.st, p->g.st, B, d * d);
   CK(cudaGetLastError());
   CK(pcg_start<float>(p, p->s, SC_BB));
-  const int chunk = 8;
-  fill_status fs = build_mixed_graph(p, chunk);
+  fill_status fs = build_mixed_graph(p);
   if (fs != FILL_OK) return fs;
-  const int limit = p->o.max_iter / chunk + 2;
-  for (int c = 0; c <= limit; ++c) {
-    CK(cudaMemcpyAsync(p->f.hst, p->f.st, sizeof(CgState) * B, cudaMemcpyDeviceToHost, p->s));
-    CK(cudaStreamSynchronize(p->s));
-    bool all = true;
-    for (int i = 0; i < B; ++i) all = all && p->f.hst[i].done;
-    if (all) break;
-    CK(cudaGraphLaunch(p->mixed_graph, p->s));
-    p->launches += p->mixed_graph_kernels;
-  }
+  fs = run_loop_graph(p, p->mixed_graph, p->mixed_graph_kernels, p->if_kernels);
+  if (fs != FILL_OK) return fs;
   // fold anything left (breakdown / limits) and report the true residual
   CK(row<double>(p, p->s, OP_U64_UPD, SC_NONE, false, true, SKIP_DONE));
   CK(col<double>(p, p->s, 0, SKIP_DONE));
@@ -682,6 +776,12 @@ fill_status setup_precision(fill_plan* p, const std::vector<double>& tinv,
     return FILL_ENOMEM;
   const int hc = std::max(p->o.history_cap, 1);
   if (p->dalloc(&P.hist, B * hc) != cudaSuccess) return FILL_ENOMEM;
+  if (p->dalloc(&P.stp, B) != cudaSuccess) return FILL_ENOMEM;
+  {
+    std::vector<CgState*> ptrs(B);
+    for (size_t i = 0; i < B; ++i) ptrs[i] = P.st + i;
+    CK(cudaMemcpy(P.stp, ptrs.data(), B * sizeof(CgState*), cudaMemcpyHostToDevice));
+  }
   std::vector<T> a(ntab), b2(ntab), w(2 * size_t(kLmax));
   for (size_t i = 0; i < ntab; ++i) {
     a[i] = (T)tinv[i];
@@ -832,8 +932,11 @@ fill_status fill_init(fill_plan** out, int ny, int nx, const double* P_half,
     return st;
   };
   cudaError_t e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap2, cudaStreamNonBlocking);
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaStreamCreate"));
   if (p->dalloc(&p->obs, bits.size()) != cudaSuccess) return fail(FILL_ENOMEM);
+  if (p->dalloc(&p->loop_counter, 2) != cudaSuccess || p->halloc(&p->hloop, 2) != cudaSuccess)
+    return fail(FILL_ENOMEM);
   e = cudaMemcpy(p->obs, bits.data(), bits.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return fail(cuda_fail(e, "upload mask"));
   // Tables [kx][ky] with the inverse DFT's 1/n folded in.
@@ -1280,6 +1383,10 @@ fill_status tune_plan_t(fill_plan* p, const char* path) {
       cudaGraphExecDestroy(P.iter_graph);
       P.iter_graph = nullptr;
     }
+    if (p->mixed_graph) {
+      cudaGraphExecDestroy(p->mixed_graph);
+      p->mixed_graph = nullptr;
+    }
   }
   return FILL_OK;
 }
@@ -1310,8 +1417,9 @@ struct fill_group {
   int mode = 1, precond = 1, max_iter = 10000, ntot = 0;
   cudaStream_t s = nullptr, cap = nullptr;
   cudaEvent_t fork = nullptr, fork_cap = nullptr;
-  int* flags = nullptr;         // device, one per class
-  int* hflags = nullptr;        // pinned
+  CgState** stp = nullptr;      // device: state pointer of every instance
+  int* counter = nullptr;       // device: loop bodies run by the last launch
+  int* hloop = nullptr;         // pinned
   cudaGraphExec_t graph = nullptr;
   long long graph_kernels = 0, launches = 0;
   std::vector<void*> dev, host;
@@ -1371,32 +1479,24 @@ fill_status group_setup(fill_group* g, int autotune, const char* path) {
   return FILL_OK;
 }
 
+// The group's CG loop graph: every loop body forks the size classes onto
+// their streams (parallel branches), runs one iteration of each, and joins.
 template <typename T>
-fill_status group_build_graph(fill_group* g, int chunk) {
+fill_status group_build_graph(fill_group* g) {
   if (g->graph) return FILL_OK;
-  cudaGraph_t graph = nullptr;
-  const long long before = g->launches;
-  CK(cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = cudaEventRecord(g->fork_cap, g->cap);
-  for (auto& c : g->cls) {
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(c.cs, g->fork_cap, 0);
-    Ctx<T> cx_ = gctx<T>(g, c);
-    for (int k = 0; k < chunk && e == cudaSuccess; ++k) e = pcg_iter<T>(cx_, c.cs);
-    if (e == cudaSuccess) e = cudaEventRecord(c.join, c.cs);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(g->cap, c.join, 0);
-  }
-  cudaError_t e2 = cudaStreamEndCapture(g->cap, &graph);
-  g->graph_kernels = g->launches - before;
-  g->launches = before;
-  if (e != cudaSuccess) {
-    if (graph) cudaGraphDestroy(graph);
-    return cuda_fail(e, "capture group iteration");
-  }
-  CK(e2);
-  e = cudaGraphInstantiate(&g->graph, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-  return FILL_OK;
+  return build_loop_graph(
+      g->cap,
+      [&](cudaStream_t cap) -> cudaError_t {
+        CE(cudaEventRecord(g->fork_cap, cap));
+        for (auto& c : g->cls) {
+          CE(cudaStreamWaitEvent(c.cs, g->fork_cap, 0));
+          CE(pcg_iter<T>(gctx<T>(g, c), c.cs));
+          CE(cudaEventRecord(c.join, c.cs));
+          CE(cudaStreamWaitEvent(cap, c.join, 0));
+        }
+        return cudaSuccess;
+      },
+      g->stp, g->ntot, g->counter, g->max_iter + 4, &g->launches, &g->graph, &g->graph_kernels);
 }
 
 // Starts every class on its own stream after `s` reaches this point, and
@@ -1442,25 +1542,10 @@ fill_status group_realize_t(fill_group* g, const void* const* d, const uint64_t*
     return pcg_start<T>(cx_, c.cs, SC_NONE);
   });
   if (fs != FILL_OK) return fs;
-  const int chunk = 8;
-  fs = group_build_graph<T>(g, chunk);
+  fs = group_build_graph<T>(g);
   if (fs != FILL_OK) return fs;
-  const int limit = g->max_iter / chunk + 2;
-  for (int it = 0; it <= limit; ++it) {
-    for (size_t ci = 0; ci < g->cls.size(); ++ci) {
-      ++g->launches;
-      k_all_done<T><<<1, 256, 0, g->s>>>(reinterpret_cast<const InstDesc<T>*>(g->cls[ci].desc),
-                                         g->cls[ci].ninst, g->flags + ci);
-    }
-    CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(g->hflags, g->flags, sizeof(int) * g->cls.size(), cudaMemcpyDeviceToHost, g->s));
-    CK(cudaStreamSynchronize(g->s));
-    bool all = true;
-    for (size_t ci = 0; ci < g->cls.size(); ++ci) all = all && g->hflags[ci];
-    if (all) break;
-    CK(cudaGraphLaunch(g->graph, g->s));
-    g->launches += g->graph_kernels;
-  }
+  CK(cudaGraphLaunch(g->graph, g->s));
+  CK(cudaMemcpyAsync(g->hloop, g->counter, sizeof(int), cudaMemcpyDeviceToHost, g->s));
   fs = group_fork_join<T>(g, [&](GroupClass& c) -> cudaError_t {
     Ctx<T> cx_ = gctx<T>(g, c);
     CE(vec<T>(cx_, c.cs, VOP_ASSEMBLE, SC_NONE, false));
@@ -1471,6 +1556,7 @@ fill_status group_realize_t(fill_group* g, const void* const* d, const uint64_t*
   });
   if (fs != FILL_OK) return fs;
   CK(cudaStreamSynchronize(g->s));
+  g->launches += 1 + (long long)(*g->hloop) * g->graph_kernels;
   if (stats) {
     for (auto& c : g->cls) {
       int k = 0;
@@ -1555,10 +1641,22 @@ fill_status fill_group_init(fill_group** out, fill_plan* const* plans, int count
     if (e == cudaSuccess) e = cudaMallocHost(&c.hst, sizeof(CgState) * c.ninst);
     if (e == cudaSuccess) g->host.push_back(c.hst);
   }
-  if (e == cudaSuccess) e = cudaMalloc(&g->flags, sizeof(int) * g->cls.size());
-  if (e == cudaSuccess) g->dev.push_back(g->flags);
-  if (e == cudaSuccess) e = cudaMallocHost(&g->hflags, sizeof(int) * g->cls.size());
-  if (e == cudaSuccess) g->host.push_back(g->hflags);
+  if (e == cudaSuccess) e = cudaMalloc(&g->counter, 2 * sizeof(int));
+  if (e == cudaSuccess) g->dev.push_back(g->counter);
+  if (e == cudaSuccess) e = cudaMallocHost(&g->hloop, sizeof(int));
+  if (e == cudaSuccess) g->host.push_back(g->hloop);
+  if (e == cudaSuccess) e = cudaMalloc(&g->stp, sizeof(CgState*) * g->ntot);
+  if (e == cudaSuccess) g->dev.push_back(g->stp);
+  if (e == cudaSuccess) {
+    std::vector<CgState*> ptrs;
+    for (auto& c : g->cls)
+      for (int pi : c.plans) {
+        fill_plan* p = g->plans[pi];
+        CgState* st = mode == FILL_MODE_FP32 ? p->f.st : p->g.st;
+        for (int i = 0; i < p->batch; ++i) ptrs.push_back(st + i);
+      }
+    e = cudaMemcpy(g->stp, ptrs.data(), sizeof(CgState*) * ptrs.size(), cudaMemcpyHostToDevice);
+  }
   if (e != cudaSuccess) return fail(cuda_fail(e, "fill_group_init"));
   fill_status fs = mode == FILL_MODE_FP32 ? group_setup<float>(g, autotune, cache_path)
                                           : group_setup<double>(g, autotune, cache_path);
