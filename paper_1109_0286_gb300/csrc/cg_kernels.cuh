@@ -18,8 +18,42 @@ template <typename T> struct KCfg;
 template <> struct KCfg<float> { static constexpr int kMaxThreads = 1024; };
 template <> struct KCfg<double> { static constexpr int kMaxThreads = 512; };
 
-__device__ __forceinline__ bool observed_bit(const uint32_t* __restrict__ obs, long long pix) {
-  return (__ldg(obs + (pix >> 5)) >> (pix & 31)) & 1u;
+// Masked flags and compact CG-vector indices of the pixel pair (pix, pix+1)
+// (pix even): one 8-byte mask-word load and a popcount.
+struct PairIdx {
+  bool m0, m1;   // pixel masked (to fill)
+  int i0, i1;    // compact indices (valid where masked)
+};
+
+__device__ __forceinline__ PairIdx pair_from_word(uint2 w, int pix) {
+  const int b = (int)(pix & 31);
+  const uint32_t mb = ~w.x;
+  PairIdx q;
+  q.m0 = (mb >> b) & 1u;
+  q.m1 = (mb >> (b + 1)) & 1u;
+  q.i0 = (int)w.y + __popc(mb & ((1u << b) - 1u));
+  q.i1 = q.i0 + (q.m0 ? 1 : 0);
+  return q;
+}
+
+__device__ __forceinline__ uint2 mask_word(const uint2* __restrict__ mw, int pix) {
+  return __ldg(mw + (pix >> 5));
+}
+
+__device__ __forceinline__ PairIdx pair_index(const uint2* __restrict__ mw, int pix) {
+  return pair_from_word(mask_word(mw, pix), pix);
+}
+
+// Compact loads / stores of a pixel pair (zero / nothing on observed pixels).
+template <typename T, typename S>
+__device__ __forceinline__ void ldc(const S* v, const PairIdx& q, T& a0, T& a1) {
+  a0 = q.m0 ? (T)v[q.i0] : (T)0;
+  a1 = q.m1 ? (T)v[q.i1] : (T)0;
+}
+template <typename T, typename S>
+__device__ __forceinline__ void stc(S* v, const PairIdx& q, T a0, T a1) {
+  if (q.m0) v[q.i0] = (S)a0;
+  if (q.m1) v[q.i1] = (S)a1;
 }
 
 // ----------------------------------------------------------------- sources
@@ -28,18 +62,16 @@ __device__ __forceinline__ bool observed_bit(const uint32_t* __restrict__ obs, l
 // all its loads before any of its stores (the loads then overlap).
 template <typename T>
 struct SrcIn {
+  uint2 w;   // mask word (indices recomputed where needed)
   T x0, x1, y0, y1, z0, z1, w0, w1;
 };
 
 template <typename T>
-__device__ __forceinline__ void src_load(int op, const InstDesc<T>& I, long long pix, SrcIn<T>& in) {
+__device__ __forceinline__ void src_load(int op, const InstDesc<T>& I, int pix, SrcIn<T>& in) {
   switch (op) {
-    case OP_LOAD_R_MASK:
-    case OP_LOAD_R:
-      ld_pair(I.r + pix, in.x0, in.x1);
-      break;
-    case OP_LOAD_U:
-      ld_pair(I.u + pix, in.x0, in.x1);
+    case OP_LOAD_W_MASK:
+      in.w = mask_word(I.mw, pix);
+      ld_pair(I.w + pix, in.x0, in.x1);
       break;
     case OP_LOAD_Y:
       ld_pair(I.y + pix, in.x0, in.x1);
@@ -47,22 +79,35 @@ __device__ __forceinline__ void src_load(int op, const InstDesc<T>& I, long long
     case OP_LOAD_W:
       ld_pair(I.w + pix, in.x0, in.x1);
       break;
+    case OP_LOAD_R:
+    case OP_LOAD_U: {
+      in.w = mask_word(I.mw, pix);
+      const PairIdx q = pair_from_word(in.w, pix);
+      ldc(op == OP_LOAD_R ? I.r : I.u, q, in.x0, in.x1);
+      break;
+    }
     case OP_P_UPD_Z:
-    case OP_P_UPD_R:
-      ld_pair((op == OP_P_UPD_Z ? I.z : I.r) + pix, in.x0, in.x1);
-      ld_pair(I.p + pix, in.y0, in.y1);
+    case OP_P_UPD_R: {
+      in.w = mask_word(I.mw, pix);
+      const PairIdx q = pair_from_word(in.w, pix);
+      ldc(op == OP_P_UPD_Z ? I.z : I.r, q, in.x0, in.x1);
+      ldc(I.p, q, in.y0, in.y1);
       break;
-    case OP_R_UPD:
-      ld_pair(I.r + pix, in.x0, in.x1);
-      ld_pair(I.q + pix, in.y0, in.y1);
-      ld_pair(I.u + pix, in.z0, in.z1);
-      ld_pair(I.p + pix, in.w0, in.w1);
+    }
+    case OP_R_UPD: {
+      in.w = mask_word(I.mw, pix);
+      const PairIdx q = pair_from_word(in.w, pix);
+      ldc(I.r, q, in.x0, in.x1);
+      ldc(I.q, q, in.y0, in.y1);
+      ldc(I.u, q, in.z0, in.z1);
+      ldc(I.p, q, in.w0, in.w1);
       break;
+    }
     case OP_U64_UPD: {
-      ld_pair(I.u + pix, in.x0, in.x1);
-      const float2 dl = *reinterpret_cast<const float2*>(I.dlt + pix);
-      in.y0 = (T)dl.x;
-      in.y1 = (T)dl.y;
+      in.w = mask_word(I.mw, pix);
+      const PairIdx q = pair_from_word(in.w, pix);
+      ldc(I.u, q, in.x0, in.x1);
+      ldc(I.dlt, q, in.y0, in.y1);
       break;
     }
     default:
@@ -71,14 +116,14 @@ __device__ __forceinline__ void src_load(int op, const InstDesc<T>& I, long long
 }
 
 template <typename T>
-__device__ __forceinline__ void src_apply(int op, const InstDesc<T>& I, long long pix,
+__device__ __forceinline__ void src_apply(int op, const InstDesc<T>& I, int pix,
                                           const SrcIn<T>& in, T alpha, T beta, T& a0, T& a1,
                                           Acc<T>& acc) {
   switch (op) {
-    case OP_LOAD_R_MASK: {
-      const uint32_t w = __ldg(I.obs + (pix >> 5));
-      a0 = ((w >> (pix & 31)) & 1u) ? (T)0 : in.x0;
-      a1 = ((w >> ((pix + 1) & 31)) & 1u) ? (T)0 : in.x1;
+    case OP_LOAD_W_MASK: {
+      const PairIdx q = pair_from_word(in.w, pix);
+      a0 = q.m0 ? in.x0 : (T)0;
+      a1 = q.m1 ? in.x1 : (T)0;
       break;
     }
     case OP_LOAD_R:
@@ -97,22 +142,26 @@ __device__ __forceinline__ void src_apply(int op, const InstDesc<T>& I, long lon
     case OP_P_UPD_R:
       a0 = in.x0 + beta * in.y0;
       a1 = in.x1 + beta * in.y1;
-      st_pair(I.p + pix, a0, a1);
+      stc(I.p, pair_from_word(in.w, pix), a0, a1);
       break;
-    case OP_R_UPD:
+    case OP_R_UPD: {
+      const PairIdx q = pair_from_word(in.w, pix);
       a0 = in.x0 - alpha * in.y0;
       a1 = in.x1 - alpha * in.y1;
-      st_pair(I.r + pix, a0, a1);
-      st_pair(I.u + pix, in.z0 + alpha * in.w0, in.z1 + alpha * in.w1);
+      stc(I.r, q, a0, a1);
+      stc(I.u, q, in.z0 + alpha * in.w0, in.z1 + alpha * in.w1);
       acc.add_prod(a0, a0);
       acc.add_prod(a1, a1);
       break;
-    case OP_U64_UPD:
+    }
+    case OP_U64_UPD: {
+      const PairIdx q = pair_from_word(in.w, pix);
       a0 = in.x0 + in.y0;
       a1 = in.x1 + in.y1;
-      st_pair(I.u + pix, a0, a1);
-      *reinterpret_cast<float2*>(I.dlt + pix) = make_float2(0.f, 0.f);   // folded
+      stc(I.u, q, a0, a1);
+      stc(I.dlt, q, 0.f, 0.f);   // folded
       break;
+    }
     default:
       a0 = a1 = (T)0;
   }
@@ -121,25 +170,25 @@ __device__ __forceinline__ void src_apply(int op, const InstDesc<T>& I, long lon
 // ----------------------------------------------------------------- middles / sinks
 template <typename T>
 struct SinkIn {
+  uint2 w;   // mask word (indices recomputed where needed)
   T x0, x1;
-  uint32_t w;
 };
 
 template <typename T>
-__device__ __forceinline__ void sink_load(int op, const InstDesc<T>& I, long long pix, SinkIn<T>& in) {
-  in.w = __ldg(I.obs + (pix >> 5));
+__device__ __forceinline__ void sink_load(int op, const InstDesc<T>& I, int pix, SinkIn<T>& in) {
+  in.w = mask_word(I.mw, pix);
   switch (op) {
     case OP_Y_W:
       ld_pair(I.d + pix, in.x0, in.x1);
       break;
     case OP_Q:
-      ld_pair(I.p + pix, in.x0, in.x1);
+      ldc(I.p, pair_from_word(in.w, pix), in.x0, in.x1);
       break;
     case OP_Z:
-      ld_pair(I.r + pix, in.x0, in.x1);
+      ldc(I.r, pair_from_word(in.w, pix), in.x0, in.x1);
       break;
     case OP_RES:
-      ld_pair(I.b + pix, in.x0, in.x1);
+      ldc(I.b, pair_from_word(in.w, pix), in.x0, in.x1);
       break;
     case OP_GRAD:
       ld_pair(I.gx + pix, in.x0, in.x1);
@@ -150,9 +199,10 @@ __device__ __forceinline__ void sink_load(int op, const InstDesc<T>& I, long lon
 }
 
 template <typename T>
-__device__ __forceinline__ void sink_apply(int op, const InstDesc<T>& I, long long pix,
+__device__ __forceinline__ void sink_apply(int op, const InstDesc<T>& I, int pix,
                                            const SinkIn<T>& in, T& a0, T& a1, Acc<T>& acc) {
-  const bool o0 = (in.w >> (pix & 31)) & 1u, o1 = (in.w >> ((pix + 1) & 31)) & 1u;
+  const int b = (int)(pix & 31);
+  const bool o0 = (in.w.x >> b) & 1u, o1 = (in.w.x >> (b + 1)) & 1u;   // observed
   switch (op) {
     case OP_MASK:
       a0 = o0 ? (T)0 : a0;
@@ -166,28 +216,37 @@ __device__ __forceinline__ void sink_apply(int op, const InstDesc<T>& I, long lo
     case OP_STORE_Y:
       st_pair(I.y + pix, a0, a1);
       break;
+    case OP_STORE_Y_MASK:
+      st_pair(I.y + pix, o0 ? (T)0 : a0, o1 ? (T)0 : a1);
+      break;
     case OP_Q:
     case OP_Z:
       a0 = o0 ? (T)0 : a0;
       a1 = o1 ? (T)0 : a1;
-      st_pair((op == OP_Q ? I.q : I.z) + pix, a0, a1);
+      stc(op == OP_Q ? I.q : I.z, pair_from_word(in.w, pix), a0, a1);
       acc.add_prod(in.x0, a0);
       acc.add_prod(in.x1, a1);
       break;
     case OP_B:
       a0 = o0 ? (T)0 : -a0;
       a1 = o1 ? (T)0 : -a1;
-      st_pair(I.r + pix, a0, a1);
-      if (I.b) st_pair(I.b + pix, a0, a1);
-      if (I.r32) *reinterpret_cast<float2*>(I.r32 + pix) = make_float2((float)a0, (float)a1);
+      {
+        const PairIdx q = pair_from_word(in.w, pix);
+        stc(I.r, q, a0, a1);
+        if (I.b) stc(I.b, q, a0, a1);
+        if (I.r32) stc(I.r32, q, a0, a1);
+      }
       acc.add_prod(a0, a0);
       acc.add_prod(a1, a1);
       break;
     case OP_RES:
       a0 = in.x0 - (o0 ? (T)0 : a0);
       a1 = in.x1 - (o1 ? (T)0 : a1);
-      st_pair(I.r + pix, a0, a1);
-      if (I.r32) *reinterpret_cast<float2*>(I.r32 + pix) = make_float2((float)a0, (float)a1);
+      {
+        const PairIdx q = pair_from_word(in.w, pix);
+        stc(I.r, q, a0, a1);
+        if (I.r32) stc(I.r32, q, a0, a1);
+      }
       acc.add_prod(a0, a0);
       acc.add_prod(a1, a1);
       break;
@@ -219,27 +278,23 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
   const InstDesc<T>& I = insts[blockIdx.y];
   if (skip_instance(a.check_done, I.st)) return;
 
-  const int rows = a.rows;
+  const int rows = a.rows, lr = a.log_rows;
   const int row = threadIdx.x / TT, tid = threadIdx.x - row * TT;
   const int y0 = blockIdx.x * rows, y = y0 + row;
   const int ny = a.ny, nx = a.nx;
   const int tstride = rows + 1;
   const XBuf<T> xb(sm + row * 2 * PADL, PADL);
-  T* tre = sm;
-  T* tim = sm + (L + 1) * tstride;
+  cx<T>* tile = reinterpret_cast<cx<T>*>(sm);   // [(L+1)][rows+1], aliases the FFT areas
   constexpr int TWS = kLmax / (2 * L);   // W_{nx}^k = table[k * TWS]
-  const long long rowpix = (long long)y * nx;
-
+  const int rowpix = y * nx;
   cx<T> v[16];
   Acc<T> acc;
 
   if constexpr (IN_SPEC) {
-    const T* spec = a.spec_sel ? I.spec2 : I.spec;
+    const T* spec = (a.spec_sel ? I.spec2 : I.spec) + 2 * y0;
     for (int e = threadIdx.x; e < (L + 1) * rows; e += blockDim.x) {
-      const int k = e / rows, rr = e - k * rows;
-      const cx<T> s = ld_cx<T>(spec + 2 * ((long long)k * ny + y0 + rr));
-      tre[k * tstride + rr] = s.r;
-      tim[k * tstride + rr] = s.i;
+      const int k = e >> lr, rr = e & (rows - 1);
+      tile[k * tstride + rr] = ld_cx<T>(spec + 2 * (k * ny + rr));
     }
     if (threadIdx.x < 16) wcol[threadIdx.x] = twiddle<T>(tw, threadIdx.x * TT * TWS);
     __syncthreads();
@@ -248,8 +303,8 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       const int k = tid + e * TT;
-      cx<T> xk{tre[k * tstride + row], tim[k * tstride + row]};
-      cx<T> xc{tre[(L - k) * tstride + row], -tim[(L - k) * tstride + row]};
+      cx<T> xk = tile[k * tstride + row];
+      cx<T> xc = conjx(tile[(L - k) * tstride + row]);
       if (k == 0) {
         xk.i = (T)0;
         xc.i = (T)0;
@@ -261,6 +316,26 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
     }
     fft_regs<T, LOG_L, true>(v, xb, tid, tw);
     // v[e] = x[2j] + i x[2j+1], j = tid + e TT
+    if constexpr (OUT_SPEC) {
+      // middle of a chain: P_x (OP_MASK) or y = v, v = (d - y) on U (OP_Y_W)
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int pix = rowpix + 2 * (tid + e * TT);
+        const uint32_t ob = __ldg(&I.mw[pix >> 5].x);
+        const int b = (int)(pix & 31);
+        const bool o0 = (ob >> b) & 1u, o1 = (ob >> (b + 1)) & 1u;
+        if (a.op == OP_Y_W) {
+          T d0, d1;
+          ld_pair(I.d + pix, d0, d1);
+          st_pair(I.y + pix, v[e].r, v[e].i);
+          v[e].r = o0 ? d0 - v[e].r : (T)0;
+          v[e].i = o1 ? d1 - v[e].i : (T)0;
+        } else {
+          v[e].r = o0 ? (T)0 : v[e].r;
+          v[e].i = o1 ? (T)0 : v[e].i;
+        }
+      }
+    } else {
     constexpr int CK = 4;   // pixel pairs whose loads are issued together
 #pragma unroll
     for (int h = 0; h < 16; h += CK) {
@@ -270,6 +345,7 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
 #pragma unroll
       for (int e = 0; e < CK; ++e)
         sink_apply<T>(a.op, I, rowpix + 2 * (tid + (h + e) * TT), in[e], v[h + e].r, v[h + e].i, acc);
+    }
     }
   } else if constexpr (XI) {
 #pragma unroll
@@ -314,21 +390,13 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
     }
     __syncthreads();
 #pragma unroll
-    for (int e = 0; e < 16; ++e) {
-      const int k = tid + e * TT;
-      tre[k * tstride + row] = v[e].r;
-      tim[k * tstride + row] = v[e].i;
-    }
-    if (tid == 0) {
-      tre[L * tstride + row] = nyq.r;
-      tim[L * tstride + row] = nyq.i;
-    }
+    for (int e = 0; e < 16; ++e) tile[(tid + e * TT) * tstride + row] = v[e];
+    if (tid == 0) tile[L * tstride + row] = nyq;
     __syncthreads();
-    T* spec = a.spec_sel ? I.spec2 : I.spec;
+    T* spec = (a.spec_sel ? I.spec2 : I.spec) + 2 * y0;
     for (int e = threadIdx.x; e < (L + 1) * rows; e += blockDim.x) {
-      const int k = e / rows, rr = e - k * rows;
-      st_cx<T>(spec + 2 * ((long long)k * ny + y0 + rr),
-               cx<T>{tre[k * tstride + rr], tim[k * tstride + rr]});
+      const int k = e >> lr, rr = e & (rows - 1);
+      st_cx<T>(spec + 2 * (k * ny + rr), tile[k * tstride + rr]);
     }
   }
 
@@ -380,72 +448,65 @@ k_vec(const InstDesc<T>* __restrict__ insts, VecArgs a) {
   const InstDesc<T>& I = insts[blockIdx.y];
   if (skip_instance(a.check_done, I.st)) return;
   Acc<T> acc;
-  const T alpha = (T)I.st->alpha;
-  const long long npair = a.npix >> 1;
-  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < npair;
-       j += (long long)gridDim.x * blockDim.x) {
-    const long long pix = 2 * j;
-    switch (a.op) {
-      case VOP_UPDATE: {
-        T r0, r1, q0, q1, u0, u1, p0, p1;
-        ld_pair(I.r + pix, r0, r1);
-        ld_pair(I.q + pix, q0, q1);
-        ld_pair(I.u + pix, u0, u1);
-        ld_pair(I.p + pix, p0, p1);
-        r0 -= alpha * q0;
-        r1 -= alpha * q1;
-        st_pair(I.r + pix, r0, r1);
-        st_pair(I.u + pix, u0 + alpha * p0, u1 + alpha * p1);
-        acc.add_prod(r0, r0);
-        acc.add_prod(r1, r1);
-        break;
+  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long gstride = (long long)gridDim.x * blockDim.x;
+  if (a.op == VOP_UPDATE || a.op == VOP_ZERO_UP) {
+    // compact CG vectors: one element per masked pixel
+    const T alpha = (T)I.st->alpha;
+    for (long long i = gid; i < I.nvec; i += gstride) {
+      if (a.op == VOP_ZERO_UP) {
+        I.u[i] = (T)0;
+        I.p[i] = (T)0;
+      } else {
+        const T r = I.r[i] - alpha * I.q[i];
+        I.r[i] = r;
+        I.u[i] = I.u[i] + alpha * I.p[i];
+        acc.add_prod(r, r);
       }
-      case VOP_ASSEMBLE: {
-        const uint32_t w = __ldg(I.obs + (pix >> 5));
-        const bool o0 = (w >> (pix & 31)) & 1u, o1 = (w >> ((pix + 1) & 31)) & 1u;
-        T d0, d1, y0, y1, u0, u1;
-        ld_pair(I.d + pix, d0, d1);
-        ld_pair(I.y + pix, y0, y1);
-        ld_pair(I.u + pix, u0, u1);
-        st_pair(I.out + pix, o0 ? d0 : y0 + u0, o1 ? d1 : y1 + u1);
-        break;
+    }
+  } else {
+    // pixel pairs of the full maps
+    for (long long j = gid; j < (a.npix >> 1); j += gstride) {
+      const int pix = 2 * j;
+      const PairIdx q = pair_index(I.mw, pix);
+      switch (a.op) {
+        case VOP_ASSEMBLE: {
+          T d0, d1, y0, y1, u0, u1;
+          ld_pair(I.d + pix, d0, d1);
+          ld_pair(I.y + pix, y0, y1);
+          ldc(I.u, q, u0, u1);
+          st_pair(I.out + pix, q.m0 ? y0 + u0 : d0, q.m1 ? y1 + u1 : d1);
+          break;
+        }
+        case VOP_COPY_D: {
+          T d0, d1;
+          ld_pair(I.d + pix, d0, d1);
+          st_pair(I.out + pix, d0, d1);
+          break;
+        }
+        case VOP_MAKE_W: {
+          T d0, d1, y0, y1, u0, u1;
+          ld_pair(I.d + pix, d0, d1);
+          ld_pair(I.y + pix, y0, y1);
+          ldc(I.u, q, u0, u1);
+          st_pair(I.w + pix, q.m0 ? u0 : d0 - y0, q.m1 ? u1 : d1 - y1);
+          break;
+        }
+        case VOP_LOAD_G: {
+          T g0, g1;
+          ld_pair(I.gx + pix, g0, g1);
+          g0 = q.m0 ? g0 : (T)0;
+          g1 = q.m1 ? g1 : (T)0;
+          stc(I.r, q, g0, g1);
+          stc(I.b, q, g0, g1);
+          if (I.r32) stc(I.r32, q, g0, g1);
+          acc.add_prod(g0, g0);
+          acc.add_prod(g1, g1);
+          break;
+        }
+        default:
+          break;
       }
-      case VOP_MAKE_W: {
-        const uint32_t w = __ldg(I.obs + (pix >> 5));
-        const bool o0 = (w >> (pix & 31)) & 1u, o1 = (w >> ((pix + 1) & 31)) & 1u;
-        T d0, d1, y0, y1, u0, u1;
-        ld_pair(I.d + pix, d0, d1);
-        ld_pair(I.y + pix, y0, y1);
-        ld_pair(I.u + pix, u0, u1);
-        st_pair(I.w + pix, o0 ? d0 - y0 : u0, o1 ? d1 - y1 : u1);
-        break;
-      }
-      case VOP_LOAD_G: {
-        const uint32_t w = __ldg(I.obs + (pix >> 5));
-        const bool o0 = (w >> (pix & 31)) & 1u, o1 = (w >> ((pix + 1) & 31)) & 1u;
-        T g0, g1;
-        ld_pair(I.gx + pix, g0, g1);
-        g0 = o0 ? (T)0 : g0;
-        g1 = o1 ? (T)0 : g1;
-        st_pair(I.r + pix, g0, g1);
-        st_pair(I.b + pix, g0, g1);
-        if (I.r32) *reinterpret_cast<float2*>(I.r32 + pix) = make_float2((float)g0, (float)g1);
-        acc.add_prod(g0, g0);
-        acc.add_prod(g1, g1);
-        break;
-      }
-      case VOP_ZERO_UP:
-        st_pair(I.u + pix, (T)0, (T)0);
-        st_pair(I.p + pix, (T)0, (T)0);
-        break;
-      case VOP_COPY_D: {
-        T d0, d1;
-        ld_pair(I.d + pix, d0, d1);
-        st_pair(I.out + pix, d0, d1);
-        break;
-      }
-      default:
-        break;
     }
   }
   if (a.sop != SC_NONE)

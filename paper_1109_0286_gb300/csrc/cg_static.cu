@@ -57,7 +57,7 @@ Layout layout(int ny, int nx) {
   L.tw = o;   o = align256(o + 2 * sizeof(float) * kLmax);
   L.tab = o;  o = align256(o + sizeof(float) * nkx * ny);
   L.spec = o; o = align256(o + 2 * sizeof(float) * nkx * ny);
-  L.bits = o; o = align256(o + sizeof(uint32_t) * ((npix + 31) / 32));
+  L.bits = o; o = align256(o + sizeof(uint2) * ((npix + 31) / 32));
   L.desc = o; o = align256(o + sizeof(InstDesc<float>));
   L.st = o;   o = align256(o + sizeof(CgState));
   L.part = o; o = align256(o + sizeof(double) * kMaxPartials);
@@ -77,7 +77,7 @@ __global__ void k_static_setup(unsigned char* base, Layout L, int ny, int nx, co
   const long long nthr = (long long)gridDim.x * blockDim.x;
   float* tw = reinterpret_cast<float*>(base + L.tw);
   float* tab = reinterpret_cast<float*>(base + L.tab);
-  uint32_t* bits = reinterpret_cast<uint32_t*>(base + L.bits);
+  uint2* bits = reinterpret_cast<uint2*>(base + L.bits);
   for (long long m = tid; m < kLmax; m += nthr) {
     double s, c;
     sincospi(2.0 * double(m) / double(kLmax), &s, &c);
@@ -95,19 +95,18 @@ __global__ void k_static_setup(unsigned char* base, Layout L, int ny, int nx, co
       const long long i = w * 32 + b;
       if (i < npix && (observed == nullptr || observed[i])) word |= 1u << b;
     }
-    bits[w] = word;
+    bits[w] = make_uint2(word, 0u);   // compact offsets unused by these passes
   }
   if (tid == 0) {
     CgState* st = reinterpret_cast<CgState*>(base + L.st);
     *st = CgState{};
     InstDesc<float> D{};
-    D.obs = bits;
+    D.mw = bits;
     D.t_inv = tab;
     D.t_sqrt = tab;
     D.spec = reinterpret_cast<float*>(base + L.spec);
-    D.r = const_cast<float*>(in);   // read only (the source pass)
-    D.y = out;                      // unmasked sink
-    D.z = out;                      // masked sink
+    D.w = const_cast<float*>(in);   // read only (the source pass)
+    D.y = out;                      // the sink
     D.st = st;
     D.partial = reinterpret_cast<double*>(base + L.part);
     *reinterpret_cast<InstDesc<float>*>(base + L.desc) = D;
@@ -161,11 +160,12 @@ extern "C" fill_status fill_apply_static(int ny, int nx, const double* P_half,
   if (rows > ny) rows = ny;
   int ffts = TN >= 256 ? 1 : 256 / TN;
   if (ffts > nx / 2 + 1) ffts = nx / 2 + 1;
-  RowArgs ra{ny, nx, rows, masked ? OP_LOAD_R_MASK : OP_LOAD_R, SC_NONE, SKIP_NEVER, 0};
+  const int lr = pow2_log(rows);
+  RowArgs ra{ny, nx, rows, lr, masked ? OP_LOAD_W_MASK : OP_LOAD_W, SC_NONE, SKIP_NEVER, 0};
   if (Launch<float>::row(log_l, false, true, desc, 1, ra, tw, s) != cudaSuccess) return FILL_ECUDA;
   ColArgs ca{ny, nx / 2 + 1, ffts, 0, SKIP_NEVER, 0};
   if (Launch<float>::col(log_n, desc, 1, ca, tw, s) != cudaSuccess) return FILL_ECUDA;
-  RowArgs rb{ny, nx, rows, masked ? OP_Z : OP_STORE_Y, SC_NONE, SKIP_NEVER, 0};
+  RowArgs rb{ny, nx, rows, lr, masked ? OP_STORE_Y_MASK : OP_STORE_Y, SC_NONE, SKIP_NEVER, 0};
   if (Launch<float>::row(log_l, true, false, desc, 1, rb, tw, s) != cudaSuccess) return FILL_ECUDA;
   return FILL_OK;
 }

@@ -1,13 +1,16 @@
 // Shared host/device data structures of the constrained-realization solver.
 //
 // Layout on the device, per realization ("instance"):
-//   * real maps (d, y, u, r, p, q, z, b, out): row-major ny x nx, 0 outside M
-//     for the CG vectors (the masked system of Sect. 2.4 lives on M only);
+//   * full maps (d, y, w, out, gx): row-major ny x nx;
+//   * CG vectors (r, p, q, z, u, b and the mixed-mode r32 / dlt): COMPACT,
+//     one value per masked pixel in row-major order (the masked system of
+//     Sect. 2.4 lives on M only; the vectors are zero on U);
 //   * half spectrum "spec": transposed, (nx/2+1) rows of ny complex values,
 //     spec[kx * ny + y]; the column pass runs along contiguous rows;
 //   * spectral tables [kx][ky] (same transposed layout), real, with the
 //     1/n of the inverse DFT folded in;
-//   * observation mask: one bit per pixel, bit 1 = observed (constraint).
+//   * mask words: for each 32 pixels, the observed bits (1 = constraint) and
+//     the compact index of the word's first masked pixel.
 #pragma once
 #include <cstdint>
 
@@ -42,7 +45,7 @@ struct CgState {
 // Per-instance pointers handed to every kernel (element type T of the pass).
 template <typename T>
 struct InstDesc {
-  const uint32_t* obs;     // observed-pixel bits
+  const uint2* mw;         // mask words: x = observed bits, y = compact offset
   const T* t_inv;          // 1 / (n P)     [kx][ky]
   const T* t_sqrt;         // sqrt(P) / n   [kx][ky]
   T* spec;                 // interleaved complex half spectrum, transposed
@@ -63,6 +66,7 @@ struct InstDesc {
   CgState* st;
   double* partial;         // per-CTA partial sums
   double* hist;            // residual history (hist_cap entries), or null
+  long long nvec;          // compact CG-vector length: masked pixels of this instance
   unsigned long long seed;
 };
 
@@ -75,7 +79,7 @@ enum RowOp : int {
   OP_P_UPD_R = 4,   // p = r + beta p; store p; v = p   (no preconditioner)
   OP_R_UPD = 5,     // r -= alpha q; u += alpha p; store; acc ||r||^2; v = r
   OP_U64_UPD = 6,   // u += (double) dlt; store; v = u  (mixed refinement)
-  OP_LOAD_R_MASK = 7,  // v = P_x r
+  OP_LOAD_W_MASK = 7,  // v = P_x w (full maps; operator checks)
   OP_LOAD_U = 8,    // v = u
   OP_LOAD_Y = 9,    // v = y
   // middles (input spectrum -> output spectrum)
@@ -83,6 +87,7 @@ enum RowOp : int {
   OP_Y_W = 11,      // store y = v; v = (d - y) on U, 0 on M
   // sinks (input spectrum, no output spectrum)
   OP_STORE_Y = 20,  // store y = v
+  OP_STORE_Y_MASK = 27,  // store y = P_x v (full maps; operator checks)
   OP_Q = 21,        // q = P_x v; store; acc p^T q
   OP_Z = 22,        // z = P_x v; store; acc r^T z
   OP_B = 23,        // b = -P_x v; store r = b (and b); acc ||b||^2
@@ -124,7 +129,8 @@ enum VecOp : int {
 // Launch arguments of the pass kernels.
 struct RowArgs {
   int ny, nx;       // grid (nx = 2 L)
-  int rows;         // rows per CTA
+  int rows;         // rows per CTA (power of two)
+  int log_rows;     // log2(rows)
   int op;           // RowOp
   int sop;          // ScalarOp (SC_NONE: no reduction)
   int check_done;   // skip instances whose CG state is done

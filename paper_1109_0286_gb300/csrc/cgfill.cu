@@ -103,7 +103,8 @@ struct fill_plan {
   cudaStream_t s = nullptr;      // caller's stream
   cudaStream_t cap = nullptr;    // plan-owned stream for graph capture
   cudaStream_t cap2 = nullptr;   // second capture stream (conditional bodies)
-  uint32_t* obs = nullptr;
+  uint2* mw = nullptr;           // mask words: observed bits, compact offset
+  long long nv = 0;              // compact vector stride per instance (>= nmasked)
   std::vector<double> P_half;    // host copy of the spectrum
   long long launches = 0;        // kernels issued by the current call
   cudaGraphExec_t mixed_graph = nullptr;   // reliable-update mixed CG loop
@@ -254,7 +255,7 @@ template <typename T>
 cudaError_t row(const Ctx<T>& c, cudaStream_t s, int op, int sop, bool in_spec, bool out_spec,
                 int skip, int spec_sel = 0) {
   ++*c.launches;
-  RowArgs a{c.ny, c.nx, c.rows, op, sop, skip, spec_sel};
+  RowArgs a{c.ny, c.nx, c.rows, ilog2(c.rows), op, sop, skip, spec_sel};
   return Launch<T>::row(c.log_l, in_spec, out_spec, c.desc, c.ninst, a, c.tw, s);
 }
 
@@ -473,8 +474,8 @@ fill_status mixed_refine(fill_plan* p, double tol) {
     ++p->launches;
     k_inner_reset<<<nb, 128, 0, p->s>>>(p->f.st, p->g.st, B, tol, p->o.inner_tol, p->o.max_iter);
     CK(cudaGetLastError());
-    CK(cudaMemsetAsync(p->f.u, 0, B * n * sizeof(float), p->s));
-    CK(cudaMemsetAsync(p->f.p, 0, B * n * sizeof(float), p->s));
+    CK(cudaMemsetAsync(p->f.u, 0, B * p->nv * sizeof(float), p->s));
+    CK(cudaMemsetAsync(p->f.p, 0, B * p->nv * sizeof(float), p->s));
     CK(pcg_start<float>(p, p->s, SC_BB));
     fill_status fs = run_pcg<float>(p);
     if (fs != FILL_OK) return fs;
@@ -621,8 +622,8 @@ fill_status mixed_reliable(fill_plan* p, double tol) {
   ++p->launches;
   k_link_states<<<nb, 128, 0, p->s>>>(p->f.st, p->g.st, B, d * d);
   CK(cudaGetLastError());
-  CK(cudaMemsetAsync(p->f.u, 0, B * n * sizeof(float), p->s));
-  CK(cudaMemsetAsync(p->f.p, 0, B * n * sizeof(float), p->s));
+  CK(cudaMemsetAsync(p->f.u, 0, B * p->nv * sizeof(float), p->s));
+  CK(cudaMemsetAsync(p->f.p, 0, B * p->nv * sizeof(float), p->s));
   // instances with b = 0 are done in the FP64 state: mirror that to FP32
   ++p->launches;
   k_inner_reset<<<nb, 128, 0, p->s>>>(p->f.st, p->g.st, B, tol, 0.0, p->o.max_iter);
@@ -702,7 +703,7 @@ fill_status backward_t(fill_plan* p, const void* d, long long d_stride, const vo
   CK(vec<T>(p, p->s, VOP_MAKE_W, SC_NONE, false));
   const bool mixed = p->o.mode == FILL_MODE_MIXED;
   CK(init_states<T>(p, tol));
-  CK(cudaMemsetAsync(P.u, 0, B * n * sizeof(T), p->s));
+  CK(cudaMemsetAsync(P.u, 0, B * p->nv * sizeof(T), p->s));
   if (mixed) {
     fill_desc<float>(p, nullptr, 0, nullptr, nullptr, nullptr);
     CK(upload_desc<float>(p));
@@ -711,7 +712,7 @@ fill_status backward_t(fill_plan* p, const void* d, long long d_stride, const vo
     fill_status fs = mixed_solve(p, tol);
     if (fs != FILL_OK) return fs;
   } else {
-    CK(cudaMemsetAsync(P.p, 0, B * n * sizeof(T), p->s));
+    CK(cudaMemsetAsync(P.p, 0, B * p->nv * sizeof(T), p->s));
     CK(vec<T>(p, p->s, VOP_LOAD_G, p->o.precond ? SC_BB : SC_BB_RHO, false));
     CK(pcg_start<T>(p, p->s, SC_NONE));
     fill_status fs = run_pcg<T>(p);
@@ -756,15 +757,16 @@ fill_status setup_precision(fill_plan* p, const std::vector<double>& tinv,
                             const std::vector<double>& tsqrt, const std::vector<double>& tw) {
   Precision<T>& P = prec<T>(p);
   P.used = true;
-  const size_t B = p->batch, n = p->npix;
+  const size_t B = p->batch, n = p->npix, nv = p->nv;
   const size_t nspec = 2 * size_t(p->nx / 2 + 1) * p->ny;
-  T** vecs[] = {&P.r, &P.p, &P.q, &P.z, &P.u, &P.y, &P.b};
-  for (T** v : vecs)
-    if (p->dalloc(v, B * n) != cudaSuccess) return FILL_ENOMEM;
+  T** cvecs[] = {&P.r, &P.p, &P.q, &P.z, &P.u, &P.b};   // compact CG vectors
+  for (T** v : cvecs)
+    if (p->dalloc(v, B * nv) != cudaSuccess) return FILL_ENOMEM;
+  if (p->dalloc(&P.y, B * n) != cudaSuccess || p->dalloc(&P.w, B * n) != cudaSuccess)
+    return FILL_ENOMEM;
   if (p->dalloc(&P.spec, B * nspec) != cudaSuccess) return FILL_ENOMEM;
   if (p->o.backward) {
-    if (p->dalloc(&P.w, B * n) != cudaSuccess || p->dalloc(&P.spec2, B * nspec) != cudaSuccess)
-      return FILL_ENOMEM;
+    if (p->dalloc(&P.spec2, B * nspec) != cudaSuccess) return FILL_ENOMEM;
   }
   const size_t ntab = size_t(p->nx / 2 + 1) * p->ny;
   if (p->dalloc(&P.t_inv, ntab) != cudaSuccess || p->dalloc(&P.t_sqrt, ntab) != cudaSuccess ||
@@ -791,8 +793,8 @@ fill_status setup_precision(fill_plan* p, const std::vector<double>& tinv,
   CK(cudaMemcpy(P.t_inv, a.data(), ntab * sizeof(T), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(P.t_sqrt, b2.data(), ntab * sizeof(T), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(P.tw, w.data(), w.size() * sizeof(T), cudaMemcpyHostToDevice));
-  CK(cudaMemset(P.u, 0, B * n * sizeof(T)));
-  CK(cudaMemset(P.p, 0, B * n * sizeof(T)));
+  CK(cudaMemset(P.u, 0, B * nv * sizeof(T)));
+  CK(cudaMemset(P.p, 0, B * nv * sizeof(T)));
   P.rows = p->o.rows_per_cta > 0 ? std::min(p->o.rows_per_cta, p->ny) : default_rows<T>(p->log_l, p->ny);
   P.ffts = p->o.ffts_per_cta > 0 ? p->o.ffts_per_cta : default_ffts<T>(p->log_n, p->nx / 2 + 1);
   const int TT = (1 << p->log_l) / 16;
@@ -804,19 +806,20 @@ fill_status setup_precision(fill_plan* p, const std::vector<double>& tinv,
   CK(Launch<T>::prepare());
   for (size_t i = 0; i < B; ++i) {
     InstDesc<T> D{};
-    D.obs = p->obs;
+    D.mw = p->mw;
+    D.nvec = p->nmasked;
     D.t_inv = P.t_inv;
     D.t_sqrt = P.t_sqrt;
     D.spec = P.spec + i * nspec;
     D.spec2 = P.spec2 ? P.spec2 + i * nspec : nullptr;
-    D.w = P.w ? P.w + i * n : nullptr;
-    D.r = P.r + i * n;
-    D.p = P.p + i * n;
-    D.q = P.q + i * n;
-    D.z = P.z + i * n;
-    D.u = P.u + i * n;
+    D.w = P.w + i * n;
+    D.r = P.r + i * nv;
+    D.p = P.p + i * nv;
+    D.q = P.q + i * nv;
+    D.z = P.z + i * nv;
+    D.u = P.u + i * nv;
     D.y = P.y + i * n;
-    D.b = P.b + i * n;
+    D.b = P.b + i * nv;
     D.st = P.st + i;
     D.partial = P.partial + i * kMaxPartials;
     D.hist = P.hist + i * hc;
@@ -906,13 +909,18 @@ fill_status fill_init(fill_plan** out, int ny, int nx, const double* P_half,
     }
   const long long npix = (long long)ny * nx;
   long long nmasked = 0;
-  std::vector<uint32_t> bits((npix + 31) / 32, 0u);
-  for (long long i = 0; i < npix; ++i) {
-    if (observed[i] > 1) return FILL_EINVAL;
-    if (observed[i])
-      bits[i >> 5] |= 1u << (i & 31);
-    else
-      ++nmasked;
+  std::vector<uint2> words((npix + 31) / 32, make_uint2(0u, 0u));
+  for (long long w = 0; w < (long long)words.size(); ++w) {
+    words[w].y = (unsigned int)nmasked;   // compact index of the word's first masked pixel
+    for (int b = 0; b < 32; ++b) {
+      const long long i = w * 32 + b;
+      if (i >= npix) break;
+      if (observed[i] > 1) return FILL_EINVAL;
+      if (observed[i])
+        words[w].x |= 1u << b;
+      else
+        ++nmasked;
+    }
   }
   fill_plan* p = new (std::nothrow) fill_plan();
   if (!p) return FILL_ENOMEM;
@@ -923,6 +931,7 @@ fill_status fill_init(fill_plan** out, int ny, int nx, const double* P_half,
   p->batch = o.batch;
   p->npix = npix;
   p->nmasked = nmasked;
+  p->nv = std::max<long long>(64, (nmasked + 63) / 64 * 64);
   p->o = o;
   p->s = reinterpret_cast<cudaStream_t>(stream);
   p->P_half.assign(P_half, P_half + (size_t)ny * nkx);
@@ -934,10 +943,10 @@ fill_status fill_init(fill_plan** out, int ny, int nx, const double* P_half,
   cudaError_t e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap2, cudaStreamNonBlocking);
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaStreamCreate"));
-  if (p->dalloc(&p->obs, bits.size()) != cudaSuccess) return fail(FILL_ENOMEM);
+  if (p->dalloc(&p->mw, words.size()) != cudaSuccess) return fail(FILL_ENOMEM);
   if (p->dalloc(&p->loop_counter, 2) != cudaSuccess || p->halloc(&p->hloop, 2) != cudaSuccess)
     return fail(FILL_ENOMEM);
-  e = cudaMemcpy(p->obs, bits.data(), bits.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+  e = cudaMemcpy(p->mw, words.data(), words.size() * sizeof(uint2), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return fail(cuda_fail(e, "upload mask"));
   // Tables [kx][ky] with the inverse DFT's 1/n folded in.
   std::vector<double> tinv((size_t)nkx * ny), tsqrt((size_t)nkx * ny), tw;
@@ -994,8 +1003,8 @@ fill_status fill_realize(fill_plan* p, const void* d, long long d_stride, const 
       fill_desc<float>(p, d, d_stride, seeds, out, nullptr);
       CK(upload_desc<float>(p));
       CK(init_states<float>(p, tol));
-      CK(cudaMemsetAsync(p->f.u, 0, B * n * sizeof(float), p->s));
-      CK(cudaMemsetAsync(p->f.p, 0, B * n * sizeof(float), p->s));
+      CK(cudaMemsetAsync(p->f.u, 0, B * p->nv * sizeof(float), p->s));
+      CK(cudaMemsetAsync(p->f.p, 0, B * p->nv * sizeof(float), p->s));
       CK(draw_and_rhs<float>(p, p->s, !p->o.precond));
       CK(pcg_start<float>(p, p->s, SC_NONE));
       fs = run_pcg<float>(p);
@@ -1006,8 +1015,8 @@ fill_status fill_realize(fill_plan* p, const void* d, long long d_stride, const 
       fill_desc<double>(p, d, d_stride, seeds, out, nullptr);
       CK(upload_desc<double>(p));
       CK(init_states<double>(p, tol));
-      CK(cudaMemsetAsync(p->g.u, 0, B * n * sizeof(double), p->s));
-      CK(cudaMemsetAsync(p->g.p, 0, B * n * sizeof(double), p->s));
+      CK(cudaMemsetAsync(p->g.u, 0, B * p->nv * sizeof(double), p->s));
+      CK(cudaMemsetAsync(p->g.p, 0, B * p->nv * sizeof(double), p->s));
       CK(draw_and_rhs<double>(p, p->s, !p->o.precond));
       CK(pcg_start<double>(p, p->s, SC_NONE));
       fs = run_pcg<double>(p);
@@ -1023,7 +1032,7 @@ fill_status fill_realize(fill_plan* p, const void* d, long long d_stride, const 
     CK(upload_desc<float>(p));
     CK(init_states<double>(p, tol));
     CK(init_states<float>(p, p->o.inner_tol));
-    CK(cudaMemsetAsync(p->g.u, 0, B * n * sizeof(double), p->s));
+    CK(cudaMemsetAsync(p->g.u, 0, B * p->nv * sizeof(double), p->s));
     CK(draw_and_rhs<double>(p, p->s, false));
     fs = mixed_solve(p, tol);
     if (fs != FILL_OK) return fs;
@@ -1071,13 +1080,13 @@ fill_status apply_t(fill_plan* p, int which, const void* in, void* out) {
   fill_desc<T>(p, nullptr, 0, nullptr, nullptr, nullptr);
   CK(upload_desc<T>(p));
   CK(init_states<T>(p, 0.0));
-  CK(cudaMemcpyAsync(P.r, in, n * sizeof(T), cudaMemcpyDeviceToDevice, p->s));
+  CK(cudaMemcpyAsync(P.w, in, n * sizeof(T), cudaMemcpyDeviceToDevice, p->s));
   const bool masked = which >= 2;
   const int table = (which == 0 || which == 2) ? 0 : 1;
-  CK(row<T>(p, p->s, masked ? OP_LOAD_R_MASK : OP_LOAD_R, SC_NONE, false, true, false, 1));
+  CK(row<T>(p, p->s, masked ? OP_LOAD_W_MASK : OP_LOAD_W, SC_NONE, false, true, false, 1));
   CK(col<T>(p, p->s, table, false, 1));
-  CK(row<T>(p, p->s, masked ? OP_Z : OP_STORE_Y, SC_NONE, true, false, false, 1));
-  CK(cudaMemcpyAsync(out, masked ? P.z : P.y, n * sizeof(T), cudaMemcpyDeviceToDevice, p->s));
+  CK(row<T>(p, p->s, masked ? OP_STORE_Y_MASK : OP_STORE_Y, SC_NONE, true, false, false, 1));
+  CK(cudaMemcpyAsync(out, P.y, n * sizeof(T), cudaMemcpyDeviceToDevice, p->s));
   CK(cudaStreamSynchronize(p->s));
   return FILL_OK;
 }
@@ -1133,13 +1142,15 @@ fill_status time_pass_t(fill_plan* p, int pass, int reps, double* ms, double* by
       default: return row<T>(p, s, OP_MASK, SC_NONE, true, true, false);
     }
   };
+  // compact CG vectors (nM values), mask words (8 bytes per 32 pixels)
+  const double nM = double(p->nmasked), MW = n / 4.0;
   double b = 0.0;
   switch (pass) {
     case 0: b = 2.0 * SB + S * t; break;
-    case 1: b = 6.0 * n * t + SB; break;
-    case 2: b = 3.0 * n * t + SB; break;
-    case 3: b = SB + 2.0 * n * t + n / 8.0; break;
-    default: b = 2.0 * SB + n / 8.0; break;
+    case 1: b = 6.0 * nM * t + SB + MW; break;
+    case 2: b = 3.0 * nM * t + SB + MW; break;
+    case 3: b = SB + 2.0 * nM * t + MW; break;
+    default: b = 2.0 * SB + MW; break;
   }
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
