@@ -71,6 +71,11 @@ typedef struct {
   int batch;             /* realizations per fill_realize call (same mask and P); default 1 */
   int max_iter;          /* CG iterations per solve; default 10000 */
   int max_refine;        /* FP64 refinement steps (mixed mode); default 10 */
+  int host_loops;        /* 0: each CG loop is one CUDA-graph launch (a conditional
+                            WHILE node; default); 1: every kernel of the loops is
+                            launched from the host, with the convergence flags read
+                            back every 8 iterations (for profilers that cannot see
+                            kernels inside conditional graph nodes) */
   double inner_tol;      /* relative tolerance floor of the FP32 inner solves
                             (mixed mode); default 1e-6 */
   int history_cap;       /* residual-history entries kept per realization; default 0 */

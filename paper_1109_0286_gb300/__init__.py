@@ -43,7 +43,8 @@ EXPORTED_SYMBOLS = [
 class FillOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("precond", ctypes.c_int),
                 ("batch", ctypes.c_int), ("max_iter", ctypes.c_int),
-                ("max_refine", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("max_refine", ctypes.c_int), ("host_loops", ctypes.c_int),
+                ("inner_tol", ctypes.c_double),
                 ("history_cap", ctypes.c_int), ("rows_per_cta", ctypes.c_int),
                 ("ffts_per_cta", ctypes.c_int), ("backward", ctypes.c_int),
                 ("update_delta", ctypes.c_double)]
@@ -287,7 +288,7 @@ class Plan:
     def __init__(self, P_half, observed, mode="mixed", precond=True, batch=1,
                  max_iter=10000, max_refine=10, inner_tol=1e-6, history_cap=0,
                  rows_per_cta=0, ffts_per_cta=0, backward=False, update_delta=1e-2,
-                 stream=None):
+                 host_loops=False, stream=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("paper_1109_0286_gb300 needs a CUDA GPU; no CPU fallback exists")
@@ -303,6 +304,7 @@ class Plan:
         o.ffts_per_cta = int(ffts_per_cta)
         o.backward = 1 if backward else 0
         o.update_delta = float(update_delta)
+        o.host_loops = 1 if host_loops else 0
         self.nbands = 0
         self.ny, self.nx = observed.shape
         self.batch = int(batch)

@@ -13,13 +13,22 @@
 #include "cg_fft.cuh"
 
 namespace cgf {
+#ifndef CGF_SRC_CK
+#define CGF_SRC_CK 4
+#endif
+#ifndef CGF_SRC_CK_BIG
+#define CGF_SRC_CK_BIG 2
+#endif
+#ifndef CGF_SINK_CK
+#define CGF_SINK_CK 4
+#endif
 
 template <typename T> struct KCfg;
 template <> struct KCfg<float> { static constexpr int kMaxThreads = 1024; };
 template <> struct KCfg<double> { static constexpr int kMaxThreads = 512; };
 
 // Masked flags and compact CG-vector indices of the pixel pair (pix, pix+1)
-// (pix even): one 8-byte mask-word load and a popcount.
+// (pix even) from the pair's mask word: a popcount.
 struct PairIdx {
   bool m0, m1;   // pixel masked (to fill)
   int i0, i1;    // compact indices (valid where masked)
@@ -36,12 +45,20 @@ __device__ __forceinline__ PairIdx pair_from_word(uint2 w, int pix) {
   return q;
 }
 
-__device__ __forceinline__ uint2 mask_word(const uint2* __restrict__ mw, int pix) {
-  return __ldg(mw + (pix >> 5));
+__device__ __forceinline__ PairIdx pair_index(const uint2* __restrict__ mw, int pix) {
+  return pair_from_word(__ldg(mw + (pix >> 5)), pix);
 }
 
-__device__ __forceinline__ PairIdx pair_index(const uint2* __restrict__ mw, int pix) {
-  return pair_from_word(mask_word(mw, pix), pix);
+// In-row pixel pair j (pixels 2j, 2j+1) from the row's mask words staged in
+// shared memory.
+__device__ __forceinline__ PairIdx pair_at(const uint2* mwr, int j) {
+  return pair_from_word(mwr[j >> 4], 2 * j);
+}
+__device__ __forceinline__ void observed_at(const uint2* mwr, int j, bool& o0, bool& o1) {
+  const uint32_t ob = mwr[j >> 4].x;
+  const int b = (2 * j) & 31;
+  o0 = (ob >> b) & 1u;
+  o1 = (ob >> (b + 1)) & 1u;
 }
 
 // Compact loads / stores of a pixel pair (zero / nothing on observed pixels).
@@ -57,216 +74,176 @@ __device__ __forceinline__ void stc(S* v, const PairIdx& q, T a0, T a1) {
 }
 
 // ----------------------------------------------------------------- sources
-// A source op produces the real values fed to the forward row transform.
-// Loads and compute/stores are split so that a chunk of pixel pairs issues
-// all its loads before any of its stores (the loads then overlap).
-template <typename T>
-struct SrcIn {
-  uint2 w;   // mask word (indices recomputed where needed)
-  T x0, x1, y0, y1, z0, z1, w0, w1;
-};
-
-template <typename T>
-__device__ __forceinline__ void src_load(int op, const InstDesc<T>& I, int pix, SrcIn<T>& in) {
-  switch (op) {
-    case OP_LOAD_W_MASK:
-      in.w = mask_word(I.mw, pix);
-      ld_pair(I.w + pix, in.x0, in.x1);
-      break;
-    case OP_LOAD_Y:
-      ld_pair(I.y + pix, in.x0, in.x1);
-      break;
-    case OP_LOAD_W:
-      ld_pair(I.w + pix, in.x0, in.x1);
-      break;
-    case OP_LOAD_R:
-    case OP_LOAD_U: {
-      in.w = mask_word(I.mw, pix);
-      const PairIdx q = pair_from_word(in.w, pix);
-      ldc(op == OP_LOAD_R ? I.r : I.u, q, in.x0, in.x1);
-      break;
-    }
-    case OP_P_UPD_Z:
-    case OP_P_UPD_R: {
-      in.w = mask_word(I.mw, pix);
-      const PairIdx q = pair_from_word(in.w, pix);
-      ldc(op == OP_P_UPD_Z ? I.z : I.r, q, in.x0, in.x1);
-      ldc(I.p, q, in.y0, in.y1);
-      break;
-    }
-    case OP_R_UPD: {
-      in.w = mask_word(I.mw, pix);
-      const PairIdx q = pair_from_word(in.w, pix);
-      ldc(I.r, q, in.x0, in.x1);
-      ldc(I.q, q, in.y0, in.y1);
-      ldc(I.u, q, in.z0, in.z1);
-      ldc(I.p, q, in.w0, in.w1);
-      break;
-    }
-    case OP_U64_UPD: {
-      in.w = mask_word(I.mw, pix);
-      const PairIdx q = pair_from_word(in.w, pix);
-      ldc(I.u, q, in.x0, in.x1);
-      ldc(I.dlt, q, in.y0, in.y1);
-      break;
-    }
-    default:
-      break;
-  }
-}
-
-template <typename T>
-__device__ __forceinline__ void src_apply(int op, const InstDesc<T>& I, int pix,
-                                          const SrcIn<T>& in, T alpha, T beta, T& a0, T& a1,
-                                          Acc<T>& acc) {
-  switch (op) {
-    case OP_LOAD_W_MASK: {
-      const PairIdx q = pair_from_word(in.w, pix);
-      a0 = q.m0 ? in.x0 : (T)0;
-      a1 = q.m1 ? in.x1 : (T)0;
-      break;
-    }
-    case OP_LOAD_R:
-      a0 = in.x0;
-      a1 = in.x1;
-      acc.add_prod(a0, a0);
-      acc.add_prod(a1, a1);
-      break;
-    case OP_LOAD_U:
-    case OP_LOAD_Y:
-    case OP_LOAD_W:
-      a0 = in.x0;
-      a1 = in.x1;
-      break;
-    case OP_P_UPD_Z:
-    case OP_P_UPD_R:
-      a0 = in.x0 + beta * in.y0;
-      a1 = in.x1 + beta * in.y1;
-      stc(I.p, pair_from_word(in.w, pix), a0, a1);
-      break;
-    case OP_R_UPD: {
-      const PairIdx q = pair_from_word(in.w, pix);
-      a0 = in.x0 - alpha * in.y0;
-      a1 = in.x1 - alpha * in.y1;
-      stc(I.r, q, a0, a1);
-      stc(I.u, q, in.z0 + alpha * in.w0, in.z1 + alpha * in.w1);
-      acc.add_prod(a0, a0);
-      acc.add_prod(a1, a1);
-      break;
-    }
-    case OP_U64_UPD: {
-      const PairIdx q = pair_from_word(in.w, pix);
-      a0 = in.x0 + in.y0;
-      a1 = in.x1 + in.y1;
-      stc(I.u, q, a0, a1);
-      stc(I.dlt, q, 0.f, 0.f);   // folded
-      break;
-    }
-    default:
-      a0 = a1 = (T)0;
-  }
-}
-
-// ----------------------------------------------------------------- middles / sinks
-template <typename T>
-struct SinkIn {
-  uint2 w;   // mask word (indices recomputed where needed)
-  T x0, x1;
-};
-
-template <typename T>
-__device__ __forceinline__ void sink_load(int op, const InstDesc<T>& I, int pix, SinkIn<T>& in) {
-  in.w = mask_word(I.mw, pix);
-  switch (op) {
-    case OP_Y_W:
-      ld_pair(I.d + pix, in.x0, in.x1);
-      break;
-    case OP_Q:
-      ldc(I.p, pair_from_word(in.w, pix), in.x0, in.x1);
-      break;
-    case OP_Z:
-      ldc(I.r, pair_from_word(in.w, pix), in.x0, in.x1);
-      break;
-    case OP_RES:
-      ldc(I.b, pair_from_word(in.w, pix), in.x0, in.x1);
-      break;
-    case OP_GRAD:
-      ld_pair(I.gx + pix, in.x0, in.x1);
-      break;
-    default:
-      break;
-  }
-}
-
-template <typename T>
-__device__ __forceinline__ void sink_apply(int op, const InstDesc<T>& I, int pix,
-                                           const SinkIn<T>& in, T& a0, T& a1, Acc<T>& acc) {
-  const int b = (int)(pix & 31);
-  const bool o0 = (in.w.x >> b) & 1u, o1 = (in.w.x >> (b + 1)) & 1u;   // observed
-  switch (op) {
-    case OP_MASK:
-      a0 = o0 ? (T)0 : a0;
-      a1 = o1 ? (T)0 : a1;
-      break;
-    case OP_Y_W:
-      st_pair(I.y + pix, a0, a1);
-      a0 = o0 ? in.x0 - a0 : (T)0;
-      a1 = o1 ? in.x1 - a1 : (T)0;
-      break;
-    case OP_STORE_Y:
-      st_pair(I.y + pix, a0, a1);
-      break;
-    case OP_STORE_Y_MASK:
-      st_pair(I.y + pix, o0 ? (T)0 : a0, o1 ? (T)0 : a1);
-      break;
-    case OP_Q:
-    case OP_Z:
-      a0 = o0 ? (T)0 : a0;
-      a1 = o1 ? (T)0 : a1;
-      stc(op == OP_Q ? I.q : I.z, pair_from_word(in.w, pix), a0, a1);
-      acc.add_prod(in.x0, a0);
-      acc.add_prod(in.x1, a1);
-      break;
-    case OP_B:
-      a0 = o0 ? (T)0 : -a0;
-      a1 = o1 ? (T)0 : -a1;
-      {
-        const PairIdx q = pair_from_word(in.w, pix);
-        stc(I.r, q, a0, a1);
-        if (I.b) stc(I.b, q, a0, a1);
-        if (I.r32) stc(I.r32, q, a0, a1);
+// A source fills v[e] = (x[2j], x[2j+1]), j = tid + e TT, with the real row
+// values fed to the forward transform.  One instantiation per op: a chunk of
+// CK pixel pairs issues all its loads (indices come from shared memory, so
+// they do not wait on a global load) before its arithmetic and stores.
+template <typename T, int TT, int OP>
+__device__ __forceinline__ void src_fill(const InstDesc<T>& I, const uint2* mwr, int rowpix,
+                                         int tid, T alpha, T beta, cx<T> (&v)[16], Acc<T>& acc) {
+  constexpr int CK = (OP == OP_R_UPD || OP == OP_U64_UPD) ? CGF_SRC_CK_BIG : CGF_SRC_CK;
+#pragma unroll
+  for (int h = 0; h < 16; h += CK) {
+    PairIdx q[CK];
+    T x0[CK], x1[CK], y0[CK], y1[CK], z0[CK], z1[CK], w0[CK], w1[CK];
+#pragma unroll
+    for (int e = 0; e < CK; ++e) {
+      const int j = tid + (h + e) * TT;
+      if constexpr (OP == OP_LOAD_W || OP == OP_LOAD_W_MASK || OP == OP_LOAD_Y) {
+        ld_pair((OP == OP_LOAD_Y ? I.y : I.w) + rowpix + 2 * j, x0[e], x1[e]);
+        if constexpr (OP == OP_LOAD_W_MASK) q[e] = pair_at(mwr, j);
+      } else {
+        q[e] = pair_at(mwr, j);
+        if constexpr (OP == OP_LOAD_R) ldc(I.r, q[e], x0[e], x1[e]);
+        if constexpr (OP == OP_LOAD_U) ldc(I.u, q[e], x0[e], x1[e]);
+        if constexpr (OP == OP_P_UPD_Z || OP == OP_P_UPD_R) {
+          ldc(OP == OP_P_UPD_Z ? I.z : I.r, q[e], x0[e], x1[e]);
+          ldc(I.p, q[e], y0[e], y1[e]);
+        }
+        if constexpr (OP == OP_R_UPD) {
+          ldc(I.r, q[e], x0[e], x1[e]);
+          ldc(I.q, q[e], y0[e], y1[e]);
+          ldc(I.u, q[e], z0[e], z1[e]);
+          ldc(I.p, q[e], w0[e], w1[e]);
+        }
+        if constexpr (OP == OP_U64_UPD) {
+          ldc(I.u, q[e], x0[e], x1[e]);
+          ldc(I.dlt, q[e], y0[e], y1[e]);
+        }
       }
-      acc.add_prod(a0, a0);
-      acc.add_prod(a1, a1);
-      break;
-    case OP_RES:
-      a0 = in.x0 - (o0 ? (T)0 : a0);
-      a1 = in.x1 - (o1 ? (T)0 : a1);
-      {
-        const PairIdx q = pair_from_word(in.w, pix);
-        stc(I.r, q, a0, a1);
-        if (I.r32) stc(I.r32, q, a0, a1);
+    }
+#pragma unroll
+    for (int e = 0; e < CK; ++e) {
+      T a0, a1;
+      if constexpr (OP == OP_LOAD_W_MASK) {
+        a0 = q[e].m0 ? x0[e] : (T)0;
+        a1 = q[e].m1 ? x1[e] : (T)0;
+      } else if constexpr (OP == OP_P_UPD_Z || OP == OP_P_UPD_R) {
+        a0 = x0[e] + beta * y0[e];
+        a1 = x1[e] + beta * y1[e];
+        stc(I.p, q[e], a0, a1);
+      } else if constexpr (OP == OP_R_UPD) {
+        a0 = x0[e] - alpha * y0[e];
+        a1 = x1[e] - alpha * y1[e];
+        stc(I.r, q[e], a0, a1);
+        stc(I.u, q[e], z0[e] + alpha * w0[e], z1[e] + alpha * w1[e]);
+        acc.add_prod(a0, a0);
+        acc.add_prod(a1, a1);
+      } else if constexpr (OP == OP_U64_UPD) {
+        a0 = x0[e] + y0[e];
+        a1 = x1[e] + y1[e];
+        stc(I.u, q[e], a0, a1);
+        stc(I.dlt, q[e], 0.f, 0.f);   // folded
+      } else {
+        a0 = x0[e];
+        a1 = x1[e];
+        if constexpr (OP == OP_LOAD_R) {
+          acc.add_prod(a0, a0);
+          acc.add_prod(a1, a1);
+        }
       }
-      acc.add_prod(a0, a0);
-      acc.add_prod(a1, a1);
-      break;
-    case OP_GRAD:
-      // v = C^-1 lam.  dL/dd_U = g_U - (C^-1 lam)_U, dL/dd_M = 0;
-      // dL/dy = h = g on M, (C^-1 lam)_U on U (kept in y).
-      st_pair(I.out + pix, o0 ? in.x0 - a0 : (T)0, o1 ? in.x1 - a1 : (T)0);
-      st_pair(I.y + pix, o0 ? a0 : in.x0, o1 ? a1 : in.x1);
-      break;
-    default:
-      break;
+      v[h + e] = cx<T>{a0, a1};
+    }
+  }
+}
+
+// ----------------------------------------------------------------- sinks
+// A sink consumes the inverse transform's row values v[e] (pairs j = tid + e
+// TT): projection, stores and the inner product of its op.
+template <typename T, int TT, int OP>
+__device__ __forceinline__ void sink_fill(const InstDesc<T>& I, const uint2* mwr, int rowpix,
+                                          int tid, const cx<T> (&v)[16], Acc<T>& acc) {
+  constexpr int CK = CGF_SINK_CK;
+#pragma unroll
+  for (int h = 0; h < 16; h += CK) {
+    PairIdx q[CK];
+    T x0[CK], x1[CK];
+#pragma unroll
+    for (int e = 0; e < CK; ++e) {
+      const int j = tid + (h + e) * TT;
+      q[e] = pair_at(mwr, j);
+      if constexpr (OP == OP_Q) ldc(I.p, q[e], x0[e], x1[e]);
+      if constexpr (OP == OP_Z) ldc(I.r, q[e], x0[e], x1[e]);
+      if constexpr (OP == OP_RES) ldc(I.b, q[e], x0[e], x1[e]);
+      if constexpr (OP == OP_GRAD) ld_pair(I.gx + rowpix + 2 * j, x0[e], x1[e]);
+    }
+#pragma unroll
+    for (int e = 0; e < CK; ++e) {
+      const int j = tid + (h + e) * TT;
+      const bool m0 = q[e].m0, m1 = q[e].m1;   // masked = not observed
+      T a0 = v[h + e].r, a1 = v[h + e].i;
+      if constexpr (OP == OP_Q || OP == OP_Z) {
+        a0 = m0 ? a0 : (T)0;
+        a1 = m1 ? a1 : (T)0;
+        stc(OP == OP_Q ? I.q : I.z, q[e], a0, a1);
+        acc.add_prod(x0[e], a0);
+        acc.add_prod(x1[e], a1);
+      } else if constexpr (OP == OP_B) {
+        a0 = m0 ? -a0 : (T)0;
+        a1 = m1 ? -a1 : (T)0;
+        stc(I.r, q[e], a0, a1);
+        if (I.b) stc(I.b, q[e], a0, a1);
+        if (I.r32) stc(I.r32, q[e], a0, a1);
+        acc.add_prod(a0, a0);
+        acc.add_prod(a1, a1);
+      } else if constexpr (OP == OP_RES) {
+        a0 = x0[e] - (m0 ? a0 : (T)0);
+        a1 = x1[e] - (m1 ? a1 : (T)0);
+        stc(I.r, q[e], a0, a1);
+        if (I.r32) stc(I.r32, q[e], a0, a1);
+        acc.add_prod(a0, a0);
+        acc.add_prod(a1, a1);
+      } else if constexpr (OP == OP_GRAD) {
+        // v = C^-1 lam.  dL/dd_U = g_U - (C^-1 lam)_U, dL/dd_M = 0;
+        // dL/dy = h = g on M, (C^-1 lam)_U on U (kept in y).
+        st_pair(I.out + rowpix + 2 * j, m0 ? (T)0 : x0[e] - a0, m1 ? (T)0 : x1[e] - a1);
+        st_pair(I.y + rowpix + 2 * j, m0 ? x0[e] : a0, m1 ? x1[e] : a1);
+      } else if constexpr (OP == OP_STORE_Y) {
+        st_pair(I.y + rowpix + 2 * j, a0, a1);
+      } else if constexpr (OP == OP_STORE_Y_MASK) {
+        st_pair(I.y + rowpix + 2 * j, m0 ? a0 : (T)0, m1 ? a1 : (T)0);
+      }
+    }
+  }
+}
+
+// Middle of a chain (between the inverse and the forward row transform):
+// P_x (OP_MASK), or y = v and v = (d - y) on U, 0 on M (OP_Y_W).
+template <typename T, int TT, int OP>
+__device__ __forceinline__ void mid_fill(const InstDesc<T>& I, const uint2* mwr, int rowpix,
+                                         int tid, cx<T> (&v)[16]) {
+#pragma unroll
+  for (int e = 0; e < 16; ++e) {
+    const int j = tid + e * TT;
+    bool o0, o1;
+    observed_at(mwr, j, o0, o1);
+    if constexpr (OP == OP_Y_W) {
+      T d0, d1;
+      ld_pair(I.d + rowpix + 2 * j, d0, d1);
+      st_pair(I.y + rowpix + 2 * j, v[e].r, v[e].i);
+      v[e].r = o0 ? d0 - v[e].r : (T)0;
+      v[e].i = o1 ? d1 - v[e].i : (T)0;
+    } else {
+      v[e].r = o0 ? (T)0 : v[e].r;
+      v[e].i = o1 ? (T)0 : v[e].i;
+    }
   }
 }
 
 // ----------------------------------------------------------------- row pass
 // CTA = `rows` consecutive grid rows, L/16 threads per row; blockIdx.y is the
 // instance.  Shared memory: per-row FFT exchange areas, aliased with the
-// transposed tile [(L+1) x (rows+1)] used for the spectrum load / store.
+// transposed tile [(L+1) x (rows+1)] used for the spectrum load / store,
+// then the rows' mask words (nx/32 = L/16 per row: one per thread).
 // XI: the source is the seed's white noise (kept out of the other source
 // kernels, whose register allocation it would otherwise burden).
+template <typename T>
+__host__ __device__ __forceinline__ size_t row_main_bytes(int log_l, int rows) {
+  const size_t L = size_t(1) << log_l, padl = L + L / 16 + 1;
+  const size_t fft = size_t(rows) * 2 * padl, tile = 2 * (L + 1) * size_t(rows + 1);
+  return ((fft > tile ? fft : tile) * sizeof(T) + 15) & ~size_t(15);
+}
+
 template <typename T, int LOG_L, bool IN_SPEC, bool OUT_SPEC, bool XI = false>
 __global__ void __launch_bounds__(KCfg<T>::kMaxThreads)
 k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw) {
@@ -281,21 +258,34 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
   const int rows = a.rows, lr = a.log_rows;
   const int row = threadIdx.x / TT, tid = threadIdx.x - row * TT;
   const int y0 = blockIdx.x * rows, y = y0 + row;
-  const int ny = a.ny, nx = a.nx;
+  const int ny = a.ny;
   const int tstride = rows + 1;
   const XBuf<T> xb(sm + row * 2 * PADL, PADL);
   cx<T>* tile = reinterpret_cast<cx<T>*>(sm);   // [(L+1)][rows+1], aliases the FFT areas
-  constexpr int TWS = kLmax / (2 * L);   // W_{nx}^k = table[k * TWS]
-  const int rowpix = y * nx;
+  uint2* mws = reinterpret_cast<uint2*>(smem_raw + row_main_bytes<T>(LOG_L, rows));
+  const uint2* mwr = mws + row * TT;            // this row's mask words
+  constexpr int TWS = kLmax / (2 * L);          // W_{nx}^k = table[k * TWS]
+  const int rowpix = y * a.nx;
+  // tile element (kk + i TT, rr) for i = 0..15 belongs to thread (kk, rr); the
+  // Nyquist row k = L to threads 0..rows-1
+  const int rr = threadIdx.x & (rows - 1), kk = threadIdx.x >> lr;
+  const size_t tstep = 2 * (size_t)TT * ny;
   cx<T> v[16];
   Acc<T> acc;
 
+  if constexpr (!XI) mws[threadIdx.x] = __ldg(I.mw + (size_t)y0 * TT + threadIdx.x);
+
   if constexpr (IN_SPEC) {
-    const T* spec = (a.spec_sel ? I.spec2 : I.spec) + 2 * y0;
-    for (int e = threadIdx.x; e < (L + 1) * rows; e += blockDim.x) {
-      const int k = e >> lr, rr = e & (rows - 1);
-      tile[k * tstride + rr] = ld_cx<T>(spec + 2 * (k * ny + rr));
-    }
+    const T* spec = (a.spec_sel ? I.spec2 : I.spec) + 2 * ((size_t)kk * ny + y0 + rr);
+    cx<T> t[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) t[i] = ldg_cx<T>(spec + i * tstep);
+    cx<T> tn{};
+    if (threadIdx.x < rows)
+      tn = ldg_cx<T>((a.spec_sel ? I.spec2 : I.spec) + 2 * ((size_t)L * ny + y0 + threadIdx.x));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) tile[(kk + i * TT) * tstride + rr] = t[i];
+    if (threadIdx.x < rows) tile[L * tstride + threadIdx.x] = tn;
     if (threadIdx.x < 16) wcol[threadIdx.x] = twiddle<T>(tw, threadIdx.x * TT * TWS);
     __syncthreads();
     // C2R: Z[k] = (X[k] + conj X[L-k]) + i e^{+2 pi i k / nx} (X[k] - conj X[L-k])
@@ -317,35 +307,23 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
     fft_regs<T, LOG_L, true>(v, xb, tid, tw);
     // v[e] = x[2j] + i x[2j+1], j = tid + e TT
     if constexpr (OUT_SPEC) {
-      // middle of a chain: P_x (OP_MASK) or y = v, v = (d - y) on U (OP_Y_W)
-#pragma unroll
-      for (int e = 0; e < 16; ++e) {
-        const int pix = rowpix + 2 * (tid + e * TT);
-        const uint32_t ob = __ldg(&I.mw[pix >> 5].x);
-        const int b = (int)(pix & 31);
-        const bool o0 = (ob >> b) & 1u, o1 = (ob >> (b + 1)) & 1u;
-        if (a.op == OP_Y_W) {
-          T d0, d1;
-          ld_pair(I.d + pix, d0, d1);
-          st_pair(I.y + pix, v[e].r, v[e].i);
-          v[e].r = o0 ? d0 - v[e].r : (T)0;
-          v[e].i = o1 ? d1 - v[e].i : (T)0;
-        } else {
-          v[e].r = o0 ? (T)0 : v[e].r;
-          v[e].i = o1 ? (T)0 : v[e].i;
-        }
-      }
+      if (a.op == OP_Y_W)
+        mid_fill<T, TT, OP_Y_W>(I, mwr, rowpix, tid, v);
+      else
+        mid_fill<T, TT, OP_MASK>(I, mwr, rowpix, tid, v);
     } else {
-    constexpr int CK = 4;   // pixel pairs whose loads are issued together
-#pragma unroll
-    for (int h = 0; h < 16; h += CK) {
-      SinkIn<T> in[CK];
-#pragma unroll
-      for (int e = 0; e < CK; ++e) sink_load<T>(a.op, I, rowpix + 2 * (tid + (h + e) * TT), in[e]);
-#pragma unroll
-      for (int e = 0; e < CK; ++e)
-        sink_apply<T>(a.op, I, rowpix + 2 * (tid + (h + e) * TT), in[e], v[h + e].r, v[h + e].i, acc);
-    }
+      switch (a.op) {
+        case OP_Q: sink_fill<T, TT, OP_Q>(I, mwr, rowpix, tid, v, acc); break;
+        case OP_Z: sink_fill<T, TT, OP_Z>(I, mwr, rowpix, tid, v, acc); break;
+        case OP_B: sink_fill<T, TT, OP_B>(I, mwr, rowpix, tid, v, acc); break;
+        case OP_RES: sink_fill<T, TT, OP_RES>(I, mwr, rowpix, tid, v, acc); break;
+        case OP_GRAD: sink_fill<T, TT, OP_GRAD>(I, mwr, rowpix, tid, v, acc); break;
+        case OP_STORE_Y: sink_fill<T, TT, OP_STORE_Y>(I, mwr, rowpix, tid, v, acc); break;
+        case OP_STORE_Y_MASK:
+          sink_fill<T, TT, OP_STORE_Y_MASK>(I, mwr, rowpix, tid, v, acc);
+          break;
+        default: break;
+      }
     }
   } else if constexpr (XI) {
 #pragma unroll
@@ -355,17 +333,30 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
       v[e] = cx<T>{(T)x0, (T)x1};
     }
   } else {
+    __syncthreads();   // mask words
     const T alpha = (T)I.st->alpha, beta = (T)I.st->beta;
-    constexpr int CK = 2;   // pixel pairs whose loads are issued together
+    switch (a.op) {
+      case OP_R_UPD: src_fill<T, TT, OP_R_UPD>(I, mwr, rowpix, tid, alpha, beta, v, acc); break;
+      case OP_P_UPD_Z:
+        src_fill<T, TT, OP_P_UPD_Z>(I, mwr, rowpix, tid, alpha, beta, v, acc);
+        break;
+      case OP_P_UPD_R:
+        src_fill<T, TT, OP_P_UPD_R>(I, mwr, rowpix, tid, alpha, beta, v, acc);
+        break;
+      case OP_LOAD_R: src_fill<T, TT, OP_LOAD_R>(I, mwr, rowpix, tid, alpha, beta, v, acc); break;
+      case OP_LOAD_U: src_fill<T, TT, OP_LOAD_U>(I, mwr, rowpix, tid, alpha, beta, v, acc); break;
+      case OP_LOAD_Y: src_fill<T, TT, OP_LOAD_Y>(I, mwr, rowpix, tid, alpha, beta, v, acc); break;
+      case OP_LOAD_W: src_fill<T, TT, OP_LOAD_W>(I, mwr, rowpix, tid, alpha, beta, v, acc); break;
+      case OP_LOAD_W_MASK:
+        src_fill<T, TT, OP_LOAD_W_MASK>(I, mwr, rowpix, tid, alpha, beta, v, acc);
+        break;
+      case OP_U64_UPD:
+        src_fill<T, TT, OP_U64_UPD>(I, mwr, rowpix, tid, alpha, beta, v, acc);
+        break;
+      default:
 #pragma unroll
-    for (int h = 0; h < 16; h += CK) {
-      SrcIn<T> in[CK];
-#pragma unroll
-      for (int e = 0; e < CK; ++e) src_load<T>(a.op, I, rowpix + 2 * (tid + (h + e) * TT), in[e]);
-#pragma unroll
-      for (int e = 0; e < CK; ++e)
-        src_apply<T>(a.op, I, rowpix + 2 * (tid + (h + e) * TT), in[e], alpha, beta, v[h + e].r,
-                     v[h + e].i, acc);
+        for (int e = 0; e < 16; ++e) v[e] = cx<T>{(T)0, (T)0};
+        break;
     }
   }
 
@@ -393,11 +384,12 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
     for (int e = 0; e < 16; ++e) tile[(tid + e * TT) * tstride + row] = v[e];
     if (tid == 0) tile[L * tstride + row] = nyq;
     __syncthreads();
-    T* spec = (a.spec_sel ? I.spec2 : I.spec) + 2 * y0;
-    for (int e = threadIdx.x; e < (L + 1) * rows; e += blockDim.x) {
-      const int k = e >> lr, rr = e & (rows - 1);
-      st_cx<T>(spec + 2 * (k * ny + rr), tile[k * tstride + rr]);
-    }
+    T* spec = (a.spec_sel ? I.spec2 : I.spec) + 2 * ((size_t)kk * ny + y0 + rr);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) st_cx<T>(spec + i * tstep, tile[(kk + i * TT) * tstride + rr]);
+    if (threadIdx.x < rows)
+      st_cx<T>((a.spec_sel ? I.spec2 : I.spec) + 2 * ((size_t)L * ny + y0 + threadIdx.x),
+               tile[L * tstride + threadIdx.x]);
   }
 
   if (a.sop != SC_NONE)

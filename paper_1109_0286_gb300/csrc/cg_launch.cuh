@@ -7,9 +7,9 @@ namespace cgf {
 
 template <typename T>
 size_t Launch<T>::row_smem(int log_l, int rows) {
-  const size_t L = size_t(1) << log_l, padl = L + L / 16 + 1;
-  const size_t fft = size_t(rows) * 2 * padl, tile = 2 * (L + 1) * size_t(rows + 1);
-  return (fft > tile ? fft : tile) * sizeof(T);
+  // FFT areas / transposed tile, then one mask word (8 bytes) per thread
+  const size_t tt = (size_t(1) << log_l) / 16;
+  return row_main_bytes<T>(log_l, rows) + size_t(rows) * tt * sizeof(uint2);
 }
 
 template <typename T>

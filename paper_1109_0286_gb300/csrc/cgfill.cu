@@ -443,6 +443,38 @@ fill_status run_loop_graph(fill_plan* p, cudaGraphExec_t exec, long long body_ke
   return FILL_OK;
 }
 
+// Host-driven form of a loop graph (opts.host_loops = 1): the body's kernels
+// are launched from the host and the instances' done flags are read back
+// every kHostCheck bodies; bodies past the last convergence cost only the
+// kernels' early exits.  For profilers that cannot see kernels inside
+// conditional graph nodes.
+constexpr int kHostCheck = 8;
+
+__global__ void k_any_running(CgState* const* sts, int n, int* flag) {
+  __shared__ int running;
+  if (threadIdx.x == 0) running = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    if (!*(volatile int*)&sts[i]->done) running = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) *flag = running;
+}
+
+template <typename Body>
+fill_status run_loop_host(cudaStream_t s, Body body, CgState* const* sts, int n, int* dflag,
+                          int* hflag, int limit, long long* launches) {
+  for (int it = 0; it < limit;) {
+    for (int k = 0; k < kHostCheck && it < limit; ++k, ++it) CK(body(s));
+    ++*launches;
+    k_any_running<<<1, 256, 0, s>>>(sts, n, dflag);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(hflag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (!*hflag) break;
+  }
+  return FILL_OK;
+}
+
 template <typename T>
 fill_status build_iter_graph(fill_plan* p) {
   Precision<T>& P = prec<T>(p);
@@ -457,6 +489,10 @@ fill_status build_iter_graph(fill_plan* p) {
 template <typename T>
 fill_status run_pcg(fill_plan* p) {
   Precision<T>& P = prec<T>(p);
+  if (p->o.host_loops)
+    return run_loop_host(
+        p->s, [&](cudaStream_t s) { return pcg_iter<T>(p, s); }, P.stp, p->batch,
+        p->loop_counter, p->hloop, p->o.max_iter + 4, &p->launches);
   fill_status fs = build_iter_graph<T>(p);
   if (fs != FILL_OK) return fs;
   return run_loop_graph(p, P.iter_graph, P.iter_graph_kernels);
@@ -562,6 +598,14 @@ cudaError_t mixed_update_passes(fill_plan* p, cudaStream_t s) {
 }
 
 cudaError_t update_if(fill_plan* p, cudaStream_t s, bool reload) {
+  if (p->o.host_loops) {
+    // no graph: the update passes run every iteration and skip the instances
+    // without an update due
+    if (reload) return mixed_update_passes(p, s);
+    CE(row<double>(p, s, OP_U64_UPD, SC_NONE, false, true, SKIP_UNLESS_UPD));
+    CE(col<double>(p, s, 0, SKIP_UNLESS_UPD));
+    return row<double>(p, s, OP_RES, SC_RES_UPD, true, false, SKIP_UNLESS_UPD);
+  }
   cudaStreamCaptureStatus st;
   cudaGraph_t g = nullptr;
   CE(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr));
@@ -632,9 +676,17 @@ fill_status mixed_reliable(fill_plan* p, double tol) {
   k_link_states<<<nb, 128, 0, p->s>>>(p->f.st, p->g.st, B, d * d);
   CK(cudaGetLastError());
   CK(pcg_start<float>(p, p->s, SC_BB));
-  fill_status fs = build_mixed_graph(p);
-  if (fs != FILL_OK) return fs;
-  fs = run_loop_graph(p, p->mixed_graph, p->mixed_graph_kernels, p->if_kernels);
+  fill_status fs;
+  if (p->o.host_loops) {
+    fs = run_loop_host(
+        p->s,
+        [&](cudaStream_t s) { return p->o.precond ? mixed_iter(p, s) : mixed_iter_plain(p, s); },
+        p->f.stp, p->batch, p->loop_counter, p->hloop, p->o.max_iter + 4, &p->launches);
+  } else {
+    fs = build_mixed_graph(p);
+    if (fs != FILL_OK) return fs;
+    fs = run_loop_graph(p, p->mixed_graph, p->mixed_graph_kernels, p->if_kernels);
+  }
   if (fs != FILL_OK) return fs;
   // fold anything left (breakdown / limits) and report the true residual
   CK(row<double>(p, p->s, OP_U64_UPD, SC_NONE, false, true, SKIP_DONE));
@@ -894,7 +946,7 @@ fill_status fill_init(fill_plan** out, int ny, int nx, const double* P_half,
   else
     fill_opts_default(&o);
   if (o.mode < 0 || o.mode > 2 || o.batch < 1 || o.batch > 65535 || o.max_iter < 1 ||
-      o.max_refine < 1 || !(o.inner_tol > 0.0) || o.history_cap < 0 || o.rows_per_cta < 0 ||
+      o.max_refine < 1 || o.host_loops < 0 || o.host_loops > 1 || !(o.inner_tol > 0.0) || o.history_cap < 0 || o.rows_per_cta < 0 ||
       o.ffts_per_cta < 0 || o.backward < 0 || o.backward > 1 || !(o.update_delta >= 0.0) ||
       !(o.update_delta < 1.0))
     return FILL_EINVAL;
@@ -1425,7 +1477,7 @@ struct fill_group {
   std::vector<fill_plan*> plans;
   std::vector<int> first;       // first flat instance of each plan
   std::vector<GroupClass> cls;
-  int mode = 1, precond = 1, max_iter = 10000, ntot = 0;
+  int mode = 1, precond = 1, max_iter = 10000, ntot = 0, host_loops = 0;
   cudaStream_t s = nullptr, cap = nullptr;
   cudaEvent_t fork = nullptr, fork_cap = nullptr;
   CgState** stp = nullptr;      // device: state pointer of every instance
@@ -1553,10 +1605,27 @@ fill_status group_realize_t(fill_group* g, const void* const* d, const uint64_t*
     return pcg_start<T>(cx_, c.cs, SC_NONE);
   });
   if (fs != FILL_OK) return fs;
-  fs = group_build_graph<T>(g);
-  if (fs != FILL_OK) return fs;
-  CK(cudaGraphLaunch(g->graph, g->s));
-  CK(cudaMemcpyAsync(g->hloop, g->counter, sizeof(int), cudaMemcpyDeviceToHost, g->s));
+  if (g->host_loops) {
+    fs = run_loop_host(
+        g->s,
+        [&](cudaStream_t s) -> cudaError_t {
+          CE(cudaEventRecord(g->fork, s));
+          for (auto& c : g->cls) {
+            CE(cudaStreamWaitEvent(c.cs, g->fork, 0));
+            CE(pcg_iter<T>(gctx<T>(g, c), c.cs));
+            CE(cudaEventRecord(c.join, c.cs));
+            CE(cudaStreamWaitEvent(s, c.join, 0));
+          }
+          return cudaSuccess;
+        },
+        g->stp, g->ntot, g->counter, g->hloop, g->max_iter + 4, &g->launches);
+    if (fs != FILL_OK) return fs;
+  } else {
+    fs = group_build_graph<T>(g);
+    if (fs != FILL_OK) return fs;
+    CK(cudaGraphLaunch(g->graph, g->s));
+    CK(cudaMemcpyAsync(g->hloop, g->counter, sizeof(int), cudaMemcpyDeviceToHost, g->s));
+  }
   fs = group_fork_join<T>(g, [&](GroupClass& c) -> cudaError_t {
     Ctx<T> cx_ = gctx<T>(g, c);
     CE(vec<T>(cx_, c.cs, VOP_ASSEMBLE, SC_NONE, false));
@@ -1567,7 +1636,7 @@ fill_status group_realize_t(fill_group* g, const void* const* d, const uint64_t*
   });
   if (fs != FILL_OK) return fs;
   CK(cudaStreamSynchronize(g->s));
-  g->launches += 1 + (long long)(*g->hloop) * g->graph_kernels;
+  if (!g->host_loops) g->launches += 1 + (long long)(*g->hloop) * g->graph_kernels;
   if (stats) {
     for (auto& c : g->cls) {
       int k = 0;
@@ -1615,6 +1684,7 @@ fill_status fill_group_init(fill_group** out, fill_plan* const* plans, int count
   g->mode = mode;
   g->precond = plans[0]->o.precond;
   g->max_iter = plans[0]->o.max_iter;
+  g->host_loops = plans[0]->o.host_loops;
   g->s = plans[0]->s;
   int flat = 0;
   for (int i = 0; i < count; ++i) {

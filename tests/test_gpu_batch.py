@@ -63,6 +63,22 @@ def test_group_equals_single_plans(mode):
     assert all(s["status"] == 0 for s in stats)
 
 
+def test_group_host_loops_equal_graph():
+    items = mixed_items([(64, 2), (128, 1)], 128, seed0=17)
+    outs = []
+    for host in (False, True):
+        plans, ds = [], []
+        for k, (n, P, obs) in enumerate(items):
+            plans.append(cg.Plan(P, obs, mode="fp32", host_loops=host))
+            d = O.draw(O.hermitian_full(P, n), 600 + k)
+            ds.append(torch.from_numpy(d).to(dtype=torch.float32, device="cuda"))
+        g = cg.Group(plans)
+        outs.append(g.realize(ds, list(range(3, 3 + g.size)), 1e-6))
+    for a, b in zip(outs[0][0], outs[1][0]):
+        assert torch.equal(a, b)
+    assert [s["iters"] for s in outs[0][1]] == [s["iters"] for s in outs[1][1]]
+
+
 def test_autotune_keeps_results_close(tmp_path):
     n = 256
     P = synth.spectrum_cmb_like(n, n, 2 * math.pi / n)

@@ -205,6 +205,28 @@ def test_batch_equals_singles():
         assert torch.equal(xb[i], xs[0])
 
 
+@pytest.mark.parametrize("mode,precond,delta", [("fp64", True, 1e-2), ("fp32", False, 1e-2),
+                                                ("mixed", True, 1e-2), ("mixed", False, 1e-2),
+                                                ("mixed", True, 0.0)])
+def test_host_loops_equal_graph_loops(mode, precond, delta):
+    """The host-driven CG loops launch the same kernels in the same order as
+    the graph loops, so the realizations agree bit for bit."""
+    P, obs = case(128, 256, seed=9)
+    d = O.draw(O.hermitian_full(P, 256), 4)
+    dt = torch.float32 if mode == "fp32" else torch.float64
+    seeds = [21, 22, 23]
+    tol = 1e-6 if mode == "fp32" else 1e-10
+    res = []
+    for host in (False, True):
+        plan = cg.Plan(P, obs, mode=mode, precond=precond, batch=3, update_delta=delta,
+                       host_loops=host)
+        res.append(plan.realize(gpu_map(d, dt), seeds, tol))
+    (xg, sg), (xh, sh) = res
+    assert torch.equal(xg, xh)
+    assert [s["iters"] for s in sg] == [s["iters"] for s in sh]
+    assert [s["status"] for s in sh] == [0, 0, 0]
+
+
 # ------------------------------------------------------------------ edge cases
 
 @pytest.mark.parametrize("mode", ["fp64", "fp32", "mixed"])
