@@ -38,14 +38,19 @@ UNIT = "realizations/s"
 # CPU time to realizations/s in the reference / cpu_baseline legs).
 FP64_ITERS_WIDE4096 = 200
 
-# DRAM traffic (read + write bytes) of one launch of the roofline kernel per
-# instance, from the ncu capture summarised in
-# profiles/k_row_sink_fp32_4096x4096x2.md (2 instances of 4096^2; scaled by the
-# instance count).  Reported only while the pass-kernel sources hash to the
-# profiled version; otherwise traffic is null.
-TRAFFIC = {"kernel": "k_row sink (C2R + q = P_x, p^T q)", "bytes_per_instance": 377.339904e6 / 2,
-           "src_hash": "c604b6f5371e03c9"}
-KERNEL_SOURCES = ["cg_types.h", "cg_common.cuh", "cg_fft.cuh", "cg_kernels.cuh"]
+# DRAM traffic (read + write bytes) of one launch of each hot-loop pass, from
+# the ncu captures summarised in profiles/k_*_fp32_4096x4096x2.md (2 instances
+# of the 4096^2 workload, FP32 kernels): (per-instance MB, shared MB), the
+# shared part (column table, mask words) read once per launch.  A launch over
+# B instances is scaled as B * per-instance + shared.  Reported only while the
+# pass-kernel sources hash to the profiled version; otherwise traffic is null.
+TRAFFIC = {"src_hash": "5a6b2225605195e9",
+           "k_col (column FFT, x 1/(nP), inverse FFT)": (106.83, 33.57),
+           "k_row src (r, u update + R2C)": (141.37, 4.19),
+           "k_row src (p update + R2C)": (90.55, 4.19),
+           "k_row sink (C2R + q = P_x, p^T q)": (95.82, 4.19),
+           "k_row mid (C2R, P_x, R2C)": (107.88, 4.19)}
+KERNEL_SOURCES = ["cg_types.h", "cg_common.cuh", "cg_fft.cuh", "cg_kernels.cuh", "cg_launch.cuh"]
 
 
 def kernel_src_hash():
@@ -313,9 +318,10 @@ def run_gpu(args):
     name, _, pms, pbytes = timing[dom]
     achieved = pbytes / (pms / 1e3) / 1e9
     traffic = None
-    if name == TRAFFIC["kernel"] and mode in ("fp32", "mixed") and \
+    if name in TRAFFIC and mode in ("fp32", "mixed") and \
             kernel_src_hash() == TRAFFIC["src_hash"] and (ny, nx) == (4096, 4096):
-        traffic = TRAFFIC["bytes_per_instance"] * B
+        per_inst, shared = TRAFFIC[name]
+        traffic = (per_inst * B + shared) * 1e6
     roofline = {"bound": "hbm", "kernel": name, "achieved": achieved,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,

@@ -163,7 +163,8 @@ fill_status fill_history(fill_plan* plan, int inst, double* hist, int cap, int* 
  * kernel over all `batch` instances, timed with CUDA events on the plan's
  * stream (`reps` launches between two events, after one warm-up launch), and
  * the algorithmic bytes of one launch (the reads and writes the pass has to
- * make).  pass: 0 column pass (forward column FFT, x 1/(nP), inverse FFT);
+ * make: each instance's spectrum and compact vectors, plus the column table or
+ * the mask words once, since the batch shares them).  pass: 0 column pass (forward column FFT, x 1/(nP), inverse FFT);
  * 1 forward row pass fused with r -= alpha q, u += alpha p; 2 forward row pass
  * fused with p = z + beta p; 3 inverse row pass fused with q = P_x(.) and
  * p^T q; 4 inverse row pass, P_x, forward row pass (middle of S S r).

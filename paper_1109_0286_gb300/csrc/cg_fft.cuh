@@ -145,9 +145,27 @@ __device__ __forceinline__ cx<T> twiddle(const T* __restrict__ tw, int m) {
   return ldg_cx<T>(tw + 2 * m);
 }
 
+// Barrier over the threads of one transform.  When a transform spans whole
+// warps and a CTA holds at most 8 of them, each transform syncs on its own
+// named barrier (1 + idx), so the transforms of a CTA advance independently;
+// otherwise the whole CTA syncs.
+struct XBar {
+  int id, n;   // id 0: __syncthreads
+  __device__ __forceinline__ void sync() const {
+    if (id == 0)
+      __syncthreads();
+    else
+      asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+  }
+  static __device__ __forceinline__ XBar make(int tpt, int count, int idx) {
+    return (tpt >= 32 && count > 1 && count <= 8) ? XBar{1 + idx, tpt} : XBar{0, 0};
+  }
+};
+
 template <typename T, int LOG_L, bool INV>
 __device__ __forceinline__ void fft_regs(cx<T> (&v)[16], const XBuf<T>& xb, int tid,
-                                         const T* __restrict__ tw) {
+                                         const T* __restrict__ tw, XBar first = XBar{0, 0},
+                                         XBar bar = XBar{0, 0}) {
   constexpr int TT = (1 << LOG_L) / 16;
   constexpr int S16 = LOG_L / 4;
   constexpr int REM = LOG_L % 4;
@@ -163,7 +181,7 @@ __device__ __forceinline__ void fft_regs(cx<T> (&v)[16], const XBuf<T>& xb, int 
 #pragma unroll
       for (int r = 0; r < R0; ++r) v[q + r * NB] = u[r];
     }
-    __syncthreads();
+    first.sync();
 #pragma unroll
     for (int q = 0; q < NB; ++q)
 #pragma unroll
@@ -176,10 +194,10 @@ __device__ __forceinline__ void fft_regs(cx<T> (&v)[16], const XBuf<T>& xb, int 
     int ns = NS0;
 #pragma unroll
     for (int t = 0; t < s; ++t) ns *= 16;
-    const bool first = (REM == 0) && (s == 0);
+    const bool first_stage = (REM == 0) && (s == 0);
     const bool last = (s == S16 - 1);
-    if (!first) {
-      __syncthreads();
+    if (!first_stage) {
+      bar.sync();
 #pragma unroll
       for (int e = 0; e < 16; ++e) v[e] = xb.ld(tid + e * TT);
       const int jm = tid & (ns - 1);
@@ -202,7 +220,10 @@ __device__ __forceinline__ void fft_regs(cx<T> (&v)[16], const XBuf<T>& xb, int 
     }
     dft16<T, INV>(v);
     if (!last) {
-      __syncthreads();
+      if (REM == 0 && s == 0)
+        first.sync();
+      else
+        bar.sync();
       const int jm = tid & (ns - 1);
       const int base = (tid - jm) * 16 + jm;
 #pragma unroll

@@ -13,15 +13,9 @@
 #include "cg_fft.cuh"
 
 namespace cgf {
-#ifndef CGF_SRC_CK
-#define CGF_SRC_CK 4
-#endif
-#ifndef CGF_SRC_CK_BIG
-#define CGF_SRC_CK_BIG 2
-#endif
-#ifndef CGF_SINK_CK
-#define CGF_SINK_CK 4
-#endif
+// Pixel pairs whose loads a source / sink issues together (register budget
+// of 64 per thread at two 512-thread CTAs per SM).
+constexpr int kSrcChunk = 4, kSrcChunkWide = 2, kSinkChunk = 4;
 
 template <typename T> struct KCfg;
 template <> struct KCfg<float> { static constexpr int kMaxThreads = 1024; };
@@ -81,7 +75,7 @@ __device__ __forceinline__ void stc(S* v, const PairIdx& q, T a0, T a1) {
 template <typename T, int TT, int OP>
 __device__ __forceinline__ void src_fill(const InstDesc<T>& I, const uint2* mwr, int rowpix,
                                          int tid, T alpha, T beta, cx<T> (&v)[16], Acc<T>& acc) {
-  constexpr int CK = (OP == OP_R_UPD || OP == OP_U64_UPD) ? CGF_SRC_CK_BIG : CGF_SRC_CK;
+  constexpr int CK = (OP == OP_R_UPD || OP == OP_U64_UPD) ? kSrcChunkWide : kSrcChunk;
 #pragma unroll
   for (int h = 0; h < 16; h += CK) {
     PairIdx q[CK];
@@ -153,7 +147,7 @@ __device__ __forceinline__ void src_fill(const InstDesc<T>& I, const uint2* mwr,
 template <typename T, int TT, int OP>
 __device__ __forceinline__ void sink_fill(const InstDesc<T>& I, const uint2* mwr, int rowpix,
                                           int tid, const cx<T> (&v)[16], Acc<T>& acc) {
-  constexpr int CK = CGF_SINK_CK;
+  constexpr int CK = kSinkChunk;
 #pragma unroll
   for (int h = 0; h < 16; h += CK) {
     PairIdx q[CK];
@@ -251,7 +245,8 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   __shared__ double red[32];
-  __shared__ cx<T> wcol[16];   // W_nx^(e TT), e = 0..15 (warp-uniform factor)
+  __shared__ cx<T> wcol[16];   // W_nx^(e TT) = W_32^e, e = 0..15 (warp-uniform factor)
+  if (threadIdx.x < 16) wcol[threadIdx.x] = twiddle<T>(tw, threadIdx.x * (kLmax / 32));
   const InstDesc<T>& I = insts[blockIdx.y];
   if (skip_instance(a.check_done, I.st)) return;
 
@@ -270,6 +265,7 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
   // Nyquist row k = L to threads 0..rows-1
   const int rr = threadIdx.x & (rows - 1), kk = threadIdx.x >> lr;
   const size_t tstep = 2 * (size_t)TT * ny;
+  const XBar cta{0, 0}, rbar = XBar::make(TT, rows, row);   // CTA / this row's barrier
   cx<T> v[16];
   Acc<T> acc;
 
@@ -286,7 +282,6 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
 #pragma unroll
     for (int i = 0; i < 16; ++i) tile[(kk + i * TT) * tstride + rr] = t[i];
     if (threadIdx.x < rows) tile[L * tstride + threadIdx.x] = tn;
-    if (threadIdx.x < 16) wcol[threadIdx.x] = twiddle<T>(tw, threadIdx.x * TT * TWS);
     __syncthreads();
     // C2R: Z[k] = (X[k] + conj X[L-k]) + i e^{+2 pi i k / nx} (X[k] - conj X[L-k])
     const cx<T> wt = twiddle<T>(tw, tid * TWS);
@@ -304,7 +299,8 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
       const cx<T> dif = cmulc(xk - xc, w);  // (X - conj X') e^{+i...}
       v[e] = cx<T>{sum.r - dif.i, sum.i + dif.r};
     }
-    fft_regs<T, LOG_L, true>(v, xb, tid, tw);
+    // the first exchange overwrites tile entries other rows still read
+    fft_regs<T, LOG_L, true>(v, xb, tid, tw, cta, rbar);
     // v[e] = x[2j] + i x[2j+1], j = tid + e TT
     if constexpr (OUT_SPEC) {
       if (a.op == OP_Y_W)
@@ -332,6 +328,7 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
       normal_pair(I.seed, (uint32_t)((rowpix >> 1) + tid + e * TT), x0, x1);
       v[e] = cx<T>{(T)x0, (T)x1};
     }
+    __syncthreads();   // wcol (written by row 0) before the row-barrier stages
   } else {
     __syncthreads();   // mask words
     const T alpha = (T)I.st->alpha, beta = (T)I.st->beta;
@@ -361,12 +358,11 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
   }
 
   if constexpr (OUT_SPEC) {
-    if (!IN_SPEC && threadIdx.x < 16) wcol[threadIdx.x] = twiddle<T>(tw, threadIdx.x * TT * TWS);
-    fft_regs<T, LOG_L, false>(v, xb, tid, tw);
-    __syncthreads();
+    fft_regs<T, LOG_L, false>(v, xb, tid, tw, rbar, rbar);
+    rbar.sync();
 #pragma unroll
     for (int e = 0; e < 16; ++e) xb.st(tid + e * TT, v[e]);
-    __syncthreads();
+    rbar.sync();
     const cx<T> wt = twiddle<T>(tw, tid * TWS);
     // R2C: X[k] = (Z[k] + conj Z[L-k]) / 2 - (i/2) e^{-2 pi i k/nx} (Z[k] - conj Z[L-k])
     cx<T> nyq{v[0].r - v[0].i, (T)0};
@@ -379,7 +375,7 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
       const cx<T> od = scal(mul_mi<T, false>(zk - zc), (T)0.5);
       v[e] = ev + cmul(od, cmul(wt, wcol[e]));
     }
-    __syncthreads();
+    __syncthreads();   // the tile overwrites other rows' exchange areas
 #pragma unroll
     for (int e = 0; e < 16; ++e) tile[(tid + e * TT) * tstride + row] = v[e];
     if (tid == 0) tile[L * tstride + row] = nyq;
@@ -399,24 +395,27 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
 // ----------------------------------------------------------------- column pass
 // CTA = `ffts` spectrum rows (one kx each), N/16 threads per row; forward
 // column FFT, multiply by the real table, inverse column FFT, in place
-// (table < 0: forward transform only).
+// (table < 0: forward transform only).  blockIdx.x is the instance, so the
+// CTAs of all instances for the same kx run together and share the table
+// row through L2.
 template <typename T, int LOG_N>
 __global__ void __launch_bounds__(KCfg<T>::kMaxThreads)
 k_col(const InstDesc<T>* __restrict__ insts, ColArgs a, const T* __restrict__ tw) {
   constexpr int N = 1 << LOG_N, TT = N / 16, PADN = N + N / 16 + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
-  const InstDesc<T>& I = insts[blockIdx.y];
+  const InstDesc<T>& I = insts[blockIdx.x];
   if (skip_instance(a.check_done, I.st)) return;
   const int f = threadIdx.x / TT, tid = threadIdx.x - f * TT;
-  const int kx = blockIdx.x * a.ffts + f;
+  const int kx = blockIdx.y * a.ffts + f;
   const bool act = kx < a.nkx;
   const XBuf<T> xb(sm + f * 2 * PADN, PADN);
+  const XBar bar = XBar::make(TT, a.ffts, f);
   T* col = (a.spec_sel ? I.spec2 : I.spec) + 2 * (long long)(act ? kx : 0) * N;
   cx<T> v[16];
 #pragma unroll
   for (int e = 0; e < 16; ++e) v[e] = act ? ld_cx<T>(col + 2 * (tid + e * TT)) : cx<T>{(T)0, (T)0};
-  fft_regs<T, LOG_N, false>(v, xb, tid, tw);
+  fft_regs<T, LOG_N, false>(v, xb, tid, tw, bar, bar);
   if (a.table >= 0) {
     const T* tab = (a.table ? I.t_sqrt : I.t_inv) + (long long)(act ? kx : 0) * N;
 #pragma unroll
@@ -424,7 +423,7 @@ k_col(const InstDesc<T>* __restrict__ insts, ColArgs a, const T* __restrict__ tw
       const T t = act ? __ldg(tab + tid + e * TT) : (T)0;
       v[e] = scal(v[e], t);
     }
-    fft_regs<T, LOG_N, true>(v, xb, tid, tw);
+    fft_regs<T, LOG_N, true>(v, xb, tid, tw, bar, bar);
   }
   if (act) {
 #pragma unroll

@@ -57,7 +57,7 @@ cudaError_t row_ll(bool in_spec, bool out_spec, const InstDesc<T>* d, int ninst,
 template <typename T, int LN>
 cudaError_t col_ln(const InstDesc<T>* d, int ninst, const ColArgs& a, const T* tw, cudaStream_t s) {
   constexpr int TT = (1 << LN) / 16;
-  dim3 grid((a.nkx + a.ffts - 1) / a.ffts, ninst), block(a.ffts * TT);
+  dim3 grid(ninst, (a.nkx + a.ffts - 1) / a.ffts), block(a.ffts * TT);
   k_col<T, LN><<<grid, block, Launch<T>::col_smem(LN, a.ffts), s>>>(d, a, tw);
   return cudaGetLastError();
 }

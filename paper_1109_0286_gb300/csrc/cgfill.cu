@@ -1194,15 +1194,16 @@ fill_status time_pass_t(fill_plan* p, int pass, int reps, double* ms, double* by
       default: return row<T>(p, s, OP_MASK, SC_NONE, true, true, false);
     }
   };
-  // compact CG vectors (nM values), mask words (8 bytes per 32 pixels)
+  // per instance: compact CG vectors (nM values), spectra; once per launch
+  // (shared by the batch): the column table, the mask words (8 bytes per 32 pixels)
   const double nM = double(p->nmasked), MW = n / 4.0;
-  double b = 0.0;
+  double b = 0.0, shared = MW;
   switch (pass) {
-    case 0: b = 2.0 * SB + S * t; break;
-    case 1: b = 6.0 * nM * t + SB + MW; break;
-    case 2: b = 3.0 * nM * t + SB + MW; break;
-    case 3: b = SB + 2.0 * nM * t + MW; break;
-    default: b = 2.0 * SB + MW; break;
+    case 0: b = 2.0 * SB; shared = S * t; break;
+    case 1: b = 6.0 * nM * t + SB; break;
+    case 2: b = 3.0 * nM * t + SB; break;
+    case 3: b = SB + 2.0 * nM * t; break;
+    default: b = 2.0 * SB; break;
   }
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
@@ -1217,7 +1218,7 @@ fill_status time_pass_t(fill_plan* p, int pass, int reps, double* ms, double* by
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   *ms = double(m) / reps;
-  *bytes = b * p->batch;
+  *bytes = b * p->batch + shared;
   return FILL_OK;
 }
 }  // namespace
