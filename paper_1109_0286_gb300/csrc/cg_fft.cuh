@@ -145,6 +145,44 @@ __device__ __forceinline__ cx<T> twiddle(const T* __restrict__ tw, int m) {
   return ldg_cx<T>(tw + 2 * m);
 }
 
+// W_32^e = exp(-2 pi i e / 32), e = 0..15: the factor W_nx^(e L/16) of the
+// real-transform pre/post-processing.  In constant memory, so that with the
+// element loops unrolled it is an instruction operand (no shared-memory or
+// register traffic).
+#define CGF_W32_TABLE(CAST)                                                             \
+  {CAST(1.0), CAST(0.0)}, {CAST(0.980785280403230449126), CAST(-0.195090322016128267848)}, \
+  {CAST(0.923879532511286756128), CAST(-0.382683432365089771728)},                        \
+  {CAST(0.831469612302545237079), CAST(-0.555570233019602224743)},                        \
+  {CAST(0.707106781186547524401), CAST(-0.707106781186547524401)},                        \
+  {CAST(0.555570233019602224743), CAST(-0.831469612302545237079)},                        \
+  {CAST(0.382683432365089771728), CAST(-0.923879532511286756128)},                        \
+  {CAST(0.195090322016128267848), CAST(-0.980785280403230449126)},                        \
+  {CAST(0.0), CAST(-1.0)}, {CAST(-0.195090322016128267848), CAST(-0.980785280403230449126)}, \
+  {CAST(-0.382683432365089771728), CAST(-0.923879532511286756128)},                       \
+  {CAST(-0.555570233019602224743), CAST(-0.831469612302545237079)},                       \
+  {CAST(-0.707106781186547524401), CAST(-0.707106781186547524401)},                       \
+  {CAST(-0.831469612302545237079), CAST(-0.555570233019602224743)},                       \
+  {CAST(-0.923879532511286756128), CAST(-0.382683432365089771728)},                       \
+  {CAST(-0.980785280403230449126), CAST(-0.195090322016128267848)}
+#define CGF_AS_FLOAT(x) ((float)(x))
+#define CGF_AS_DOUBLE(x) (x)
+static __constant__ float2 c_w32f[16] = {CGF_W32_TABLE(CGF_AS_FLOAT)};
+static __constant__ double2 c_w32d[16] = {CGF_W32_TABLE(CGF_AS_DOUBLE)};
+#undef CGF_AS_FLOAT
+#undef CGF_AS_DOUBLE
+#undef CGF_W32_TABLE
+
+template <typename T>
+__device__ __forceinline__ cx<T> w32(int e);
+template <>
+__device__ __forceinline__ cx<float> w32<float>(int e) {
+  return {c_w32f[e].x, c_w32f[e].y};
+}
+template <>
+__device__ __forceinline__ cx<double> w32<double>(int e) {
+  return {c_w32d[e].x, c_w32d[e].y};
+}
+
 // Barrier over the threads of one transform.  When a transform spans whole
 // warps and a CTA holds at most 8 of them, each transform syncs on its own
 // named barrier (1 + idx), so the transforms of a CTA advance independently;

@@ -227,14 +227,14 @@ __device__ __forceinline__ void mid_fill(const InstDesc<T>& I, const uint2* mwr,
 // ----------------------------------------------------------------- row pass
 // CTA = `rows` consecutive grid rows, L/16 threads per row; blockIdx.y is the
 // instance.  Shared memory: per-row FFT exchange areas, aliased with the
-// transposed tile [(L+1) x (rows+1)] used for the spectrum load / store,
+// transposed tile [(L+1) x rows] used for the spectrum load / store,
 // then the rows' mask words (nx/32 = L/16 per row: one per thread).
 // XI: the source is the seed's white noise (kept out of the other source
 // kernels, whose register allocation it would otherwise burden).
 template <typename T>
 __host__ __device__ __forceinline__ size_t row_main_bytes(int log_l, int rows) {
   const size_t L = size_t(1) << log_l, padl = L + L / 16 + 1;
-  const size_t fft = size_t(rows) * 2 * padl, tile = 2 * (L + 1) * size_t(rows + 1);
+  const size_t fft = size_t(rows) * 2 * padl, tile = 2 * (L + 1) * size_t(rows);
   return ((fft > tile ? fft : tile) * sizeof(T) + 15) & ~size_t(15);
 }
 
@@ -245,8 +245,6 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   __shared__ double red[32];
-  __shared__ cx<T> wcol[16];   // W_nx^(e TT) = W_32^e, e = 0..15 (warp-uniform factor)
-  if (threadIdx.x < 16) wcol[threadIdx.x] = twiddle<T>(tw, threadIdx.x * (kLmax / 32));
   const InstDesc<T>& I = insts[blockIdx.y];
   if (skip_instance(a.check_done, I.st)) return;
 
@@ -254,9 +252,14 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
   const int row = threadIdx.x / TT, tid = threadIdx.x - row * TT;
   const int y0 = blockIdx.x * rows, y = y0 + row;
   const int ny = a.ny;
-  const int tstride = rows + 1;
   const XBuf<T> xb(sm + row * 2 * PADL, PADL);
-  cx<T>* tile = reinterpret_cast<cx<T>*>(sm);   // [(L+1)][rows+1], aliases the FFT areas
+  // transposed tile [(L+1)][rows], aliases the FFT areas; column r of row k at
+  // k rows + (r ^ g(k)), g(k) = (k >> gs) & (rows - 1): both the
+  // consecutive-k accesses of one row and the (k, r) sweep of the global
+  // loads / stores are free of bank conflicts
+  cx<T>* tile = reinterpret_cast<cx<T>*>(sm);
+  const int gs = lr < 4 ? 4 - lr : 0;
+  auto tix = [&](int k, int r) { return (k << lr) + (r ^ ((k >> gs) & (rows - 1))); };
   uint2* mws = reinterpret_cast<uint2*>(smem_raw + row_main_bytes<T>(LOG_L, rows));
   const uint2* mwr = mws + row * TT;            // this row's mask words
   constexpr int TWS = kLmax / (2 * L);          // W_{nx}^k = table[k * TWS]
@@ -280,21 +283,21 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
     if (threadIdx.x < rows)
       tn = ldg_cx<T>((a.spec_sel ? I.spec2 : I.spec) + 2 * ((size_t)L * ny + y0 + threadIdx.x));
 #pragma unroll
-    for (int i = 0; i < 16; ++i) tile[(kk + i * TT) * tstride + rr] = t[i];
-    if (threadIdx.x < rows) tile[L * tstride + threadIdx.x] = tn;
+    for (int i = 0; i < 16; ++i) tile[tix(kk + i * TT, rr)] = t[i];
+    if (threadIdx.x < rows) tile[tix(L, threadIdx.x)] = tn;
     __syncthreads();
     // C2R: Z[k] = (X[k] + conj X[L-k]) + i e^{+2 pi i k / nx} (X[k] - conj X[L-k])
     const cx<T> wt = twiddle<T>(tw, tid * TWS);
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       const int k = tid + e * TT;
-      cx<T> xk = tile[k * tstride + row];
-      cx<T> xc = conjx(tile[(L - k) * tstride + row]);
+      cx<T> xk = tile[tix(k, row)];
+      cx<T> xc = conjx(tile[tix(L - k, row)]);
       if (k == 0) {
         xk.i = (T)0;
         xc.i = (T)0;
       }
-      const cx<T> w = cmul(wt, wcol[e]);   // W_nx^k, k = tid + e TT
+      const cx<T> w = cmul(wt, w32<T>(e));   // W_nx^k, k = tid + e TT
       const cx<T> sum = xk + xc;
       const cx<T> dif = cmulc(xk - xc, w);  // (X - conj X') e^{+i...}
       v[e] = cx<T>{sum.r - dif.i, sum.i + dif.r};
@@ -328,7 +331,6 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
       normal_pair(I.seed, (uint32_t)((rowpix >> 1) + tid + e * TT), x0, x1);
       v[e] = cx<T>{(T)x0, (T)x1};
     }
-    __syncthreads();   // wcol (written by row 0) before the row-barrier stages
   } else {
     __syncthreads();   // mask words
     const T alpha = (T)I.st->alpha, beta = (T)I.st->beta;
@@ -359,33 +361,29 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
 
   if constexpr (OUT_SPEC) {
     fft_regs<T, LOG_L, false>(v, xb, tid, tw, rbar, rbar);
-    rbar.sync();
-#pragma unroll
-    for (int e = 0; e < 16; ++e) xb.st(tid + e * TT, v[e]);
-    rbar.sync();
-    const cx<T> wt = twiddle<T>(tw, tid * TWS);
+    // Z (the half-length transform) into the transposed tile; the threads of
+    // the global stores form X from Z[k] and Z[L-k]:
     // R2C: X[k] = (Z[k] + conj Z[L-k]) / 2 - (i/2) e^{-2 pi i k/nx} (Z[k] - conj Z[L-k])
-    cx<T> nyq{v[0].r - v[0].i, (T)0};
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-      const int k = tid + e * TT;
-      const cx<T> zc = conjx(xb.ld((L - k) & (L - 1)));
-      const cx<T> zk = v[e];
-      const cx<T> ev = scal(zk + zc, (T)0.5);
-      const cx<T> od = scal(mul_mi<T, false>(zk - zc), (T)0.5);
-      v[e] = ev + cmul(od, cmul(wt, wcol[e]));
-    }
     __syncthreads();   // the tile overwrites other rows' exchange areas
 #pragma unroll
-    for (int e = 0; e < 16; ++e) tile[(tid + e * TT) * tstride + row] = v[e];
-    if (tid == 0) tile[L * tstride + row] = nyq;
+    for (int e = 0; e < 16; ++e) tile[tix(tid + e * TT, row)] = v[e];
     __syncthreads();
+    const cx<T> wt = twiddle<T>(tw, kk * TWS);
     T* spec = (a.spec_sel ? I.spec2 : I.spec) + 2 * ((size_t)kk * ny + y0 + rr);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) st_cx<T>(spec + i * tstep, tile[(kk + i * TT) * tstride + rr]);
-    if (threadIdx.x < rows)
+    for (int i = 0; i < 16; ++i) {
+      const int k = kk + i * TT;
+      const cx<T> zk = tile[tix(k, rr)];
+      const cx<T> zc = conjx(tile[tix((L - k) & (L - 1), rr)]);
+      const cx<T> ev = scal(zk + zc, (T)0.5);
+      const cx<T> od = scal(mul_mi<T, false>(zk - zc), (T)0.5);
+      st_cx<T>(spec + i * tstep, ev + cmul(od, cmul(wt, w32<T>(i))));
+    }
+    if (threadIdx.x < rows) {   // Nyquist: X[L] = Re Z[0] - Im Z[0]
+      const cx<T> z0 = tile[tix(0, threadIdx.x)];
       st_cx<T>((a.spec_sel ? I.spec2 : I.spec) + 2 * ((size_t)L * ny + y0 + threadIdx.x),
-               tile[L * tstride + threadIdx.x]);
+               cx<T>{z0.r - z0.i, (T)0});
+    }
   }
 
   if (a.sop != SC_NONE)
