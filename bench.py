@@ -76,6 +76,8 @@ def parse():
                     help="precision mode of the timed arm (profiling cases)")
     ap.add_argument("--batch", type=int, default=0, help="realizations per step (0: workload's)")
     ap.add_argument("--tol", type=float, default=0.0, help="CG tolerance (0: workload's)")
+    ap.add_argument("--update-delta", type=float, default=1e-2,
+                    help="mixed mode: FP32 residual drop that triggers an FP64 residual update")
     ap.add_argument("--host-loops", action="store_true",
                     help="launch the CG loops' kernels from the host instead of one graph "
                          "launch per loop (profilers cannot see kernels in conditional nodes)")
@@ -253,7 +255,8 @@ def run_gpu(args):
     mode = args.mode
     fdt = torch.float32 if mode == "fp32" else torch.float64
     esz = 4 if mode == "fp32" else 8
-    plan = cg.Plan(P, obs, mode=mode, batch=B, host_loops=args.host_loops)
+    plan = cg.Plan(P, obs, mode=mode, batch=B, host_loops=args.host_loops,
+                   update_delta=args.update_delta)
     d = plan.draw([spec["data_seed"]] * B)[0].clone()       # data drawn from P(k)
     seeds = lambda k: [spec["seeds"][0] + i + 100_003 * k + 10_000_019 * rank  # noqa: E731
                        for i in range(B)]
@@ -376,6 +379,7 @@ def run_gpu(args):
                            "masked_fraction": round(float((obs == 0).mean()), 4),
                            "parallelism": f"replicas{world}",
                            "loops": "host" if args.host_loops else "graph",
+                           "update_delta": args.update_delta,
                            "l2": "inputs larger than L2 (no flush)"},
                 "cg_iters_per_s": iters_per_s,
                 "iters_per_realization": iters / (B * args.steps),
