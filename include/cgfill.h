@@ -159,6 +159,26 @@ fill_status fill_apply(fill_plan* plan, int which, const void* in, void* out);
 fill_status fill_history(fill_plan* plan, int inst, double* hist, int cap, int* count);
 
 /*
+ * fill_lanczos -- Lanczos estimate of the extreme eigenvalues of the
+ * preconditioned operator (Sect. 6.4: the condition number predicts the CG
+ * convergence rate and guides the stopping rule; the tridiagonal Lanczos
+ * matrix comes from the CG coefficients, cf. Golub & Van Loan) for
+ * realization `inst` of the last fill_realize.  The device records the step
+ * lengths alpha_j and direction updates beta_j of the first history_cap
+ * iterations (FP32 / FP64 modes: the PCG; mixed mode: the FP32 PCG of the
+ * last inner solve, the whole solve with reliable updates); this call builds
+ *   T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1},  T_{j,j+1} = sqrt(beta_j)/alpha_j
+ * (k x k, k = *count) and returns its smallest and largest eigenvalues (Sturm
+ * bisection on the host) in *lmin, *lmax; kappa ~ lmax / lmin.
+ * alpha, beta: host arrays of capacity cap receiving alpha_j and beta_j
+ * (j < min(k, cap); beta of the last iteration is 0), or NULL.  Needs
+ * opts.history_cap > 0.  Errors: FILL_EINVAL, FILL_EBREAKDOWN (an alpha_j
+ * <= 0 was recorded), FILL_ECUDA.
+ */
+fill_status fill_lanczos(fill_plan* plan, int inst, double* alpha, double* beta, int cap,
+                         int* count, double* lmin, double* lmax);
+
+/*
  * fill_time_pass -- average device time of one launch of a hot-loop pass
  * kernel over all `batch` instances, timed with CUDA events on the plan's
  * stream (`reps` launches between two events, after one warm-up launch), and

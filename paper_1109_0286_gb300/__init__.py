@@ -22,7 +22,7 @@ from . import _build
 __all__ = [
     "FillOpts", "FillStats", "FillError", "load", "lib_path", "fill_opts_default",
     "fill_init", "fill_realize", "fill_draw", "fill_apply", "fill_history",
-    "fill_time_pass", "fill_set_bands", "fill_backward", "fill_autotune", "fill_group_init",
+    "fill_lanczos", "fill_time_pass", "fill_set_bands", "fill_backward", "fill_autotune", "fill_group_init",
     "fill_group_realize", "fill_group_size", "fill_group_destroy", "Group", "fill_apply_static",
     "fill_masked_count", "fill_destroy", "fill_strerror", "fill_last_error",
     "fill_version", "Plan", "MODES", "EXPORTED_SYMBOLS",
@@ -33,7 +33,8 @@ STATUS = {0: "FILL_OK", 1: "FILL_EINVAL", 2: "FILL_ENOMEM", 3: "FILL_ENOTCONV",
           4: "FILL_EBREAKDOWN", 5: "FILL_ETIMEOUT", 6: "FILL_ECUDA"}
 EXPORTED_SYMBOLS = [
     "fill_opts_default", "fill_init", "fill_realize", "fill_draw", "fill_apply",
-    "fill_history", "fill_time_pass", "fill_set_bands", "fill_backward", "fill_autotune",
+    "fill_history", "fill_lanczos", "fill_time_pass", "fill_set_bands", "fill_backward",
+    "fill_autotune",
     "fill_group_init", "fill_group_realize", "fill_group_size", "fill_group_destroy",
     "fill_apply_static", "fill_masked_count", "fill_destroy", "fill_strerror",
     "fill_last_error", "fill_version",
@@ -100,6 +101,9 @@ def load() -> ctypes.CDLL:
     lib.fill_apply.restype = _ci
     lib.fill_history.argtypes = [_vp, _ci, _vp, _ci, ctypes.POINTER(_ci)]
     lib.fill_history.restype = _ci
+    lib.fill_lanczos.argtypes = [_vp, _ci, _vp, _vp, _ci, ctypes.POINTER(_ci),
+                                 ctypes.POINTER(_cd), ctypes.POINTER(_cd)]
+    lib.fill_lanczos.restype = _ci
     lib.fill_time_pass.argtypes = [_vp, _ci, _ci, _ci, ctypes.POINTER(_cd), ctypes.POINTER(_cd)]
     lib.fill_time_pass.restype = _ci
     lib.fill_set_bands.argtypes = [_vp, _ci, _vp, _vp]
@@ -183,6 +187,20 @@ def fill_history(plan, inst, cap):
     if st != 0:
         raise FillError(st, "fill_history")
     return buf[: cnt.value].copy()
+
+
+def fill_lanczos(plan, inst, cap):
+    """CG coefficients and the Lanczos extreme eigenvalues of realization
+    ``inst`` of the last realize: ``(alpha, beta, lmin, lmax)``."""
+    a = np.zeros(max(cap, 1), dtype=np.float64)
+    b = np.zeros(max(cap, 1), dtype=np.float64)
+    cnt, lo, hi = _ci(0), _cd(0), _cd(0)
+    st = load().fill_lanczos(_vp(plan), int(inst), a.ctypes.data, b.ctypes.data, int(cap),
+                             ctypes.byref(cnt), ctypes.byref(lo), ctypes.byref(hi))
+    if st != 0:
+        raise FillError(st, "fill_lanczos")
+    k = min(cnt.value, cap)
+    return a[:k].copy(), b[:k].copy(), lo.value, hi.value
 
 
 def fill_time_pass(plan, pass_id, precision, reps):
@@ -389,6 +407,13 @@ class Plan:
 
     def history(self, inst=0):
         return fill_history(self._plan, inst, self.history_cap)
+
+    def lanczos(self, inst=0):
+        """Lanczos estimate from the recorded CG coefficients (needs
+        ``history_cap`` > 0): dict with alpha, beta, lmin, lmax, kappa."""
+        a, b, lo, hi = fill_lanczos(self._plan, inst, self.history_cap)
+        return {"alpha": a, "beta": b, "lmin": lo, "lmax": hi,
+                "kappa": hi / lo if lo > 0 else float("inf")}
 
     @property
     def masked_count(self) -> int:

@@ -162,6 +162,16 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return s;
 }
 
+// CG coefficient record for the Lanczos estimate (Sect. 6.4): alpha_j when
+// computed (j = iterations completed so far), beta_j after iteration j.
+__device__ __forceinline__ void record_alpha(CgState* st) {
+  if (st->coef && st->iter < st->hist_cap) st->coef[2 * st->iter] = st->alpha;
+}
+__device__ __forceinline__ void record_beta(CgState* st) {
+  if (st->coef && st->iter >= 1 && st->iter - 1 < st->hist_cap)
+    st->coef[2 * (st->iter - 1) + 1] = st->beta;
+}
+
 // Scalar update executed once per instance by the last CTA of a pass, with
 // the sum of all CTA partials (fixed order, so results are reproducible).
 __device__ __forceinline__ void scalar_update(int sop, CgState* st, double sum) {
@@ -191,6 +201,7 @@ __device__ __forceinline__ void scalar_update(int sop, CgState* st, double sum) 
         st->done = 1;
       } else {
         st->alpha = st->rho / sum;
+        record_alpha(st);
       }
       break;
     case SC_RCHECK:
@@ -209,6 +220,7 @@ __device__ __forceinline__ void scalar_update(int sop, CgState* st, double sum) 
       } else if (sop == SC_RCHECK_BETA) {
         st->beta = sum / st->rho;
         st->rho = sum;
+        record_beta(st);
       }
       break;
     }
@@ -223,6 +235,7 @@ __device__ __forceinline__ void scalar_update(int sop, CgState* st, double sum) 
       } else {
         st->beta = sum / st->rho;
         st->rho = sum;
+        record_beta(st);
       }
       break;
     case SC_RCHECK_UPD: {

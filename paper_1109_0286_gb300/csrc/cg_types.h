@@ -38,8 +38,10 @@ struct CgState {
   int refine;      // FP64 residual recomputations (mixed refinement)
   int total_iter;  // inner iterations summed over refinement steps
   int upd;         // reliable updates: FP64 update (FP64 state) / reload (FP32 state) due
+  int last_iter;   // mixed mode, FP32 state: iterations of the last inner solve
   CgState* peer;   // the other precision's state of the same instance (mixed mode)
   double* hist;    // ||r_k|| / ||b||, k = 0..iter
+  double* coef;    // CG coefficients: alpha_j at [2j], beta_j at [2j+1], j < hist_cap
 };
 
 // Per-instance pointers handed to every kernel (element type T of the pass).
@@ -66,6 +68,7 @@ struct InstDesc {
   CgState* st;
   double* partial;         // per-CTA partial sums
   double* hist;            // residual history (hist_cap entries), or null
+  double* coef;            // CG coefficients (2 hist_cap entries), or null
   long long nvec;          // compact CG-vector length: masked pixels of this instance
   unsigned long long seed;
 };

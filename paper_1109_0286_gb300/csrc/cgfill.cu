@@ -85,6 +85,7 @@ struct Precision {
   CgState* hst = nullptr;       // pinned mirror
   double* partial = nullptr;
   double* hist = nullptr;
+  double* coef = nullptr;       // CG coefficients, 2 history_cap per instance
   InstDesc<T>* desc = nullptr;  // device, batch
   InstDesc<T>* hdesc = nullptr; // pinned
   int rows = 0, ffts = 0;
@@ -183,6 +184,7 @@ __global__ void k_state_init(const InstDesc<T>* desc, int n, double tol2, int ma
   s.first = 1;
   s.hist_cap = hist_cap;
   s.hist = desc[i].hist;
+  s.coef = desc[i].coef;
   *desc[i].st = s;
 }
 
@@ -222,6 +224,7 @@ __global__ void k_inner_collect(CgState* st32, CgState* st64, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   st64[i].total_iter += st32[i].iter;
+  st32[i].last_iter = st32[i].iter;
   st32[i].iter = 0;
 }
 
@@ -830,6 +833,7 @@ fill_status setup_precision(fill_plan* p, const std::vector<double>& tinv,
     return FILL_ENOMEM;
   const int hc = std::max(p->o.history_cap, 1);
   if (p->dalloc(&P.hist, B * hc) != cudaSuccess) return FILL_ENOMEM;
+  if (p->o.history_cap > 0 && p->dalloc(&P.coef, 2 * B * hc) != cudaSuccess) return FILL_ENOMEM;
   if (p->dalloc(&P.stp, B) != cudaSuccess) return FILL_ENOMEM;
   {
     std::vector<CgState*> ptrs(B);
@@ -875,6 +879,7 @@ fill_status setup_precision(fill_plan* p, const std::vector<double>& tinv,
     D.st = P.st + i;
     D.partial = P.partial + i * kMaxPartials;
     D.hist = P.hist + i * hc;
+    D.coef = P.coef ? P.coef + 2 * i * hc : nullptr;
     P.hdesc[i] = D;
   }
   return FILL_OK;
@@ -1170,6 +1175,76 @@ fill_status fill_history(fill_plan* p, int inst, double* hist, int cap, int* cou
   m = p->o.history_cap == 0 ? 0 : std::min(std::min(cap, hc), m);
   if (m > 0) CK(cudaMemcpy(hist, src + size_t(inst) * hc, m * sizeof(double), cudaMemcpyDeviceToHost));
   if (count) *count = m;
+  return FILL_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// Number of eigenvalues below x of the symmetric tridiagonal matrix with
+// diagonal d and off-diagonal e (Sturm sequence of the LDL^T pivots).
+int sturm_below(const std::vector<double>& d, const std::vector<double>& e, double x) {
+  int c = 0;
+  double q = 1.0;
+  for (size_t i = 0; i < d.size(); ++i) {
+    q = d[i] - x - (i > 0 ? e[i - 1] * e[i - 1] / q : 0.0);
+    if (q == 0.0) q = -1e-300;
+    if (q < 0.0) ++c;
+  }
+  return c;
+}
+
+// The m-th smallest eigenvalue (0-based) of that matrix, by bisection inside
+// its Gershgorin interval down to a few ulp.
+double tridiag_eig(const std::vector<double>& d, const std::vector<double>& e, int m) {
+  double lo = d[0], hi = d[0];
+  for (size_t i = 0; i < d.size(); ++i) {
+    const double r = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < d.size() ? std::fabs(e[i]) : 0.0);
+    lo = std::min(lo, d[i] - r);
+    hi = std::max(hi, d[i] + r);
+  }
+  for (int it = 0; it < 200 && hi - lo > 4e-16 * std::max(std::fabs(lo), std::fabs(hi)); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (sturm_below(d, e, mid) > m)
+      hi = mid;
+    else
+      lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+}  // namespace
+
+extern "C" {
+
+fill_status fill_lanczos(fill_plan* p, int inst, double* alpha, double* beta, int cap, int* count,
+                         double* lmin, double* lmax) {
+  if (!p || inst < 0 || inst >= p->batch || cap < 0 || p->o.history_cap <= 0) return FILL_EINVAL;
+  const bool f32 = p->o.mode != FILL_MODE_FP64;
+  const CgState& st = f32 ? p->f.hst[inst] : p->g.hst[inst];
+  const double* src = f32 ? p->f.coef : p->g.coef;
+  const int hc = p->o.history_cap;
+  const int k = std::min(p->o.mode == FILL_MODE_MIXED ? st.last_iter : st.iter, hc);
+  if (count) *count = k;
+  if (lmin) *lmin = 0.0;
+  if (lmax) *lmax = 0.0;
+  if (k <= 0) return FILL_OK;
+  std::vector<double> c(2 * size_t(k));
+  CK(cudaMemcpy(c.data(), src + 2 * size_t(inst) * hc, c.size() * sizeof(double),
+                cudaMemcpyDeviceToHost));
+  for (int j = 0; j < std::min(k, cap); ++j) {
+    if (alpha) alpha[j] = c[2 * j];
+    if (beta) beta[j] = j + 1 < k ? c[2 * j + 1] : 0.0;
+  }
+  // T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1}, T_{j,j+1} = sqrt(beta_j)/alpha_j
+  std::vector<double> d(k), e(k > 1 ? k - 1 : 0);
+  for (int j = 0; j < k; ++j) {
+    const double a = c[2 * j];
+    if (!(a > 0.0)) return FILL_EBREAKDOWN;
+    d[j] = 1.0 / a + (j > 0 ? c[2 * j - 1] / c[2 * j - 2] : 0.0);
+    if (j + 1 < k) e[j] = std::sqrt(std::max(c[2 * j + 1], 0.0)) / a;
+  }
+  if (lmin) *lmin = tridiag_eig(d, e, 0);
+  if (lmax) *lmax = tridiag_eig(d, e, k - 1);
   return FILL_OK;
 }
 

@@ -227,6 +227,56 @@ def test_host_loops_equal_graph_loops(mode, precond, delta):
     assert [s["status"] for s in sh] == [0, 0, 0]
 
 
+# ------------------------------------------------------------------ Lanczos estimate
+
+def _dense_precond_spectrum(P, obs):
+    n = obs.shape[1]
+    Pf = O.hermitian_full(P, n)
+    idx = np.nonzero(obs.ravel() == 0)[0]
+    Q = O.dense_matrix(O.circulant_corr(Pf, -1.0), idx, idx)
+    Sh = O.dense_matrix(O.circulant_corr(Pf, 0.5), idx, idx)
+    return np.linalg.eigvalsh(Sh @ Q @ Sh)
+
+
+def test_lanczos_fp64_matches_oracle_and_dense_spectrum():
+    """The recorded CG coefficients equal the oracle's (first iterations, to
+    rounding); the Lanczos extremes lie inside the dense spectrum of the
+    preconditioned operator and reach its top; the library's eigenvalue
+    solve agrees with NumPy on the returned coefficients."""
+    P, obs = case(64, 64, seed=4)
+    d = O.draw(O.hermitian_full(P, 64), 3)
+    plan = cg.Plan(P, obs, mode="fp64", history_cap=4000)
+    _, st = plan.realize(gpu_map(d, torch.float64), [5], 1e-12)
+    lz = plan.lanczos(0)
+    ref = O.realize(P, obs, d, 5, tol=1e-12)
+    al, be = np.array(ref.pcg.alphas), np.array(ref.pcg.betas)
+    assert len(lz["alpha"]) == st[0]["iters"]
+    k = 10
+    assert np.allclose(lz["alpha"][:k], al[:k], rtol=1e-9, atol=0)
+    assert np.allclose(lz["beta"][:k], be[:k], rtol=1e-9, atol=0)
+    ev = _dense_precond_spectrum(P, obs)
+    assert ev.min() * (1 - 1e-6) <= lz["lmin"] and lz["lmax"] <= ev.max() * (1 + 1e-6)
+    assert abs(lz["lmax"] - ev.max()) < 1e-3 * ev.max()
+    w = np.linalg.eigvalsh(O.lanczos_tridiag(lz["alpha"], lz["beta"]))
+    assert abs(w.min() - lz["lmin"]) <= 1e-9 * w.max()
+    assert abs(w.max() - lz["lmax"]) <= 1e-9 * w.max()
+
+
+@pytest.mark.parametrize("mode", ["fp32", "mixed"])
+def test_lanczos_fp32_paths_bracket_spectrum(mode):
+    P, obs = case(64, 64, seed=4)
+    d = O.draw(O.hermitian_full(P, 64), 3)
+    dt = torch.float32 if mode == "fp32" else torch.float64
+    plan = cg.Plan(P, obs, mode=mode, history_cap=4000)
+    _, st = plan.realize(gpu_map(d, dt), [5], 1e-6 if mode == "fp32" else 1e-10)
+    lz = plan.lanczos(0)
+    ev = _dense_precond_spectrum(P, obs)
+    assert len(lz["alpha"]) > 10
+    assert ev.min() * (1 - 1e-3) <= lz["lmin"] and lz["lmax"] <= ev.max() * (1 + 1e-3)
+    assert abs(lz["lmax"] - ev.max()) < 1e-2 * ev.max()
+    assert lz["kappa"] > 1.0
+
+
 # ------------------------------------------------------------------ edge cases
 
 @pytest.mark.parametrize("mode", ["fp64", "fp32", "mixed"])
