@@ -2,7 +2,8 @@
 """Benchmark: constrained Gaussian realizations per second (and CG iterations
 per second) on the 4096^2 wide-cut workload -- 20% band plus 2000 discs of
 radius 2-20 px, a CMB-like P(k), batches of 8 realizations of one data map,
-mixed precision (FP32 FFT operator, FP64 residuals and iterative refinement)
+mixed precision (FP32 FFT operator and PCG; draw, right-hand side and true
+residuals in double-float arithmetic, about 48 significant bits)
 down to a relative residual of 1e-10 -- next to the plain FP64 GPU PCG on the
 same inputs and the FP64 CPU oracle on the host cores.
 
@@ -77,7 +78,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=0, help="realizations per step (0: workload's)")
     ap.add_argument("--tol", type=float, default=0.0, help="CG tolerance (0: workload's)")
     ap.add_argument("--update-delta", type=float, default=1e-2,
-                    help="mixed mode: FP32 residual drop that triggers an FP64 residual update")
+                    help="mixed mode: FP32 residual drop that triggers a true-residual update")
     ap.add_argument("--host-loops", action="store_true",
                     help="launch the CG loops' kernels from the host instead of one graph "
                          "launch per loop (profilers cannot see kernels in conditional nodes)")
@@ -372,7 +373,7 @@ def run_gpu(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": {"mixed": "f32+f64", "fp32": "f32", "fp64": "f64"}[mode],
+                "dtype": {"mixed": "f32+df64", "fp32": "f32", "fp64": "f64"}[mode],
                 "data": "synthetic",
                 "config": {"workload": args.workload, "grid": [ny, nx], "batch": B,
                            "tol": tol, "mode": mode, "precond": "sqrtC",

@@ -60,8 +60,10 @@ typedef enum {
   FILL_MODE_FP64 = 0,   /* every step in FP64 ("plain FP64 PCG") */
   FILL_MODE_FP32 = 1,   /* FP32 FFT operator and vectors, FP64-accurate inner
                            products; maps are float */
-  FILL_MODE_MIXED = 2   /* FP64 draw, right-hand side and residuals; FP32 PCG
-                           iterations with FP64 residual updates; maps double */
+  FILL_MODE_MIXED = 2   /* high-precision draw, right-hand side and true residuals
+                           in double-float arithmetic (pairs of FP32 values,
+                           about 48 significant bits, run on the FP32 pipes);
+                           FP32 PCG iterations with residual updates; maps double */
 } fill_mode;
 
 typedef struct {
@@ -70,7 +72,7 @@ typedef struct {
                             1: sqrt(C) split preconditioner (Sect. 2.4); default 1 */
   int batch;             /* realizations per fill_realize call (same mask and P); default 1 */
   int max_iter;          /* CG iterations per solve; default 10000 */
-  int max_refine;        /* FP64 refinement steps (mixed mode); default 10 */
+  int max_refine;        /* refinement steps (mixed mode, update_delta = 0); default 10 */
   int host_loops;        /* 0: each CG loop is one CUDA-graph launch (a conditional
                             WHILE node; default); 1: every kernel of the loops is
                             launched from the host, with the convergence flags read
@@ -83,19 +85,19 @@ typedef struct {
   int ffts_per_cta;      /* column FFTs per CTA, 0 = default schedule */
   int backward;          /* 1: allocate the buffers fill_backward needs; default 0 */
   double update_delta;   /* mixed mode: one FP32 PCG with reliable updates -- the FP32
-                            correction is folded into the FP64 solution and the
-                            residual recomputed in FP64 whenever the FP32 residual
-                            has fallen by this factor; default 1e-2.  0: restarted
-                            iterative refinement (FP32 solves to inner_tol) */
+                            correction is folded into the double-float solution and
+                            the residual recomputed in double-float whenever the FP32
+                            residual has fallen by this factor; default 1e-2.  0:
+                            restarted iterative refinement (FP32 solves to inner_tol) */
 } fill_opts;
 
 typedef struct {
   int iters;             /* CG operator applications (all inner solves in mixed mode) */
-  int refine_steps;      /* FP64 residual recomputations (mixed mode) */
+  int refine_steps;      /* true-residual recomputations (mixed mode) */
   int status;            /* fill_status of this realization */
   int launches;          /* kernels launched by the whole call (same for every entry) */
   double rel_resid;      /* recurrence ||r|| / ||b|| at exit (last inner solve) */
-  double true_rel_resid; /* FP64 ||b - A u|| / ||b|| (mixed mode), else -1 */
+  double true_rel_resid; /* ||b - A u|| / ||b|| in double-float (mixed mode), else -1 */
   double ms;             /* wall time of the whole call */
 } fill_stats;
 
@@ -122,7 +124,7 @@ fill_status fill_init(fill_plan** plan, int ny, int nx, const double* P_half,
  *          consecutive maps (0 = one map shared by the whole batch).
  * seeds:   host, batch uint64; the seed alone fixes the white noise xi.
  * tol:     stop when ||b - A u|| <= tol ||b|| (recurrence residual in the
- *          FP32/FP64 modes; the FP64 true residual in mixed mode).
+ *          FP32/FP64 modes; the double-float true residual in mixed mode).
  * out:     device, batch contiguous maps of ny*nx (same type as d);
  *          out_U = d_U exactly, out_M = y_M + u.
  * stats:   host array of batch entries, or NULL.
@@ -152,7 +154,7 @@ fill_status fill_apply(fill_plan* plan, int which, const void* in, void* out);
  * fill_history -- copies the residual history ||r_k||/||b||, k = 0..iters, of
  * realization `inst` of the last fill_realize into host array hist of
  * capacity cap (FP32 / FP64 modes: the CG recurrence residual per iteration;
- * mixed mode: the FP64 true residual after each refinement step, k = 0 being
+ * mixed mode: the true residual after each residual update, k = 0 being
  * the start).  Needs opts.history_cap > 0 at fill_init; *count receives the
  * number of entries written.  Errors: FILL_EINVAL, FILL_ECUDA.
  */

@@ -32,15 +32,48 @@ __device__ __forceinline__ cx<T> conjx(cx<T> a) { return {a.r, -a.i}; }
 template <typename T>
 __device__ __forceinline__ cx<T> scal(cx<T> a, T s) { return {a.r * s, a.i * s}; }
 
+// Double-float arithmetic (error-free transformations: Knuth's TwoSum for
+// the high parts, FMA-exact products; Dekker's renormalisation).  Relative
+// error of an operation about 2^-46 of the operands' magnitude.
+__device__ __forceinline__ df operator+(df a, df b) {
+  const float s = a.hi + b.hi;
+  const float v = s - a.hi;
+  const float e = ((a.hi - (s - v)) + (b.hi - v)) + (a.lo + b.lo);
+  const float h = s + e;
+  return df(h, e - (h - s));
+}
+__device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+__device__ __forceinline__ df operator*(df a, df b) {
+  const float p = a.hi * b.hi;
+  const float e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, fmaf(a.hi, b.hi, -p)));
+  const float h = p + e;
+  return df(h, e - (h - p));
+}
+
 // Vector types for 8- / 16-byte global accesses.
 template <typename T> struct V2;
 template <> struct V2<float> { using t = float2; };
 template <> struct V2<double> { using t = double2; };
+template <> struct V2<df> { using t = df2; };
 
 template <typename T>
 __device__ __forceinline__ cx<T> ldg_cx(const T* p) {
   typename V2<T>::t v = __ldg(reinterpret_cast<const typename V2<T>::t*>(p));
   return {v.x, v.y};
+}
+// Read-only scalar load.
+template <typename T>
+__device__ __forceinline__ T ldg1(const T* p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ df ldg1<df>(const df* p) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return df(v.x, v.y);
+}
+template <>
+__device__ __forceinline__ cx<df> ldg_cx<df>(const df* p) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  return {df(v.x, v.y), df(v.z, v.w)};
 }
 template <typename T>
 __device__ __forceinline__ cx<T> ld_cx(const T* p) {
@@ -67,6 +100,23 @@ __device__ __forceinline__ void st_pair(T* p, T a, T b) {
   v.x = a;
   v.y = b;
   *reinterpret_cast<typename V2<T>::t*>(p) = v;
+}
+
+// Pixel pairs of the caller's maps, converted to / from the pass element type.
+template <typename T>
+__device__ __forceinline__ void ld_map_pair(const typename MapOf<T>::type* p, T& a, T& b) {
+  using M = typename MapOf<T>::type;
+  typename V2<M>::t v = *reinterpret_cast<const typename V2<M>::t*>(p);
+  a = (T)v.x;
+  b = (T)v.y;
+}
+template <typename T>
+__device__ __forceinline__ void st_map_pair(typename MapOf<T>::type* p, T a, T b) {
+  using M = typename MapOf<T>::type;
+  typename V2<M>::t v;
+  v.x = static_cast<M>(a);
+  v.y = static_cast<M>(b);
+  *reinterpret_cast<typename V2<M>::t*>(p) = v;
 }
 
 // ---------------------------------------------------------------------------
@@ -131,6 +181,13 @@ struct Acc<float> {
     hi = t;
   }
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+template <>
+struct Acc<df> {
+  df s = df(0.f, 0.f);
+  __device__ __forceinline__ void add_prod(df a, df b) { s = s + a * b; }
+  __device__ __forceinline__ double value() const { return (double)s.hi + (double)s.lo; }
 };
 
 template <>

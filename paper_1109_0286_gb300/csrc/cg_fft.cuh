@@ -49,6 +49,20 @@ struct XBuf<double> {
   }
 };
 
+template <>
+struct XBuf<df> {   // same layout as FP64: split real / imaginary arrays of 8-byte elements
+  df* re;
+  df* im;
+  __device__ __forceinline__ XBuf(df* base, int padl) : re(base), im(base + padl) {}
+  __device__ __forceinline__ void st(int i, cx<df> v) const {
+    re[i + (i >> 4)] = v.r;
+    im[i + (i >> 4)] = v.i;
+  }
+  __device__ __forceinline__ cx<df> ld(int i) const {
+    return {re[i + (i >> 4)], im[i + (i >> 4)]};
+  }
+};
+
 // a * (-i) for the forward transform, a * (+i) for the inverse.
 template <typename T, bool INV>
 __device__ __forceinline__ cx<T> mul_mi(cx<T> a) {
@@ -166,8 +180,11 @@ __device__ __forceinline__ cx<T> twiddle(const T* __restrict__ tw, int m) {
   {CAST(-0.980785280403230449126), CAST(-0.195090322016128267848)}
 #define CGF_AS_FLOAT(x) ((float)(x))
 #define CGF_AS_DOUBLE(x) (x)
+#define CGF_AS_DF(x) df(x)
 static __constant__ float2 c_w32f[16] = {CGF_W32_TABLE(CGF_AS_FLOAT)};
 static __constant__ double2 c_w32d[16] = {CGF_W32_TABLE(CGF_AS_DOUBLE)};
+static __constant__ df2 c_w32h[16] = {CGF_W32_TABLE(CGF_AS_DF)};
+#undef CGF_AS_DF
 #undef CGF_AS_FLOAT
 #undef CGF_AS_DOUBLE
 #undef CGF_W32_TABLE
@@ -181,6 +198,10 @@ __device__ __forceinline__ cx<float> w32<float>(int e) {
 template <>
 __device__ __forceinline__ cx<double> w32<double>(int e) {
   return {c_w32d[e].x, c_w32d[e].y};
+}
+template <>
+__device__ __forceinline__ cx<df> w32<df>(int e) {
+  return {c_w32h[e].x, c_w32h[e].y};
 }
 
 // Barrier over the threads of one transform.  When a transform spans whole

@@ -20,6 +20,7 @@ constexpr int kSrcChunk = 4, kSrcChunkWide = 2, kSinkChunk = 4;
 template <typename T> struct KCfg;
 template <> struct KCfg<float> { static constexpr int kMaxThreads = 1024; };
 template <> struct KCfg<double> { static constexpr int kMaxThreads = 512; };
+template <> struct KCfg<df> { static constexpr int kMaxThreads = 512; };
 
 // Masked flags and compact CG-vector indices of the pixel pair (pix, pix+1)
 // (pix even) from the pair's mask word: a popcount.
@@ -159,7 +160,7 @@ __device__ __forceinline__ void sink_fill(const InstDesc<T>& I, const uint2* mwr
       if constexpr (OP == OP_Q) ldc(I.p, q[e], x0[e], x1[e]);
       if constexpr (OP == OP_Z) ldc(I.r, q[e], x0[e], x1[e]);
       if constexpr (OP == OP_RES) ldc(I.b, q[e], x0[e], x1[e]);
-      if constexpr (OP == OP_GRAD) ld_pair(I.gx + rowpix + 2 * j, x0[e], x1[e]);
+      if constexpr (OP == OP_GRAD) ld_map_pair<T>(I.gx + rowpix + 2 * j, x0[e], x1[e]);
     }
 #pragma unroll
     for (int e = 0; e < CK; ++e) {
@@ -190,7 +191,7 @@ __device__ __forceinline__ void sink_fill(const InstDesc<T>& I, const uint2* mwr
       } else if constexpr (OP == OP_GRAD) {
         // v = C^-1 lam.  dL/dd_U = g_U - (C^-1 lam)_U, dL/dd_M = 0;
         // dL/dy = h = g on M, (C^-1 lam)_U on U (kept in y).
-        st_pair(I.out + rowpix + 2 * j, m0 ? (T)0 : x0[e] - a0, m1 ? (T)0 : x1[e] - a1);
+        st_map_pair<T>(I.out + rowpix + 2 * j, m0 ? (T)0 : x0[e] - a0, m1 ? (T)0 : x1[e] - a1);
         st_pair(I.y + rowpix + 2 * j, m0 ? x0[e] : a0, m1 ? x1[e] : a1);
       } else if constexpr (OP == OP_STORE_Y) {
         st_pair(I.y + rowpix + 2 * j, a0, a1);
@@ -213,7 +214,7 @@ __device__ __forceinline__ void mid_fill(const InstDesc<T>& I, const uint2* mwr,
     observed_at(mwr, j, o0, o1);
     if constexpr (OP == OP_Y_W) {
       T d0, d1;
-      ld_pair(I.d + rowpix + 2 * j, d0, d1);
+      ld_map_pair<T>(I.d + rowpix + 2 * j, d0, d1);
       st_pair(I.y + rowpix + 2 * j, v[e].r, v[e].i);
       v[e].r = o0 ? d0 - v[e].r : (T)0;
       v[e].i = o1 ? d1 - v[e].i : (T)0;
@@ -418,7 +419,7 @@ k_col(const InstDesc<T>* __restrict__ insts, ColArgs a, const T* __restrict__ tw
     const T* tab = (a.table ? I.t_sqrt : I.t_inv) + (long long)(act ? kx : 0) * N;
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
-      const T t = act ? __ldg(tab + tid + e * TT) : (T)0;
+      const T t = act ? ldg1(tab + tid + e * TT) : (T)0;
       v[e] = scal(v[e], t);
     }
     fft_regs<T, LOG_N, true>(v, xb, tid, tw, bar, bar);
@@ -459,31 +460,46 @@ k_vec(const InstDesc<T>* __restrict__ insts, VecArgs a) {
       const int pix = 2 * j;
       const PairIdx q = pair_index(I.mw, pix);
       switch (a.op) {
-        case VOP_ASSEMBLE: {
-          T d0, d1, y0, y1, u0, u1;
+        case VOP_ASSEMBLE: {   // observed pixels: the caller's values, bit for bit
+          using M = typename MapOf<T>::type;
+          M d0, d1;
+          T y0, y1, u0, u1;
           ld_pair(I.d + pix, d0, d1);
           ld_pair(I.y + pix, y0, y1);
           ldc(I.u, q, u0, u1);
-          st_pair(I.out + pix, q.m0 ? y0 + u0 : d0, q.m1 ? y1 + u1 : d1);
+          st_pair(I.out + pix, q.m0 ? static_cast<M>(y0 + u0) : d0,
+                  q.m1 ? static_cast<M>(y1 + u1) : d1);
           break;
         }
         case VOP_COPY_D: {
-          T d0, d1;
+          typename MapOf<T>::type d0, d1;
           ld_pair(I.d + pix, d0, d1);
           st_pair(I.out + pix, d0, d1);
           break;
         }
         case VOP_MAKE_W: {
           T d0, d1, y0, y1, u0, u1;
-          ld_pair(I.d + pix, d0, d1);
+          ld_map_pair<T>(I.d + pix, d0, d1);
           ld_pair(I.y + pix, y0, y1);
           ldc(I.u, q, u0, u1);
           st_pair(I.w + pix, q.m0 ? u0 : d0 - y0, q.m1 ? u1 : d1 - y1);
           break;
         }
+        case VOP_MAP_IN: {
+          T a0, a1;
+          ld_map_pair<T>(I.d + pix, a0, a1);
+          st_pair(I.w + pix, a0, a1);
+          break;
+        }
+        case VOP_MAP_OUT: {
+          T a0, a1;
+          ld_pair(I.y + pix, a0, a1);
+          st_map_pair<T>(I.out + pix, a0, a1);
+          break;
+        }
         case VOP_LOAD_G: {
           T g0, g1;
-          ld_pair(I.gx + pix, g0, g1);
+          ld_map_pair<T>(I.gx + pix, g0, g1);
           g0 = q.m0 ? g0 : (T)0;
           g1 = q.m1 ? g1 : (T)0;
           stc(I.r, q, g0, g1);
@@ -518,7 +534,7 @@ k_band_dot(const InstDesc<T>* __restrict__ insts, DotArgs a) {
   for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.nmodes;
        m += (long long)gridDim.x * blockDim.x) {
     const cx<T> x = ld_cx<T>(I.spec + 2 * m), z = ld_cx<T>(I.spec2 + 2 * m);
-    const double v = (double)((x.r * z.r + x.i * z.i) * __ldg(coef + m));
+    const double v = (double)((x.r * z.r + x.i * z.i) * ldg1(coef + m));
     atomicAdd(&hist[__ldg(a.band + m)], v);
   }
   __syncthreads();

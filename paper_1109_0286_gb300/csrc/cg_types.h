@@ -44,6 +44,39 @@ struct CgState {
   double* coef;    // CG coefficients: alpha_j at [2j], beta_j at [2j+1], j < hist_cap
 };
 
+#ifdef __CUDACC__
+#define CGF_HD __host__ __device__
+#else
+#define CGF_HD
+#endif
+
+// Double-float number hi + lo (|lo| <= ulp(hi) / 2, about 48 significant
+// bits): the high-precision type of the mixed mode, whose arithmetic runs on
+// the FP32 pipes (GB300's FP64 rate is 1/58 of its FP32 rate).
+struct df {
+  float hi, lo;
+  df() = default;
+  CGF_HD constexpr df(float h, float l) : hi(h), lo(l) {}
+  CGF_HD constexpr df(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
+  CGF_HD constexpr df(float x) : hi(x), lo(0.f) {}
+  CGF_HD constexpr df(int x) : df((double)x) {}
+  CGF_HD explicit operator float() const { return hi + lo; }
+  CGF_HD explicit operator double() const { return (double)hi + (double)lo; }
+};
+struct alignas(16) df2 {
+  df x, y;
+};
+
+// Element type of the caller's maps (d, out, dL/dx) for a pass element type.
+template <typename T>
+struct MapOf {
+  using type = T;
+};
+template <>
+struct MapOf<df> {
+  using type = double;
+};
+
 // Per-instance pointers handed to every kernel (element type T of the pass).
 template <typename T>
 struct InstDesc {
@@ -59,9 +92,9 @@ struct InstDesc {
   T* u;
   T* y;
   T* b;
-  const T* d;              // caller's data map
-  T* out;                  // caller's output map (dL/dd in the backward pass)
-  const T* gx;             // caller's dL/dx (backward pass)
+  const typename MapOf<T>::type* d;    // caller's data map
+  typename MapOf<T>::type* out;        // caller's output map (dL/dd in the backward pass)
+  const typename MapOf<T>::type* gx;   // caller's dL/dx (backward pass)
   T* w;                    // w = d - y on U, u on M (backward pass)
   float* dlt;              // FP32 correction (mixed refinement, FP64 passes)
   float* r32;              // FP32 residual target (mixed refinement, FP64 passes)
@@ -127,6 +160,8 @@ enum VecOp : int {
   VOP_MAKE_W = 5,     // w = d - y on U, u on M
   VOP_LOAD_G = 6,     // r = b = P_x g (r32 = (float) r if set); acc ||r||^2
   VOP_ZERO_UP = 7,    // u = 0, p = 0
+  VOP_MAP_IN = 8,     // w = d (caller's map -> pass element type)
+  VOP_MAP_OUT = 9,    // out = y (pass element type -> caller's map)
 };
 
 // Launch arguments of the pass kernels.

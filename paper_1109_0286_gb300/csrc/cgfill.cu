@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/cgfill.h"
@@ -114,13 +115,15 @@ struct fill_plan {
   int* hloop = nullptr;          // pinned mirror
   long long if_kernels = 0;      // kernels inside the update IF node
   Precision<float> f;
-  Precision<double> g;
+  Precision<double> g;           // FP64 mode
+  Precision<df> h;               // mixed mode's high precision (double-float)
   std::vector<void*> dev;
   std::vector<void*> host;
   ~fill_plan() {
     if (mixed_graph) cudaGraphExecDestroy(mixed_graph);
     if (f.iter_graph) cudaGraphExecDestroy(f.iter_graph);
     if (g.iter_graph) cudaGraphExecDestroy(g.iter_graph);
+    if (h.iter_graph) cudaGraphExecDestroy(h.iter_graph);
     for (void* p : dev) cudaFree(p);
     for (void* p : host) cudaFreeHost(p);
     if (cap) cudaStreamDestroy(cap);
@@ -235,6 +238,8 @@ template <>
 Precision<float>& prec<float>(fill_plan* p) { return p->f; }
 template <>
 Precision<double>& prec<double>(fill_plan* p) { return p->g; }
+template <>
+Precision<df>& prec<df>(fill_plan* p) { return p->h; }
 
 // Launch context: one grid size, one descriptor array (a plan's instances or
 // a size class of a group).
@@ -507,28 +512,27 @@ fill_status run_pcg(fill_plan* p) {
 // residual r = b - A u in FP64 (iterative refinement).
 fill_status mixed_refine(fill_plan* p, double tol) {
   const int B = p->batch;
-  const size_t n = p->npix;
   const int nb = (B + 127) / 128;
   for (int outer = 0; outer < p->o.max_refine; ++outer) {
     ++p->launches;
-    k_inner_reset<<<nb, 128, 0, p->s>>>(p->f.st, p->g.st, B, tol, p->o.inner_tol, p->o.max_iter);
+    k_inner_reset<<<nb, 128, 0, p->s>>>(p->f.st, p->h.st, B, tol, p->o.inner_tol, p->o.max_iter);
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(p->f.u, 0, B * p->nv * sizeof(float), p->s));
     CK(cudaMemsetAsync(p->f.p, 0, B * p->nv * sizeof(float), p->s));
     CK(pcg_start<float>(p, p->s, SC_BB));
     fill_status fs = run_pcg<float>(p);
     if (fs != FILL_OK) return fs;
-    CK(row<double>(p, p->s, OP_U64_UPD, SC_NONE, false, true, true));
-    CK(col<double>(p, p->s, 0, true));
-    CK(row<double>(p, p->s, OP_RES, SC_RES, true, false, true));
-    CK(cudaMemcpyAsync(p->g.hst, p->g.st, sizeof(CgState) * B, cudaMemcpyDeviceToHost, p->s));
+    CK(row<df>(p, p->s, OP_U64_UPD, SC_NONE, false, true, true));
+    CK(col<df>(p, p->s, 0, true));
+    CK(row<df>(p, p->s, OP_RES, SC_RES, true, false, true));
+    CK(cudaMemcpyAsync(p->h.hst, p->h.st, sizeof(CgState) * B, cudaMemcpyDeviceToHost, p->s));
     CK(cudaStreamSynchronize(p->s));
     bool all = true;
-    for (int i = 0; i < B; ++i) all = all && p->g.hst[i].done;
+    for (int i = 0; i < B; ++i) all = all && p->h.hst[i].done;
     if (all) break;
   }
   ++p->launches;
-  k_inner_collect<<<nb, 128, 0, p->s>>>(p->f.st, p->g.st, B);
+  k_inner_collect<<<nb, 128, 0, p->s>>>(p->f.st, p->h.st, B);
   CK(cudaGetLastError());
   return FILL_OK;
 }
@@ -594,9 +598,9 @@ cudaError_t capture_if(cudaStream_t s, cudaStream_t s2, cudaGraphConditionalHand
 // The update passes sit in an IF node that runs only when some instance has
 // an update due (kernels inside still skip the instances without one).
 cudaError_t mixed_update_passes(fill_plan* p, cudaStream_t s) {
-  CE(row<double>(p, s, OP_U64_UPD, SC_NONE, false, true, SKIP_UNLESS_UPD));
-  CE(col<double>(p, s, 0, SKIP_UNLESS_UPD));
-  CE(row<double>(p, s, OP_RES, SC_RES_UPD, true, false, SKIP_UNLESS_UPD));
+  CE(row<df>(p, s, OP_U64_UPD, SC_NONE, false, true, SKIP_UNLESS_UPD));
+  CE(col<df>(p, s, 0, SKIP_UNLESS_UPD));
+  CE(row<df>(p, s, OP_RES, SC_RES_UPD, true, false, SKIP_UNLESS_UPD));
   return row<float>(p, s, OP_LOAD_R, SC_CLEAR_UPD, false, true, SKIP_UNLESS_UPD);
 }
 
@@ -605,9 +609,9 @@ cudaError_t update_if(fill_plan* p, cudaStream_t s, bool reload) {
     // no graph: the update passes run every iteration and skip the instances
     // without an update due
     if (reload) return mixed_update_passes(p, s);
-    CE(row<double>(p, s, OP_U64_UPD, SC_NONE, false, true, SKIP_UNLESS_UPD));
-    CE(col<double>(p, s, 0, SKIP_UNLESS_UPD));
-    return row<double>(p, s, OP_RES, SC_RES_UPD, true, false, SKIP_UNLESS_UPD);
+    CE(row<df>(p, s, OP_U64_UPD, SC_NONE, false, true, SKIP_UNLESS_UPD));
+    CE(col<df>(p, s, 0, SKIP_UNLESS_UPD));
+    return row<df>(p, s, OP_RES, SC_RES_UPD, true, false, SKIP_UNLESS_UPD);
   }
   cudaStreamCaptureStatus st;
   cudaGraph_t g = nullptr;
@@ -615,14 +619,14 @@ cudaError_t update_if(fill_plan* p, cudaStream_t s, bool reload) {
   cudaGraphConditionalHandle h;
   CE(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
   ++p->launches;
-  k_if_any_upd<<<1, 256, 0, s>>>(h, p->g.stp, p->batch, p->loop_counter);
+  k_if_any_upd<<<1, 256, 0, s>>>(h, p->h.stp, p->batch, p->loop_counter);
   CE(cudaGetLastError());
   const long long before = p->launches;
   cudaError_t e = capture_if(s, p->cap2, h, [&](cudaStream_t s2) -> cudaError_t {
     if (reload) return mixed_update_passes(p, s2);
-    CE(row<double>(p, s2, OP_U64_UPD, SC_NONE, false, true, SKIP_UNLESS_UPD));
-    CE(col<double>(p, s2, 0, SKIP_UNLESS_UPD));
-    return row<double>(p, s2, OP_RES, SC_RES_UPD, true, false, SKIP_UNLESS_UPD);
+    CE(row<df>(p, s2, OP_U64_UPD, SC_NONE, false, true, SKIP_UNLESS_UPD));
+    CE(col<df>(p, s2, 0, SKIP_UNLESS_UPD));
+    return row<df>(p, s2, OP_RES, SC_RES_UPD, true, false, SKIP_UNLESS_UPD);
   });
   p->if_kernels = p->launches - before;
   return e;
@@ -663,20 +667,19 @@ fill_status build_mixed_graph(fill_plan* p) {
 // with ||b||^2 are set; u64 = 0).
 fill_status mixed_reliable(fill_plan* p, double tol) {
   const int B = p->batch;
-  const size_t n = p->npix;
   const int nb = (B + 127) / 128;
   const double d = p->o.update_delta;
   ++p->launches;
-  k_link_states<<<nb, 128, 0, p->s>>>(p->f.st, p->g.st, B, d * d);
+  k_link_states<<<nb, 128, 0, p->s>>>(p->f.st, p->h.st, B, d * d);
   CK(cudaGetLastError());
   CK(cudaMemsetAsync(p->f.u, 0, B * p->nv * sizeof(float), p->s));
   CK(cudaMemsetAsync(p->f.p, 0, B * p->nv * sizeof(float), p->s));
   // instances with b = 0 are done in the FP64 state: mirror that to FP32
   ++p->launches;
-  k_inner_reset<<<nb, 128, 0, p->s>>>(p->f.st, p->g.st, B, tol, 0.0, p->o.max_iter);
+  k_inner_reset<<<nb, 128, 0, p->s>>>(p->f.st, p->h.st, B, tol, 0.0, p->o.max_iter);
   CK(cudaGetLastError());
   ++p->launches;
-  k_link_states<<<nb, 128, 0, p->s>>>(p->f.st, p->g.st, B, d * d);
+  k_link_states<<<nb, 128, 0, p->s>>>(p->f.st, p->h.st, B, d * d);
   CK(cudaGetLastError());
   CK(pcg_start<float>(p, p->s, SC_BB));
   fill_status fs;
@@ -692,11 +695,11 @@ fill_status mixed_reliable(fill_plan* p, double tol) {
   }
   if (fs != FILL_OK) return fs;
   // fold anything left (breakdown / limits) and report the true residual
-  CK(row<double>(p, p->s, OP_U64_UPD, SC_NONE, false, true, SKIP_DONE));
-  CK(col<double>(p, p->s, 0, SKIP_DONE));
-  CK(row<double>(p, p->s, OP_RES, SC_RES, true, false, SKIP_DONE));
+  CK(row<df>(p, p->s, OP_U64_UPD, SC_NONE, false, true, SKIP_DONE));
+  CK(col<df>(p, p->s, 0, SKIP_DONE));
+  CK(row<df>(p, p->s, OP_RES, SC_RES, true, false, SKIP_DONE));
   ++p->launches;
-  k_inner_collect<<<nb, 128, 0, p->s>>>(p->f.st, p->g.st, B);
+  k_inner_collect<<<nb, 128, 0, p->s>>>(p->f.st, p->h.st, B);
   CK(cudaGetLastError());
   return FILL_OK;
 }
@@ -752,7 +755,6 @@ fill_status backward_t(fill_plan* p, const void* d, long long d_stride, const vo
                        double tol, void* grad_d, double* grad_bands) {
   Precision<T>& P = prec<T>(p);
   const int B = p->batch;
-  const size_t n = p->npix;
   fill_desc<T>(p, d, d_stride, nullptr, grad_d, gx);
   CK(upload_desc<T>(p));
   CK(vec<T>(p, p->s, VOP_MAKE_W, SC_NONE, false));
@@ -793,9 +795,10 @@ void fill_desc(fill_plan* p, const void* d, long long d_stride, const uint64_t* 
   for (int i = 0; i < p->batch; ++i) {
     InstDesc<T>& D = P.hdesc[i];
     const size_t off = size_t(i) * p->npix;
-    D.d = d ? reinterpret_cast<const T*>(d) + size_t(d_stride) * i : nullptr;
-    D.out = out ? reinterpret_cast<T*>(out) + off : nullptr;
-    D.gx = gx ? reinterpret_cast<const T*>(gx) + off : nullptr;
+    using M = typename MapOf<T>::type;
+    D.d = d ? reinterpret_cast<const M*>(d) + size_t(d_stride) * i : nullptr;
+    D.out = out ? reinterpret_cast<M*>(out) + off : nullptr;
+    D.gx = gx ? reinterpret_cast<const M*>(gx) + off : nullptr;
     if (seeds) D.seed = (unsigned long long)seeds[i];
   }
 }
@@ -901,7 +904,7 @@ void collect_stats(fill_plan* p, fill_stats* stats, double ms, fill_status* wors
     fill_stats st{};
     if (mixed) {
       const CgState& a = p->f.hst[i];
-      const CgState& g = p->g.hst[i];
+      const CgState& g = p->h.hst[i];
       st.iters = g.total_iter;
       st.refine_steps = g.refine;
       const bool conv = g.rr <= g.tol2 * g.bb;
@@ -1018,14 +1021,16 @@ fill_status fill_init(fill_plan** out, int ny, int nx, const double* P_half,
     fs = setup_precision<float>(p, tinv, tsqrt, tw);
     if (fs != FILL_OK) return fail(fs);
   }
-  if (o.mode == FILL_MODE_FP64 || o.mode == FILL_MODE_MIXED) {
+  if (o.mode == FILL_MODE_FP64) {
     fs = setup_precision<double>(p, tinv, tsqrt, tw);
     if (fs != FILL_OK) return fail(fs);
   }
   if (o.mode == FILL_MODE_MIXED) {
+    fs = setup_precision<df>(p, tinv, tsqrt, tw);
+    if (fs != FILL_OK) return fail(fs);
     for (int i = 0; i < p->batch; ++i) {
-      p->g.hdesc[i].dlt = p->f.hdesc[i].u;
-      p->g.hdesc[i].r32 = p->f.hdesc[i].r;
+      p->h.hdesc[i].dlt = p->f.hdesc[i].u;
+      p->h.hdesc[i].r32 = p->f.hdesc[i].r;
     }
   }
   e = cudaDeviceSynchronize();
@@ -1083,18 +1088,18 @@ fill_status fill_realize(fill_plan* p, const void* d, long long d_stride, const 
     }
   } else {
     // Mixed: FP64 draw / RHS / residual, FP32 inner PCG, FP64 refinement.
-    fill_desc<double>(p, d, d_stride, seeds, out, nullptr);
+    fill_desc<df>(p, d, d_stride, seeds, out, nullptr);
     fill_desc<float>(p, nullptr, 0, seeds, nullptr, nullptr);
-    CK(upload_desc<double>(p));
+    CK(upload_desc<df>(p));
     CK(upload_desc<float>(p));
-    CK(init_states<double>(p, tol));
+    CK(init_states<df>(p, tol));
     CK(init_states<float>(p, p->o.inner_tol));
-    CK(cudaMemsetAsync(p->g.u, 0, B * p->nv * sizeof(double), p->s));
-    CK(draw_and_rhs<double>(p, p->s, false));
+    CK(cudaMemsetAsync(p->h.u, 0, B * p->nv * sizeof(df), p->s));
+    CK(draw_and_rhs<df>(p, p->s, false));
     fs = mixed_solve(p, tol);
     if (fs != FILL_OK) return fs;
-    CK(vec<double>(p, p->s, VOP_ASSEMBLE, SC_NONE, false));
-    CK(cudaMemcpyAsync(p->g.hst, p->g.st, sizeof(CgState) * B, cudaMemcpyDeviceToHost, p->s));
+    CK(vec<df>(p, p->s, VOP_ASSEMBLE, SC_NONE, false));
+    CK(cudaMemcpyAsync(p->h.hst, p->h.st, sizeof(CgState) * B, cudaMemcpyDeviceToHost, p->s));
     CK(cudaMemcpyAsync(p->f.hst, p->f.st, sizeof(CgState) * B, cudaMemcpyDeviceToHost, p->s));
   }
   CK(cudaStreamSynchronize(p->s));
@@ -1114,7 +1119,7 @@ fill_status fill_draw(fill_plan* p, const uint64_t* seeds, void* out) {
     CK(col<float>(p, p->s, 1, false));
     CK(row<float>(p, p->s, OP_STORE_Y, SC_NONE, true, false, false));
     CK(cudaMemcpyAsync(out, p->f.y, p->batch * n * sizeof(float), cudaMemcpyDeviceToDevice, p->s));
-  } else {
+  } else if (p->o.mode == FILL_MODE_FP64) {
     fill_desc<double>(p, nullptr, 0, seeds, nullptr, nullptr);
     CK(upload_desc<double>(p));
     CK(init_states<double>(p, 0.0));
@@ -1122,6 +1127,14 @@ fill_status fill_draw(fill_plan* p, const uint64_t* seeds, void* out) {
     CK(col<double>(p, p->s, 1, false));
     CK(row<double>(p, p->s, OP_STORE_Y, SC_NONE, true, false, false));
     CK(cudaMemcpyAsync(out, p->g.y, p->batch * n * sizeof(double), cudaMemcpyDeviceToDevice, p->s));
+  } else {
+    fill_desc<df>(p, nullptr, 0, seeds, out, nullptr);
+    CK(upload_desc<df>(p));
+    CK(init_states<df>(p, 0.0));
+    CK(row<df>(p, p->s, OP_XI, SC_NONE, false, true, false));
+    CK(col<df>(p, p->s, 1, false));
+    CK(row<df>(p, p->s, OP_STORE_Y, SC_NONE, true, false, false));
+    CK(vec<df>(p, p->s, VOP_MAP_OUT, SC_NONE, false));
   }
   CK(cudaStreamSynchronize(p->s));
   return FILL_OK;
@@ -1134,16 +1147,23 @@ template <typename T>
 fill_status apply_t(fill_plan* p, int which, const void* in, void* out) {
   Precision<T>& P = prec<T>(p);
   const size_t n = p->npix;
-  fill_desc<T>(p, nullptr, 0, nullptr, nullptr, nullptr);
+  constexpr bool same = std::is_same<T, typename MapOf<T>::type>::value;
+  fill_desc<T>(p, in, 0, nullptr, out, nullptr);
   CK(upload_desc<T>(p));
   CK(init_states<T>(p, 0.0));
-  CK(cudaMemcpyAsync(P.w, in, n * sizeof(T), cudaMemcpyDeviceToDevice, p->s));
+  if (same)
+    CK(cudaMemcpyAsync(P.w, in, n * sizeof(T), cudaMemcpyDeviceToDevice, p->s));
+  else
+    CK(vec<T>(ctx<T>(p, 1), p->s, VOP_MAP_IN, SC_NONE, false));
   const bool masked = which >= 2;
   const int table = (which == 0 || which == 2) ? 0 : 1;
   CK(row<T>(p, p->s, masked ? OP_LOAD_W_MASK : OP_LOAD_W, SC_NONE, false, true, false, 1));
   CK(col<T>(p, p->s, table, false, 1));
   CK(row<T>(p, p->s, masked ? OP_STORE_Y_MASK : OP_STORE_Y, SC_NONE, true, false, false, 1));
-  CK(cudaMemcpyAsync(out, P.y, n * sizeof(T), cudaMemcpyDeviceToDevice, p->s));
+  if (same)
+    CK(cudaMemcpyAsync(out, P.y, n * sizeof(T), cudaMemcpyDeviceToDevice, p->s));
+  else
+    CK(vec<T>(ctx<T>(p, 1), p->s, VOP_MAP_OUT, SC_NONE, false));
   CK(cudaStreamSynchronize(p->s));
   return FILL_OK;
 }
@@ -1153,8 +1173,9 @@ extern "C" {
 
 fill_status fill_apply(fill_plan* p, int which, const void* in, void* out) {
   if (!p || !in || !out || which < 0 || which > 3 || in == out) return FILL_EINVAL;
-  return p->o.mode == FILL_MODE_FP32 ? apply_t<float>(p, which, in, out)
-                                     : apply_t<double>(p, which, in, out);
+  return p->o.mode == FILL_MODE_FP32   ? apply_t<float>(p, which, in, out)
+         : p->o.mode == FILL_MODE_FP64 ? apply_t<double>(p, which, in, out)
+                                       : apply_t<df>(p, which, in, out);
 }
 
 fill_status fill_history(fill_plan* p, int inst, double* hist, int cap, int* count) {
@@ -1163,8 +1184,8 @@ fill_status fill_history(fill_plan* p, int inst, double* hist, int cap, int* cou
   int m = 0;
   const double* src = nullptr;
   if (p->o.mode == FILL_MODE_MIXED) {
-    m = p->g.hst[inst].refine + 1;  // FP64 true residual after each refinement step
-    src = p->g.hist;
+    m = p->h.hst[inst].refine + 1;  // high-precision true residual after each update
+    src = p->h.hist;
   } else if (p->o.mode == FILL_MODE_FP32) {
     m = p->f.hst[inst].iter + 1;
     src = p->f.hist;
@@ -1304,8 +1325,9 @@ fill_status fill_time_pass(fill_plan* p, int pass, int precision, int reps, doub
                            double* bytes) {
   if (!p || !ms || !bytes || pass < 0 || pass > 4 || reps < 1 || precision < 0 || precision > 1)
     return FILL_EINVAL;
-  return precision == 0 ? time_pass_t<float>(p, pass, reps, ms, bytes)
-                        : time_pass_t<double>(p, pass, reps, ms, bytes);
+  if (precision == 0) return time_pass_t<float>(p, pass, reps, ms, bytes);
+  return p->o.mode == FILL_MODE_MIXED ? time_pass_t<df>(p, pass, reps, ms, bytes)
+                                      : time_pass_t<double>(p, pass, reps, ms, bytes);
 }
 
 }  // extern "C"
@@ -1354,6 +1376,7 @@ fill_status fill_set_bands(fill_plan* p, int nbands, const int32_t* band_of_k,
     if (band_of_k[i] < 0 || band_of_k[i] >= nbands || !std::isfinite(sig_half[i])) return FILL_EINVAL;
   fill_status fs = set_bands_t<float>(p, nbands, band_of_k, sig_half);
   if (fs == FILL_OK) fs = set_bands_t<double>(p, nbands, band_of_k, sig_half);
+  if (fs == FILL_OK) fs = set_bands_t<df>(p, nbands, band_of_k, sig_half);
   return fs;
 }
 
@@ -1361,15 +1384,17 @@ fill_status fill_backward(fill_plan* p, const void* d, long long d_stride, const
                           double tol, void* grad_d, double* grad_bands, fill_stats* stats) {
   if (!p || !d || !grad_x || !grad_d || !(tol >= 0.0) || d_stride < 0) return FILL_EINVAL;
   if (!p->o.backward) return FILL_EINVAL;
-  const bool f32 = p->o.mode == FILL_MODE_FP32;
-  if (grad_bands && (f32 ? p->f.nbands : p->g.nbands) == 0) return FILL_EINVAL;
+  const bool f32 = p->o.mode == FILL_MODE_FP32, mixed = p->o.mode == FILL_MODE_MIXED;
+  if (grad_bands && (f32 ? p->f.nbands : mixed ? p->h.nbands : p->g.nbands) == 0)
+    return FILL_EINVAL;
   const auto t0 = std::chrono::steady_clock::now();
   p->launches = 0;
-  fill_status fs = f32 ? backward_t<float>(p, d, d_stride, grad_x, tol, grad_d, grad_bands)
-                       : backward_t<double>(p, d, d_stride, grad_x, tol, grad_d, grad_bands);
+  fill_status fs = f32     ? backward_t<float>(p, d, d_stride, grad_x, tol, grad_d, grad_bands)
+                   : mixed ? backward_t<df>(p, d, d_stride, grad_x, tol, grad_d, grad_bands)
+                           : backward_t<double>(p, d, d_stride, grad_x, tol, grad_d, grad_bands);
   if (fs != FILL_OK) return fs;
-  if (p->o.mode == FILL_MODE_MIXED) {
-    CK(cudaMemcpyAsync(p->g.hst, p->g.st, sizeof(CgState) * p->batch, cudaMemcpyDeviceToHost, p->s));
+  if (mixed) {
+    CK(cudaMemcpyAsync(p->h.hst, p->h.st, sizeof(CgState) * p->batch, cudaMemcpyDeviceToHost, p->s));
     CK(cudaMemcpyAsync(p->f.hst, p->f.st, sizeof(CgState) * p->batch, cudaMemcpyDeviceToHost, p->s));
   } else if (f32) {
     CK(cudaMemcpyAsync(p->f.hst, p->f.st, sizeof(CgState) * p->batch, cudaMemcpyDeviceToHost, p->s));
@@ -1478,6 +1503,12 @@ cudaError_t autotune_ctx(Ctx<T> c, cudaStream_t s, int* best_rows, int* best_fft
 }
 
 // Autotune cache: lines "prec ny nx ninst rows ffts".
+// Precision code of the tuning cache: 0 FP32, 1 FP64, 2 double-float.
+template <typename T>
+int prec_code() {
+  return std::is_same<T, float>::value ? 0 : std::is_same<T, double>::value ? 1 : 2;
+}
+
 bool cache_lookup(const char* path, int prec, int ny, int nx, int ninst, int* rows, int* ffts) {
   if (!path) return false;
   FILE* f = std::fopen(path, "r");
@@ -1506,7 +1537,7 @@ template <typename T>
 fill_status tune_plan_t(fill_plan* p, const char* path) {
   Precision<T>& P = prec<T>(p);
   if (!P.used) return FILL_OK;
-  const int pr = sizeof(T) == 4 ? 0 : 1;
+  const int pr = prec_code<T>();
   int rows = P.rows, ffts = P.ffts;
   if (!cache_lookup(path, pr, p->ny, p->nx, p->batch, &rows, &ffts)) {
     fill_desc<T>(p, nullptr, 0, nullptr, nullptr, nullptr);
@@ -1604,7 +1635,7 @@ fill_status group_setup(fill_group* g, int autotune, const char* path) {
     c.ffts = prec<T>(p0).ffts;
     CK(cudaMemcpy(c.desc, c.hdesc, nb, cudaMemcpyHostToDevice));
     if (autotune) {
-      const int pr = sizeof(T) == 4 ? 0 : 1;
+      const int pr = prec_code<T>();
       if (!cache_lookup(path, pr, c.ny, c.nx, c.ninst, &c.rows, &c.ffts)) {
         Ctx<T> cx_ = gctx<T>(g, c);
         k_state_init<T><<<(c.ninst + 127) / 128, 128, 0, g->s>>>(
@@ -1741,6 +1772,7 @@ fill_status fill_autotune(fill_plan* p, const char* cache_path) {
   if (!p) return FILL_EINVAL;
   fill_status fs = tune_plan_t<float>(p, cache_path);
   if (fs == FILL_OK) fs = tune_plan_t<double>(p, cache_path);
+  if (fs == FILL_OK) fs = tune_plan_t<df>(p, cache_path);
   if (fs == FILL_OK) CK(cudaStreamSynchronize(p->s));
   return fs;
 }
