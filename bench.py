@@ -150,6 +150,36 @@ def dist_env():
     return rank, world, local
 
 
+def replica_seeds(seed0, batch, step, rank):
+    """Realization seeds of one step of one replica: disjoint across steps
+    (stride 100003 per step) and ranks (stride 10000019 per rank) for any
+    batch up to 100003 and fewer than 100 steps per rank."""
+    return [seed0 + i + 100_003 * step + 10_000_019 * rank for i in range(batch)]
+
+
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time: the job's time (replicas, max over ranks)."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(batch, steps, world, ms_max):
+    """Whole-job realizations/s: every rank's realizations over the slowest
+    rank's time."""
+    return batch * steps * world / (ms_max / 1e3)
+
+
+def workload_config(name, grid, batch, tol, mode, masked_fraction, world, **extra):
+    cfg = {"workload": name, "grid": list(grid), "batch": batch, "tol": tol, "mode": mode,
+           "precond": "sqrtC", "masked_fraction": round(float(masked_fraction), 4),
+           "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (no flush)"}
+    cfg.update(extra)
+    return cfg
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -220,8 +250,10 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_iter * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "grid": [obs.shape[0], obs.shape[1]],
-                       "batch": 1, "tol": spec["tol"]},
+            "config": workload_config(args.workload, obs.shape, args.batch or len(spec["seeds"]),
+                                      args.tol or spec["tol"], "oracle-fp64", masked.mean(), 1,
+                                      sample="one realization's draw and right-hand side, "
+                                             "iterations timed one per step"),
             "cg_iters_per_s": 1.0 / t_iter,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
@@ -259,8 +291,7 @@ def run_gpu(args):
     plan = cg.Plan(P, obs, mode=mode, batch=B, host_loops=args.host_loops,
                    update_delta=args.update_delta)
     d = plan.draw([spec["data_seed"]] * B)[0].clone()       # data drawn from P(k)
-    seeds = lambda k: [spec["seeds"][0] + i + 100_003 * k + 10_000_019 * rank  # noqa: E731
-                       for i in range(B)]
+    seeds = lambda k: replica_seeds(spec["seeds"][0], B, k, rank)  # noqa: E731
 
     for k in range(args.warmup):
         plan.realize(d, seeds(k), tol)
@@ -282,11 +313,8 @@ def run_gpu(args):
         torch.cuda.synchronize()
     barrier()
     ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = B * args.steps * world / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, dist, "cuda")
+    value = job_throughput(B, args.steps, world, ms_max)
     iters_per_s = iters * world / (ms_max / 1e3)
 
     # end to end through the public API with host buffers: every step copies
@@ -398,13 +426,10 @@ def run_gpu(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": {"mixed": "f32+df64", "fp32": "f32", "fp64": "f64"}[mode],
                 "data": "synthetic",
-                "config": {"workload": args.workload, "grid": [ny, nx], "batch": B,
-                           "tol": tol, "mode": mode, "precond": "sqrtC",
-                           "masked_fraction": round(float((obs == 0).mean()), 4),
-                           "parallelism": f"replicas{world}",
-                           "loops": "host" if args.host_loops else "graph",
-                           "update_delta": args.update_delta,
-                           "l2": "inputs larger than L2 (no flush)"},
+                "config": workload_config(args.workload, (ny, nx), B, tol, mode,
+                                          (obs == 0).mean(), world,
+                                          loops="host" if args.host_loops else "graph",
+                                          update_delta=args.update_delta),
                 "cg_iters_per_s": iters_per_s,
                 "iters_per_realization": iters / (B * args.steps),
                 "worst_true_rel_resid": worst_resid,
