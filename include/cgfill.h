@@ -135,6 +135,17 @@ fill_status fill_realize(fill_plan* plan, const void* d, long long d_stride,
                          const uint64_t* seeds, double tol, void* out, fill_stats* stats);
 
 /*
+ * fill_ml -- maximum-likelihood fill (Sect. 2.1): x_M = -((C^-1)_MM)^-1 (C^-1)_MU d_U,
+ * x_U = d_U, the mean of the constrained field (the Hoffman-Ribak
+ * realization without its random part: y = 0).  Same solver, precision
+ * and arguments as fill_realize without the seeds; each of the batch
+ * entries fills its own data map (d_stride as in fill_realize).
+ * Errors: as fill_realize.
+ */
+fill_status fill_ml(fill_plan* plan, const void* d, long long d_stride, double tol, void* out,
+                    fill_stats* stats);
+
+/*
  * fill_draw -- unconstrained realizations y = F^-1[sqrt(P) F xi(seed)] with
  * covariance C (Sect. 2.3, the draw that needs no cuts).  out: device, batch
  * maps (plan element type).  Errors: FILL_EINVAL, FILL_ECUDA.

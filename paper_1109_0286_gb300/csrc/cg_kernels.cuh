@@ -89,6 +89,7 @@ __device__ __forceinline__ void src_fill(const InstDesc<T>& I, const uint2* mwr,
         if constexpr (OP == OP_LOAD_W_MASK) q[e] = pair_at(mwr, j);
       } else {
         q[e] = pair_at(mwr, j);
+        if constexpr (OP == OP_LOAD_D_U) ld_map_pair<T>(I.d + rowpix + 2 * j, x0[e], x1[e]);
         if constexpr (OP == OP_LOAD_R) ldc(I.r, q[e], x0[e], x1[e]);
         if constexpr (OP == OP_LOAD_U) ldc(I.u, q[e], x0[e], x1[e]);
         if constexpr (OP == OP_P_UPD_Z || OP == OP_P_UPD_R) {
@@ -113,6 +114,9 @@ __device__ __forceinline__ void src_fill(const InstDesc<T>& I, const uint2* mwr,
       if constexpr (OP == OP_LOAD_W_MASK) {
         a0 = q[e].m0 ? x0[e] : (T)0;
         a1 = q[e].m1 ? x1[e] : (T)0;
+      } else if constexpr (OP == OP_LOAD_D_U) {
+        a0 = q[e].m0 ? (T)0 : x0[e];
+        a1 = q[e].m1 ? (T)0 : x1[e];
       } else if constexpr (OP == OP_P_UPD_Z || OP == OP_P_UPD_R) {
         a0 = x0[e] + beta * y0[e];
         a1 = x1[e] + beta * y1[e];
@@ -349,6 +353,9 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
       case OP_LOAD_W: src_fill<T, TT, OP_LOAD_W>(I, mwr, rowpix, tid, alpha, beta, v, acc); break;
       case OP_LOAD_W_MASK:
         src_fill<T, TT, OP_LOAD_W_MASK>(I, mwr, rowpix, tid, alpha, beta, v, acc);
+        break;
+      case OP_LOAD_D_U:
+        src_fill<T, TT, OP_LOAD_D_U>(I, mwr, rowpix, tid, alpha, beta, v, acc);
         break;
       case OP_U64_UPD:
         src_fill<T, TT, OP_U64_UPD>(I, mwr, rowpix, tid, alpha, beta, v, acc);

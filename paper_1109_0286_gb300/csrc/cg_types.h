@@ -118,6 +118,7 @@ enum RowOp : int {
   OP_LOAD_W_MASK = 7,  // v = P_x w (full maps; operator checks)
   OP_LOAD_U = 8,    // v = u
   OP_LOAD_Y = 9,    // v = y
+  OP_LOAD_D_U = 28, // v = d on U, 0 on M (maximum-likelihood right-hand side)
   // middles (input spectrum -> output spectrum)
   OP_MASK = 10,     // v = P_x v
   OP_Y_W = 11,      // store y = v; v = (d - y) on U, 0 on M

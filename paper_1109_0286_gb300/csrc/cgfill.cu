@@ -352,8 +352,14 @@ cudaError_t pcg_iter(const Ctx<T>& c, cudaStream_t s) {
 }
 
 template <typename T>
-cudaError_t draw_and_rhs(fill_plan* p, cudaStream_t s, bool plain_cg) {
-  return draw_and_rhs<T>(ctx<T>(p), s, plain_cg);
+cudaError_t draw_and_rhs(fill_plan* p, cudaStream_t s, bool plain_cg, bool ml = false) {
+  if (!ml) return draw_and_rhs<T>(ctx<T>(p), s, plain_cg);
+  // maximum-likelihood fill (Sect. 2.1): y = 0, b = -P_x F^-1 (1/P) F (d on U)
+  const Ctx<T> c = ctx<T>(p);
+  CE(cudaMemsetAsync(prec<T>(p).y, 0, size_t(p->batch) * p->npix * sizeof(T), s));
+  CE(row<T>(c, s, OP_LOAD_D_U, SC_NONE, false, true, false));
+  CE(col<T>(c, s, 0, false));
+  return row<T>(c, s, OP_B, plain_cg ? SC_BB_RHO : SC_BB, true, false, false);
 }
 template <typename T>
 cudaError_t pcg_start(fill_plan* p, cudaStream_t s, int load_sop) {
@@ -1039,9 +1045,13 @@ fill_status fill_init(fill_plan** out, int ny, int nx, const double* P_half,
   return FILL_OK;
 }
 
-fill_status fill_realize(fill_plan* p, const void* d, long long d_stride, const uint64_t* seeds,
-                         double tol, void* out, fill_stats* stats) {
-  if (!p || !d || !seeds || !out || !(tol >= 0.0) || d_stride < 0) return FILL_EINVAL;
+}  // extern "C"
+
+namespace {
+// fill_realize (ml = false) and fill_ml (ml = true: no random part, y = 0).
+fill_status realize_impl(fill_plan* p, const void* d, long long d_stride, const uint64_t* seeds,
+                         double tol, void* out, fill_stats* stats, bool ml) {
+  if (!p || !d || (!seeds && !ml) || !out || !(tol >= 0.0) || d_stride < 0) return FILL_EINVAL;
   const auto t0 = std::chrono::steady_clock::now();
   const int B = p->batch;
   p->launches = 0;
@@ -1067,7 +1077,7 @@ fill_status fill_realize(fill_plan* p, const void* d, long long d_stride, const 
       CK(init_states<float>(p, tol));
       CK(cudaMemsetAsync(p->f.u, 0, B * p->nv * sizeof(float), p->s));
       CK(cudaMemsetAsync(p->f.p, 0, B * p->nv * sizeof(float), p->s));
-      CK(draw_and_rhs<float>(p, p->s, !p->o.precond));
+      CK(draw_and_rhs<float>(p, p->s, !p->o.precond, ml));
       CK(pcg_start<float>(p, p->s, SC_NONE));
       fs = run_pcg<float>(p);
       if (fs != FILL_OK) return fs;
@@ -1079,7 +1089,7 @@ fill_status fill_realize(fill_plan* p, const void* d, long long d_stride, const 
       CK(init_states<double>(p, tol));
       CK(cudaMemsetAsync(p->g.u, 0, B * p->nv * sizeof(double), p->s));
       CK(cudaMemsetAsync(p->g.p, 0, B * p->nv * sizeof(double), p->s));
-      CK(draw_and_rhs<double>(p, p->s, !p->o.precond));
+      CK(draw_and_rhs<double>(p, p->s, !p->o.precond, ml));
       CK(pcg_start<double>(p, p->s, SC_NONE));
       fs = run_pcg<double>(p);
       if (fs != FILL_OK) return fs;
@@ -1095,7 +1105,7 @@ fill_status fill_realize(fill_plan* p, const void* d, long long d_stride, const 
     CK(init_states<df>(p, tol));
     CK(init_states<float>(p, p->o.inner_tol));
     CK(cudaMemsetAsync(p->h.u, 0, B * p->nv * sizeof(df), p->s));
-    CK(draw_and_rhs<df>(p, p->s, false));
+    CK(draw_and_rhs<df>(p, p->s, false, ml));
     fs = mixed_solve(p, tol);
     if (fs != FILL_OK) return fs;
     CK(vec<df>(p, p->s, VOP_ASSEMBLE, SC_NONE, false));
@@ -1106,6 +1116,19 @@ fill_status fill_realize(fill_plan* p, const void* d, long long d_stride, const 
   const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   collect_stats(p, stats, ms, &worst);
   return worst;
+}
+}  // namespace
+
+extern "C" {
+
+fill_status fill_realize(fill_plan* p, const void* d, long long d_stride, const uint64_t* seeds,
+                         double tol, void* out, fill_stats* stats) {
+  return realize_impl(p, d, d_stride, seeds, tol, out, stats, false);
+}
+
+fill_status fill_ml(fill_plan* p, const void* d, long long d_stride, double tol, void* out,
+                    fill_stats* stats) {
+  return realize_impl(p, d, d_stride, nullptr, tol, out, stats, true);
 }
 
 fill_status fill_draw(fill_plan* p, const uint64_t* seeds, void* out) {

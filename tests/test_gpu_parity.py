@@ -229,6 +229,48 @@ def test_host_loops_equal_graph_loops(mode, precond, delta):
     assert [s["status"] for s in sh] == [0, 0, 0]
 
 
+# ------------------------------------------------------------------ maximum-likelihood fill
+
+@pytest.mark.parametrize("mode,bound", [("fp64", 1e-9), ("mixed", 1e-8)])
+def test_ml_fill_matches_dense_forms(mode, bound):
+    """fill_ml on the 64x64 plain workload against the two dense ML forms of
+    Sect. 2.1 (covariance form by Cholesky, precision form by a dense solve)."""
+    P, obs, spec = workload("plain64")
+    Pf = O.hermitian_full(P, 64)
+    d = O.draw(Pf, spec["data_seed"])
+    plan = cg.Plan(P, obs, mode=mode, batch=2)
+    out, st = plan.ml(gpu_map(d, torch.float64), 1e-12)
+    m = obs == 0
+    dU = d.ravel()[obs.ravel() == 1]
+    cov = O.ml_dense_cov(Pf, obs, dU)
+    prec = O.ml_dense_prec(Pf, obs, dU)
+    for i in range(2):
+        x = out[i].cpu().numpy()
+        assert np.array_equal(x[~m], d[~m])
+        assert rel(x.ravel()[m.ravel()], cov) <= bound
+        assert rel(x.ravel()[m.ravel()], prec) <= bound
+    assert torch.equal(out[0], out[1])
+
+
+def test_ml_fill_fp32_1024_per_instance_maps():
+    """FP32 ML fills of two different data maps (d_stride) at 1024^2 against
+    the oracle's PCG on the y = 0 system at the same tolerance."""
+    P, obs, spec = workload("patch1024")
+    Pf = O.hermitian_full(P, 1024)
+    ds = [O.draw(Pf, 31), O.draw(Pf, 32)]
+    plan = cg.Plan(P, obs, mode="fp32", batch=2)
+    dev = torch.from_numpy(np.stack(ds)).float().cuda()
+    out, st = plan.ml(dev, 1e-6)
+    m = obs == 0
+    for i, d in enumerate(ds):
+        b = O.rhs(Pf, obs, d, np.zeros_like(d))
+        res = O.pcg(lambda v: O.apply_A(v, Pf, m), b,
+                    lambda v: O.apply_S(O.apply_S(v, Pf, m), Pf, m), tol=1e-6)
+        x = out[i].cpu().numpy().astype(np.float64)
+        assert np.array_equal(x[~m], d.astype(np.float32)[~m].astype(np.float64))
+        assert rel(x[m], res.u[m]) <= 1e-5, rel(x[m], res.u[m])
+
+
 # ------------------------------------------------------------------ Lanczos estimate
 
 def _dense_precond_spectrum(P, obs):
