@@ -289,7 +289,7 @@ def run_gpu(args):
     fdt = torch.float32 if mode == "fp32" else torch.float64
     esz = 4 if mode == "fp32" else 8
     plan = cg.Plan(P, obs, mode=mode, batch=B, host_loops=args.host_loops,
-                   update_delta=args.update_delta)
+                   update_delta=args.update_delta, history_cap=2048)
     d = plan.draw([spec["data_seed"]] * B)[0].clone()       # data drawn from P(k)
     seeds = lambda k: replica_seeds(spec["seeds"][0], B, k, rank)  # noqa: E731
 
@@ -357,6 +357,14 @@ def run_gpu(args):
     e2e = {"value": B * world / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": d_host.numel() * esz,
            "d2h_bytes_per_step": out_host[0].numel() * esz}
+
+    # Lanczos estimate of the preconditioned operator's spectrum from the CG
+    # coefficients of the last realization (Sect. 6.4)
+    t0 = time.perf_counter()
+    lz = plan.lanczos(0)
+    lanczos = {"lmin": lz["lmin"], "lmax": lz["lmax"], "kappa": lz["kappa"],
+               "iterations": int(len(lz["alpha"])),
+               "ms": (time.perf_counter() - t0) * 1e3}
 
     # roofline of the hot-loop passes (CUDA events on the plan's stream)
     peaks, peak_src = measured_peaks()
@@ -436,7 +444,8 @@ def run_gpu(args):
                 "fp64_pcg": fp64,
                 "speedup_vs_fp64": (value / world / fp64["value"]) if fp64 else None,
                 "gpu_launches": launches, "e2e": e2e, "roofline": roofline,
-                "passes": pass_table, "clocks": clk.summary(), "cpu_baseline": cpu}
+                "passes": pass_table, "lanczos": lanczos, "clocks": clk.summary(),
+                "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -17,6 +17,9 @@ Gaussian realizations" (arXiv:1109.0286):
   optionally preconditioned by ``P_x C^{1/2} P_x`` on both sides.
 * Sect. 4: on the torus the DFT is exactly unitary, so ``C^s`` is the
   diagonal ``P(k)^s`` in Fourier space.
+* Sect. 5 (eqs. kern:rel, Boo, Algo): writing ``C^-1 = a (delta - K)`` with
+  ``a`` the white high-k level of the precision, the ML fill satisfies
+  ``x = K * x`` on M; iterating ``x_M <- (K * x)_M`` is the kernel relaxation.
 
 DFT convention: ``F x(k) = sum_r x(r) exp(-i k.r)`` (unnormalised) and
 ``F^-1`` carries ``1/n``; ``C^s = F^-1 diag(P^s) F``.  The FFT itself is a
@@ -38,6 +41,7 @@ __all__ = [
     "apply_S", "pcg", "PcgResult", "realize", "Realization",
     "dft2_direct", "circulant_corr", "dense_matrix", "ml_dense_cov",
     "ml_dense_prec", "constrained_cov_dense", "backward", "band_full",
+    "relax_kernel", "relax",
     "loss_masked_sq", "lanczos_tridiag",
 ]
 
@@ -391,3 +395,41 @@ def lanczos_tridiag(alphas, betas):
         if j + 1 < k:
             T[j, j + 1] = T[j + 1, j] = math.sqrt(betas[j]) / alphas[j]
     return T
+
+
+# ---------------------------------------------------------------------------
+# Kernel relaxation (Sect. 5, eqs. kern:rel, Boo and Algo) on the torus
+# ---------------------------------------------------------------------------
+
+def relax_kernel(P_full):
+    """``(a, K)`` with ``C^-1 = a (delta - K)`` as in eq. kern:rel: ``a`` is the
+    white (high-k) level of the precision, ``a = max_k 1/P(k)`` (for
+    ``P = S + N`` with white noise N, ``a = 1/N`` once the signal has died
+    off), so that ``K^(k) = 1 - 1/(a P(k))`` lies in [0, 1) and the convolution
+    with K is a weighted average (the singular part of C^-1 is the delta term,
+    the smooth regular part -a K).  K at every displacement comes from the
+    correlation function of C^-1 (no FFT)."""
+    q = circulant_corr(P_full, -1.0)
+    a = float(np.max(1.0 / P_full))
+    K = -q / a
+    K[0, 0] += 1.0
+    return a, K
+
+
+def relax(P_half, observed, d, iters):
+    """Kernel relaxation, eq. Algo: from ``x_M = 0`` and ``x_U = d_U``, repeat
+    ``x_M <- (K * x)_M`` with the kernel of ``relax_kernel``, i.e.
+    ``x_M <- x_M - (C^-1 x)_M / a``.  Its fixed point solves ``(C^-1 x)_M = 0``
+    (eq. Boo: the ML fill), and since ``0 < C^-1/a <= 1`` it contracts.
+    Returns the map and ``||(C^-1 x)_M||`` before each step."""
+    ny, nx = observed.shape
+    P_full = hermitian_full(P_half, nx)
+    obs = observed.astype(bool)
+    a = float(np.max(1.0 / P_full))
+    x = project(np.asarray(d, dtype=np.float64), obs)
+    norms = []
+    for _ in range(iters):
+        v = apply_power(x, P_full, -1.0)
+        norms.append(float(np.linalg.norm(v[~obs])))
+        x[~obs] -= v[~obs] / a
+    return x, norms

@@ -386,3 +386,48 @@ def test_same_tolerance_spread_is_inherent():
     assert abs(alt[1e-8].pcg.iters - ref[1e-8].pcg.iters) <= 1
     assert e8 > 1e-10          # the same-tolerance spread exceeds 1e-10 ...
     assert e13 < 1e-11         # ... and vanishes once both are converged
+
+
+# ----------------------------------------------------------------- kernel relaxation (Sect. 5)
+
+def test_relax_kernel_normalisation_and_one_step_by_convolution():
+    """C^-1 = a (delta - K) (eq. kern:rel): K sums to 1 - 1/(a P(0)), its
+    spectrum (direct DFT, no FFT) lies in [0, 1), and one relaxation step
+    equals the brute-force circular convolution (K * x) on the masked pixels."""
+    P, obs = _small_case(16, 16, seed=6)
+    Pf = O.hermitian_full(P, 16)
+    a, K = O.relax_kernel(Pf)
+    assert abs(a - np.max(1.0 / Pf)) <= 1e-15 * a
+    assert abs(K.sum() - (1.0 - 1.0 / (a * Pf[0, 0]))) < 1e-12
+    Kh = np.real(O.dft2_direct(K))
+    assert Kh.min() > -1e-12 and Kh.max() < 1.0
+    assert np.allclose(Kh, 1.0 - 1.0 / (a * Pf), atol=1e-12)
+    d = O.draw(Pf, 3)
+    x1, _ = O.relax(P, obs, d, 1)
+    x0 = np.where(obs == 1, d, 0.0)
+    conv = np.zeros_like(x0)
+    for i in range(16):
+        for j in range(16):
+            conv[i, j] = sum(K[(i - p) % 16, (j - q) % 16] * x0[p, q]
+                             for p in range(16) for q in range(16))
+    m = obs == 0
+    assert np.allclose(x1[m], conv[m], rtol=0, atol=1e-12 * np.abs(conv).max())
+    assert np.array_equal(x1[~m], d[~m])
+
+
+def test_relax_converges_to_ml_fill():
+    """The fixed point of eq. Algo is the ML fill (eq. Boo): the sweeps
+    contract and reach the dense precision-form solution (a spectrum with a
+    2% white floor, so that the relaxation converges in a few hundred sweeps;
+    its rate is set by the condition number of C^-1, Sect. 5)."""
+    _, obs = _small_case(16, 16, seed=6)
+    P = synth.spectrum_lorentz_beam(16, 16, k0=2 * math.pi / 8, sb=0.8)
+    P = P + 0.02 * P.max()
+    Pf = O.hermitian_full(P, 16)
+    d = O.draw(Pf, 3)
+    x, norms = O.relax(P, obs, d, 600)
+    dU = d.ravel()[obs.ravel() == 1]
+    ml = O.ml_dense_prec(Pf, obs, dU)
+    m = obs.ravel() == 0
+    assert np.all(np.diff(norms) <= 1e-12 * norms[0])
+    assert np.linalg.norm(x.ravel()[m] - ml) <= 1e-8 * np.linalg.norm(ml)
