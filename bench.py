@@ -366,6 +366,14 @@ def run_gpu(args):
                "iterations": int(len(lz["alpha"])),
                "ms": (time.perf_counter() - t0) * 1e3}
 
+    # kernel relaxation (Sect. 5, eq. Algo) on the same workload: sweeps/s
+    torch.cuda.synchronize()
+    rsweeps = 20
+    t0 = time.perf_counter()
+    _, rst = plan.relax(d, rsweeps)
+    relax = {"sweeps": rsweeps, "ms_per_sweep": (time.perf_counter() - t0) * 1e3 / rsweeps,
+             "rel_resid": rst[0]["rel_resid"], "batch": B}
+
     # roofline of the hot-loop passes (CUDA events on the plan's stream)
     peaks, peak_src = measured_peaks()
     passes = {0: ("k_col (column FFT, x 1/(nP), inverse FFT)", 3),
@@ -444,7 +452,8 @@ def run_gpu(args):
                 "fp64_pcg": fp64,
                 "speedup_vs_fp64": (value / world / fp64["value"]) if fp64 else None,
                 "gpu_launches": launches, "e2e": e2e, "roofline": roofline,
-                "passes": pass_table, "lanczos": lanczos, "clocks": clk.summary(),
+                "passes": pass_table, "lanczos": lanczos, "relax": relax,
+                "clocks": clk.summary(),
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -146,6 +146,21 @@ fill_status fill_ml(fill_plan* plan, const void* d, long long d_stride, double t
                     fill_stats* stats);
 
 /*
+ * fill_relax -- the kernel relaxation of Sect. 5 (eqs. kern:rel, Boo, Algo) on the
+ * torus: writing C^-1 = a (delta - K) with a = max_k 1/P(k), the white level of the
+ * precision (so that K's spectrum 1 - 1/(aP) lies in [0, 1) and K * x is a
+ * weighted average), it repeats x_M <- (K * x)_M = x_M - (C^-1 x)_M / a from
+ * x_M = 0, x_U = d_U, `iters` times (three passes per sweep).  Its fixed point is
+ * the ML fill (eq. Boo); convergence is geometric with a rate set by the condition
+ * number of C^-1, which is why the paper turns to multi-scale kernels and CG.
+ * d, d_stride, out as in fill_ml; out_U = d_U exactly.  stats: iters = sweeps,
+ * rel_resid = ||(C^-1 x)_M|| / ||(C^-1 x_0)_M|| before the last sweep.
+ * Precision: the plan's (mixed mode: double-float).  Errors: FILL_EINVAL, FILL_ECUDA.
+ */
+fill_status fill_relax(fill_plan* plan, const void* d, long long d_stride, int iters, void* out,
+                       fill_stats* stats);
+
+/*
  * fill_draw -- unconstrained realizations y = F^-1[sqrt(P) F xi(seed)] with
  * covariance C (Sect. 2.3, the draw that needs no cuts).  out: device, batch
  * maps (plan element type).  Errors: FILL_EINVAL, FILL_ECUDA.

@@ -21,7 +21,7 @@ from . import _build
 
 __all__ = [
     "FillOpts", "FillStats", "FillError", "load", "lib_path", "fill_opts_default",
-    "fill_init", "fill_realize", "fill_ml", "fill_draw", "fill_apply", "fill_history",
+    "fill_init", "fill_realize", "fill_ml", "fill_relax", "fill_draw", "fill_apply", "fill_history",
     "fill_lanczos", "fill_time_pass", "fill_set_bands", "fill_backward", "fill_autotune", "fill_group_init",
     "fill_group_realize", "fill_group_size", "fill_group_destroy", "Group", "fill_apply_static",
     "fill_masked_count", "fill_destroy", "fill_strerror", "fill_last_error",
@@ -32,7 +32,8 @@ MODES = {"fp64": 0, "fp32": 1, "mixed": 2}
 STATUS = {0: "FILL_OK", 1: "FILL_EINVAL", 2: "FILL_ENOMEM", 3: "FILL_ENOTCONV",
           4: "FILL_EBREAKDOWN", 5: "FILL_ETIMEOUT", 6: "FILL_ECUDA"}
 EXPORTED_SYMBOLS = [
-    "fill_opts_default", "fill_init", "fill_realize", "fill_ml", "fill_draw", "fill_apply",
+    "fill_opts_default", "fill_init", "fill_realize", "fill_ml", "fill_relax", "fill_draw",
+    "fill_apply",
     "fill_history", "fill_lanczos", "fill_time_pass", "fill_set_bands", "fill_backward",
     "fill_autotune",
     "fill_group_init", "fill_group_realize", "fill_group_size", "fill_group_destroy",
@@ -97,6 +98,8 @@ def load() -> ctypes.CDLL:
     lib.fill_realize.restype = _ci
     lib.fill_ml.argtypes = [_vp, _vp, _cll, _cd, _vp, ctypes.POINTER(FillStats)]
     lib.fill_ml.restype = _ci
+    lib.fill_relax.argtypes = [_vp, _vp, _cll, _ci, _vp, ctypes.POINTER(FillStats)]
+    lib.fill_relax.restype = _ci
     lib.fill_draw.argtypes = [_vp, _vp, _vp]
     lib.fill_draw.restype = _ci
     lib.fill_apply.argtypes = [_vp, _ci, _vp, _vp]
@@ -172,6 +175,13 @@ def fill_realize(plan, d_ptr, d_stride, seeds, tol, out_ptr, batch):
 def fill_ml(plan, d_ptr, d_stride, tol, out_ptr, batch):
     stats = (FillStats * batch)()
     st = load().fill_ml(_vp(plan), _vp(d_ptr), _cll(d_stride), _cd(tol), _vp(out_ptr), stats)
+    return st, [x.as_dict() for x in stats]
+
+
+def fill_relax(plan, d_ptr, d_stride, iters, out_ptr, batch):
+    stats = (FillStats * batch)()
+    st = load().fill_relax(_vp(plan), _vp(d_ptr), _cll(d_stride), int(iters), _vp(out_ptr),
+                           stats)
     return st, [x.as_dict() for x in stats]
 
 
@@ -380,6 +390,21 @@ class Plan:
                             out.data_ptr(), self.batch)
         if check and st != 0:
             raise FillError(st, "fill_ml")
+        return out, stats
+
+    def relax(self, d, iters, out=None, check=True):
+        """Kernel-relaxation sweeps (Sect. 5, eq. Algo) from x_M = 0: returns
+        ``(out, stats)``."""
+        import torch
+        shared = d.numel() == self.ny * self.nx
+        self._check(d, "d", 1 if shared else self.batch)
+        if out is None:
+            out = torch.empty((self.batch, self.ny, self.nx), dtype=self.dtype, device=d.device)
+        self._check(out, "out", self.batch)
+        st, stats = fill_relax(self._plan, d.data_ptr(), 0 if shared else self.ny * self.nx,
+                               iters, out.data_ptr(), self.batch)
+        if check and st != 0:
+            raise FillError(st, "fill_relax")
         return out, stats
 
     def set_bands(self, band_of_k, sig_half):

@@ -165,6 +165,7 @@ __device__ __forceinline__ void sink_fill(const InstDesc<T>& I, const uint2* mwr
       if constexpr (OP == OP_Z) ldc(I.r, q[e], x0[e], x1[e]);
       if constexpr (OP == OP_RES) ldc(I.b, q[e], x0[e], x1[e]);
       if constexpr (OP == OP_GRAD) ld_map_pair<T>(I.gx + rowpix + 2 * j, x0[e], x1[e]);
+      if constexpr (OP == OP_RELAX) ld_pair(I.w + rowpix + 2 * j, x0[e], x1[e]);
     }
 #pragma unroll
     for (int e = 0; e < CK; ++e) {
@@ -197,6 +198,13 @@ __device__ __forceinline__ void sink_fill(const InstDesc<T>& I, const uint2* mwr
         // dL/dy = h = g on M, (C^-1 lam)_U on U (kept in y).
         st_map_pair<T>(I.out + rowpix + 2 * j, m0 ? (T)0 : x0[e] - a0, m1 ? (T)0 : x1[e] - a1);
         st_pair(I.y + rowpix + 2 * j, m0 ? x0[e] : a0, m1 ? x1[e] : a1);
+      } else if constexpr (OP == OP_RELAX) {
+        const T step = (T)I.st->alpha;
+        a0 = m0 ? a0 : (T)0;
+        a1 = m1 ? a1 : (T)0;
+        st_pair(I.w + rowpix + 2 * j, x0[e] - step * a0, x1[e] - step * a1);
+        acc.add_prod(a0, a0);
+        acc.add_prod(a1, a1);
       } else if constexpr (OP == OP_STORE_Y) {
         st_pair(I.y + rowpix + 2 * j, a0, a1);
       } else if constexpr (OP == OP_STORE_Y_MASK) {
@@ -322,6 +330,7 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
         case OP_B: sink_fill<T, TT, OP_B>(I, mwr, rowpix, tid, v, acc); break;
         case OP_RES: sink_fill<T, TT, OP_RES>(I, mwr, rowpix, tid, v, acc); break;
         case OP_GRAD: sink_fill<T, TT, OP_GRAD>(I, mwr, rowpix, tid, v, acc); break;
+        case OP_RELAX: sink_fill<T, TT, OP_RELAX>(I, mwr, rowpix, tid, v, acc); break;
         case OP_STORE_Y: sink_fill<T, TT, OP_STORE_Y>(I, mwr, rowpix, tid, v, acc); break;
         case OP_STORE_Y_MASK:
           sink_fill<T, TT, OP_STORE_Y_MASK>(I, mwr, rowpix, tid, v, acc);
@@ -502,6 +511,21 @@ k_vec(const InstDesc<T>* __restrict__ insts, VecArgs a) {
           T a0, a1;
           ld_pair(I.y + pix, a0, a1);
           st_map_pair<T>(I.out + pix, a0, a1);
+          break;
+        }
+        case VOP_W_FROM_D: {
+          T a0, a1;
+          ld_map_pair<T>(I.d + pix, a0, a1);
+          st_pair(I.w + pix, q.m0 ? (T)0 : a0, q.m1 ? (T)0 : a1);
+          break;
+        }
+        case VOP_W_TO_OUT: {   // observed pixels: the caller's values, bit for bit
+          using M = typename MapOf<T>::type;
+          M d0, d1;
+          T a0, a1;
+          ld_pair(I.d + pix, d0, d1);
+          ld_pair(I.w + pix, a0, a1);
+          st_pair(I.out + pix, q.m0 ? static_cast<M>(a0) : d0, q.m1 ? static_cast<M>(a1) : d1);
           break;
         }
         case VOP_LOAD_G: {

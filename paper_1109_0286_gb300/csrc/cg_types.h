@@ -130,6 +130,8 @@ enum RowOp : int {
   OP_B = 23,        // b = -P_x v; store r = b (and b); acc ||b||^2
   OP_RES = 24,      // r = b - P_x v; store; acc ||r||^2; r32 = (float) r
   OP_GRAD = 25,     // v = C^-1 lam: out = (g - v) on U, 0 on M; y = h = g on M, v on U
+  OP_RELAX = 29,    // v = C^-1 w: w -= alpha v on M (alpha = 1/a, Sect. 5 relaxation);
+                    // acc ||v_M||^2
   OP_LOAD_W = 26,   // (source) v = w
 };
 
@@ -163,6 +165,8 @@ enum VecOp : int {
   VOP_ZERO_UP = 7,    // u = 0, p = 0
   VOP_MAP_IN = 8,     // w = d (caller's map -> pass element type)
   VOP_MAP_OUT = 9,    // out = y (pass element type -> caller's map)
+  VOP_W_FROM_D = 10,  // w = d on U, 0 on M
+  VOP_W_TO_OUT = 11,  // out = w (pass element type -> caller's map)
 };
 
 // Launch arguments of the pass kernels.

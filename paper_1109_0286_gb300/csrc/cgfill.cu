@@ -109,6 +109,7 @@ struct fill_plan {
   long long nv = 0;              // compact vector stride per instance (>= nmasked)
   std::vector<double> P_half;    // host copy of the spectrum
   long long launches = 0;        // kernels issued by the current call
+  double relax_a = 0.0;          // max_k 1/P(k): white level of C^-1 (Sect. 5 relaxation)
   cudaGraphExec_t mixed_graph = nullptr;   // reliable-update mixed CG loop
   long long mixed_graph_kernels = 0;
   int* loop_counter = nullptr;   // device [2]: loop bodies, IF bodies of the last loop graph
@@ -1019,6 +1020,7 @@ fill_status fill_init(fill_plan** out, int ny, int nx, const double* P_half,
   for (int ky = 0; ky < ny; ++ky)
     for (int kx = 0; kx < nkx; ++kx) {
       const double P = P_half[(size_t)ky * nkx + kx];
+      p->relax_a = std::max(p->relax_a, 1.0 / P);
       tinv[(size_t)kx * ny + ky] = 1.0 / (P * double(npix));
       tsqrt[(size_t)kx * ny + ky] = std::sqrt(P) / double(npix);
     }
@@ -1129,6 +1131,66 @@ fill_status fill_realize(fill_plan* p, const void* d, long long d_stride, const 
 fill_status fill_ml(fill_plan* p, const void* d, long long d_stride, double tol, void* out,
                     fill_stats* stats) {
   return realize_impl(p, d, d_stride, nullptr, tol, out, stats, true);
+}
+
+}  // extern "C"
+
+namespace {
+__global__ void k_set_step(CgState* const* sts, int n, double step) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) sts[i]->alpha = step;
+}
+
+// Kernel relaxation (Sect. 5, eq. Algo): w_M <- (K * w)_M = w_M - (C^-1 w)_M / a,
+// three passes per sweep, from w = d on U, 0 on M.
+template <typename T>
+fill_status relax_t(fill_plan* p, const void* d, long long d_stride, int iters, void* out,
+                    fill_stats* stats) {
+  Precision<T>& P = prec<T>(p);
+  const auto t0 = std::chrono::steady_clock::now();
+  const int B = p->batch;
+  p->launches = 0;
+  fill_desc<T>(p, d, d_stride, nullptr, out, nullptr);
+  CK(upload_desc<T>(p));
+  CK(init_states<T>(p, 0.0));
+  ++p->launches;
+  k_set_step<<<(B + 127) / 128, 128, 0, p->s>>>(P.stp, B, 1.0 / p->relax_a);
+  CK(cudaGetLastError());
+  CK(vec<T>(p, p->s, VOP_W_FROM_D, SC_NONE, SKIP_NEVER));
+  for (int k = 0; k < iters; ++k) {
+    CK(row<T>(p, p->s, OP_LOAD_W, SC_NONE, false, true, SKIP_NEVER));
+    CK(col<T>(p, p->s, 0, SKIP_NEVER));
+    CK(row<T>(p, p->s, OP_RELAX, k == 0 ? SC_BB : SC_RES, true, false, SKIP_NEVER));
+  }
+  CK(vec<T>(p, p->s, VOP_W_TO_OUT, SC_NONE, SKIP_NEVER));
+  CK(cudaMemcpyAsync(P.hst, P.st, sizeof(CgState) * B, cudaMemcpyDeviceToHost, p->s));
+  CK(cudaStreamSynchronize(p->s));
+  const double ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (stats)
+    for (int i = 0; i < B; ++i) {
+      const CgState& a = P.hst[i];
+      fill_stats st{};
+      st.iters = iters;
+      st.status = a.status == 4 ? FILL_EBREAKDOWN : FILL_OK;
+      st.launches = (int)p->launches;
+      st.rel_resid = a.bb > 0 ? std::sqrt(a.rr / a.bb) : 0.0;
+      st.true_rel_resid = -1.0;
+      st.ms = ms;
+      stats[i] = st;
+    }
+  return FILL_OK;
+}
+}  // namespace
+
+extern "C" {
+
+fill_status fill_relax(fill_plan* p, const void* d, long long d_stride, int iters, void* out,
+                       fill_stats* stats) {
+  if (!p || !d || !out || iters < 0 || d_stride < 0) return FILL_EINVAL;
+  return p->o.mode == FILL_MODE_FP32   ? relax_t<float>(p, d, d_stride, iters, out, stats)
+         : p->o.mode == FILL_MODE_FP64 ? relax_t<double>(p, d, d_stride, iters, out, stats)
+                                       : relax_t<df>(p, d, d_stride, iters, out, stats);
 }
 
 fill_status fill_draw(fill_plan* p, const uint64_t* seeds, void* out) {

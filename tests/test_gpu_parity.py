@@ -271,6 +271,30 @@ def test_ml_fill_fp32_1024_per_instance_maps():
         assert rel(x[m], res.u[m]) <= 1e-5, rel(x[m], res.u[m])
 
 
+# ------------------------------------------------------------------ kernel relaxation (Sect. 5)
+
+@pytest.mark.parametrize("mode,bound", [("fp64", 1e-11), ("mixed", 1e-10), ("fp32", 1e-5)])
+def test_relax_matches_oracle(mode, bound):
+    """fill_relax sweeps against the oracle's eq. Algo iteration, map by map
+    (two data maps), and the residual history's last value."""
+    P, obs = case(128, 256, seed=12)
+    Pf = O.hermitian_full(P, 256)
+    ds = [O.draw(Pf, 41), O.draw(Pf, 42)]
+    dt = torch.float32 if mode == "fp32" else torch.float64
+    plan = cg.Plan(P, obs, mode=mode, batch=2)
+    dev = torch.from_numpy(np.stack(ds)).to(dtype=dt, device="cuda")
+    out, st = plan.relax(dev, 40)
+    m = obs == 0
+    npdt = np.float32 if mode == "fp32" else np.float64
+    for i, d in enumerate(ds):
+        ref, norms = O.relax(P, obs, d, 40)
+        x = out[i].cpu().numpy().astype(np.float64)
+        assert np.array_equal(x[~m], d.astype(npdt)[~m].astype(np.float64))
+        assert rel(x[m], ref[m]) <= bound, rel(x[m], ref[m])
+        assert st[i]["iters"] == 40
+        assert abs(st[i]["rel_resid"] - norms[-1] / norms[0]) <= 1e-4 * norms[-1] / norms[0] + bound
+
+
 # ------------------------------------------------------------------ Lanczos estimate
 
 def _dense_precond_spectrum(P, obs):
