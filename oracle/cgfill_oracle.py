@@ -41,7 +41,7 @@ __all__ = [
     "apply_S", "pcg", "PcgResult", "realize", "Realization",
     "dft2_direct", "circulant_corr", "dense_matrix", "ml_dense_cov",
     "ml_dense_prec", "constrained_cov_dense", "backward", "band_full",
-    "relax_kernel", "relax",
+    "relax_kernel", "relax", "disc_offsets", "subdivide", "strip_refine",
     "loss_masked_sq", "lanczos_tridiag",
 ]
 
@@ -433,3 +433,55 @@ def relax(P_half, observed, d, iters):
         norms.append(float(np.linalg.norm(v[~obs])))
         x[~obs] -= v[~obs] / a
     return x, norms
+
+
+# ---------------------------------------------------------------------------
+# Subdivision of the mask (Sect. 6.2) and strip refinement (Sect. 6.4)
+# ---------------------------------------------------------------------------
+
+def disc_offsets(radius):
+    """Lattice offsets ``(dy, dx)`` with ``dy^2 + dx^2 <= radius^2``."""
+    R = int(math.floor(radius))
+    return [(dy, dx) for dy in range(-R, R + 1) for dx in range(-R, R + 1)
+            if dy * dy + dx * dx <= radius * radius]
+
+
+def subdivide(observed, delta, threshold=0.03):
+    """Sect. 6.2: the boundary layer of width ``delta``: convolve the observed
+    indicator (1 on U, 0 on M) with the normalised top hat of radius
+    ``delta / 2`` (periodic) and keep the masked pixels whose value exceeds
+    ``threshold``.  The convolution is a pixel count over the disc, computed
+    here by FFT and rounded to the integer it equals; the comparison
+    ``count > threshold * |disc|`` is then exact.  Returns a bool map."""
+    ny, nx = observed.shape
+    offs = disc_offsets(delta / 2.0)
+    disc = np.zeros((ny, nx))
+    for dy, dx in offs:
+        disc[dy % ny, dx % nx] = 1.0
+    obs = observed.astype(bool)
+    count = np.rint(np.real(np.fft.ifft2(np.fft.fft2(obs.astype(np.float64)) *
+                                         np.fft.fft2(disc)))).astype(np.int64)
+    return (~obs) & (count * 100 > round(threshold * 100) * len(offs))
+
+
+def strip_refine(S_half, N_half, observed, d, stages, tol=1e-8, max_iter=10000, x0=None):
+    """Sect. 6.4 on the torus: for each ``(beta, w)`` in turn, the strip
+    ``D = subdivide(observed, w)`` of the original mask is refilled with the
+    maximum-likelihood solution for the boosted-noise spectrum
+    ``P = S + beta N``, the current map outside the strip acting as data
+    (PCG with the sqrt(C) preconditioner to ``tol``).  Starts from ``x0`` on
+    the mask (default 0); ``d`` on U is never changed.  Returns the map."""
+    ny, nx = observed.shape
+    obs = observed.astype(bool)
+    x = np.where(obs, np.asarray(d, dtype=np.float64), 0.0 if x0 is None else x0)
+    for beta, w in stages:
+        strip = subdivide(observed, w)
+        if not strip.any():
+            continue
+        P_full = hermitian_full(S_half + beta * N_half, nx)
+        b = rhs(P_full, (~strip).astype(np.uint8), x, np.zeros_like(x))
+        res = pcg(lambda v: apply_A(v, P_full, strip), b,
+                  lambda v: apply_S(apply_S(v, P_full, strip), P_full, strip),
+                  tol=tol, max_iter=max_iter)
+        x = np.where(strip, res.u, x)
+    return x

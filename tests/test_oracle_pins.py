@@ -431,3 +431,61 @@ def test_relax_converges_to_ml_fill():
     m = obs.ravel() == 0
     assert np.all(np.diff(norms) <= 1e-12 * norms[0])
     assert np.linalg.norm(x.ravel()[m] - ml) <= 1e-8 * np.linalg.norm(ml)
+
+
+# ----------------------------------------------------------------- subdivision and strips (Sect. 6)
+
+def test_subdivide_counts_match_brute_force_and_nest():
+    """The top-hat convolution of Sect. 6.2 equals the brute-force periodic
+    disc count; the layers are inside the mask and nest as delta shrinks."""
+    _, obs = _small_case(32, 32, seed=2, band=8, discs=3, r=3.0)
+    m = obs == 0
+    for delta in (3.0, 7.0, 10.0):
+        offs = O.disc_offsets(delta / 2)
+        layer = O.subdivide(obs, delta)
+        brute = np.zeros_like(m)
+        for y in range(32):
+            for x in range(32):
+                c = sum(int(obs[(y + dy) % 32, (x + dx) % 32]) for dy, dx in offs)
+                brute[y, x] = m[y, x] and c * 100 > 3 * len(offs)
+        assert np.array_equal(layer, brute)
+        assert not (layer & ~m).any()
+    assert not (O.subdivide(obs, 5.0) & ~O.subdivide(obs, 9.0)).any()
+    assert len(O.disc_offsets(2.0)) == 13 and len(O.disc_offsets(1.5)) == 9
+
+
+def test_strip_refine_single_full_stage_is_ml_fill():
+    """One stage with beta = 1 whose strip covers the whole mask is the exact
+    ML fill (Sect. 2.1), here against the dense precision form."""
+    _, obs = _small_case(32, 32, seed=2, band=4, discs=2, r=2.0)
+    S = synth.spectrum_lorentz_beam(32, 32, k0=2 * math.pi / 8, sb=0.8, noise_frac=0.0)
+    N = np.full_like(S, 1e-3 * S.max())
+    d = O.draw(O.hermitian_full(S + N, 32), 5)
+    assert np.array_equal(O.subdivide(obs, 40.0), obs == 0)
+    x = O.strip_refine(S, N, obs, d, [(1.0, 40.0)], tol=1e-13)
+    Pf = O.hermitian_full(S + N, 32)
+    ml = O.ml_dense_prec(Pf, obs, d.ravel()[obs.ravel() == 1])
+    m = obs.ravel() == 0
+    assert np.linalg.norm(x.ravel()[m] - ml) <= 1e-10 * np.linalg.norm(ml)
+    assert np.array_equal(x[obs == 1], d[obs == 1])
+
+
+def test_strip_refine_approaches_ml_fill_near_the_boundary():
+    """Each stage of the paper's sequence (noise boosts falling to 1 over
+    narrowing strips) brings the map closer to the exact ML fill in the last,
+    narrowest strip."""
+    _, obs = _small_case(64, 64, seed=3, band=12, discs=3, r=4.0)
+    S = synth.spectrum_lorentz_beam(64, 64, k0=2 * math.pi / 16, sb=1.0, noise_frac=0.0)
+    N = np.full_like(S, 1e-4 * S.max())
+    Pf = O.hermitian_full(S + N, 64)
+    d = O.draw(Pf, 6)
+    ml = O.ml_dense_prec(Pf, obs, d.ravel()[obs.ravel() == 1])
+    full = np.where(obs == 1, d, 0.0).ravel()
+    full[obs.ravel() == 0] = ml
+    last = O.subdivide(obs, 4.0).ravel()
+    stages = [(2000.0, 24.0), (40.0, 10.0), (1.0, 4.0)]
+    errs = []
+    for k in range(1, len(stages) + 1):
+        x = O.strip_refine(S, N, obs, d, stages[:k], tol=1e-10)
+        errs.append(np.linalg.norm(x.ravel()[last] - full[last]) / np.linalg.norm(full[last]))
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 0.25, errs
