@@ -161,6 +161,22 @@ fill_status fill_relax(fill_plan* plan, const void* d, long long d_stride, int i
                        fill_stats* stats);
 
 /*
+ * fill_subdivide -- the boundary layer of width delta (Sect. 6.2): the observed
+ * indicator convolved with the normalised top hat of radius delta/2 on the
+ * periodic grid, i.e. the fraction of the disc {dy^2 + dx^2 <= (delta/2)^2}
+ * around each pixel that is observed; layer[i] = 1 for masked pixels where it
+ * exceeds `threshold` (0.03 in the paper), else 0.  The fraction is an exact
+ * pixel count (per-row prefix sums), and the test is
+ * count * 100 > round(100 threshold) * |disc|.  No plan, no allocation.
+ * observed: device, ny*nx (1 = observed); scratch: device, ny*(nx+1) int32;
+ * layer: device, ny*nx uint8 (out).  Needs 2 floor(delta/2) + 1 <= ny, nx.
+ * Asynchronous on `stream`.  Errors: FILL_EINVAL (message via fill_last_error),
+ * FILL_ECUDA.
+ */
+fill_status fill_subdivide(int ny, int nx, const uint8_t* observed, double delta,
+                           double threshold, int32_t* scratch, uint8_t* layer, void* stream);
+
+/*
  * fill_draw -- unconstrained realizations y = F^-1[sqrt(P) F xi(seed)] with
  * covariance C (Sect. 2.3, the draw that needs no cuts).  out: device, batch
  * maps (plan element type).  Errors: FILL_EINVAL, FILL_ECUDA.

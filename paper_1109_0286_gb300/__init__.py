@@ -21,7 +21,7 @@ from . import _build
 
 __all__ = [
     "FillOpts", "FillStats", "FillError", "load", "lib_path", "fill_opts_default",
-    "fill_init", "fill_realize", "fill_ml", "fill_relax", "fill_draw", "fill_apply", "fill_history",
+    "fill_init", "fill_realize", "fill_ml", "fill_relax", "fill_subdivide", "fill_draw", "fill_apply", "fill_history",
     "fill_lanczos", "fill_time_pass", "fill_set_bands", "fill_backward", "fill_autotune", "fill_group_init",
     "fill_group_realize", "fill_group_size", "fill_group_destroy", "Group", "fill_apply_static",
     "fill_masked_count", "fill_destroy", "fill_strerror", "fill_last_error",
@@ -32,8 +32,8 @@ MODES = {"fp64": 0, "fp32": 1, "mixed": 2}
 STATUS = {0: "FILL_OK", 1: "FILL_EINVAL", 2: "FILL_ENOMEM", 3: "FILL_ENOTCONV",
           4: "FILL_EBREAKDOWN", 5: "FILL_ETIMEOUT", 6: "FILL_ECUDA"}
 EXPORTED_SYMBOLS = [
-    "fill_opts_default", "fill_init", "fill_realize", "fill_ml", "fill_relax", "fill_draw",
-    "fill_apply",
+    "fill_opts_default", "fill_init", "fill_realize", "fill_ml", "fill_relax", "fill_subdivide",
+    "fill_draw", "fill_apply",
     "fill_history", "fill_lanczos", "fill_time_pass", "fill_set_bands", "fill_backward",
     "fill_autotune",
     "fill_group_init", "fill_group_realize", "fill_group_size", "fill_group_destroy",
@@ -65,7 +65,7 @@ class FillStats(ctypes.Structure):
 class FillError(RuntimeError):
     def __init__(self, status: int, where: str):
         msg = f"{where}: {STATUS.get(status, status)} ({fill_strerror(status)})"
-        if status == 6 or (status == 1 and where == "fill_apply_static"):
+        if status == 6 or (status == 1 and where in ("fill_apply_static", "fill_subdivide")):
             msg += ": " + fill_last_error()
         super().__init__(msg)
         self.status = status
@@ -100,6 +100,8 @@ def load() -> ctypes.CDLL:
     lib.fill_ml.restype = _ci
     lib.fill_relax.argtypes = [_vp, _vp, _cll, _ci, _vp, ctypes.POINTER(FillStats)]
     lib.fill_relax.restype = _ci
+    lib.fill_subdivide.argtypes = [_ci, _ci, _vp, _cd, _cd, _vp, _vp, _vp]
+    lib.fill_subdivide.restype = _ci
     lib.fill_draw.argtypes = [_vp, _vp, _vp]
     lib.fill_draw.restype = _ci
     lib.fill_apply.argtypes = [_vp, _ci, _vp, _vp]
@@ -183,6 +185,24 @@ def fill_relax(plan, d_ptr, d_stride, iters, out_ptr, batch):
     st = load().fill_relax(_vp(plan), _vp(d_ptr), _cll(d_stride), int(iters), _vp(out_ptr),
                            stats)
     return st, [x.as_dict() for x in stats]
+
+
+def fill_subdivide(observed, delta, threshold=0.03, stream=None):
+    """Boundary layer of width ``delta`` (Sect. 6.2) of a device uint8 mask
+    (1 = observed): returns a device uint8 map, 1 on the layer's pixels."""
+    import torch
+    if not (isinstance(observed, torch.Tensor) and observed.is_cuda and
+            observed.dtype == torch.uint8 and observed.dim() == 2 and observed.is_contiguous()):
+        raise ValueError("observed: expected a contiguous 2-D uint8 CUDA tensor")
+    ny, nx = observed.shape
+    scratch = torch.empty(ny * (nx + 1), dtype=torch.int32, device=observed.device)
+    layer = torch.empty_like(observed)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    st = load().fill_subdivide(ny, nx, _vp(observed.data_ptr()), float(delta), float(threshold),
+                               _vp(scratch.data_ptr()), _vp(layer.data_ptr()), _vp(s.cuda_stream))
+    if st != 0:
+        raise FillError(st, "fill_subdivide")
+    return layer
 
 
 def fill_draw(plan, seeds, out_ptr):
