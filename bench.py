@@ -77,6 +77,8 @@ def parse():
                     help="precision mode of the timed arm (profiling cases)")
     ap.add_argument("--batch", type=int, default=0, help="realizations per step (0: workload's)")
     ap.add_argument("--tol", type=float, default=0.0, help="CG tolerance (0: workload's)")
+    ap.add_argument("--no-strips", action="store_true",
+                    help="skip the strip-refinement measurement (Sect. 6.4)")
     ap.add_argument("--update-delta", type=float, default=1e-2,
                     help="mixed mode: FP32 residual drop that triggers a true-residual update")
     ap.add_argument("--host-loops", action="store_true",
@@ -178,6 +180,63 @@ def workload_config(name, grid, batch, tol, mode, masked_fraction, world, **extr
            "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (no flush)"}
     cfg.update(extra)
     return cfg
+
+
+def strips_measurement():
+    """Noise-boosted strip refinement (Sect. 6.4) with the paper's four
+    (beta, w) stages on the 1024^2 patch workload (10% band of 102 rows,
+    discs of radius 2-12: masks no wider than the paper's ~100-pixel limit),
+    mixed precision: wall time, CG iterations per stage, and the distance to
+    the exact ML fill (fill_ml to 1e-8) over the mask and in the last strip.
+    The oracle runs the same procedure on the 256^2 version, timed beside the
+    GPU on that size."""
+    import numpy as np
+    import torch
+    import oracle as O
+    import paper_1109_0286_gb300 as cg
+    from paper_1109_0286_gb300 import strips
+    from workloads import synth, workload
+
+    def case(scale):
+        P, obs, spec = workload("patch1024", scale=scale)
+        N = np.full_like(P, synth.cmb_noise_level(spec["k_lo"]))
+        n = obs.shape[1]
+        d = O.draw(O.hermitian_full(P, n), spec["data_seed"])
+        return P - N, N, obs, d
+
+    out = {"workload": "patch1024 (1024^2, 10% band + 200 discs)", "stages": strips.PAPER_STAGES,
+           "mode": "mixed", "tol": 1e-8}
+    S, N, obs, d = case(1)
+    dd = torch.from_numpy(d).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x, log = strips.strip_refine(S, N, obs, dd, mode="mixed", tol=1e-8)
+    torch.cuda.synchronize()
+    out["ms"] = (time.perf_counter() - t0) * 1e3
+    out["cg_iters_per_stage"] = [entry[3] for entry in log]
+    out["strip_pixels"] = [entry[2] for entry in log]
+    plan = cg.Plan(S + N, obs, mode="mixed")
+    ml, _ = plan.ml(dd, 1e-8)
+    plan.close()
+    x, ml = x.cpu().numpy(), ml[0].cpu().numpy()
+    m = obs == 0
+    last = cg.fill_subdivide(torch.from_numpy(obs).cuda(), strips.PAPER_STAGES[-1][1])
+    last = last.cpu().numpy().astype(bool)
+    out["rel_err_mask"] = float(np.linalg.norm(x[m] - ml[m]) / np.linalg.norm(ml[m]))
+    out["rel_err_last_strip"] = float(np.linalg.norm(x[last] - ml[last]) / np.linalg.norm(ml[last]))
+    S4, N4, obs4, d4 = case(4)
+    stages4 = [(b, w / 4.0) for b, w in strips.PAPER_STAGES]
+    t0 = time.perf_counter()
+    strips.strip_refine(S4, N4, obs4, torch.from_numpy(d4).cuda(), stages4, mode="mixed",
+                        tol=1e-8)
+    torch.cuda.synchronize()
+    g4 = (time.perf_counter() - t0) * 1e3
+    t0 = time.perf_counter()
+    O.strip_refine(S4, N4, obs4, d4, stages4, tol=1e-8)
+    o4 = (time.perf_counter() - t0) * 1e3
+    out["at_256"] = {"gpu_ms": g4, "oracle_ms": o4, "oracle_cores": threads_used(),
+                     "stages": stages4}
+    return out
 
 
 def measured_peaks():
@@ -374,6 +433,8 @@ def run_gpu(args):
     relax = {"sweeps": rsweeps, "ms_per_sweep": (time.perf_counter() - t0) * 1e3 / rsweeps,
              "rel_resid": rst[0]["rel_resid"], "batch": B}
 
+    strip_meas = strips_measurement() if (rank == 0 and not args.no_strips) else None
+
     # roofline of the hot-loop passes (CUDA events on the plan's stream)
     peaks, peak_src = measured_peaks()
     passes = {0: ("k_col (column FFT, x 1/(nP), inverse FFT)", 3),
@@ -452,7 +513,7 @@ def run_gpu(args):
                 "fp64_pcg": fp64,
                 "speedup_vs_fp64": (value / world / fp64["value"]) if fp64 else None,
                 "gpu_launches": launches, "e2e": e2e, "roofline": roofline,
-                "passes": pass_table, "lanczos": lanczos, "relax": relax,
+                "passes": pass_table, "lanczos": lanczos, "relax": relax, "strips": strip_meas,
                 "clocks": clk.summary(),
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
