@@ -413,6 +413,46 @@ def test_iteration_limit_reports_not_converged():
 
 # ------------------------------------------------------------------ full size
 
+@pytest.mark.parametrize("ny,nx", [(8192, 32), (16, 8192)])
+@pytest.mark.parametrize("mode,bound", [("fp64", 1e-9), ("mixed", 1e-8), ("fp32", 1e-4)])
+def test_extreme_shapes_match_oracle(ny, nx, mode, bound):
+    """The largest transforms (8192-point columns, 8192-pixel rows) and the
+    smallest ones against the oracle, converged (tol 1e-10, FP32 1e-6)."""
+    P = synth.spectrum_cmb_like(ny, nx, 2 * math.pi / max(ny, nx))
+    obs = synth.mask_band_discs(ny, nx, max(1, ny // 8), 4, 2.0, 5.0, 3)
+    d = O.draw(O.hermitian_full(P, nx), 8)
+    tol = 1e-6 if mode == "fp32" else 1e-10
+    dt = torch.float32 if mode == "fp32" else torch.float64
+    plan = cg.Plan(P, obs, mode=mode)
+    out, st = plan.realize(gpu_map(d, dt), [9], tol)
+    ref = O.realize(P, obs, d, 9, tol=1e-12)
+    x = out[0].cpu().numpy().astype(np.float64)
+    m = obs == 0
+    assert st[0]["status"] == 0
+    assert rel(x[m], ref.x[m]) <= bound, rel(x[m], ref.x[m])
+
+
+def test_max_grid_8192_certificate():
+    """8192 x 8192 (the largest grid fill_init accepts), FP32: observed
+    pixels equal the data, and the ML certificate of the realization,
+    evaluated with the oracle's operator, holds to the tolerance."""
+    n = 8192
+    P = synth.spectrum_cmb_like(n, n, 2 * math.pi / n)
+    obs = synth.mask_band_discs(n, n, n // 10, 400, 2.0, 12.0, 21)
+    Pf = O.hermitian_full(P, n)
+    d = O.draw(Pf, 4)
+    plan = cg.Plan(P, obs, mode="fp32")
+    out, st = plan.realize(gpu_map(d, torch.float32), [5], 1e-5)
+    x = out[0].cpu().numpy().astype(np.float64)
+    m = obs == 0
+    assert np.array_equal(x[~m], d.astype(np.float32)[~m].astype(np.float64))
+    y = O.draw(Pf, 5)
+    w = np.where(m, x - y, d.astype(np.float32).astype(np.float64) - y)
+    b = O.rhs(Pf, obs, d.astype(np.float32).astype(np.float64), y)
+    cert = np.linalg.norm(np.where(m, O.apply_power(w, Pf, -1.0), 0)) / np.linalg.norm(b)
+    assert st[0]["status"] == 0 and cert <= 1e-4, cert
+
+
 def test_wide4096_full_size_certificate():
     """4096^2, batch 8, mixed refinement to 1e-10, in the launch configuration
     the benchmark times.  Checks at full size: observed pixels equal the data;
