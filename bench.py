@@ -78,7 +78,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=0, help="realizations per step (0: workload's)")
     ap.add_argument("--tol", type=float, default=0.0, help="CG tolerance (0: workload's)")
     ap.add_argument("--no-strips", action="store_true",
-                    help="skip the strip-refinement measurement (Sect. 6.4)")
+                    help="skip the Sect. 6 measurements (strip refinement, far-interior test)")
     ap.add_argument("--update-delta", type=float, default=1e-2,
                     help="mixed mode: FP32 residual drop that triggers a true-residual update")
     ap.add_argument("--host-loops", action="store_true",
@@ -237,6 +237,33 @@ def strips_measurement():
     out["at_256"] = {"gpu_ms": g4, "oracle_ms": o4, "oracle_cores": threads_used(),
                      "stages": stages4}
     return out
+
+
+def far_interior_measurement():
+    """Sect. 6.1 at 4096^2: the exact ML fill of the 819-row band (20%), then
+    the Laplace interpolation into its interior after removing 82 rows along
+    each boundary: the relative L2 and max difference inside, and the time."""
+    import numpy as np
+    import torch
+    import oracle as O
+    from paper_1109_0286_gb300 import laplace
+    from workloads import synth
+    n, rows, layer = 4096, 819, 82
+    P = synth.spectrum_cmb_like(n, n, 2 * np.pi / 4096)
+    d = O.draw(O.hermitian_full(P, n), 3)
+    dd = torch.from_numpy(d).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lap, ml, inner, (sm, sl) = laplace.far_interior(P, dd, rows, layer, mode="mixed", tol=1e-8)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3
+    m = torch.from_numpy(inner == 0).cuda()
+    diff = (lap - ml)[m]
+    ref = ml[m]
+    return {"grid": [n, n], "band_rows": rows, "layer_rows": layer, "mode": "mixed", "ms": ms,
+            "ml_iters": sm["iters"], "laplace_iters": sl["iters"],
+            "rel_l2": float(torch.linalg.norm(diff) / torch.linalg.norm(ref)),
+            "max_rel": float(diff.abs().max() / ref.abs().max())}
 
 
 def measured_peaks():
@@ -434,6 +461,7 @@ def run_gpu(args):
              "rel_resid": rst[0]["rel_resid"], "batch": B}
 
     strip_meas = strips_measurement() if (rank == 0 and not args.no_strips) else None
+    far = far_interior_measurement() if (rank == 0 and not args.no_strips) else None
 
     # roofline of the hot-loop passes (CUDA events on the plan's stream)
     peaks, peak_src = measured_peaks()
@@ -514,6 +542,7 @@ def run_gpu(args):
                 "speedup_vs_fp64": (value / world / fp64["value"]) if fp64 else None,
                 "gpu_launches": launches, "e2e": e2e, "roofline": roofline,
                 "passes": pass_table, "lanczos": lanczos, "relax": relax, "strips": strip_meas,
+                "far_interior": far,
                 "clocks": clk.summary(),
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)

@@ -59,3 +59,62 @@ def test_strip_refine_matches_oracle(mode, bound):
     assert np.linalg.norm(x[m] - ref[m]) <= bound * np.linalg.norm(ref[m])
     for (beta, w, npx, iters), (b2, w2) in zip(log, stages):
         assert (beta, w) == (b2, w2) and npx == int(O.subdivide(obs, w).sum()) and iters > 0
+
+
+# ------------------------------------------------------------------ Laplace interpolation (Sect. 6.1)
+
+from paper_1109_0286_gb300 import laplace  # noqa: E402
+
+
+def _oracle_laplace(obs_inner, x, tol=1e-12):
+    ny, nx = x.shape
+    Pl = O.hermitian_full(laplace.stencil_spectrum(ny, nx), nx)
+    m = obs_inner == 0
+    b = O.rhs(Pl, obs_inner, x, np.zeros_like(x))
+    res = O.pcg(lambda v: O.apply_A(v, Pl, m), b,
+                lambda v: O.apply_S(O.apply_S(v, Pl, m), Pl, m), tol=tol, max_iter=20000)
+    return np.where(m, res.u, x)
+
+
+@pytest.mark.parametrize("mode,bound", [("fp64", 1e-8), ("mixed", 1e-8)])
+def test_laplace_fill_matches_oracle_and_stencil(mode, bound):
+    """Harmonic interpolation into a band (the 5-point-stencil ML fill):
+    against the oracle, and the stencil equation holds on the band."""
+    n = 256
+    x = O.draw(O.hermitian_full(synth.spectrum_cmb_like(n, n, 2 * math.pi / n), n), 2)
+    inner = laplace.band_rows(n, n, 60)
+    got, st = laplace.laplace_fill(inner, torch.from_numpy(x).cuda(), mode=mode, tol=1e-12)
+    got = got.cpu().numpy()
+    ref = _oracle_laplace(inner, x)
+    m = inner == 0
+    assert np.array_equal(got[~m], x[~m])
+    assert np.linalg.norm(got[m] - ref[m]) <= bound * np.linalg.norm(ref[m])
+    lap = 4 * got - (np.roll(got, 1, 0) + np.roll(got, -1, 0) + np.roll(got, 1, 1) +
+                     np.roll(got, -1, 1))
+    assert np.abs(lap[m]).max() <= 1e-6 * np.abs(got).max()
+
+
+def test_far_interior_laplace_vs_exact_1024():
+    """Sect. 6.1 at 1024^2: a 410-row band (40%) with 82-row boundary layers
+    removed; the Laplace interpolation from the exact ML values there differs
+    from the ML fill inside by about 5% (L2), the same figure the oracle
+    gets, and the paper's "< 5%" scale."""
+    n = 1024
+    P = synth.spectrum_cmb_like(n, n, 2 * math.pi / 4096)
+    d = O.draw(O.hermitian_full(P, n), 3)
+    lap, ml, inner, _ = laplace.far_interior(P, torch.from_numpy(d).cuda(), 410, 82,
+                                             mode="mixed", tol=1e-8)
+    lap, ml = lap.cpu().numpy(), ml.cpu().numpy()
+    m = inner == 0
+    gpu = np.linalg.norm(lap[m] - ml[m]) / np.linalg.norm(ml[m])
+    Pf = O.hermitian_full(P, n)
+    outer = laplace.band_rows(n, n, 410)
+    mo = outer == 0
+    b = O.rhs(Pf, outer, d, np.zeros_like(d))
+    res = O.pcg(lambda v: O.apply_A(v, Pf, mo), b,
+                lambda v: O.apply_S(O.apply_S(v, Pf, mo), Pf, mo), tol=1e-8)
+    ml_o = np.where(mo, res.u, d)
+    lap_o = _oracle_laplace(inner, ml_o, tol=1e-10)
+    orc = np.linalg.norm(lap_o[m] - ml_o[m]) / np.linalg.norm(ml_o[m])
+    assert abs(gpu - orc) <= 2e-3 * orc, (gpu, orc)
+    assert gpu < 0.06, gpu
