@@ -26,7 +26,7 @@ struct CgState {
   double rr;       // ||r||^2 after the last update
   double tol2;     // tol^2 (stop when rr <= tol2 * bb)
   double pq;       // last p^T A p
-  double rrmax;    // ||r||^2 at the last FP64 residual update (reliable updates)
+  double rrmax;    // ||r||^2 at the last true-residual update (reliable updates)
   double delta2;   // update when rr <= delta2 * rrmax (reliable updates)
   int iter;        // completed operator applications
   int max_iter;
@@ -35,9 +35,9 @@ struct CgState {
   int first;       // 1 before the first z: beta = 0
   int hist_cap;
   unsigned int ticket;  // last-CTA counter for the grid reductions
-  int refine;      // FP64 residual recomputations (mixed refinement)
+  int refine;      // true-residual recomputations (mixed mode)
   int total_iter;  // inner iterations summed over refinement steps
-  int upd;         // reliable updates: FP64 update (FP64 state) / reload (FP32 state) due
+  int upd;         // reliable updates: update (high-precision state) / reload (FP32 state) due
   int last_iter;   // mixed mode, FP32 state: iterations of the last inner solve
   CgState* peer;   // the other precision's state of the same instance (mixed mode)
   double* hist;    // ||r_k|| / ||b||, k = 0..iter
@@ -96,8 +96,8 @@ struct InstDesc {
   typename MapOf<T>::type* out;        // caller's output map (dL/dd in the backward pass)
   const typename MapOf<T>::type* gx;   // caller's dL/dx (backward pass)
   T* w;                    // w = d - y on U, u on M (backward pass)
-  float* dlt;              // FP32 correction (mixed refinement, FP64 passes)
-  float* r32;              // FP32 residual target (mixed refinement, FP64 passes)
+  float* dlt;              // FP32 correction (mixed mode, high-precision passes)
+  float* r32;              // FP32 residual target (mixed mode, high-precision passes)
   CgState* st;
   double* partial;         // per-CTA partial sums
   double* hist;            // residual history (hist_cap entries), or null
@@ -114,7 +114,7 @@ enum RowOp : int {
   OP_P_UPD_Z = 3,   // p = z + beta p; store p; v = p
   OP_P_UPD_R = 4,   // p = r + beta p; store p; v = p   (no preconditioner)
   OP_R_UPD = 5,     // r -= alpha q; u += alpha p; store; acc ||r||^2; v = r
-  OP_U64_UPD = 6,   // u += (double) dlt; store; v = u  (mixed refinement)
+  OP_U64_UPD = 6,   // u += dlt (FP32 correction); store; v = u  (mixed mode)
   OP_LOAD_W_MASK = 7,  // v = P_x w (full maps; operator checks)
   OP_LOAD_U = 8,    // v = u
   OP_LOAD_Y = 9,    // v = y
@@ -144,10 +144,10 @@ enum ScalarOp : int {
   SC_RCHECK = 4,      // rr = sum; iter++; convergence / iteration limit
   SC_RCHECK_BETA = 5, // SC_RCHECK, then beta = rr / rho; rho = rr
   SC_BETA = 6,        // rz = sum; beta = rz / rho (0 on the first); rho = rz
-  SC_RES = 7,         // rr = sum (FP64 true residual); refine++; done if rr <= tol2 bb
-  SC_RCHECK_UPD = 8,  // reliable updates, FP32 state: rr = sum; iter++; request an FP64
+  SC_RES = 7,         // rr = sum (true residual); refine++; done if rr <= tol2 bb
+  SC_RCHECK_UPD = 8,  // reliable updates, FP32 state: rr = sum; iter++; request a
                       // update when rr <= delta2 rrmax or rr <= tol2 bb or at max_iter
-  SC_RES_UPD = 9,     // reliable updates, FP64 state: true residual; converged -> both
+  SC_RES_UPD = 9,     // reliable updates, high-precision state: true residual; converged -> both
                       // done; else FP32 residual replaced, reload of its spectrum due
   SC_CLEAR_UPD = 10,  // upd = 0 (after the reload)
 };

@@ -513,10 +513,10 @@ fill_status run_pcg(fill_plan* p) {
   return run_loop_graph(p, P.iter_graph, P.iter_graph_kernels);
 }
 
-// Mixed-precision solve of A u = b: b, r (FP64) and r32 are set and the FP64
+// Mixed-precision solve of A u = b: b, r (double-float) and r32 are set and the high-precision
 // state holds ||b||^2.  Each step runs an FP32 PCG on A delta = r32 to the
 // tolerance the outer target still needs, then u += delta and the true
-// residual r = b - A u in FP64 (iterative refinement).
+// residual r = b - A u in double-float (iterative refinement).
 fill_status mixed_refine(fill_plan* p, double tol) {
   const int B = p->batch;
   const int nb = (B + 127) / 128;
@@ -544,7 +544,7 @@ fill_status mixed_refine(fill_plan* p, double tol) {
   return FILL_OK;
 }
 
-// Links the FP32 and FP64 states of each instance and sets the reliable-update
+// Links the FP32 and high-precision states of each instance and sets the reliable-update
 // threshold on the FP32 state.
 __global__ void k_link_states(CgState* st32, CgState* st64, int n, double delta2) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -598,8 +598,8 @@ cudaError_t capture_if(cudaStream_t s, cudaStream_t s2, cudaGraphConditionalHand
 
 // One iteration of the mixed reliable-update PCG: an FP32 CG step; if the
 // FP32 residual has dropped by update_delta since the last update (or looks
-// converged), fold the FP32 correction into the FP64 solution, recompute the
-// true residual r = b - A u in FP64, restart the FP32 residual from it and
+// converged), fold the FP32 correction into the double-float solution, recompute
+// the true residual r = b - A u in double-float, restart the FP32 residual from it and
 // keep the search direction; then the preconditioned residual.  The update
 // passes skip every instance without a pending update.
 // The update passes sit in an IF node that runs only when some instance has
@@ -670,7 +670,7 @@ fill_status build_mixed_graph(fill_plan* p) {
       &p->mixed_graph_kernels);
 }
 
-// Mixed-precision solve with reliable updates (b, r, r32 and the FP64 state
+// Mixed-precision solve with reliable updates (b, r, r32 and the high-precision state
 // with ||b||^2 are set; u64 = 0).
 fill_status mixed_reliable(fill_plan* p, double tol) {
   const int B = p->batch;
@@ -681,7 +681,7 @@ fill_status mixed_reliable(fill_plan* p, double tol) {
   CK(cudaGetLastError());
   CK(cudaMemsetAsync(p->f.u, 0, B * p->nv * sizeof(float), p->s));
   CK(cudaMemsetAsync(p->f.p, 0, B * p->nv * sizeof(float), p->s));
-  // instances with b = 0 are done in the FP64 state: mirror that to FP32
+  // instances with b = 0 are done in the high-precision state: mirror that to FP32
   ++p->launches;
   k_inner_reset<<<nb, 128, 0, p->s>>>(p->f.st, p->h.st, B, tol, 0.0, p->o.max_iter);
   CK(cudaGetLastError());
@@ -1099,7 +1099,7 @@ fill_status realize_impl(fill_plan* p, const void* d, long long d_stride, const 
       CK(cudaMemcpyAsync(p->g.hst, p->g.st, sizeof(CgState) * B, cudaMemcpyDeviceToHost, p->s));
     }
   } else {
-    // Mixed: FP64 draw / RHS / residual, FP32 inner PCG, FP64 refinement.
+    // Mixed: double-float draw / RHS / residuals, FP32 PCG with residual updates.
     fill_desc<df>(p, d, d_stride, seeds, out, nullptr);
     fill_desc<float>(p, nullptr, 0, seeds, nullptr, nullptr);
     CK(upload_desc<df>(p));
