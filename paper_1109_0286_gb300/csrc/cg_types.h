@@ -145,7 +145,7 @@ enum ScalarOp : int {
   SC_RCHECK_BETA = 5, // SC_RCHECK, then beta = rr / rho; rho = rr
   SC_BETA = 6,        // rz = sum; beta = rz / rho (0 on the first); rho = rz
   SC_RES = 7,         // rr = sum (true residual); refine++; done if rr <= tol2 bb
-  SC_RCHECK_UPD = 8,  // reliable updates, FP32 state: rr = sum; iter++; request a
+  SC_RCHECK_UPD = 8,  // reliable updates, FP32 state: rr = sum; iter++; request an
                       // update when rr <= delta2 rrmax or rr <= tol2 bb or at max_iter
   SC_RES_UPD = 9,     // reliable updates, high-precision state: true residual; converged -> both
                       // done; else FP32 residual replaced, reload of its spectrum due
