@@ -200,14 +200,14 @@ def strips_measurement():
     def case(scale):
         P, obs, spec = workload("patch1024", scale=scale)
         N = np.full_like(P, synth.cmb_noise_level(spec["k_lo"]))
-        n = obs.shape[1]
-        d = O.draw(O.hermitian_full(P, n), spec["data_seed"])
+        plan = cg.Plan(P, obs, mode="mixed")
+        d = plan.draw([spec["data_seed"]])[0].clone()      # data drawn from P(k)
+        plan.close()
         return P - N, N, obs, d
 
     out = {"workload": "patch1024 (1024^2, 10% band + 200 discs)", "stages": strips.PAPER_STAGES,
            "mode": "mixed", "tol": 1e-8}
-    S, N, obs, d = case(1)
-    dd = torch.from_numpy(d).cuda()
+    S, N, obs, dd = case(1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     x, log = strips.strip_refine(S, N, obs, dd, mode="mixed", tol=1e-8)
@@ -224,18 +224,19 @@ def strips_measurement():
     last = last.cpu().numpy().astype(bool)
     out["rel_err_mask"] = float(np.linalg.norm(x[m] - ml[m]) / np.linalg.norm(ml[m]))
     out["rel_err_last_strip"] = float(np.linalg.norm(x[last] - ml[last]) / np.linalg.norm(ml[last]))
+    # CPU baseline leg: the oracle runs the same procedure on the 256^2 version
     S4, N4, obs4, d4 = case(4)
     stages4 = [(b, w / 4.0) for b, w in strips.PAPER_STAGES]
     t0 = time.perf_counter()
-    strips.strip_refine(S4, N4, obs4, torch.from_numpy(d4).cuda(), stages4, mode="mixed",
-                        tol=1e-8)
+    strips.strip_refine(S4, N4, obs4, d4, stages4, mode="mixed", tol=1e-8)
     torch.cuda.synchronize()
     g4 = (time.perf_counter() - t0) * 1e3
+    d4h = d4.cpu().numpy()
     t0 = time.perf_counter()
-    O.strip_refine(S4, N4, obs4, d4, stages4, tol=1e-8)
+    O.strip_refine(S4, N4, obs4, d4h, stages4, tol=1e-8)
     o4 = (time.perf_counter() - t0) * 1e3
-    out["at_256"] = {"gpu_ms": g4, "oracle_ms": o4, "oracle_cores": threads_used(),
-                     "stages": stages4}
+    out["at_256"] = {"gpu_ms": g4, "stages": stages4,
+                     "cpu_baseline": {"ms": o4, "cores": threads_used(), "kind": "oracle"}}
     return out
 
 
@@ -245,13 +246,14 @@ def far_interior_measurement():
     each boundary: the relative L2 and max difference inside, and the time."""
     import numpy as np
     import torch
-    import oracle as O
+    import paper_1109_0286_gb300 as cg
     from paper_1109_0286_gb300 import laplace
     from workloads import synth
     n, rows, layer = 4096, 819, 82
     P = synth.spectrum_cmb_like(n, n, 2 * np.pi / 4096)
-    d = O.draw(O.hermitian_full(P, n), 3)
-    dd = torch.from_numpy(d).cuda()
+    plan = cg.Plan(P, laplace.band_rows(n, n, rows), mode="mixed")
+    dd = plan.draw([3])[0].clone()                          # data drawn from P(k)
+    plan.close()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     lap, ml, inner, (sm, sl) = laplace.far_interior(P, dd, rows, layer, mode="mixed", tol=1e-8)
@@ -515,7 +517,6 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        import oracle as O
         dn = d.cpu().numpy().astype("float64")
         setup, t_iter = oracle_sample(P, obs, dn, spec["seeds"][0], 1)
         n_it = fp64["iters_per_realization"] if fp64 else FP64_ITERS_WIDE4096
