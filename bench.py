@@ -45,12 +45,12 @@ FP64_ITERS_WIDE4096 = 200
 # shared part (column table, mask words) read once per launch.  A launch over
 # B instances is scaled as B * per-instance + shared.  Reported only while the
 # pass-kernel sources hash to the profiled version; otherwise traffic is null.
-TRAFFIC = {"src_hash": "752ddfd985e2a946",
-           "k_col (column FFT, x 1/(nP), inverse FFT)": (107.00, 33.57),
-           "k_row src (r, u update + R2C)": (141.41, 4.19),
-           "k_row src (p update + R2C)": (90.57, 4.19),
-           "k_row sink (C2R + q = P_x, p^T q)": (95.70, 4.19),
-           "k_row mid (C2R, P_x, R2C)": (108.18, 4.19)}
+TRAFFIC = {"src_hash": "e77a96e3325c418d",
+           "k_col (column FFT, x 1/(nP), inverse FFT)": (106.90, 33.57),
+           "k_row src (r, u update + R2C)": (140.69, 4.19),
+           "k_row src (p update + R2C)": (90.59, 4.19),
+           "k_row sink (C2R + q = P_x, p^T q)": (95.65, 4.19),
+           "k_row mid (C2R, P_x, R2C)": (108.23, 4.19)}
 KERNEL_SOURCES = ["cg_types.h", "cg_common.cuh", "cg_fft.cuh", "cg_kernels.cuh", "cg_launch.cuh"]
 
 
