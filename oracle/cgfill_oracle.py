@@ -42,6 +42,7 @@ __all__ = [
     "dft2_direct", "circulant_corr", "dense_matrix", "ml_dense_cov",
     "ml_dense_prec", "constrained_cov_dense", "backward", "band_full",
     "relax_kernel", "relax", "disc_offsets", "subdivide", "strip_refine",
+    "ms_radii", "annulus_offsets", "ms_classes", "laplace_ms",
     "loss_masked_sq", "lanczos_tridiag",
 ]
 
@@ -484,4 +485,67 @@ def strip_refine(S_half, N_half, observed, d, stages, tol=1e-8, max_iter=10000, 
                   lambda v: apply_S(apply_S(v, P_full, strip), P_full, strip),
                   tol=tol, max_iter=max_iter)
         x = np.where(strip, res.u, x)
+    return x
+
+
+# ---------------------------------------------------------------------------
+# Multi-scale kernel Laplace solver (Sect. 6.3) on the torus
+# ---------------------------------------------------------------------------
+
+def ms_radii(nk=9, rho0=1.5, q=1.55):
+    """``nk`` annuli ``(r_in, r_out)`` with centre radii ``rho_j = rho0 q^j`` in
+    geometric progression and bounds at the geometric midpoints
+    ``rho_j / sqrt(q)``, ``rho_j sqrt(q)``, so consecutive annuli tile the
+    plane; the smallest is solid (``r_in = 0``, centre pixel excluded)."""
+    out = []
+    for j in range(nk):
+        rho = rho0 * q ** j
+        out.append((0.0 if j == 0 else rho / math.sqrt(q), rho * math.sqrt(q)))
+    return out
+
+
+def annulus_offsets(r_in, r_out):
+    """Lattice offsets with ``r_in^2 < dy^2 + dx^2 <= r_out^2`` (never the centre)."""
+    R = int(math.floor(r_out))
+    return [(dy, dx) for dy in range(-R, R + 1) for dx in range(-R, R + 1)
+            if max(r_in * r_in, 0.0) < dy * dy + dx * dx <= r_out * r_out and (dy or dx)]
+
+
+def ms_classes(observed, radii):
+    """Kernel index of every masked pixel: the largest ``j`` whose disc of
+    radius ``r_out_j`` around the pixel holds no observed pixel, else 0 (the
+    thin boundary layer, where the smallest kernel reaches the observed
+    region and carries its values in).  Observed pixels get 0."""
+    obs = observed.astype(bool)
+    cls = np.zeros(observed.shape, dtype=np.int64)
+    for j, (_, r_out) in enumerate(radii):
+        inside = (~obs) & ~subdivide(observed, 2.0 * r_out, 0.0)
+        cls[inside] = j
+    return cls
+
+
+def laplace_ms(observed, d, radii, iters):
+    """Sect. 6.3 on the torus: from 0 on the mask and ``d`` on the observed
+    pixels, every sweep replaces each masked value by the average of the
+    previous map over its class's annulus (Jacobi: all averages from the same
+    map), by FFT convolution with the normalised annulus.  Returns the map."""
+    ny, nx = observed.shape
+    obs = observed.astype(bool)
+    cls = ms_classes(observed, radii)
+    spectra = []
+    for r_in, r_out in radii:
+        k = np.zeros((ny, nx))
+        offs = annulus_offsets(r_in, r_out)
+        for dy, dx in offs:
+            k[dy % ny, dx % nx] = 1.0 / len(offs)
+        spectra.append(np.fft.fft2(k))
+    x = np.where(obs, np.asarray(d, dtype=np.float64), 0.0)
+    for _ in range(iters):
+        X = np.fft.fft2(x)
+        new = x.copy()
+        for j, K in enumerate(spectra):
+            sel = (~obs) & (cls == j)
+            if sel.any():
+                new[sel] = np.real(np.fft.ifft2(X * K))[sel]
+        x = new
     return x

@@ -489,3 +489,53 @@ def test_strip_refine_approaches_ml_fill_near_the_boundary():
         x = O.strip_refine(S, N, obs, d, stages[:k], tol=1e-10)
         errs.append(np.linalg.norm(x.ravel()[last] - full[last]) / np.linalg.norm(full[last]))
     assert errs[0] > errs[1] > errs[2] and errs[2] < 0.25, errs
+
+
+# ----------------------------------------------------------------- kernel Laplace solver (Sect. 6.3)
+
+def test_ms_radii_tile_the_plane_and_classes_by_brute_force():
+    radii = O.ms_radii()
+    assert radii[0][0] == 0.0 and len(radii) == 9
+    for (a, b), (c, e) in zip(radii, radii[1:]):
+        assert abs(b - c) < 1e-12 and e > b
+    assert len(O.annulus_offsets(*radii[0])) == 8     # the solid kernel: 8 neighbours
+    assert all(len(O.annulus_offsets(*r)) > 0 for r in radii)
+    _, obs = _small_case(48, 48, seed=5, band=16, discs=2, r=4.0)
+    small = O.ms_radii(nk=5)
+    cls = O.ms_classes(obs, small)
+    m = obs == 0
+    for y in range(48):
+        for x in range(48):
+            if not m[y, x]:
+                assert cls[y, x] == 0
+                continue
+            def clear(r):
+                R = int(math.floor(r))
+                return all(obs[(y + dy) % 48, (x + dx) % 48] == 0
+                           for dy in range(-R, R + 1) for dx in range(-R, R + 1)
+                           if dy * dy + dx * dx <= r * r)
+            want = max([j for j, (_, ro) in enumerate(small) if clear(ro)], default=0)
+            assert cls[y, x] == want, (y, x)
+
+
+def test_laplace_ms_constant_data_is_a_fixed_point_and_sweeps_approach_harmonic():
+    """Each kernel is an average, so constant boundary data stays constant
+    (the Fig. of Sect. 6.3 starts from boundary 1, interior 0 and converges
+    to 1); with smooth boundary data the sweeps approach the discrete
+    harmonic interpolation (5-point-stencil ML fill)."""
+    _, obs = _small_case(64, 64, seed=5, band=24, discs=0, r=2.0)
+    radii = O.ms_radii(nk=6)
+    one = O.laplace_ms(obs, np.ones((64, 64)), radii, 200)
+    assert np.abs(one - 1.0).max() < 1e-6
+    assert np.abs(O.laplace_ms(obs, np.ones((64, 64)), radii, 0)[obs == 0]).max() == 0.0
+    yy, xx = np.mgrid[0:64, 0:64]
+    d = np.cos(2 * np.pi * xx / 64) + 0.5 * np.sin(4 * np.pi * xx / 64)
+    x = O.laplace_ms(obs, d, radii, 400)
+    lam = _stencil_spectrum(64, 64, 1e-10)
+    Pl = O.hermitian_full(lam, 64)
+    m = obs == 0
+    b = O.rhs(Pl, obs, d, np.zeros_like(d))
+    res = O.pcg(lambda v: O.apply_A(v, Pl, m), b,
+                lambda v: O.apply_S(O.apply_S(v, Pl, m), Pl, m), tol=1e-12, max_iter=20000)
+    err = np.linalg.norm(x[m] - res.u[m]) / np.linalg.norm(res.u[m])
+    assert err < 0.01, err
