@@ -177,6 +177,29 @@ fill_status fill_subdivide(int ny, int nx, const uint8_t* observed, double delta
                            double threshold, int32_t* scratch, uint8_t* layer, void* stream);
 
 /*
+ * fill_set_annuli / fill_laplace_ms -- the kernel-based Laplace solver of
+ * Sect. 6.3: each masked pixel is repeatedly replaced by the average of the map
+ * over an annulus around it -- the mean-value property of harmonic functions --
+ * taking the largest of a family of annuli that stays inside the mask, so that
+ * information crosses wide holes in a number of sweeps growing like a power of
+ * log(width) instead of width^2.
+ * fill_set_annuli: nk annuli r_in[j]^2 < |offset|^2 <= r_out[j]^2 (the centre
+ * never included; 2 r_out < nx, ny); builds their normalised transforms as
+ * column-pass tables with the plan's own transforms (allocates on the first
+ * call or when nk grows).  fill_laplace_ms: `iters` Jacobi sweeps from 0 on the
+ * mask and d on U; cls: device, ny*nx uint8, the annulus index of every masked
+ * pixel (the solver of the paper takes the largest annulus whose disc holds no
+ * observed pixel, and the smallest -- which reaches the observed region -- in
+ * the thin layer along the boundary); d, d_stride, out as in fill_ml (out_U =
+ * d_U exactly).  stats.rel_resid = the last sweep's change over the first's
+ * (L2 over the mask).  Precision: the plan's.  Errors: FILL_EINVAL (no annuli
+ * set, bad radii), FILL_ENOMEM, FILL_ECUDA.
+ */
+fill_status fill_set_annuli(fill_plan* plan, int nk, const double* r_in, const double* r_out);
+fill_status fill_laplace_ms(fill_plan* plan, const void* d, long long d_stride, int iters,
+                            const uint8_t* cls, void* out, fill_stats* stats);
+
+/*
  * fill_draw -- unconstrained realizations y = F^-1[sqrt(P) F xi(seed)] with
  * covariance C (Sect. 2.3, the draw that needs no cuts).  out: device, batch
  * maps (plan element type).  Errors: FILL_EINVAL, FILL_ECUDA.

@@ -21,7 +21,8 @@ from . import _build
 
 __all__ = [
     "FillOpts", "FillStats", "FillError", "load", "lib_path", "fill_opts_default",
-    "fill_init", "fill_realize", "fill_ml", "fill_relax", "fill_subdivide", "fill_draw", "fill_apply", "fill_history",
+    "fill_init", "fill_realize", "fill_ml", "fill_relax", "fill_subdivide", "fill_set_annuli",
+    "fill_laplace_ms", "fill_draw", "fill_apply", "fill_history",
     "fill_lanczos", "fill_time_pass", "fill_set_bands", "fill_backward", "fill_autotune", "fill_group_init",
     "fill_group_realize", "fill_group_size", "fill_group_destroy", "Group", "fill_apply_static",
     "fill_masked_count", "fill_destroy", "fill_strerror", "fill_last_error",
@@ -33,7 +34,7 @@ STATUS = {0: "FILL_OK", 1: "FILL_EINVAL", 2: "FILL_ENOMEM", 3: "FILL_ENOTCONV",
           4: "FILL_EBREAKDOWN", 5: "FILL_ETIMEOUT", 6: "FILL_ECUDA"}
 EXPORTED_SYMBOLS = [
     "fill_opts_default", "fill_init", "fill_realize", "fill_ml", "fill_relax", "fill_subdivide",
-    "fill_draw", "fill_apply",
+    "fill_set_annuli", "fill_laplace_ms", "fill_draw", "fill_apply",
     "fill_history", "fill_lanczos", "fill_time_pass", "fill_set_bands", "fill_backward",
     "fill_autotune",
     "fill_group_init", "fill_group_realize", "fill_group_size", "fill_group_destroy",
@@ -102,6 +103,10 @@ def load() -> ctypes.CDLL:
     lib.fill_relax.restype = _ci
     lib.fill_subdivide.argtypes = [_ci, _ci, _vp, _cd, _cd, _vp, _vp, _vp]
     lib.fill_subdivide.restype = _ci
+    lib.fill_set_annuli.argtypes = [_vp, _ci, _vp, _vp]
+    lib.fill_set_annuli.restype = _ci
+    lib.fill_laplace_ms.argtypes = [_vp, _vp, _cll, _ci, _vp, _vp, ctypes.POINTER(FillStats)]
+    lib.fill_laplace_ms.restype = _ci
     lib.fill_draw.argtypes = [_vp, _vp, _vp]
     lib.fill_draw.restype = _ci
     lib.fill_apply.argtypes = [_vp, _ci, _vp, _vp]
@@ -203,6 +208,21 @@ def fill_subdivide(observed, delta, threshold=0.03, stream=None):
     if st != 0:
         raise FillError(st, "fill_subdivide")
     return layer
+
+
+def fill_set_annuli(plan, r_in, r_out):
+    a = np.ascontiguousarray(r_in, dtype=np.float64)
+    b = np.ascontiguousarray(r_out, dtype=np.float64)
+    st = load().fill_set_annuli(_vp(plan), int(a.size), a.ctypes.data, b.ctypes.data)
+    if st != 0:
+        raise FillError(st, "fill_set_annuli")
+
+
+def fill_laplace_ms(plan, d_ptr, d_stride, iters, cls_ptr, out_ptr, batch):
+    stats = (FillStats * batch)()
+    st = load().fill_laplace_ms(_vp(plan), _vp(d_ptr), _cll(d_stride), int(iters), _vp(cls_ptr),
+                                _vp(out_ptr), stats)
+    return st, [x.as_dict() for x in stats]
 
 
 def fill_draw(plan, seeds, out_ptr):
@@ -425,6 +445,28 @@ class Plan:
                                iters, out.data_ptr(), self.batch)
         if check and st != 0:
             raise FillError(st, "fill_relax")
+        return out, stats
+
+    def set_annuli(self, r_in, r_out):
+        """Annuli of the kernel Laplace solver (Sect. 6.3)."""
+        fill_set_annuli(self._plan, r_in, r_out)
+
+    def laplace_ms(self, d, iters, cls, out=None, check=True):
+        """Sweeps of the kernel Laplace solver with per-pixel annulus index
+        ``cls`` (device uint8 map).  Returns ``(out, stats)``."""
+        import torch
+        shared = d.numel() == self.ny * self.nx
+        self._check(d, "d", 1 if shared else self.batch)
+        if not (isinstance(cls, torch.Tensor) and cls.is_cuda and cls.dtype == torch.uint8
+                and cls.numel() == self.ny * self.nx and cls.is_contiguous()):
+            raise ValueError("cls: expected a contiguous uint8 CUDA map")
+        if out is None:
+            out = torch.empty((self.batch, self.ny, self.nx), dtype=self.dtype, device=d.device)
+        self._check(out, "out", self.batch)
+        st, stats = fill_laplace_ms(self._plan, d.data_ptr(), 0 if shared else self.ny * self.nx,
+                                    iters, cls.data_ptr(), out.data_ptr(), self.batch)
+        if check and st != 0:
+            raise FillError(st, "fill_laplace_ms")
         return out, stats
 
     def set_bands(self, band_of_k, sig_half):

@@ -151,7 +151,8 @@ __device__ __forceinline__ void src_fill(const InstDesc<T>& I, const uint2* mwr,
 // TT): projection, stores and the inner product of its op.
 template <typename T, int TT, int OP>
 __device__ __forceinline__ void sink_fill(const InstDesc<T>& I, const uint2* mwr, int rowpix,
-                                          int tid, const cx<T> (&v)[16], Acc<T>& acc) {
+                                          int tid, const cx<T> (&v)[16], Acc<T>& acc,
+                                          int param = 0) {
   constexpr int CK = kSinkChunk;
 #pragma unroll
   for (int h = 0; h < 16; h += CK) {
@@ -205,6 +206,10 @@ __device__ __forceinline__ void sink_fill(const InstDesc<T>& I, const uint2* mwr
         st_pair(I.w + rowpix + 2 * j, x0[e] - step * a0, x1[e] - step * a1);
         acc.add_prod(a0, a0);
         acc.add_prod(a1, a1);
+      } else if constexpr (OP == OP_KSEL) {
+        const uchar2 c = *reinterpret_cast<const uchar2*>(I.cls + rowpix + 2 * j);
+        if (m0 && c.x == param) I.y[rowpix + 2 * j] = a0;
+        if (m1 && c.y == param) I.y[rowpix + 2 * j + 1] = a1;
       } else if constexpr (OP == OP_STORE_Y) {
         st_pair(I.y + rowpix + 2 * j, a0, a1);
       } else if constexpr (OP == OP_STORE_Y_MASK) {
@@ -331,6 +336,7 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
         case OP_RES: sink_fill<T, TT, OP_RES>(I, mwr, rowpix, tid, v, acc); break;
         case OP_GRAD: sink_fill<T, TT, OP_GRAD>(I, mwr, rowpix, tid, v, acc); break;
         case OP_RELAX: sink_fill<T, TT, OP_RELAX>(I, mwr, rowpix, tid, v, acc); break;
+        case OP_KSEL: sink_fill<T, TT, OP_KSEL>(I, mwr, rowpix, tid, v, acc, a.param); break;
         case OP_STORE_Y: sink_fill<T, TT, OP_STORE_Y>(I, mwr, rowpix, tid, v, acc); break;
         case OP_STORE_Y_MASK:
           sink_fill<T, TT, OP_STORE_Y_MASK>(I, mwr, rowpix, tid, v, acc);
@@ -432,7 +438,8 @@ k_col(const InstDesc<T>* __restrict__ insts, ColArgs a, const T* __restrict__ tw
   for (int e = 0; e < 16; ++e) v[e] = act ? ld_cx<T>(col + 2 * (tid + e * TT)) : cx<T>{(T)0, (T)0};
   fft_regs<T, LOG_N, false>(v, xb, tid, tw, bar, bar);
   if (a.table >= 0) {
-    const T* tab = (a.table ? I.t_sqrt : I.t_inv) + (long long)(act ? kx : 0) * N;
+    const T* tab = (a.table >= 2 ? I.kt + (long long)(a.table - 2) * a.nkx * N
+                    : a.table ? I.t_sqrt : I.t_inv) + (long long)(act ? kx : 0) * N;
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       const T t = act ? ldg1(tab + tid + e * TT) : (T)0;
@@ -511,6 +518,29 @@ k_vec(const InstDesc<T>* __restrict__ insts, VecArgs a) {
           T a0, a1;
           ld_pair(I.y + pix, a0, a1);
           st_map_pair<T>(I.out + pix, a0, a1);
+          break;
+        }
+        case VOP_ANNULUS: {   // offsets by minimum image from pixel 0
+          const long long nx = a.nx, ny = a.npix / a.nx;
+          T av[2];
+          for (int t = 0; t < 2; ++t) {
+            const long long pp = pix + t, yy = pp / nx, xx = pp % nx;
+            const double dy = (double)(yy <= ny / 2 ? yy : yy - ny);
+            const double dx = (double)(xx <= nx / 2 ? xx : xx - nx);
+            const double r2 = dy * dy + dx * dx;
+            av[t] = (r2 > a.p0 && r2 <= a.p1 && r2 > 0.0) ? (T)1 : (T)0;
+          }
+          st_pair(I.w + pix, av[0], av[1]);
+          break;
+        }
+        case VOP_Y_TO_W_M: {
+          T w0, w1, y0, y1;
+          ld_pair(I.w + pix, w0, w1);
+          ld_pair(I.y + pix, y0, y1);
+          const T d0 = q.m0 ? y0 - w0 : (T)0, d1 = q.m1 ? y1 - w1 : (T)0;
+          st_pair(I.w + pix, q.m0 ? y0 : w0, q.m1 ? y1 : w1);
+          acc.add_prod(d0, d0);
+          acc.add_prod(d1, d1);
           break;
         }
         case VOP_W_FROM_D: {

@@ -102,6 +102,8 @@ struct InstDesc {
   double* partial;         // per-CTA partial sums
   double* hist;            // residual history (hist_cap entries), or null
   double* coef;            // CG coefficients (2 hist_cap entries), or null
+  const T* kt;             // kernel tables [j][kx][ky] of the Sect. 6.3 solver, or null
+  const uint8_t* cls;      // kernel class of every pixel (Sect. 6.3 solver), or null
   long long nvec;          // compact CG-vector length: masked pixels of this instance
   unsigned long long seed;
 };
@@ -132,6 +134,7 @@ enum RowOp : int {
   OP_GRAD = 25,     // v = C^-1 lam: out = (g - v) on U, 0 on M; y = h = g on M, v on U
   OP_RELAX = 29,    // v = C^-1 w: w -= alpha v on M (alpha = 1/a, Sect. 5 relaxation);
                     // acc ||v_M||^2
+  OP_KSEL = 30,     // v = kernel j * w: y = v on the masked pixels of class j (Sect. 6.3)
   OP_LOAD_W = 26,   // (source) v = w
 };
 
@@ -167,6 +170,8 @@ enum VecOp : int {
   VOP_MAP_OUT = 9,    // out = y (pass element type -> caller's map)
   VOP_W_FROM_D = 10,  // w = d on U, 0 on M
   VOP_W_TO_OUT = 11,  // out = w (pass element type -> caller's map)
+  VOP_ANNULUS = 12,   // w = 1 where r_in^2 < |offset|^2 <= r_out^2 (offset from pixel 0), else 0
+  VOP_Y_TO_W_M = 13,  // w = y on M; acc ||y - w||^2 over M
 };
 
 // Launch arguments of the pass kernels.
@@ -178,13 +183,14 @@ struct RowArgs {
   int sop;          // ScalarOp (SC_NONE: no reduction)
   int check_done;   // skip instances whose CG state is done
   int spec_sel;     // 0: spec, 1: spec2
+  int param;        // op parameter (OP_KSEL: the kernel class)
 };
 
 struct ColArgs {
   int ny;           // column length (FFT size)
   int nkx;          // nx/2 + 1 spectrum rows
   int ffts;         // column FFTs per CTA
-  int table;        // 0: 1/(nP), 1: sqrt(P)/n; -1: forward transform only
+  int table;        // 0: 1/(nP), 1: sqrt(P)/n; j + 2: kernel table j; -1: forward only
   int check_done;
   int spec_sel;     // 0: spec, 1: spec2
 };
@@ -203,6 +209,8 @@ struct VecArgs {
   int op;           // VecOp
   int sop;
   int check_done;
+  double p0, p1;    // op parameters (VOP_ANNULUS: r_in^2, r_out^2)
+  int nx;           // row length (VOP_ANNULUS)
 };
 
 constexpr int kLmax = 8192;        // twiddle master table: W_8192^m

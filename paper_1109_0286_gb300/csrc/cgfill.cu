@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "../../include/cgfill.h"
+#include "cg_common.cuh"
 #include "cg_launch.h"
 #include "cg_types.h"
 
@@ -87,6 +88,8 @@ struct Precision {
   double* partial = nullptr;
   double* hist = nullptr;
   double* coef = nullptr;       // CG coefficients, 2 history_cap per instance
+  T* kt = nullptr;              // kernel tables of the Sect. 6.3 solver
+  int nk = 0, nk_cap = 0;
   InstDesc<T>* desc = nullptr;  // device, batch
   InstDesc<T>* hdesc = nullptr; // pinned
   int rows = 0, ffts = 0;
@@ -262,9 +265,9 @@ Ctx<T> ctx(fill_plan* p, int ninst = -1) {
 
 template <typename T>
 cudaError_t row(const Ctx<T>& c, cudaStream_t s, int op, int sop, bool in_spec, bool out_spec,
-                int skip, int spec_sel = 0) {
+                int skip, int spec_sel = 0, int param = 0) {
   ++*c.launches;
-  RowArgs a{c.ny, c.nx, c.rows, ilog2(c.rows), op, sop, skip, spec_sel};
+  RowArgs a{c.ny, c.nx, c.rows, ilog2(c.rows), op, sop, skip, spec_sel, param};
   return Launch<T>::row(c.log_l, in_spec, out_spec, c.desc, c.ninst, a, c.tw, s);
 }
 
@@ -276,9 +279,10 @@ cudaError_t col(const Ctx<T>& c, cudaStream_t s, int table, int skip, int spec_s
 }
 
 template <typename T>
-cudaError_t vec(const Ctx<T>& c, cudaStream_t s, int op, int sop, int skip) {
+cudaError_t vec(const Ctx<T>& c, cudaStream_t s, int op, int sop, int skip, double p0 = 0.0,
+                double p1 = 0.0) {
   ++*c.launches;
-  VecArgs a{c.npix, op, sop, skip};
+  VecArgs a{c.npix, op, sop, skip, p0, p1, c.nx};
   const long long pairs = c.npix / 2;
   const int nblk = (int)std::min<long long>((pairs + 255) / 256, 1024);
   return Launch<T>::vec(c.desc, c.ninst, a, nblk, s);
@@ -1191,6 +1195,130 @@ fill_status fill_relax(fill_plan* p, const void* d, long long d_stride, int iter
   return p->o.mode == FILL_MODE_FP32   ? relax_t<float>(p, d, d_stride, iters, out, stats)
          : p->o.mode == FILL_MODE_FP64 ? relax_t<double>(p, d, d_stride, iters, out, stats)
                                        : relax_t<df>(p, d, d_stride, iters, out, stats);
+}
+
+}  // extern "C"
+
+namespace {
+// Real part of a transposed spectrum, scaled: the kernel table of one annulus.
+template <typename T>
+__global__ void k_spec_to_table(const T* spec, T* tab, long long n, double scale) {
+  const T sc = (T)scale;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    tab[i] = spec[2 * i] * sc;
+}
+
+long long annulus_count(double r_in, double r_out) {
+  const int R = (int)std::floor(r_out);
+  long long c = 0;
+  for (int dy = -R; dy <= R; ++dy)
+    for (int dx = -R; dx <= R; ++dx) {
+      const double r2 = double(dy) * dy + double(dx) * dx;
+      if (r2 > r_in * r_in && r2 <= r_out * r_out && r2 > 0.0) ++c;
+    }
+  return c;
+}
+
+// Kernel tables 1/(count n) Re F(annulus_j) of the Sect. 6.3 solver, from the
+// annulus images by the plan's own forward transforms (instance 0's buffers).
+template <typename T>
+fill_status set_annuli_t(fill_plan* p, int nk, const double* r_in, const double* r_out) {
+  Precision<T>& P = prec<T>(p);
+  if (!P.used) return FILL_OK;
+  const size_t ntab = size_t(p->nx / 2 + 1) * p->ny;
+  if (nk > P.nk_cap) {
+    if (p->dalloc(&P.kt, size_t(nk) * ntab) != cudaSuccess) return FILL_ENOMEM;
+    P.nk_cap = nk;
+  }
+  P.nk = nk;
+  for (int i = 0; i < p->batch; ++i) P.hdesc[i].kt = P.kt;
+  fill_desc<T>(p, nullptr, 0, nullptr, nullptr, nullptr);
+  CK(upload_desc<T>(p));
+  CK(init_states<T>(p, 0.0));
+  const Ctx<T> c1 = ctx<T>(p, 1);
+  for (int j = 0; j < nk; ++j) {
+    const long long cnt = annulus_count(r_in[j], r_out[j]);
+    CK(vec<T>(c1, p->s, VOP_ANNULUS, SC_NONE, SKIP_NEVER, r_in[j] * r_in[j], r_out[j] * r_out[j]));
+    CK(row<T>(c1, p->s, OP_LOAD_W, SC_NONE, false, true, SKIP_NEVER));
+    CK(col<T>(c1, p->s, -1, SKIP_NEVER));
+    ++p->launches;
+    k_spec_to_table<T><<<256, 256, 0, p->s>>>(P.spec, P.kt + size_t(j) * ntab, (long long)ntab,
+                                            1.0 / (double(cnt) * double(p->npix)));
+    CK(cudaGetLastError());
+  }
+  CK(cudaStreamSynchronize(p->s));
+  return FILL_OK;
+}
+
+// Multi-scale kernel Laplace solver (Sect. 6.3): every sweep averages the map
+// over each masked pixel's annulus (class map `cls`), all from the same map.
+template <typename T>
+fill_status laplace_ms_t(fill_plan* p, const void* d, long long d_stride, int iters,
+                         const uint8_t* cls, void* out, fill_stats* stats) {
+  Precision<T>& P = prec<T>(p);
+  if (P.nk < 1) return FILL_EINVAL;
+  const auto t0 = std::chrono::steady_clock::now();
+  const int B = p->batch;
+  p->launches = 0;
+  fill_desc<T>(p, d, d_stride, nullptr, out, nullptr);
+  for (int i = 0; i < B; ++i) {
+    P.hdesc[i].cls = cls;
+    P.hdesc[i].kt = P.kt;
+  }
+  CK(upload_desc<T>(p));
+  CK(init_states<T>(p, 0.0));
+  const Ctx<T> c = ctx<T>(p);
+  CK(vec<T>(c, p->s, VOP_W_FROM_D, SC_NONE, SKIP_NEVER));
+  for (int k = 0; k < iters; ++k) {
+    for (int j = 0; j < P.nk; ++j) {
+      CK(row<T>(c, p->s, OP_LOAD_W, SC_NONE, false, true, SKIP_NEVER));
+      CK(col<T>(c, p->s, 2 + j, SKIP_NEVER));
+      CK(row<T>(c, p->s, OP_KSEL, SC_NONE, true, false, SKIP_NEVER, 0, j));
+    }
+    CK(vec<T>(c, p->s, VOP_Y_TO_W_M, k == 0 ? SC_BB : SC_RES, SKIP_NEVER));
+  }
+  CK(vec<T>(c, p->s, VOP_W_TO_OUT, SC_NONE, SKIP_NEVER));
+  CK(cudaMemcpyAsync(P.hst, P.st, sizeof(CgState) * B, cudaMemcpyDeviceToHost, p->s));
+  CK(cudaStreamSynchronize(p->s));
+  const double ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (stats)
+    for (int i = 0; i < B; ++i) {
+      const CgState& a = P.hst[i];
+      fill_stats st{};
+      st.iters = iters;
+      st.status = FILL_OK;
+      st.launches = (int)p->launches;
+      st.rel_resid = a.bb > 0 ? std::sqrt(a.rr / a.bb) : 0.0;
+      st.true_rel_resid = -1.0;
+      st.ms = ms;
+      stats[i] = st;
+    }
+  return FILL_OK;
+}
+}  // namespace
+
+extern "C" {
+
+fill_status fill_set_annuli(fill_plan* p, int nk, const double* r_in, const double* r_out) {
+  if (!p || nk < 1 || nk > 250 || !r_in || !r_out) return FILL_EINVAL;
+  for (int j = 0; j < nk; ++j)
+    if (!(r_in[j] >= 0.0) || !(r_out[j] > r_in[j]) || 2.0 * r_out[j] >= double(p->nx) ||
+        2.0 * r_out[j] >= double(p->ny) || annulus_count(r_in[j], r_out[j]) == 0)
+      return FILL_EINVAL;
+  fill_status fs = set_annuli_t<float>(p, nk, r_in, r_out);
+  if (fs == FILL_OK) fs = set_annuli_t<double>(p, nk, r_in, r_out);
+  if (fs == FILL_OK) fs = set_annuli_t<df>(p, nk, r_in, r_out);
+  return fs;
+}
+
+fill_status fill_laplace_ms(fill_plan* p, const void* d, long long d_stride, int iters,
+                            const uint8_t* cls, void* out, fill_stats* stats) {
+  if (!p || !d || !cls || !out || iters < 0 || d_stride < 0) return FILL_EINVAL;
+  return p->o.mode == FILL_MODE_FP32   ? laplace_ms_t<float>(p, d, d_stride, iters, cls, out, stats)
+         : p->o.mode == FILL_MODE_FP64 ? laplace_ms_t<double>(p, d, d_stride, iters, cls, out, stats)
+                                       : laplace_ms_t<df>(p, d, d_stride, iters, cls, out, stats);
 }
 
 fill_status fill_draw(fill_plan* p, const uint64_t* seeds, void* out) {

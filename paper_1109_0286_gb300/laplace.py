@@ -1,5 +1,5 @@
-"""Laplace interpolation into a masked region and the far-interior test of
-Sect. 6.1.
+"""Laplace interpolation into a masked region: the exact discrete solve, the
+far-interior test of Sect. 6.1, and the kernel-based solver of Sect. 6.3.
 
 The discrete Laplace equation on the masked pixels with the map outside as
 Dirichlet data is the maximum-likelihood fill for the spectrum
@@ -14,7 +14,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import Plan
+from . import Plan, fill_subdivide
 
 
 def stencil_spectrum(ny, nx, m2=1e-8):
@@ -57,3 +57,46 @@ def far_interior(P_half, d, rows, layer, mode="mixed", tol=1e-8):
     plan.close()
     lap, st_lap = laplace_fill(inner, ml[0], mode=mode)
     return lap, ml[0], inner, (st_ml[0], st_lap)
+
+
+def ms_radii(nk=9, rho0=1.5, q=1.55):
+    """The Sect. 6.3 solver's annuli ``(r_in, r_out)``: centre radii
+    ``rho0 q^j`` in geometric progression, bounds at the geometric midpoints
+    (consecutive annuli tile the plane), the smallest solid (the centre pixel
+    excluded: the eight neighbours)."""
+    out = []
+    for j in range(nk):
+        rho = rho0 * q ** j
+        out.append((0.0 if j == 0 else rho / np.sqrt(q), rho * np.sqrt(q)))
+    return out
+
+
+def ms_classes(obs_dev, radii):
+    """Annulus index of every masked pixel (device uint8 map): the largest
+    ``j`` whose disc of radius ``r_out_j`` holds no observed pixel (the Sect.
+    6.2 layer of width ``2 r_out_j`` at threshold 0 does not contain it), else
+    0: the thin layer along the boundary, where the smallest annulus reaches
+    the observed region."""
+    import torch
+    obs = obs_dev.cpu().numpy().astype(bool)
+    cls = np.zeros(obs.shape, dtype=np.uint8)
+    for j, (_, r_out) in enumerate(radii):
+        layer = fill_subdivide(obs_dev, 2.0 * r_out, 0.0).cpu().numpy().astype(bool)
+        cls[~obs & ~layer] = j
+    return torch.from_numpy(cls).to(obs_dev.device)
+
+
+def laplace_ms(observed, d, iters, radii=None, mode="mixed"):
+    """``iters`` sweeps of the kernel-based Laplace solver of Sect. 6.3 on the
+    device map ``d`` (values on the mask ignored; the sweeps start from 0
+    there).  Returns ``(map, stats)``."""
+    import torch
+    radii = ms_radii() if radii is None else radii
+    observed = np.ascontiguousarray(observed, dtype=np.uint8)
+    ny, nx = observed.shape
+    plan = Plan(np.ones((ny, nx // 2 + 1)), observed, mode=mode)
+    plan.set_annuli([r[0] for r in radii], [r[1] for r in radii])
+    cls = ms_classes(torch.from_numpy(observed).to(d.device), radii)
+    out, st = plan.laplace_ms(d.to(plan.dtype).contiguous(), iters, cls)
+    plan.close()
+    return out[0], st[0]

@@ -15,7 +15,7 @@ if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 import paper_1109_0286_gb300 as cg  # noqa: E402
-from paper_1109_0286_gb300 import strips  # noqa: E402
+from paper_1109_0286_gb300 import laplace, strips  # noqa: E402
 
 
 @pytest.mark.parametrize("name,deltas", [("patch1024", (3.0, 7.0, 15.0, 35.0, 100.0)),
@@ -62,8 +62,6 @@ def test_strip_refine_matches_oracle(mode, bound):
 
 
 # ------------------------------------------------------------------ Laplace interpolation (Sect. 6.1)
-
-from paper_1109_0286_gb300 import laplace  # noqa: E402
 
 
 def _oracle_laplace(obs_inner, x, tol=1e-12):
@@ -118,3 +116,68 @@ def test_far_interior_laplace_vs_exact_1024():
     orc = np.linalg.norm(lap_o[m] - ml_o[m]) / np.linalg.norm(ml_o[m])
     assert abs(gpu - orc) <= 2e-3 * orc, (gpu, orc)
     assert gpu < 0.06, gpu
+
+
+def _ms_case(n=256):
+    _, obs, _ = workload("wide4096", scale=4096 // n)
+    obs = np.array(obs, dtype=np.uint8)
+    yy, xx = np.mgrid[:n, :n]
+    obs[(yy - n // 3) ** 2 + (xx - n // 2) ** 2 < (n // 5) ** 2] = 0   # one wide hole
+    S = synth.spectrum_lorentz_beam(n, n, k0=2 * math.pi / 24, sb=1.0, noise_frac=0.0)
+    d = O.draw(O.hermitian_full(S, n), 11)
+    return obs, d
+
+
+def test_ms_classes_match_oracle():
+    obs, _ = _ms_case()
+    radii = O.ms_radii()
+    got = laplace.ms_classes(torch.from_numpy(obs).cuda(), radii).cpu().numpy()
+    ref = O.ms_classes(obs, radii)
+    assert np.array_equal(got[obs == 0], ref[obs == 0])
+    assert len(np.unique(ref[obs == 0])) >= 5   # several annuli take part
+
+
+@pytest.mark.parametrize("mode,bound", [("fp64", 1e-11), ("mixed", 1e-10), ("fp32", 2e-5)])
+def test_laplace_ms_matches_oracle(mode, bound):
+    obs, d = _ms_case()
+    radii = O.ms_radii()
+    for iters in (0, 1, 12):
+        x, st = laplace.laplace_ms(obs, torch.from_numpy(d).cuda(), iters, radii, mode=mode)
+        x = x.cpu().numpy()
+        ref = O.laplace_ms(obs, d, radii, iters)
+        m = obs == 0
+        assert np.array_equal(x[~m], d.astype(x.dtype)[~m])
+        if iters == 0:
+            assert not x[m].any()
+            continue
+        assert np.linalg.norm(x[m] - ref[m]) <= bound * np.linalg.norm(ref[m]), iters
+        assert st["iters"] == iters and st["rel_resid"] >= 0
+
+
+def test_laplace_ms_constant_map_converges_to_the_constant():
+    """Averages of a constant are that constant: the sweeps from 0 rise
+    monotonically towards it and stay below it."""
+    obs, _ = _ms_case(128)
+    radii = O.ms_radii(nk=7)
+    d = torch.full((128, 128), 3.0, dtype=torch.float64, device="cuda")
+    prev = np.zeros(int((obs == 0).sum()))
+    for iters in (5, 20, 80):
+        x, _ = laplace.laplace_ms(obs, d, iters, radii, mode="fp64")
+        v = x.cpu().numpy()[obs == 0]
+        assert np.all(v <= 3.0 + 1e-12) and np.all(v >= prev - 1e-12)
+        prev = v
+    assert np.max(np.abs(prev - 3.0)) < 3e-2   # within 1% after 80 sweeps
+
+
+def test_set_annuli_rejects_bad_radii():
+    obs, _ = _ms_case(64)
+    plan = cg.Plan(np.ones((64, 33)), obs, mode="fp64")
+    try:
+        for r_in, r_out in (([0.0], [32.0]), ([2.0], [1.5]), ([0.5], [0.9])):
+            with pytest.raises(cg.FillError):
+                plan.set_annuli(r_in, r_out)
+        with pytest.raises(cg.FillError):   # no annuli set yet
+            plan.laplace_ms(torch.zeros((64, 64), dtype=torch.float64, device="cuda"), 1,
+                            torch.zeros((64, 64), dtype=torch.uint8, device="cuda"))
+    finally:
+        plan.close()
