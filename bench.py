@@ -45,12 +45,12 @@ FP64_ITERS_WIDE4096 = 200
 # shared part (column table, mask words) read once per launch.  A launch over
 # B instances is scaled as B * per-instance + shared.  Reported only while the
 # pass-kernel sources hash to the profiled version; otherwise traffic is null.
-TRAFFIC = {"src_hash": "e77a96e3325c418d",
-           "k_col (column FFT, x 1/(nP), inverse FFT)": (106.90, 33.57),
-           "k_row src (r, u update + R2C)": (140.69, 4.19),
-           "k_row src (p update + R2C)": (90.59, 4.19),
-           "k_row sink (C2R + q = P_x, p^T q)": (95.65, 4.19),
-           "k_row mid (C2R, P_x, R2C)": (108.23, 4.19)}
+TRAFFIC = {"src_hash": "7a0a90ed1a6a0caf",
+           "k_col (column FFT, x 1/(nP), inverse FFT)": (107.12, 33.57),
+           "k_row src (r, u update + R2C)": (140.81, 4.19),
+           "k_row src (p update + R2C)": (90.56, 4.19),
+           "k_row sink (C2R + q = P_x, p^T q)": (95.71, 4.19),
+           "k_row mid (C2R, P_x, R2C)": (108.21, 4.19)}
 KERNEL_SOURCES = ["cg_types.h", "cg_common.cuh", "cg_fft.cuh", "cg_kernels.cuh", "cg_launch.cuh"]
 
 
@@ -268,6 +268,71 @@ def far_interior_measurement():
             "max_rel": float(diff.abs().max() / ref.abs().max())}
 
 
+def laplace_ms_measurement():
+    """The kernel-based Laplace solver of Sect. 6.3 at 4096^2 on the 819-row
+    band (20%) with 13 annuli (the largest disc, radius 359, fits the band's
+    half-width): ms per sweep (FP32) and the distance to the exact 5-point
+    Laplace fill after 50/100/200/400 sweeps, beside the single 3x3 kernel
+    (plain Jacobi).  The oracle runs the 512^2 version (102-row band, 8
+    annuli) for 50 sweeps, timed beside the GPU."""
+    import numpy as np
+    import torch
+    import oracle as O
+    import paper_1109_0286_gb300 as cg
+    from paper_1109_0286_gb300 import laplace
+    from workloads import synth
+
+    def case(n, rows):
+        P = synth.spectrum_cmb_like(n, n, 2 * np.pi / 4096)
+        obs = laplace.band_rows(n, n, rows)
+        plan = cg.Plan(P, obs, mode="mixed")
+        d = plan.draw([3])[0].clone()                       # data drawn from P(k)
+        plan.close()
+        return obs, d
+
+    def sweeps(plan, d, cls, k):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, _ = plan.laplace_ms(d, k, cls)
+        torch.cuda.synchronize()
+        return x[0], (time.perf_counter() - t0) * 1e3
+
+    n, rows = 4096, 819
+    obs, d = case(n, rows)
+    exact, st = laplace.laplace_fill(obs, d, mode="mixed", tol=1e-10)
+    m = torch.from_numpy(obs == 0).cuda()
+    ref = exact[m]
+    out = {"grid": [n, n], "band_rows": rows, "mode": "fp32", "exact_cg_iters": st["iters"]}
+    d32 = d.float().contiguous()
+    for nk, ks in ((13, (50, 100, 200, 400)), (1, (400,))):
+        radii = laplace.ms_radii(nk=nk)
+        plan = cg.Plan(np.ones((n, n // 2 + 1)), obs, mode="fp32")
+        plan.set_annuli([r[0] for r in radii], [r[1] for r in radii])
+        cls = laplace.ms_classes(torch.from_numpy(obs).cuda(), radii)
+        sweeps(plan, d32, cls, 2)                            # warm-up
+        errs = {}
+        for k in ks:
+            x, ms = sweeps(plan, d32, cls, k)
+            errs[k] = float(torch.linalg.norm(x[m].double() - ref) / torch.linalg.norm(ref))
+        plan.close()
+        out[f"annuli_{nk}"] = {"rel_l2_vs_exact": errs, "ms_per_sweep": ms / ks[-1],
+                               "r_out_max": radii[-1][1]}
+    # CPU baseline leg: the oracle on the 512^2 version, 50 sweeps
+    obs5, d5 = case(512, 102)
+    radii5 = laplace.ms_radii(nk=8)
+    d5h = d5.cpu().numpy()
+    t0 = time.perf_counter()
+    laplace.laplace_ms(obs5, d5, 50, radii5, mode="fp32")
+    torch.cuda.synchronize()
+    g5 = (time.perf_counter() - t0) * 1e3
+    t0 = time.perf_counter()
+    O.laplace_ms(obs5, d5h, radii5, 50)
+    o5 = (time.perf_counter() - t0) * 1e3
+    out["at_512"] = {"sweeps": 50, "annuli": 8, "gpu_ms_incl_setup": g5,
+                     "cpu_baseline": {"ms": o5, "cores": threads_used(), "kind": "oracle"}}
+    return out
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -464,6 +529,7 @@ def run_gpu(args):
 
     strip_meas = strips_measurement() if (rank == 0 and not args.no_strips) else None
     far = far_interior_measurement() if (rank == 0 and not args.no_strips) else None
+    lms = laplace_ms_measurement() if (rank == 0 and not args.no_strips) else None
 
     # roofline of the hot-loop passes (CUDA events on the plan's stream)
     peaks, peak_src = measured_peaks()
@@ -543,7 +609,7 @@ def run_gpu(args):
                 "speedup_vs_fp64": (value / world / fp64["value"]) if fp64 else None,
                 "gpu_launches": launches, "e2e": e2e, "roofline": roofline,
                 "passes": pass_table, "lanczos": lanczos, "relax": relax, "strips": strip_meas,
-                "far_interior": far,
+                "far_interior": far, "laplace_ms": lms,
                 "clocks": clk.summary(),
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)

@@ -416,10 +416,11 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
 // ----------------------------------------------------------------- column pass
 // CTA = `ffts` spectrum rows (one kx each), N/16 threads per row; forward
 // column FFT, multiply by the real table, inverse column FFT, in place
-// (table < 0: forward transform only).  blockIdx.x is the instance, so the
+// (table < 0: forward transform only; PRE: start from the forward transform
+// held in spec and write to the buffer spec_sel names).  blockIdx.x is the instance, so the
 // CTAs of all instances for the same kx run together and share the table
 // row through L2.
-template <typename T, int LOG_N>
+template <typename T, int LOG_N, bool PRE = false>
 __global__ void __launch_bounds__(KCfg<T>::kMaxThreads)
 k_col(const InstDesc<T>* __restrict__ insts, ColArgs a, const T* __restrict__ tw) {
   constexpr int N = 1 << LOG_N, TT = N / 16, PADN = N + N / 16 + 1;
@@ -433,10 +434,11 @@ k_col(const InstDesc<T>* __restrict__ insts, ColArgs a, const T* __restrict__ tw
   const XBuf<T> xb(sm + f * 2 * PADN, PADN);
   const XBar bar = XBar::make(TT, a.ffts, f);
   T* col = (a.spec_sel ? I.spec2 : I.spec) + 2 * (long long)(act ? kx : 0) * N;
+  const T* src = PRE ? I.spec + 2 * (long long)(act ? kx : 0) * N : col;
   cx<T> v[16];
 #pragma unroll
-  for (int e = 0; e < 16; ++e) v[e] = act ? ld_cx<T>(col + 2 * (tid + e * TT)) : cx<T>{(T)0, (T)0};
-  fft_regs<T, LOG_N, false>(v, xb, tid, tw, bar, bar);
+  for (int e = 0; e < 16; ++e) v[e] = act ? ld_cx<T>(src + 2 * (tid + e * TT)) : cx<T>{(T)0, (T)0};
+  if constexpr (!PRE) fft_regs<T, LOG_N, false>(v, xb, tid, tw, bar, bar);
   if (a.table >= 0) {
     const T* tab = (a.table >= 2 ? I.kt + (long long)(a.table - 2) * a.nkx * N
                     : a.table ? I.t_sqrt : I.t_inv) + (long long)(act ? kx : 0) * N;

@@ -58,7 +58,11 @@ template <typename T, int LN>
 cudaError_t col_ln(const InstDesc<T>* d, int ninst, const ColArgs& a, const T* tw, cudaStream_t s) {
   constexpr int TT = (1 << LN) / 16;
   dim3 grid(ninst, (a.nkx + a.ffts - 1) / a.ffts), block(a.ffts * TT);
-  k_col<T, LN><<<grid, block, Launch<T>::col_smem(LN, a.ffts), s>>>(d, a, tw);
+  const size_t sm = Launch<T>::col_smem(LN, a.ffts);
+  if (a.pre)
+    k_col<T, LN, true><<<grid, block, sm, s>>>(d, a, tw);
+  else
+    k_col<T, LN><<<grid, block, sm, s>>>(d, a, tw);
   return cudaGetLastError();
 }
 
@@ -118,7 +122,9 @@ cudaError_t Launch<T>::prepare() {
   CGF_PREP_ROW(4) CGF_PREP_ROW(5) CGF_PREP_ROW(6) CGF_PREP_ROW(7) CGF_PREP_ROW(8)
   CGF_PREP_ROW(9) CGF_PREP_ROW(10) CGF_PREP_ROW(11) CGF_PREP_ROW(12)
 #undef CGF_PREP_ROW
-#define CGF_PREP_COL(LN) if (e == cudaSuccess) e = detail::allow_smem(k_col<T, LN>);
+#define CGF_PREP_COL(LN)                                             \
+  if (e == cudaSuccess) e = detail::allow_smem(k_col<T, LN>);        \
+  if (e == cudaSuccess) e = detail::allow_smem(k_col<T, LN, true>);
   CGF_PREP_COL(4) CGF_PREP_COL(5) CGF_PREP_COL(6) CGF_PREP_COL(7) CGF_PREP_COL(8)
   CGF_PREP_COL(9) CGF_PREP_COL(10) CGF_PREP_COL(11) CGF_PREP_COL(12) CGF_PREP_COL(13)
 #undef CGF_PREP_COL

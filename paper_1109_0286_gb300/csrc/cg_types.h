@@ -193,6 +193,8 @@ struct ColArgs {
   int table;        // 0: 1/(nP), 1: sqrt(P)/n; j + 2: kernel table j; -1: forward only
   int check_done;
   int spec_sel;     // 0: spec, 1: spec2
+  int pre;          // 1: the input is spec, already column-transformed (table >= 0; the
+                    // forward FFT is skipped and the result goes to spec_sel's buffer)
 };
 
 // Band-binned spectral products for the band-power gradient.

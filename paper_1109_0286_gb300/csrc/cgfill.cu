@@ -272,9 +272,10 @@ cudaError_t row(const Ctx<T>& c, cudaStream_t s, int op, int sop, bool in_spec, 
 }
 
 template <typename T>
-cudaError_t col(const Ctx<T>& c, cudaStream_t s, int table, int skip, int spec_sel = 0) {
+cudaError_t col(const Ctx<T>& c, cudaStream_t s, int table, int skip, int spec_sel = 0,
+                int pre = 0) {
   ++*c.launches;
-  ColArgs a{c.ny, c.nx / 2 + 1, c.ffts, table, skip, spec_sel};
+  ColArgs a{c.ny, c.nx / 2 + 1, c.ffts, table, skip, spec_sel, pre};
   return Launch<T>::col(c.log_n, c.desc, c.ninst, a, c.tw, s);
 }
 
@@ -1231,8 +1232,14 @@ fill_status set_annuli_t(fill_plan* p, int nk, const double* r_in, const double*
     if (p->dalloc(&P.kt, size_t(nk) * ntab) != cudaSuccess) return FILL_ENOMEM;
     P.nk_cap = nk;
   }
+  const size_t nspec = 2 * ntab;
+  if (!P.spec2 && p->dalloc(&P.spec2, size_t(p->batch) * nspec) != cudaSuccess)
+    return FILL_ENOMEM;
   P.nk = nk;
-  for (int i = 0; i < p->batch; ++i) P.hdesc[i].kt = P.kt;
+  for (int i = 0; i < p->batch; ++i) {
+    P.hdesc[i].kt = P.kt;
+    P.hdesc[i].spec2 = P.spec2 + size_t(i) * nspec;
+  }
   fill_desc<T>(p, nullptr, 0, nullptr, nullptr, nullptr);
   CK(upload_desc<T>(p));
   CK(init_states<T>(p, 0.0));
@@ -1253,6 +1260,10 @@ fill_status set_annuli_t(fill_plan* p, int nk, const double* r_in, const double*
 
 // Multi-scale kernel Laplace solver (Sect. 6.3): every sweep averages the map
 // over each masked pixel's annulus (class map `cls`), all from the same map.
+// One forward transform per sweep (row pass, then the column pass in forward
+// mode, into spec); per annulus the column pass multiplies by its table and
+// inverts into spec2, from which the inverse row pass writes the pixels of
+// that class.
 template <typename T>
 fill_status laplace_ms_t(fill_plan* p, const void* d, long long d_stride, int iters,
                          const uint8_t* cls, void* out, fill_stats* stats) {
@@ -1271,10 +1282,11 @@ fill_status laplace_ms_t(fill_plan* p, const void* d, long long d_stride, int it
   const Ctx<T> c = ctx<T>(p);
   CK(vec<T>(c, p->s, VOP_W_FROM_D, SC_NONE, SKIP_NEVER));
   for (int k = 0; k < iters; ++k) {
+    CK(row<T>(c, p->s, OP_LOAD_W, SC_NONE, false, true, SKIP_NEVER));
+    CK(col<T>(c, p->s, -1, SKIP_NEVER));
     for (int j = 0; j < P.nk; ++j) {
-      CK(row<T>(c, p->s, OP_LOAD_W, SC_NONE, false, true, SKIP_NEVER));
-      CK(col<T>(c, p->s, 2 + j, SKIP_NEVER));
-      CK(row<T>(c, p->s, OP_KSEL, SC_NONE, true, false, SKIP_NEVER, 0, j));
+      CK(col<T>(c, p->s, 2 + j, SKIP_NEVER, 1, 1));
+      CK(row<T>(c, p->s, OP_KSEL, SC_NONE, true, false, SKIP_NEVER, 1, j));
     }
     CK(vec<T>(c, p->s, VOP_Y_TO_W_M, k == 0 ? SC_BB : SC_RES, SKIP_NEVER));
   }

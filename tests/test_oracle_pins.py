@@ -539,3 +539,23 @@ def test_laplace_ms_constant_data_is_a_fixed_point_and_sweeps_approach_harmonic(
                 lambda v: O.apply_S(O.apply_S(v, Pl, m), Pl, m), tol=1e-12, max_iter=20000)
     err = np.linalg.norm(x[m] - res.u[m]) / np.linalg.norm(res.u[m])
     assert err < 0.01, err
+
+
+def test_laplace_ms_one_sweep_is_the_annulus_mean_by_brute_force():
+    """One sweep from 0 on the mask: every masked pixel holds the plain mean
+    of the starting map over its class's annulus (periodic offsets)."""
+    _, obs = _small_case(40, 40, seed=9, band=14, discs=2, r=3.0)
+    radii = O.ms_radii(nk=4)
+    rng = np.random.default_rng(4)
+    d = rng.standard_normal((40, 40))
+    x = O.laplace_ms(obs, d, radii, 1)
+    cls = O.ms_classes(obs, radii)
+    start = np.where(obs == 1, d, 0.0)
+    for y in range(40):
+        for xx in range(40):
+            if obs[y, xx]:
+                assert x[y, xx] == d[y, xx]
+                continue
+            offs = O.annulus_offsets(*radii[cls[y, xx]])
+            want = sum(start[(y + dy) % 40, (xx + dx) % 40] for dy, dx in offs) / len(offs)
+            assert abs(x[y, xx] - want) < 1e-12, (y, xx)
