@@ -333,6 +333,50 @@ def laplace_ms_measurement():
     return out
 
 
+def act_measurement():
+    """The flat-sky season map of Sect. 3 (7000 x 600, ~400 point-source
+    holes, a mixed-radix grid), 4 maps per step, mixed precision refined to
+    1e-10, with and without the preconditioner (the paper ran plain CG and
+    reports 20 minutes per map on one processor, residual halving per
+    iteration): realizations/s by CUDA events over 3 steps after 2 warm-up
+    steps, iterations per map, the worst true residual, and the oracle timed
+    on one host core (draw + right-hand side, one CG iteration, scaled)."""
+    import numpy as np
+    import torch
+    import paper_1109_0286_gb300 as cg
+    from workloads import workload
+    P, obs, spec = workload("act7000x600")
+    ny, nx = obs.shape
+    B, tol = len(spec["seeds"]), spec["tol"]
+    out = {"grid": [ny, nx], "batch": B, "tol": tol, "mode": "mixed",
+           "masked_fraction": float((obs == 0).mean()),
+           "paper": "1200 s per map, plain CG, one processor (2011), residual x0.5 per iteration"}
+    d = None
+    for precond in (True, False):
+        plan = cg.Plan(P, obs, mode="mixed", batch=B, precond=precond)
+        if d is None:
+            d = plan.draw([spec["data_seed"]])[0].clone()   # data drawn from P(k)
+        for k in range(2):
+            plan.realize(d, [s + 10 * k for s in spec["seeds"]], tol)
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        iters, worst = 0, 0.0
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for k in range(3):
+            _, st = plan.realize(d, [s + 100 + 10 * k for s in spec["seeds"]], tol)
+            iters += sum(x["iters"] for x in st)
+            worst = max([worst] + [x["true_rel_resid"] for x in st])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        out["precond" if precond else "plain_cg"] = {
+            "realizations_per_s": B / (ms / 1e3), "ms_per_step": ms,
+            "iters_per_realization": iters / (3 * B), "worst_true_rel_resid": worst}
+        plan.close()
+    return out, P, obs, d, spec
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -530,6 +574,7 @@ def run_gpu(args):
     strip_meas = strips_measurement() if (rank == 0 and not args.no_strips) else None
     far = far_interior_measurement() if (rank == 0 and not args.no_strips) else None
     lms = laplace_ms_measurement() if (rank == 0 and not args.no_strips) else None
+    act = act_measurement() if (rank == 0 and not args.no_strips) else None
 
     # roofline of the hot-loop passes (CUDA events on the plan's stream)
     peaks, peak_src = measured_peaks()
@@ -591,6 +636,16 @@ def run_gpu(args):
                "sample": (f"NumPy FP64 oracle on the full {ny}x{nx} workload: draw + RHS "
                           f"({setup:.1f} s) and 1 preconditioned CG iteration ({t_iter:.1f} s), "
                           f"scaled to {n_it:.0f} iterations per realization")}
+        if act is not None:   # the same oracle sample on the Sect. 3 map
+            a_out, aP, aobs, ad, aspec = act
+            setup, t_iter = oracle_sample(aP, aobs, ad.cpu().numpy().astype("float64"),
+                                          aspec["seeds"][0], 1)
+            n_it = a_out["precond"]["iters_per_realization"]
+            a_out["precond"]["cpu_baseline"] = {
+                "value": 1.0 / (setup + n_it * t_iter), "unit": UNIT, "cores": threads_used(),
+                "kind": "oracle",
+                "sample": (f"draw + RHS ({setup:.1f} s) and 1 preconditioned CG iteration "
+                           f"({t_iter:.2f} s), scaled to {n_it:.0f} iterations")}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -610,6 +665,7 @@ def run_gpu(args):
                 "gpu_launches": launches, "e2e": e2e, "roofline": roofline,
                 "passes": pass_table, "lanczos": lanczos, "relax": relax, "strips": strip_meas,
                 "far_interior": far, "laplace_ms": lms,
+                "act7000x600": act[0] if act is not None else None,
                 "clocks": clk.summary(),
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)

@@ -18,8 +18,12 @@
  *   preconditioned form with B = S S, which exposes the true residual).
  *
  * Conventions shared by every entry point:
- *   - Grid ny x nx, row-major, periodic; nx and ny powers of two with
- *     32 <= nx <= 8192 and 16 <= ny <= 8192.
+ *   - Grid ny x nx, row-major, periodic; either nx and ny powers of two
+ *     with 32 <= nx <= 8192 and 16 <= ny <= 8192 (register-resident FFT
+ *     passes), or a mixed-radix grid: nx even, nx/2 and ny products of
+ *     2, 3, 5 and 7 with 8 <= nx/2 <= 4096 and 8 <= ny <= 4096 (shared-memory
+ *     Stockham passes of radix 2, 3, 4, 5, 7; the flat-sky workloads of
+ *     Sect. 3 such as 7000 x 600 = 2^3 5^3 7 x 2^3 3 5^2).
  *   - DFT: F x(k) = sum_r x(r) exp(-i k.r), F^-1 carries 1/n, n = ny*nx,
  *     k = 2 pi m / N with m in [-N/2, N/2).
  *   - P_half: host, float64, ny x (nx/2+1) row-major (the half plane of a
@@ -298,6 +302,7 @@ fill_status fill_backward(fill_plan* plan, const void* d, long long d_stride,
  * the row passes, column FFTs per CTA of the column pass) by timing every
  * valid candidate on the device; results are cached as text lines in
  * cache_path (NULL: no cache).  Call after fill_init, before fill_realize.
+ * Mixed-radix grids keep their fixed schedule (returns FILL_OK at once).
  * Errors: FILL_EINVAL, FILL_ECUDA.
  */
 fill_status fill_autotune(fill_plan* plan, const char* cache_path);
@@ -305,7 +310,8 @@ fill_status fill_autotune(fill_plan* plan, const char* cache_path);
 /*
  * Groups: many realizations over masks and grid sizes in one call.
  * fill_group_init collects plans (all FILL_MODE_FP32 or all FILL_MODE_FP64,
- * same precond and stream; each keeps its own mask, spectrum and buffers).
+ * same precond and stream, power-of-two grids; each keeps its own mask,
+ * spectrum and buffers).
  * Plans with the same grid form a size class whose instances share every pass
  * launch; the classes run concurrently as parallel branches of one captured
  * CUDA graph per chunk of CG iterations.  autotune != 0 tunes each class's

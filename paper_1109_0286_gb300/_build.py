@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "_lib")
 LIBNAME = "libcgfill.so"
 SOURCES = ["cg_launch_f32.cu", "cg_launch_f64.cu", "cg_launch_df.cu", "cgfill.cu", "cg_static.cu",
-           "cg_subdivide.cu"]
+           "cg_subdivide.cu", "cg_generic.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

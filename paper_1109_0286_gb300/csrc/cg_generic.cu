@@ -1,0 +1,31 @@
+// Instantiations of the mixed-radix pass kernels (FP32, FP64, double-float)
+// and the host-side factorisation of a transform length.
+#include "cg_generic.cuh"
+
+namespace cgf {
+
+bool gen_factor(int n, GenLen* g) {
+  if (n < 2 || n > kGenMaxLen) return false;
+  int m = n, k = 0;
+  auto take = [&](int r) {
+    while (m % r == 0 && k < kGenMaxStages) {
+      g->radix[k++] = r;
+      m /= r;
+    }
+  };
+  take(4);
+  take(2);
+  take(3);
+  take(5);
+  take(7);
+  if (m != 1) return false;
+  g->n = n;
+  g->nst = k;
+  return true;
+}
+
+template struct GenLaunch<float>;
+template struct GenLaunch<double>;
+template struct GenLaunch<df>;
+
+}  // namespace cgf

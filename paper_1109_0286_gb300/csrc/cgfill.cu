@@ -20,6 +20,7 @@
 
 #include "../../include/cgfill.h"
 #include "cg_common.cuh"
+#include "cg_generic.h"
 #include "cg_launch.h"
 #include "cg_types.h"
 
@@ -90,6 +91,7 @@ struct Precision {
   double* coef = nullptr;       // CG coefficients, 2 history_cap per instance
   T* kt = nullptr;              // kernel tables of the Sect. 6.3 solver
   int nk = 0, nk_cap = 0;
+  T* gwl = nullptr; T* gwx = nullptr; T* gwn = nullptr;   // mixed-radix twiddles
   InstDesc<T>* desc = nullptr;  // device, batch
   InstDesc<T>* hdesc = nullptr; // pinned
   int rows = 0, ffts = 0;
@@ -103,6 +105,8 @@ struct Precision {
 
 struct fill_plan {
   int ny = 0, nx = 0, log_l = 0, log_n = 0, batch = 1;
+  bool gen = false;              // mixed-radix grid (cg_generic.h kernels)
+  cgf::GenLen grow{}, gcol{};    // its row (nx/2) and column (ny) transforms
   long long npix = 0, nmasked = 0;
   fill_opts o{};
   cudaStream_t s = nullptr;      // caller's stream
@@ -254,13 +258,26 @@ struct Ctx {
   const InstDesc<T>* desc;
   const T* tw;
   long long* launches;
+  const GenLen* grow = nullptr;   // mixed-radix grids: transforms and twiddles
+  const GenLen* gcol = nullptr;
+  const T* gwl = nullptr;
+  const T* gwx = nullptr;
+  const T* gwn = nullptr;
 };
 
 template <typename T>
 Ctx<T> ctx(fill_plan* p, int ninst = -1) {
   Precision<T>& P = prec<T>(p);
-  return Ctx<T>{p->ny, p->nx, p->log_l, p->log_n, P.rows, P.ffts,
-                ninst < 0 ? p->batch : ninst, p->o.precond, p->npix, P.desc, P.tw, &p->launches};
+  Ctx<T> c{p->ny, p->nx, p->log_l, p->log_n, P.rows, P.ffts,
+           ninst < 0 ? p->batch : ninst, p->o.precond, p->npix, P.desc, P.tw, &p->launches};
+  if (p->gen) {
+    c.grow = &p->grow;
+    c.gcol = &p->gcol;
+    c.gwl = P.gwl;
+    c.gwx = P.gwx;
+    c.gwn = P.gwn;
+  }
+  return c;
 }
 
 template <typename T>
@@ -268,6 +285,8 @@ cudaError_t row(const Ctx<T>& c, cudaStream_t s, int op, int sop, bool in_spec, 
                 int skip, int spec_sel = 0, int param = 0) {
   ++*c.launches;
   RowArgs a{c.ny, c.nx, c.rows, ilog2(c.rows), op, sop, skip, spec_sel, param};
+  if (c.grow)
+    return GenLaunch<T>::row(in_spec, out_spec, c.desc, c.ninst, a, *c.grow, c.gwl, c.gwx, s);
   return Launch<T>::row(c.log_l, in_spec, out_spec, c.desc, c.ninst, a, c.tw, s);
 }
 
@@ -276,6 +295,7 @@ cudaError_t col(const Ctx<T>& c, cudaStream_t s, int table, int skip, int spec_s
                 int pre = 0) {
   ++*c.launches;
   ColArgs a{c.ny, c.nx / 2 + 1, c.ffts, table, skip, spec_sel, pre};
+  if (c.gcol) return GenLaunch<T>::col(c.desc, c.ninst, a, *c.gcol, c.gwn, s);
   return Launch<T>::col(c.log_n, c.desc, c.ninst, a, c.tw, s);
 }
 
@@ -822,6 +842,83 @@ cudaError_t upload_desc(fill_plan* p) {
                          p->s);
 }
 
+// W_n^t = exp(-2 pi i t / n), t < count, from angles reduced to [0, pi/4]
+// (octant symmetry), so every entry carries the FP64 cos / sin accuracy.
+void twiddles_len(int n, int count, std::vector<double>& w) {
+  w.resize(2 * size_t(count));
+  for (int t = 0; t < count; ++t) {
+    // 8 t / n = o + f: angle 2 pi t / n = (pi/4) (o + f)
+    const long long m = (long long)8 * (t % n);
+    const int o = (int)(m / n);
+    const double f = double(m % n) / double(n);
+    double c, sn;   // cos, sin of the angle
+    const double th = (o & 1) ? (1.0 - f) * M_PI / 4.0 : f * M_PI / 4.0;
+    const double c0 = std::cos(th), s0 = std::sin(th);
+    switch (o) {
+      case 0: c = c0; sn = s0; break;
+      case 1: c = s0; sn = c0; break;
+      case 2: c = -s0; sn = c0; break;
+      case 3: c = -c0; sn = s0; break;
+      case 4: c = -c0; sn = -s0; break;
+      case 5: c = -s0; sn = -c0; break;
+      case 6: c = s0; sn = -c0; break;
+      default: c = c0; sn = -s0; break;
+    }
+    w[2 * size_t(t)] = c;
+    w[2 * size_t(t) + 1] = -sn;
+  }
+}
+
+// Mixed-radix schedule and twiddle tables of one precision: rows per CTA
+// (4, 2 or 1, dividing ny, within the thread and shared-memory limits) and
+// column FFTs per CTA, unless the options fix them.
+template <typename T>
+fill_status setup_generic(fill_plan* p) {
+  Precision<T>& P = prec<T>(p);
+  const int L = p->nx / 2, ny = p->ny, maxt = GenLaunch<T>::max_threads();
+  const size_t smax = 200 * 1024;
+  auto row_ok = [&](int r) {
+    return r >= 1 && ny % r == 0 && r * p->grow.nt <= maxt && ny / r <= kMaxPartials &&
+           GenLaunch<T>::row_smem(L, r) <= smax;
+  };
+  auto col_ok = [&](int f) {
+    return f >= 1 && f * p->gcol.nt <= maxt && GenLaunch<T>::col_smem(ny, f) <= smax;
+  };
+  if (p->o.rows_per_cta > 0) {
+    P.rows = p->o.rows_per_cta;
+  } else {
+    P.rows = 1;
+    for (int r : {4, 2})
+      if (row_ok(r)) {
+        P.rows = r;
+        break;
+      }
+  }
+  if (p->o.ffts_per_cta > 0) {
+    P.ffts = p->o.ffts_per_cta;
+  } else {
+    P.ffts = 1;
+    while (col_ok(2 * P.ffts) && 2 * P.ffts * p->gcol.nt <= 512 && 2 * P.ffts <= 16) P.ffts *= 2;
+  }
+  if (!row_ok(P.rows) || !col_ok(P.ffts)) return FILL_EINVAL;
+  std::vector<double> wl, wx, wn;
+  twiddles_len(L, L, wl);
+  twiddles_len(p->nx, L + 1, wx);
+  twiddles_len(ny, ny, wn);
+  auto upload = [&](T** dst, const std::vector<double>& src) -> cudaError_t {
+    std::vector<T> h(src.size());
+    for (size_t i = 0; i < src.size(); ++i) h[i] = (T)src[i];
+    cudaError_t e = p->dalloc(dst, h.size());
+    if (e == cudaSuccess) e = cudaMemcpy(*dst, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+  };
+  CK(upload(&P.gwl, wl));
+  CK(upload(&P.gwx, wx));
+  CK(upload(&P.gwn, wn));
+  CK(GenLaunch<T>::prepare());
+  return FILL_OK;
+}
+
 template <typename T>
 fill_status setup_precision(fill_plan* p, const std::vector<double>& tinv,
                             const std::vector<double>& tsqrt, const std::vector<double>& tw) {
@@ -866,14 +963,20 @@ fill_status setup_precision(fill_plan* p, const std::vector<double>& tinv,
   CK(cudaMemcpy(P.tw, w.data(), w.size() * sizeof(T), cudaMemcpyHostToDevice));
   CK(cudaMemset(P.u, 0, B * nv * sizeof(T)));
   CK(cudaMemset(P.p, 0, B * nv * sizeof(T)));
-  P.rows = p->o.rows_per_cta > 0 ? std::min(p->o.rows_per_cta, p->ny) : default_rows<T>(p->log_l, p->ny);
-  P.ffts = p->o.ffts_per_cta > 0 ? p->o.ffts_per_cta : default_ffts<T>(p->log_n, p->nx / 2 + 1);
-  const int TT = (1 << p->log_l) / 16;
-  if (P.rows * TT > Launch<T>::max_threads() || p->ny % P.rows != 0 ||
-      p->ny / P.rows > kMaxPartials || Launch<T>::row_smem(p->log_l, P.rows) > 227 * 1024 ||
-      P.ffts * ((1 << p->log_n) / 16) > Launch<T>::max_threads() ||
-      Launch<T>::col_smem(p->log_n, P.ffts) > 227 * 1024)
-    return FILL_EINVAL;
+  if (p->gen) {
+    fill_status gs = setup_generic<T>(p);
+    if (gs != FILL_OK) return gs;
+  } else {
+    P.rows = p->o.rows_per_cta > 0 ? std::min(p->o.rows_per_cta, p->ny)
+                                   : default_rows<T>(p->log_l, p->ny);
+    P.ffts = p->o.ffts_per_cta > 0 ? p->o.ffts_per_cta : default_ffts<T>(p->log_n, p->nx / 2 + 1);
+    const int TT = (1 << p->log_l) / 16;
+    if (P.rows * TT > Launch<T>::max_threads() || p->ny % P.rows != 0 ||
+        p->ny / P.rows > kMaxPartials || Launch<T>::row_smem(p->log_l, P.rows) > 227 * 1024 ||
+        P.ffts * ((1 << p->log_n) / 16) > Launch<T>::max_threads() ||
+        Launch<T>::col_smem(p->log_n, P.ffts) > 227 * 1024)
+      return FILL_EINVAL;
+  }
   CK(Launch<T>::prepare());
   for (size_t i = 0; i < B; ++i) {
     InstDesc<T> D{};
@@ -959,7 +1062,15 @@ fill_status fill_init(fill_plan** out, int ny, int nx, const double* P_half,
                       const uint8_t* observed, const fill_opts* opts, void* stream) {
   if (!out || !P_half || !observed) return FILL_EINVAL;
   *out = nullptr;
-  if (!pow2(nx) || !pow2(ny) || nx < 32 || nx > 8192 || ny < 16 || ny > 8192) return FILL_EINVAL;
+  const bool po2 = pow2(nx) && pow2(ny) && nx >= 32 && nx <= 8192 && ny >= 16 && ny <= 8192;
+  cgf::GenLen grow{}, gcol{};
+  if (!po2) {
+    // mixed-radix grid: nx/2 and ny products of 2, 3, 5, 7, at most 4096
+    if (nx % 2 != 0 || nx < 16 || ny < 8 || !gen_factor(nx / 2, &grow) || !gen_factor(ny, &gcol))
+      return FILL_EINVAL;
+    // threads per transform: about 8 values each (a multiple of 32, at most 512)
+    for (cgf::GenLen* g : {&grow, &gcol}) g->nt = std::min(512, (g->n / 8 + 31) / 32 * 32);
+  }
   fill_opts o;
   if (opts)
     o = *opts;
@@ -998,8 +1109,11 @@ fill_status fill_init(fill_plan** out, int ny, int nx, const double* P_half,
   if (!p) return FILL_ENOMEM;
   p->ny = ny;
   p->nx = nx;
-  p->log_l = ilog2(nx / 2);
-  p->log_n = ilog2(ny);
+  p->gen = !po2;
+  p->grow = grow;
+  p->gcol = gcol;
+  p->log_l = po2 ? ilog2(nx / 2) : -1;
+  p->log_n = po2 ? ilog2(ny) : -1;
   p->batch = o.batch;
   p->npix = npix;
   p->nmasked = nmasked;
@@ -1995,6 +2109,7 @@ extern "C" {
 
 fill_status fill_autotune(fill_plan* p, const char* cache_path) {
   if (!p) return FILL_EINVAL;
+  if (p->gen) return FILL_OK;   // mixed-radix grids keep their fixed schedule
   fill_status fs = tune_plan_t<float>(p, cache_path);
   if (fs == FILL_OK) fs = tune_plan_t<double>(p, cache_path);
   if (fs == FILL_OK) fs = tune_plan_t<df>(p, cache_path);
@@ -2022,7 +2137,7 @@ fill_status fill_group_init(fill_group** out, fill_plan* const* plans, int count
   int flat = 0;
   for (int i = 0; i < count; ++i) {
     fill_plan* p = plans[i];
-    if (!p || p->o.mode != mode || p->o.precond != g->precond || p->s != g->s)
+    if (!p || p->gen || p->o.mode != mode || p->o.precond != g->precond || p->s != g->s)
       return fail(FILL_EINVAL);
     g->plans.push_back(p);
     g->first.push_back(flat);

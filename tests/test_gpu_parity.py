@@ -392,8 +392,8 @@ def test_invalid_inputs_rejected():
     bad[1, 0] *= 1.01
     with pytest.raises(cg.FillError):
         cg.Plan(bad, obs)
-    with pytest.raises(cg.FillError):
-        cg.Plan(synth.spectrum_cmb_like(48, 48, 0.1), np.ones((48, 48), np.uint8))
+    with pytest.raises(cg.FillError):   # nx / 2 = 22 = 2 x 11: no supported transform
+        cg.Plan(synth.spectrum_cmb_like(48, 44, 0.1), np.ones((48, 44), np.uint8))
     obs2 = obs.copy()
     obs2[0, 0] = 2
     with pytest.raises(cg.FillError):

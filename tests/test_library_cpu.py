@@ -10,7 +10,7 @@ import pytest
 
 import paper_1109_0286_gb300 as cg
 from paper_1109_0286_gb300 import _build
-from workloads import synth, WORKLOADS
+from workloads import synth, workload, WORKLOADS
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -44,11 +44,12 @@ def test_host_only_calls(lib):
     assert cg.fill_version() == 1
     assert cg.fill_strerror(0) == "ok"
     assert "converged" in cg.fill_strerror(3)
-    # argument validation happens before any device work
+    # argument validation happens before any device work (nx / 2 = 22 = 2 x 11:
+    # neither a power of two nor a product of 2, 3, 5, 7)
     plan = ctypes.c_void_p()
     P = np.ones((64, 33))
     m = np.ones((64, 64), np.uint8)
-    st = lib.fill_init(ctypes.byref(plan), 64, 48, P.ctypes.data, m.ctypes.data,
+    st = lib.fill_init(ctypes.byref(plan), 64, 44, P.ctypes.data, m.ctypes.data,
                        ctypes.byref(o), None)
     assert st == 1 and not plan.value
     assert lib.fill_realize(None, None, 0, None, 1e-6, None, None) == 1
@@ -89,6 +90,12 @@ def test_spectra_hermitian_and_positive():
 
 
 def test_workload_table():
-    assert set(WORKLOADS) == {"plain64", "patch1024", "batch_mixed", "grad2048", "wide4096"}
+    assert set(WORKLOADS) == {"plain64", "patch1024", "batch_mixed", "grad2048", "wide4096",
+                              "act7000x600"}
     sizes = WORKLOADS["batch_mixed"]["sizes"]
     assert sum(c for _, c in sizes) == 256
+    # the Sect. 3 season map: 7000 x 600, ~400 holes of 0.01 deg^2 (~141 pixels
+    # of 0.5 arcmin); nx/2 = 3500 = 2^2 5^3 7, ny = 600 = 2^3 3 5^2
+    _, obs, spec = workload("act7000x600")
+    assert obs.shape == (600, 7000) and spec["ndiscs"] == 400
+    assert 0.8 * 400 * 141 <= int((obs == 0).sum()) <= 400 * 141 * 1.05

@@ -191,6 +191,15 @@ WORKLOADS = {
                      band_frac=0.15, ndiscs=500, rmin=2.0, rmax=12.0,
                      mask_seed=14, data_seed=6, seeds=[7], tol=1e-6,
                      nbands=32, precision="fp32"),
+    # The flat-sky season map of Sect. 3: 7000 x 600 pixels (about 0.5 arcmin,
+    # 300 square degrees) with about 400 point-source holes of 0.01 square
+    # degrees (radius about 6.7 pixels) and no band; a mixed-radix grid
+    # (nx/2 = 3500 = 2^2 5^3 7, ny = 600 = 2^3 3 5^2).  Batch of 4 (the
+    # four simulated maps), mixed precision refined to 1e-10.
+    "act7000x600": dict(ny=600, nx=7000, spectrum="cmb", k_lo_n=4096,
+                        band_frac=0.0, ndiscs=400, rmin=6.7, rmax=6.7,
+                        mask_seed=16, data_seed=9, seeds=list(range(200, 204)),
+                        tol=1e-10, precision="mixed"),
     # 4096^2 wide cut, batch of 8, refined to a relative residual of 1e-10.
     "wide4096": dict(ny=4096, nx=4096, spectrum="cmb", k_lo_n=4096,
                      band_frac=0.20, ndiscs=2000, rmin=2.0, rmax=20.0,
