@@ -373,6 +373,15 @@ def act_measurement():
         out["precond" if precond else "plain_cg"] = {
             "realizations_per_s": B / (ms / 1e3), "ms_per_step": ms,
             "iters_per_realization": iters / (3 * B), "worst_true_rel_resid": worst}
+        if precond:   # the mixed-radix passes (FP32), CUDA events on the plan's stream
+            out["passes"] = {}
+            for pid, name in enumerate(("k_col_gen", "k_row_gen src (r, u update + R2C)",
+                                        "k_row_gen src (p update + R2C)",
+                                        "k_row_gen sink (C2R + q = P_x, p^T q)",
+                                        "k_row_gen mid (C2R, P_x, R2C)")):
+                pms, pbytes = plan.time_pass(pid, reps=10)
+                out["passes"][name] = {"ms": round(pms, 4),
+                                       "GB/s": round(pbytes / pms / 1e6, 1)}
         plan.close()
     return out, P, obs, d, spec
 
