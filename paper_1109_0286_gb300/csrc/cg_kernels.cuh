@@ -286,6 +286,11 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
   // Nyquist row k = L to threads 0..rows-1
   const int rr = threadIdx.x & (rows - 1), kk = threadIdx.x >> lr;
   const size_t tstep = 2 * (size_t)TT * ny;
+  // From L = 512 on, TT is a multiple of 2^max(lr, 4) (rows * TT <= 1024), so
+  // adding multiples of TT to k leaves the swizzle bits g(k) unchanged: a
+  // thread's tile indices for k0 + i TT are one base plus i (TT rows).
+  constexpr bool HOIST = LOG_L >= 9;
+  const int ts = TT << lr;
   const XBar cta{0, 0}, rbar = XBar::make(TT, rows, row);   // CTA / this row's barrier
   cx<T> v[16];
   Acc<T> acc;
@@ -300,17 +305,19 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
     cx<T> tn{};
     if (threadIdx.x < rows)
       tn = ldg_cx<T>((a.spec_sel ? I.spec2 : I.spec) + 2 * ((size_t)L * ny + y0 + threadIdx.x));
+    const int tb = tix(kk, rr);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) tile[tix(kk + i * TT, rr)] = t[i];
+    for (int i = 0; i < 16; ++i) tile[HOIST ? tb + i * ts : tix(kk + i * TT, rr)] = t[i];
     if (threadIdx.x < rows) tile[tix(L, threadIdx.x)] = tn;
     __syncthreads();
     // C2R: Z[k] = (X[k] + conj X[L-k]) + i e^{+2 pi i k / nx} (X[k] - conj X[L-k])
     const cx<T> wt = twiddle<T>(tw, tid * TWS);
+    const int cb = tix(tid, row), cm = tix(L - tid, row);
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       const int k = tid + e * TT;
-      cx<T> xk = tile[tix(k, row)];
-      cx<T> xc = conjx(tile[tix(L - k, row)]);
+      cx<T> xk = tile[HOIST ? cb + e * ts : tix(k, row)];
+      cx<T> xc = conjx(tile[HOIST ? cm - e * ts : tix(L - k, row)]);
       if (k == 0) {
         xk.i = (T)0;
         xc.i = (T)0;
@@ -388,16 +395,19 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
     // the global stores form X from Z[k] and Z[L-k]:
     // R2C: X[k] = (Z[k] + conj Z[L-k]) / 2 - (i/2) e^{-2 pi i k/nx} (Z[k] - conj Z[L-k])
     __syncthreads();   // the tile overwrites other rows' exchange areas
+    const int cb = tix(tid, row);
 #pragma unroll
-    for (int e = 0; e < 16; ++e) tile[tix(tid + e * TT, row)] = v[e];
+    for (int e = 0; e < 16; ++e) tile[HOIST ? cb + e * ts : tix(tid + e * TT, row)] = v[e];
     __syncthreads();
     const cx<T> wt = twiddle<T>(tw, kk * TWS);
     T* spec = (a.spec_sel ? I.spec2 : I.spec) + 2 * ((size_t)kk * ny + y0 + rr);
+    const int tb = tix(kk, rr), tm = tix(L - kk, rr);   // L - kk: the Nyquist row when kk = 0
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
       const int k = kk + i * TT;
-      const cx<T> zk = tile[tix(k, rr)];
-      const cx<T> zc = conjx(tile[tix((L - k) & (L - 1), rr)]);
+      const cx<T> zk = tile[HOIST ? tb + i * ts : tix(k, rr)];
+      const int im = (i == 0 && kk == 0) ? tix(0, rr) : tm - i * ts;
+      const cx<T> zc = conjx(tile[HOIST ? im : tix((L - k) & (L - 1), rr)]);
       const cx<T> ev = scal(zk + zc, (T)0.5);
       const cx<T> od = scal(mul_mi<T, false>(zk - zc), (T)0.5);
       st_cx<T>(spec + i * tstep, ev + cmul(od, cmul(wt, w32<T>(i))));
