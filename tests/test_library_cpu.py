@@ -52,6 +52,13 @@ def test_host_only_calls(lib):
     st = lib.fill_init(ctypes.byref(plan), 64, 44, P.ctypes.data, m.ctypes.data,
                        ctypes.byref(o), None)
     assert st == 1 and not plan.value
+    # sizes neither power-of-two nor mixed-radix-valid: odd nx, a prime factor
+    # above 7, nx/2 or ny above 4096, ny below 8
+    big, mbig = np.ones(400_000), np.ones(700_000, np.uint8)   # cover ny * nx of every case
+    for ny, nx in ((60, 85), (66, 84), (60, 86), (8200, 84), (60, 8400), (6, 84), (4, 64)):
+        st = lib.fill_init(ctypes.byref(plan), ny, nx, big.ctypes.data, mbig.ctypes.data,
+                           ctypes.byref(o), None)
+        assert st == 1 and not plan.value, (ny, nx)
     assert lib.fill_realize(None, None, 0, None, 1e-6, None, None) == 1
     lib.fill_destroy(None)
 

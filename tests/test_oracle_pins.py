@@ -64,16 +64,19 @@ def test_white_noise_moments():
 
 # ----------------------------------------------------------------- transforms
 
-def test_fft_matches_direct_dft():
+@pytest.mark.parametrize("ny,nx", [(8, 16), (15, 14), (21, 10)])
+def test_fft_matches_direct_dft(ny, nx):
+    """Power-of-two and mixed-radix (3, 5, 7) grids."""
     rng = np.random.default_rng(0)
-    x = rng.standard_normal((8, 16))
+    x = rng.standard_normal((ny, nx))
     assert np.allclose(np.fft.fft2(x), O.dft2_direct(x), rtol=0, atol=1e-12)
 
 
-def test_apply_power_is_dense_circulant():
+@pytest.mark.parametrize("ny,nx", [(8, 16), (15, 14), (12, 20)])
+def test_apply_power_is_dense_circulant(ny, nx):
     """C x through the FFT equals the dense circulant matrix built from the
-    definition c(D) = (1/n) sum_k P(k) cos(k.D) (no FFT involved)."""
-    ny, nx = 8, 16
+    definition c(D) = (1/n) sum_k P(k) cos(k.D) (no FFT involved); odd and
+    mixed-radix grids included."""
     P = synth.spectrum_lorentz_beam(ny, nx, k0=1.0, sb=0.5)
     Pf = O.hermitian_full(P, nx)
     x = np.random.default_rng(1).standard_normal((ny, nx))
@@ -146,11 +149,14 @@ def test_dense_ml_two_forms_agree(n):
     assert np.linalg.norm(a - b) <= 1e-9 * np.linalg.norm(a)
 
 
-@pytest.mark.parametrize("n,precond", [(16, True), (32, True), (32, False)])
+@pytest.mark.parametrize("n,precond", [(16, True), (32, True), (32, False), ((15, 28), True),
+                                       ((24, 20), False)])
 def test_realization_matches_dense_solve(n, precond):
-    """x_M = y_M + C_MU C_UU^-1 (d - y)_U by Cholesky, vs the PCG pipeline."""
-    P, obs = _small_case(n, n, seed=n + 1)
-    Pf = O.hermitian_full(P, n)
+    """x_M = y_M + C_MU C_UU^-1 (d - y)_U by Cholesky, vs the PCG pipeline
+    (square power-of-two grids, and mixed-radix ones with odd ny)."""
+    ny, nx = n if isinstance(n, tuple) else (n, n)
+    P, obs = _small_case(ny, nx, seed=ny + nx + 1)
+    Pf = O.hermitian_full(P, nx)
     d = O.draw(Pf, 99)
     r = O.realize(P, obs, d, seed=5, tol=1e-13, precond=precond)
     m = obs.ravel() == 0
