@@ -45,12 +45,12 @@ FP64_ITERS_WIDE4096 = 200
 # shared part (column table, mask words) read once per launch.  A launch over
 # B instances is scaled as B * per-instance + shared.  Reported only while the
 # pass-kernel sources hash to the profiled version; otherwise traffic is null.
-TRAFFIC = {"src_hash": "7a0a90ed1a6a0caf",
+TRAFFIC = {"src_hash": "7262950242584565",
            "k_col (column FFT, x 1/(nP), inverse FFT)": (107.12, 33.57),
-           "k_row src (r, u update + R2C)": (140.81, 4.19),
-           "k_row src (p update + R2C)": (90.56, 4.19),
-           "k_row sink (C2R + q = P_x, p^T q)": (95.71, 4.19),
-           "k_row mid (C2R, P_x, R2C)": (108.21, 4.19)}
+           "k_row src (r, u update + R2C)": (140.76, 4.19),
+           "k_row src (p update + R2C)": (90.61, 4.19),
+           "k_row sink (C2R + q = P_x, p^T q)": (95.66, 4.19),
+           "k_row mid (C2R, P_x, R2C)": (108.26, 4.19)}
 KERNEL_SOURCES = ["cg_types.h", "cg_common.cuh", "cg_fft.cuh", "cg_kernels.cuh", "cg_launch.cuh"]
 
 
