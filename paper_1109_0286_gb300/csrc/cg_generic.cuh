@@ -14,10 +14,15 @@ __device__ __forceinline__ cx<T> tw_at(const T* w, int t) {
   return ldg_cx<T>(w + 2 * t);
 }
 
-// In-register DFT of R points, y_q = sum_m v_m W_R^{qm}, W_R^s = W_n^{s n/R}
-// from the length-n table (forward sign).
+// In-register DFT of R points, y_q = sum_m v_m W_R^{qm} (forward sign).  For
+// odd R the terms m and R - m pair up: with S_m = v_m + v_{R-m},
+// D_m = v_m - v_{R-m} (m = 1..H, H = (R-1)/2) and theta = 2 pi q m / R,
+//   y_q = v_0 + sum_m cos(theta) S_m - i sum_m sin(theta) D_m,
+//   y_{R-q} = the same with +i,
+// so each half-pair costs real-by-complex products only.  cs[j] = W_R^j
+// (j = 1..H) = (cos 2 pi j/R, -sin 2 pi j/R).
 template <typename T, int R>
-__device__ __forceinline__ void dft(cx<T> (&v)[R], const T* w, int n) {
+__device__ __forceinline__ void dft(cx<T> (&v)[R], const cx<T>* cs) {
   if constexpr (R == 2) {
     const cx<T> a = v[0], b = v[1];
     v[0] = a + b;
@@ -30,14 +35,29 @@ __device__ __forceinline__ void dft(cx<T> (&v)[R], const T* w, int n) {
     v[1] = d02 + d13;
     v[3] = d02 - d13;
   } else {
-    const int nr = n / R;
+    constexpr int H = (R - 1) / 2;
+    cx<T> S[H + 1], D[H + 1];
+    cx<T> y0 = v[0];
+#pragma unroll
+    for (int m = 1; m <= H; ++m) {
+      S[m] = v[m] + v[R - m];
+      D[m] = v[m] - v[R - m];
+      y0 = y0 + S[m];
+    }
     cx<T> y[R];
+    y[0] = y0;
 #pragma unroll
-    for (int q = 0; q < R; ++q) {
-      cx<T> s = v[0];
+    for (int q = 1; q <= H; ++q) {
+      cx<T> a = v[0], b{(T)0, (T)0};
 #pragma unroll
-      for (int m = 1; m < R; ++m) s = s + cmul(v[m], tw_at(w, ((q * m) % R) * nr));
-      y[q] = s;
+      for (int m = 1; m <= H; ++m) {
+        const int j = (q * m) % R, jj = j <= H ? j : R - j;
+        const T c = cs[jj].r, sn = j <= H ? -cs[jj].i : cs[jj].i;   // cos, sin of 2 pi j / R
+        a = a + scal(S[m], c);
+        b = b + scal(D[m], sn);
+      }
+      y[q] = cx<T>{a.r + b.i, a.i - b.r};       // a - i b
+      y[R - q] = cx<T>{a.r - b.i, a.i + b.r};   // a + i b
     }
 #pragma unroll
     for (int q = 0; q < R; ++q) v[q] = y[q];
@@ -52,6 +72,11 @@ template <typename T, int R>
 __device__ __forceinline__ void stage(const cx<T>* in, cx<T>* out, int n, int ns, const T* w,
                                       int t, int nt, bool cin, bool cout) {
   const int nb = n / R, step = n / (ns * R);
+  cx<T> cs[R / 2 + 1];   // W_R^j, j = 1..(R-1)/2, for the odd radices
+  if constexpr (R % 2 == 1) {
+#pragma unroll
+    for (int j = 1; j <= R / 2; ++j) cs[j] = tw_at(w, j * nb);
+  }
   for (int b = t; b < nb; b += nt) {
     const int k = b % ns;
     cx<T> v[R];
@@ -64,7 +89,7 @@ __device__ __forceinline__ void stage(const cx<T>* in, cx<T>* out, int n, int ns
 #pragma unroll
       for (int m = 1; m < R; ++m) v[m] = cmul(v[m], tw_at(w, m * k * step));
     }
-    dft<T, R>(v, w, n);
+    dft<T, R>(v, cs);
     const int base = (b - k) * R + k;
 #pragma unroll
     for (int m = 0; m < R; ++m) out[base + m * ns] = cout ? conjx(v[m]) : v[m];
