@@ -77,8 +77,10 @@ __device__ __forceinline__ void stage(const cx<T>* in, cx<T>* out, int n, int ns
 #pragma unroll
     for (int j = 1; j <= R / 2; ++j) cs[j] = tw_at(w, j * nb);
   }
+  // b = j ns + k, stepped by nt without a division per butterfly
+  int j = t / ns, k = t - j * ns;
+  const int dj = nt / ns, dk = nt - dj * ns, nsr = ns * R;
   for (int b = t; b < nb; b += nt) {
-    const int k = b % ns;
     cx<T> v[R];
 #pragma unroll
     for (int m = 0; m < R; ++m) {
@@ -90,9 +92,15 @@ __device__ __forceinline__ void stage(const cx<T>* in, cx<T>* out, int n, int ns
       for (int m = 1; m < R; ++m) v[m] = cmul(v[m], tw_at(w, m * k * step));
     }
     dft<T, R>(v, cs);
-    const int base = (b - k) * R + k;
+    const int base = j * nsr + k;   // (b - k) R + k
 #pragma unroll
     for (int m = 0; m < R; ++m) out[base + m * ns] = cout ? conjx(v[m]) : v[m];
+    k += dk;
+    j += dj;
+    if (k >= ns) {
+      k -= ns;
+      ++j;
+    }
   }
 }
 
@@ -123,75 +131,97 @@ __device__ cx<T>* fft(cx<T>* a, cx<T>* b, const GenLen& g, const T* w, int t, bo
 }
 
 // ----------------------------------------------------------------- per-pair operations
+// Each row loop takes kGenChunk pixel pairs per thread at a time: their mask
+// words first, then every operand load, then the arithmetic and stores, so
+// the loads of a chunk are in flight together.
+constexpr int kGenChunk = 4;
+
+struct Opnd {   // one pixel pair: mask flags, compact indices, pixel index
+  PairIdx q;
+  int pix;
+  bool ok;
+};
+
 template <typename T, int OP>
-__device__ __forceinline__ cx<T> src(const InstDesc<T>& I, int pix, T alpha, T beta, Acc<T>& acc) {
-  T a0 = (T)0, a1 = (T)0;
-  if constexpr (OP == OP_LOAD_W || OP == OP_LOAD_Y) {
-    ld_pair((OP == OP_LOAD_Y ? I.y : I.w) + pix, a0, a1);
-  } else {
-    const PairIdx q = pair_index(I.mw, pix);
-    if constexpr (OP == OP_LOAD_W_MASK) {
-      T x0, x1;
-      ld_pair(I.w + pix, x0, x1);
-      a0 = q.m0 ? x0 : (T)0;
-      a1 = q.m1 ? x1 : (T)0;
-    } else if constexpr (OP == OP_LOAD_D_U) {
-      T x0, x1;
-      ld_map_pair<T>(I.d + pix, x0, x1);
-      a0 = q.m0 ? (T)0 : x0;
-      a1 = q.m1 ? (T)0 : x1;
-    } else if constexpr (OP == OP_LOAD_R || OP == OP_LOAD_U) {
-      ldc(OP == OP_LOAD_R ? I.r : I.u, q, a0, a1);
-      if constexpr (OP == OP_LOAD_R) {
-        acc.add_prod(a0, a0);
-        acc.add_prod(a1, a1);
-      }
-    } else if constexpr (OP == OP_P_UPD_Z || OP == OP_P_UPD_R) {
-      T x0, x1, y0, y1;
-      ldc(OP == OP_P_UPD_Z ? I.z : I.r, q, x0, x1);
-      ldc(I.p, q, y0, y1);
-      a0 = x0 + beta * y0;
-      a1 = x1 + beta * y1;
-      stc(I.p, q, a0, a1);
-    } else if constexpr (OP == OP_R_UPD) {
-      T x0, x1, y0, y1, z0, z1, w0, w1;
-      ldc(I.r, q, x0, x1);
-      ldc(I.q, q, y0, y1);
-      ldc(I.u, q, z0, z1);
-      ldc(I.p, q, w0, w1);
-      a0 = x0 - alpha * y0;
-      a1 = x1 - alpha * y1;
-      stc(I.r, q, a0, a1);
-      stc(I.u, q, z0 + alpha * w0, z1 + alpha * w1);
-      acc.add_prod(a0, a0);
-      acc.add_prod(a1, a1);
-    } else if constexpr (OP == OP_U64_UPD) {
-      T x0, x1, y0, y1;
-      ldc(I.u, q, x0, x1);
-      ldc(I.dlt, q, y0, y1);
-      a0 = x0 + y0;
-      a1 = x1 + y1;
-      stc(I.u, q, a0, a1);
-      stc(I.dlt, q, 0.f, 0.f);
-    }
+__device__ __forceinline__ void src_load(const InstDesc<T>& I, const Opnd& o, T (&x)[8]) {
+  if constexpr (OP == OP_LOAD_W || OP == OP_LOAD_Y || OP == OP_LOAD_W_MASK) {
+    ld_pair((OP == OP_LOAD_Y ? I.y : I.w) + o.pix, x[0], x[1]);
+  } else if constexpr (OP == OP_LOAD_D_U) {
+    ld_map_pair<T>(I.d + o.pix, x[0], x[1]);
+  } else if constexpr (OP == OP_LOAD_R || OP == OP_LOAD_U) {
+    ldc(OP == OP_LOAD_R ? I.r : I.u, o.q, x[0], x[1]);
+  } else if constexpr (OP == OP_P_UPD_Z || OP == OP_P_UPD_R) {
+    ldc(OP == OP_P_UPD_Z ? I.z : I.r, o.q, x[0], x[1]);
+    ldc(I.p, o.q, x[2], x[3]);
+  } else if constexpr (OP == OP_R_UPD) {
+    ldc(I.r, o.q, x[0], x[1]);
+    ldc(I.q, o.q, x[2], x[3]);
+    ldc(I.u, o.q, x[4], x[5]);
+    ldc(I.p, o.q, x[6], x[7]);
+  } else if constexpr (OP == OP_U64_UPD) {
+    ldc(I.u, o.q, x[0], x[1]);
+    ldc(I.dlt, o.q, x[2], x[3]);
+  }
+}
+
+template <typename T, int OP>
+__device__ __forceinline__ cx<T> src_op(const InstDesc<T>& I, const Opnd& o, const T (&x)[8],
+                                        T alpha, T beta, Acc<T>& acc) {
+  const PairIdx& q = o.q;
+  T a0 = x[0], a1 = x[1];
+  if constexpr (OP == OP_LOAD_W_MASK) {
+    a0 = q.m0 ? a0 : (T)0;
+    a1 = q.m1 ? a1 : (T)0;
+  } else if constexpr (OP == OP_LOAD_D_U) {
+    a0 = q.m0 ? (T)0 : a0;
+    a1 = q.m1 ? (T)0 : a1;
+  } else if constexpr (OP == OP_LOAD_R) {
+    acc.add_prod(a0, a0);
+    acc.add_prod(a1, a1);
+  } else if constexpr (OP == OP_P_UPD_Z || OP == OP_P_UPD_R) {
+    a0 = x[0] + beta * x[2];
+    a1 = x[1] + beta * x[3];
+    stc(I.p, q, a0, a1);
+  } else if constexpr (OP == OP_R_UPD) {
+    a0 = x[0] - alpha * x[2];
+    a1 = x[1] - alpha * x[3];
+    stc(I.r, q, a0, a1);
+    stc(I.u, q, x[4] + alpha * x[6], x[5] + alpha * x[7]);
+    acc.add_prod(a0, a0);
+    acc.add_prod(a1, a1);
+  } else if constexpr (OP == OP_U64_UPD) {
+    a0 = x[0] + x[2];
+    a1 = x[1] + x[3];
+    stc(I.u, q, a0, a1);
+    stc(I.dlt, q, 0.f, 0.f);
   }
   return cx<T>{a0, a1};
 }
 
 template <typename T, int OP>
-__device__ __forceinline__ void sink(const InstDesc<T>& I, int pix, cx<T> v, Acc<T>& acc,
-                                     int param) {
-  const PairIdx q = pair_index(I.mw, pix);
+__device__ __forceinline__ void sink_load(const InstDesc<T>& I, const Opnd& o, T (&x)[2]) {
+  if constexpr (OP == OP_Q || OP == OP_Z || OP == OP_RES) {
+    ldc(OP == OP_Q ? I.p : OP == OP_Z ? I.r : I.b, o.q, x[0], x[1]);
+  } else if constexpr (OP == OP_GRAD) {
+    ld_map_pair<T>(I.gx + o.pix, x[0], x[1]);
+  } else if constexpr (OP == OP_RELAX) {
+    ld_pair(I.w + o.pix, x[0], x[1]);
+  }
+}
+
+template <typename T, int OP>
+__device__ __forceinline__ void sink_op(const InstDesc<T>& I, const Opnd& o, const T (&x)[2],
+                                        cx<T> v, Acc<T>& acc, int param) {
+  const PairIdx& q = o.q;
+  const int pix = o.pix;
   const bool m0 = q.m0, m1 = q.m1;   // masked = not observed
   T a0 = v.r, a1 = v.i;
   if constexpr (OP == OP_Q || OP == OP_Z) {
-    T x0, x1;
-    ldc(OP == OP_Q ? I.p : I.r, q, x0, x1);
     a0 = m0 ? a0 : (T)0;
     a1 = m1 ? a1 : (T)0;
     stc(OP == OP_Q ? I.q : I.z, q, a0, a1);
-    acc.add_prod(x0, a0);
-    acc.add_prod(x1, a1);
+    acc.add_prod(x[0], a0);
+    acc.add_prod(x[1], a1);
   } else if constexpr (OP == OP_B) {
     a0 = m0 ? -a0 : (T)0;
     a1 = m1 ? -a1 : (T)0;
@@ -201,26 +231,20 @@ __device__ __forceinline__ void sink(const InstDesc<T>& I, int pix, cx<T> v, Acc
     acc.add_prod(a0, a0);
     acc.add_prod(a1, a1);
   } else if constexpr (OP == OP_RES) {
-    T x0, x1;
-    ldc(I.b, q, x0, x1);
-    a0 = x0 - (m0 ? a0 : (T)0);
-    a1 = x1 - (m1 ? a1 : (T)0);
+    a0 = x[0] - (m0 ? a0 : (T)0);
+    a1 = x[1] - (m1 ? a1 : (T)0);
     stc(I.r, q, a0, a1);
     if (I.r32) stc(I.r32, q, a0, a1);
     acc.add_prod(a0, a0);
     acc.add_prod(a1, a1);
   } else if constexpr (OP == OP_GRAD) {
-    T x0, x1;
-    ld_map_pair<T>(I.gx + pix, x0, x1);
-    st_map_pair<T>(I.out + pix, m0 ? (T)0 : x0 - a0, m1 ? (T)0 : x1 - a1);
-    st_pair(I.y + pix, m0 ? x0 : a0, m1 ? x1 : a1);
+    st_map_pair<T>(I.out + pix, m0 ? (T)0 : x[0] - a0, m1 ? (T)0 : x[1] - a1);
+    st_pair(I.y + pix, m0 ? x[0] : a0, m1 ? x[1] : a1);
   } else if constexpr (OP == OP_RELAX) {
-    T x0, x1;
-    ld_pair(I.w + pix, x0, x1);
     const T step = (T)I.st->alpha;
     a0 = m0 ? a0 : (T)0;
     a1 = m1 ? a1 : (T)0;
-    st_pair(I.w + pix, x0 - step * a0, x1 - step * a1);
+    st_pair(I.w + pix, x[0] - step * a0, x[1] - step * a1);
     acc.add_prod(a0, a0);
     acc.add_prod(a1, a1);
   } else if constexpr (OP == OP_KSEL) {
@@ -235,32 +259,75 @@ __device__ __forceinline__ void sink(const InstDesc<T>& I, int pix, cx<T> v, Acc
 }
 
 template <typename T, int OP>
-__device__ __forceinline__ cx<T> mid(const InstDesc<T>& I, int pix, cx<T> v) {
-  const PairIdx q = pair_index(I.mw, pix);
+__device__ __forceinline__ cx<T> mid_op(const InstDesc<T>& I, const Opnd& o, T d0, T d1, cx<T> v) {
   if constexpr (OP == OP_Y_W) {
-    T d0, d1;
-    ld_map_pair<T>(I.d + pix, d0, d1);
-    st_pair(I.y + pix, v.r, v.i);
-    return cx<T>{q.m0 ? (T)0 : d0 - v.r, q.m1 ? (T)0 : d1 - v.i};
+    st_pair(I.y + o.pix, v.r, v.i);
+    return cx<T>{o.q.m0 ? (T)0 : d0 - v.r, o.q.m1 ? (T)0 : d1 - v.i};
   } else {
-    return cx<T>{q.m0 ? v.r : (T)0, q.m1 ? v.i : (T)0};
+    return cx<T>{o.q.m0 ? v.r : (T)0, o.q.m1 ? v.i : (T)0};
+  }
+}
+
+// Operands of the chunk's pixel pairs j = j0 + u nt: mask words first.
+template <int OP_NEEDS_WORD>
+__device__ __forceinline__ void chunk_words(const uint2* mw, int rowpix, int j0, int nt, int L,
+                                            Opnd (&o)[kGenChunk]) {
+#pragma unroll
+  for (int u = 0; u < kGenChunk; ++u) {
+    const int j = j0 + u * nt;
+    o[u].ok = j < L;
+    o[u].pix = rowpix + 2 * (o[u].ok ? j : 0);
+    if (OP_NEEDS_WORD) o[u].q = pair_index(mw, o[u].pix);
   }
 }
 
 template <typename T, int OP>
 __device__ __forceinline__ void src_row(const InstDesc<T>& I, int rowpix, cx<T>* z, int L, int t,
                                         int nt, T alpha, T beta, Acc<T>& acc) {
-  for (int j = t; j < L; j += nt) z[j] = src<T, OP>(I, rowpix + 2 * j, alpha, beta, acc);
+  constexpr bool W = !(OP == OP_LOAD_W || OP == OP_LOAD_Y);
+  for (int j0 = t; j0 < L; j0 += kGenChunk * nt) {
+    Opnd o[kGenChunk];
+    chunk_words<W>(I.mw, rowpix, j0, nt, L, o);
+    T x[kGenChunk][8];
+#pragma unroll
+    for (int u = 0; u < kGenChunk; ++u)
+      if (o[u].ok) src_load<T, OP>(I, o[u], x[u]);
+#pragma unroll
+    for (int u = 0; u < kGenChunk; ++u)
+      if (o[u].ok) z[j0 + u * nt] = src_op<T, OP>(I, o[u], x[u], alpha, beta, acc);
+  }
 }
+
 template <typename T, int OP>
 __device__ __forceinline__ void sink_row(const InstDesc<T>& I, int rowpix, const cx<T>* z, int L,
                                          int t, int nt, Acc<T>& acc, int param) {
-  for (int j = t; j < L; j += nt) sink<T, OP>(I, rowpix + 2 * j, z[j], acc, param);
+  for (int j0 = t; j0 < L; j0 += kGenChunk * nt) {
+    Opnd o[kGenChunk];
+    chunk_words<1>(I.mw, rowpix, j0, nt, L, o);
+    T x[kGenChunk][2];
+#pragma unroll
+    for (int u = 0; u < kGenChunk; ++u)
+      if (o[u].ok) sink_load<T, OP>(I, o[u], x[u]);
+#pragma unroll
+    for (int u = 0; u < kGenChunk; ++u)
+      if (o[u].ok) sink_op<T, OP>(I, o[u], x[u], z[j0 + u * nt], acc, param);
+  }
 }
+
 template <typename T, int OP>
 __device__ __forceinline__ void mid_row(const InstDesc<T>& I, int rowpix, cx<T>* z, int L, int t,
                                         int nt) {
-  for (int j = t; j < L; j += nt) z[j] = mid<T, OP>(I, rowpix + 2 * j, z[j]);
+  for (int j0 = t; j0 < L; j0 += kGenChunk * nt) {
+    Opnd o[kGenChunk];
+    chunk_words<1>(I.mw, rowpix, j0, nt, L, o);
+    T d[kGenChunk][2];
+#pragma unroll
+    for (int u = 0; u < kGenChunk; ++u)
+      if (o[u].ok && OP == OP_Y_W) ld_map_pair<T>(I.d + o[u].pix, d[u][0], d[u][1]);
+#pragma unroll
+    for (int u = 0; u < kGenChunk; ++u)
+      if (o[u].ok) z[j0 + u * nt] = mid_op<T, OP>(I, o[u], d[u][0], d[u][1], z[j0 + u * nt]);
+  }
 }
 
 }  // namespace gen
@@ -289,9 +356,20 @@ k_row_gen(const InstDesc<T>* __restrict__ insts, RowArgs a, GenLen g, const T* _
   if constexpr (IN_SPEC) {
     const T* spec = a.spec_sel ? I.spec2 : I.spec;
     // X[k] of the `rows` rows: consecutive threads take consecutive rows of one k
-    for (int f = threadIdx.x; f < (L + 1) * rows; f += blockDim.x) {
-      const int k = f / rows, r = f - k * rows;
-      base[r * stride + k] = ldg_cx<T>(spec + 2 * ((size_t)k * ny + y0 + r));
+    const int total = (L + 1) * rows;
+    for (int f0 = threadIdx.x; f0 < total; f0 += gen::kGenChunk * blockDim.x) {
+      cx<T> tv[gen::kGenChunk];
+#pragma unroll
+      for (int u = 0; u < gen::kGenChunk; ++u) {
+        const int f = f0 + u * blockDim.x;
+        if (f < total)
+          tv[u] = ldg_cx<T>(spec + 2 * ((size_t)(f >> a.log_rows) * ny + y0 + (f & (rows - 1))));
+      }
+#pragma unroll
+      for (int u = 0; u < gen::kGenChunk; ++u) {
+        const int f = f0 + u * blockDim.x;
+        if (f < total) base[(f & (rows - 1)) * stride + (f >> a.log_rows)] = tv[u];
+      }
     }
     __syncthreads();
     // C2R: Z[k] = (X[k] + conj X[L-k]) + i e^{+2 pi i k/nx} (X[k] - conj X[L-k])
@@ -371,7 +449,7 @@ k_row_gen(const InstDesc<T>* __restrict__ insts, RowArgs a, GenLen g, const T* _
     // X[L] = Re Z[0] - Im Z[0]; stored transposed, consecutive threads on consecutive rows
     T* spec = a.spec_sel ? I.spec2 : I.spec;
     for (int f = threadIdx.x; f < (L + 1) * rows; f += blockDim.x) {
-      const int k = f / rows, r = f - k * rows;
+      const int k = f >> a.log_rows, r = f & (rows - 1);
       const cx<T>* Zr = base + r * stride + off;
       cx<T> X;
       if (k < L) {

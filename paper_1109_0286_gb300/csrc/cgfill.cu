@@ -869,6 +869,35 @@ void twiddles_len(int n, int count, std::vector<double>& w) {
   }
 }
 
+// Threads per mixed-radix transform (a multiple of 32, at most 512).  A stage
+// of radix R has n/R butterflies, shared round-robin by the transform's
+// threads; the last round leaves threads idle.  Among the candidates, take the
+// one with the best product of stage efficiency (butterflies / thread slots
+// over all stages) and SM occupancy (transforms resident per SM by shared
+// memory -- `slots` complex values each -- times threads, against the
+// threads the registers allow: 1024 at 64 per thread for FP32, 512 at 128
+// for FP64 and double-float).
+void gen_threads(GenLen* g, size_t slots, bool wide) {
+  const double tmax = wide ? 512.0 : 1024.0;
+  const size_t bytes = slots * (wide ? 16 : 8), per_sm = size_t(225) * 1024 / bytes;
+  double best = -1.0;
+  for (int nt = 32; nt <= 512; nt += 32) {
+    long long slots_used = 0, work = 0;
+    for (int s = 0; s < g->nst; ++s) {
+      const int nb = g->n / g->radix[s];
+      work += nb;
+      slots_used += (long long)((nb + nt - 1) / nt) * nt;
+    }
+    const double eff = double(work) / double(slots_used);
+    const double resident = std::min<double>(double(per_sm), std::floor(tmax / nt));
+    const double score = eff * std::min(1.0, resident * nt / tmax);
+    if (score > best + 1e-9 || (score > best - 1e-9 && nt > g->nt)) {
+      best = std::max(best, score);
+      g->nt = nt;
+    }
+  }
+}
+
 // Mixed-radix schedule and twiddle tables of one precision: rows per CTA
 // (4, 2 or 1, dividing ny, within the thread and shared-memory limits) and
 // column FFTs per CTA, unless the options fix them.
@@ -878,18 +907,20 @@ fill_status setup_generic(fill_plan* p) {
   const int L = p->nx / 2, ny = p->ny, maxt = GenLaunch<T>::max_threads();
   const size_t smax = 200 * 1024;
   auto row_ok = [&](int r) {
-    return r >= 1 && ny % r == 0 && r * p->grow.nt <= maxt && ny / r <= kMaxPartials &&
+    return r >= 1 && pow2(r) && ny % r == 0 && r * p->grow.nt <= maxt && ny / r <= kMaxPartials &&
            GenLaunch<T>::row_smem(L, r) <= smax;
   };
   auto col_ok = [&](int f) {
     return f >= 1 && f * p->gcol.nt <= maxt && GenLaunch<T>::col_smem(ny, f) <= smax;
   };
+  // defaults: CTAs of at most 512 threads and 113 KB, so that two fit an SM
+  const size_t half = 113 * 1024;
   if (p->o.rows_per_cta > 0) {
     P.rows = p->o.rows_per_cta;
   } else {
     P.rows = 1;
     for (int r : {4, 2})
-      if (row_ok(r)) {
+      if (row_ok(r) && r * p->grow.nt <= 512 && GenLaunch<T>::row_smem(L, r) <= half) {
         P.rows = r;
         break;
       }
@@ -898,7 +929,9 @@ fill_status setup_generic(fill_plan* p) {
     P.ffts = p->o.ffts_per_cta;
   } else {
     P.ffts = 1;
-    while (col_ok(2 * P.ffts) && 2 * P.ffts * p->gcol.nt <= 512 && 2 * P.ffts <= 16) P.ffts *= 2;
+    while (col_ok(2 * P.ffts) && 2 * P.ffts * p->gcol.nt <= 512 &&
+           GenLaunch<T>::col_smem(ny, 2 * P.ffts) <= half && 2 * P.ffts <= 16)
+      P.ffts *= 2;
   }
   if (!row_ok(P.rows) || !col_ok(P.ffts)) return FILL_EINVAL;
   std::vector<double> wl, wx, wn;
@@ -1068,8 +1101,10 @@ fill_status fill_init(fill_plan** out, int ny, int nx, const double* P_half,
     // mixed-radix grid: nx/2 and ny products of 2, 3, 5, 7, at most 4096
     if (nx % 2 != 0 || nx < 16 || ny < 8 || !gen_factor(nx / 2, &grow) || !gen_factor(ny, &gcol))
       return FILL_EINVAL;
-    // threads per transform: about 8 values each (a multiple of 32, at most 512)
-    for (cgf::GenLen* g : {&grow, &gcol}) g->nt = std::min(512, (g->n / 8 + 31) / 32 * 32);
+    // threads per transform, for the precision that carries the CG loop
+    const bool wide = opts && opts->mode == FILL_MODE_FP64;
+    gen_threads(&grow, size_t(2) * (nx / 2 + 1), wide);
+    gen_threads(&gcol, size_t(2) * ny, wide);
   }
   fill_opts o;
   if (opts)
