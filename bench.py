@@ -657,7 +657,9 @@ def run_gpu(args):
                            f"({t_iter:.2f} s), scaled to {n_it:.0f} iterations")}
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        metric = METRIC if args.workload == "wide4096" else \
+            f"constrained realizations/s at {ny}x{nx} ({args.workload}, refined to {tol:g})"
+        line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": {"mixed": "f32+df64", "fp32": "f32", "fp64": "f64"}[mode],
