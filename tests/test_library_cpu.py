@@ -106,3 +106,12 @@ def test_workload_table():
     _, obs, spec = workload("act7000x600")
     assert obs.shape == (600, 7000) and spec["ndiscs"] == 400
     assert 0.8 * 400 * 141 <= int((obs == 0).sum()) <= 400 * 141 * 1.05
+
+
+def test_laplace_radii_match_the_oracle():
+    """The package's annulus radii (used by the bench and the wrapper) are the
+    oracle's reading of the Sect. 6.3 kernels."""
+    import oracle as O
+    from paper_1109_0286_gb300 import laplace
+    for nk in (1, 5, 9, 13):
+        assert np.allclose(laplace.ms_radii(nk), O.ms_radii(nk), rtol=1e-15, atol=0)
