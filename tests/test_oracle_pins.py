@@ -441,18 +441,20 @@ def test_relax_converges_to_ml_fill():
 
 # ----------------------------------------------------------------- subdivision and strips (Sect. 6)
 
-def test_subdivide_counts_match_brute_force_and_nest():
+@pytest.mark.parametrize("ny,nx", [(32, 32), (21, 30)])
+def test_subdivide_counts_match_brute_force_and_nest(ny, nx):
     """The top-hat convolution of Sect. 6.2 equals the brute-force periodic
-    disc count; the layers are inside the mask and nest as delta shrinks."""
-    _, obs = _small_case(32, 32, seed=2, band=8, discs=3, r=3.0)
+    disc count (a square power-of-two grid and an odd mixed-radix one); the
+    layers are inside the mask and nest as delta shrinks."""
+    _, obs = _small_case(ny, nx, seed=2, band=8, discs=3, r=3.0)
     m = obs == 0
     for delta in (3.0, 7.0, 10.0):
         offs = O.disc_offsets(delta / 2)
         layer = O.subdivide(obs, delta)
         brute = np.zeros_like(m)
-        for y in range(32):
-            for x in range(32):
-                c = sum(int(obs[(y + dy) % 32, (x + dx) % 32]) for dy, dx in offs)
+        for y in range(ny):
+            for x in range(nx):
+                c = sum(int(obs[(y + dy) % ny, (x + dx) % nx]) for dy, dx in offs)
                 brute[y, x] = m[y, x] and c * 100 > 3 * len(offs)
         assert np.array_equal(layer, brute)
         assert not (layer & ~m).any()
@@ -547,21 +549,22 @@ def test_laplace_ms_constant_data_is_a_fixed_point_and_sweeps_approach_harmonic(
     assert err < 0.01, err
 
 
-def test_laplace_ms_one_sweep_is_the_annulus_mean_by_brute_force():
+@pytest.mark.parametrize("ny,nx", [(40, 40), (35, 42)])
+def test_laplace_ms_one_sweep_is_the_annulus_mean_by_brute_force(ny, nx):
     """One sweep from 0 on the mask: every masked pixel holds the plain mean
     of the starting map over its class's annulus (periodic offsets)."""
-    _, obs = _small_case(40, 40, seed=9, band=14, discs=2, r=3.0)
+    _, obs = _small_case(ny, nx, seed=9, band=14, discs=2, r=3.0)
     radii = O.ms_radii(nk=4)
     rng = np.random.default_rng(4)
-    d = rng.standard_normal((40, 40))
+    d = rng.standard_normal((ny, nx))
     x = O.laplace_ms(obs, d, radii, 1)
     cls = O.ms_classes(obs, radii)
     start = np.where(obs == 1, d, 0.0)
-    for y in range(40):
-        for xx in range(40):
+    for y in range(ny):
+        for xx in range(nx):
             if obs[y, xx]:
                 assert x[y, xx] == d[y, xx]
                 continue
             offs = O.annulus_offsets(*radii[cls[y, xx]])
-            want = sum(start[(y + dy) % 40, (xx + dx) % 40] for dy, dx in offs) / len(offs)
+            want = sum(start[(y + dy) % ny, (xx + dx) % nx] for dy, dx in offs) / len(offs)
             assert abs(x[y, xx] - want) < 1e-12, (y, xx)
