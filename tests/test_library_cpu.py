@@ -115,3 +115,15 @@ def test_laplace_radii_match_the_oracle():
     from paper_1109_0286_gb300 import laplace
     for nk in (1, 5, 9, 13):
         assert np.allclose(laplace.ms_radii(nk), O.ms_radii(nk), rtol=1e-15, atol=0)
+
+
+def test_profile_summaries_are_text_with_their_commands():
+    """Every ncu summary under profiles/ is short text naming the command that
+    made it, with the clocks left alone (--clock-control none)."""
+    root = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "profiles")
+    names = sorted(os.listdir(root))
+    assert names and all(n.endswith((".md", ".txt")) for n in names)
+    for n in names:
+        text = open(os.path.join(root, n)).read()
+        assert len(text) < 16384, n
+        assert "ncu " in text and "--clock-control none" in text, n
