@@ -386,6 +386,93 @@ def act_measurement():
     return out, P, obs, d, spec
 
 
+def cufft_pcg_realize(P_half, masked, d, y, tol, precond=True, max_iter=5000, check_every=8):
+    """Timed comparison only, never part of the library: the same constrained
+    realization (Sects. 2.1-2.4) written with PyTorch's FFT (cuFFT on the GPU)
+    and elementwise ops.  P_half (ny, nx/2+1), masked (ny, nx) bool, d (ny, nx)
+    and the draws y (B, ny, nx) are tensors on one device, in one real dtype.
+    PCG with B = S S (S = P_x C^{1/2} P_x) until ||r|| <= tol ||b|| for every
+    map (tested every `check_every` iterations).  Returns (x, iterations)."""
+    import torch
+    ny, nx = masked.shape
+    m = masked.to(d.dtype)
+    Pinv, Psq = 1.0 / P_half, torch.sqrt(P_half)
+
+    def apply(x, Ps):   # C^s x = F^-1 diag(P^s) F x (irfft2 carries 1/n)
+        return torch.fft.irfft2(torch.fft.rfft2(x) * Ps, s=(ny, nx))
+
+    def A(v):
+        return m * apply(m * v, Pinv)
+
+    def prec(v):
+        return m * apply(m * apply(m * v, Psq), Psq) if precond else v
+
+    def dot(a, b):
+        return (a * b).sum(dim=(1, 2))
+
+    b = -m * apply((1.0 - m) * (d - y), Pinv)
+    u = torch.zeros_like(b)
+    r = b.clone()
+    z = prec(r)
+    p = z.clone()
+    rz = dot(r, z)
+    thr = tol * tol * dot(b, b)
+    it = 0
+    while it < max_iter:
+        q = A(p)
+        pq = dot(p, q)
+        alpha = torch.where(pq > 0, rz / pq, torch.zeros_like(pq))[:, None, None]
+        u += alpha * p
+        r -= alpha * q
+        it += 1
+        if it % check_every == 0 and bool((dot(r, r) <= thr).all()):
+            break
+        z = prec(r)
+        rz_new = dot(r, z)
+        beta = torch.where(rz > 0, rz_new / rz, torch.zeros_like(rz))[:, None, None]
+        rz = rz_new
+        p = z + beta * p
+    return torch.where(masked, y + u, d), it
+
+
+def cufft_arm(P, obs, d, batch, tol64):
+    """cuFFT-based PCG timed beside the library (spec comparison):
+    FP32 to 1e-5 on `batch` maps, FP64 to tol64 on one map; each timed
+    realization includes its draw (torch.randn + one transform pair), the
+    right-hand side, the PCG loop and the assembly.  One warm-up realization
+    each, then one timed by CUDA events."""
+    import torch
+    out = {"note": "PyTorch FFT (cuFFT) + elementwise ops; comparison only"}
+    for name, dt, B, tol in (("fp32", torch.float32, batch, 1e-5), ("fp64", torch.float64, 1, tol64)):
+        try:
+            dev = torch.device("cuda")
+            Ph = torch.as_tensor(P, dtype=dt, device=dev)
+            masked = torch.as_tensor(obs == 0, device=dev)
+            dd = d.to(dtype=dt)
+            ny, nx = masked.shape
+
+            def one(seed):
+                g = torch.Generator(device=dev).manual_seed(seed)
+                xi = torch.randn((B, ny, nx), generator=g, dtype=dt, device=dev)
+                y = torch.fft.irfft2(torch.fft.rfft2(xi) * torch.sqrt(Ph), s=(ny, nx))
+                return cufft_pcg_realize(Ph, masked, dd, y, tol, max_iter=2000)
+
+            one(1)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, it = one(2)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            out[name] = {"realizations_per_s": B / (ms / 1e3), "ms_per_step": ms, "batch": B,
+                         "tol": tol, "iters": it}
+        except Exception as e:   # comparison only: never fail the bench line
+            out[name] = {"error": repr(e)[:200]}
+        torch.cuda.empty_cache()
+    return out
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -635,6 +722,9 @@ def run_gpu(args):
                 "iters_per_realization": it64 / (B * args.fp64_steps)}
         p64.close()
 
+    # cuFFT-based PCG (timed comparison, not part of the library)
+    cufft = cufft_arm(P, obs, d, B, tol) if (rank == 0 and not args.no_fp64) else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         dn = d.cpu().numpy().astype("float64")
@@ -672,6 +762,7 @@ def run_gpu(args):
                 "iters_per_realization": iters / (B * args.steps),
                 "worst_true_rel_resid": worst_resid,
                 "fp64_pcg": fp64,
+                "cufft_pcg": cufft,
                 "speedup_vs_fp64": (value / world / fp64["value"]) if fp64 else None,
                 "gpu_launches": launches, "e2e": e2e, "roofline": roofline,
                 "passes": pass_table, "lanczos": lanczos, "relax": relax, "strips": strip_meas,

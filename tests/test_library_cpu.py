@@ -127,3 +127,27 @@ def test_profile_summaries_are_text_with_their_commands():
         text = open(os.path.join(root, n)).read()
         assert len(text) < 16384, n
         assert "ncu " in text and "--clock-control none" in text, n
+
+
+@pytest.mark.parametrize("ny,nx,precond", [(32, 48, True), (24, 32, False)])
+def test_cufft_comparison_arm_computes_the_realization(ny, nx, precond):
+    """The bench's cuFFT comparison (PyTorch FFT, here on the CPU) computes
+    the same constrained realization as the oracle from the same draw."""
+    import sys
+    import torch
+    import oracle as O
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    P = synth.spectrum_cmb_like(ny, nx, 2 * np.pi / nx)
+    obs = synth.mask_band_discs(ny, nx, 5, 2, 2.0, 3.0, 4)
+    Pf = O.hermitian_full(P, nx)
+    d = O.draw(Pf, 7)
+    y = O.draw(Pf, 11)
+    x, it = bench.cufft_pcg_realize(torch.from_numpy(P), torch.from_numpy(obs == 0),
+                                    torch.from_numpy(d), torch.from_numpy(y)[None], 1e-12,
+                                    precond=precond)
+    ref = O.realize(P, obs, d, 11, tol=1e-13, precond=precond)
+    m = obs == 0
+    got = x[0].numpy()
+    assert np.array_equal(got[~m], d[~m]) and it > 0
+    assert np.linalg.norm(got[m] - ref.x[m]) <= 1e-9 * np.linalg.norm(ref.x[m])
