@@ -22,8 +22,10 @@ Gaussian realizations" (arXiv:1109.0286):
   ``x = K * x`` on M; iterating ``x_M <- (K * x)_M`` is the kernel relaxation.
 
 DFT convention: ``F x(k) = sum_r x(r) exp(-i k.r)`` (unnormalised) and
-``F^-1`` carries ``1/n``; ``C^s = F^-1 diag(P^s) F``.  The FFT itself is a
-library primitive (``numpy.fft``), pinned in the tests against a direct DFT.
+``F^-1`` carries ``1/n``; ``C^s = F^-1 diag(P^s) F``.  The transform is the
+oracle's own (``oracle_fft.c``: recursive mixed-radix decimation in time with
+twiddles ``cos/sin(2 pi j/N)`` evaluated directly in FP64, rows and columns
+split over host threads), pinned in the tests against a direct DFT.
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 except the spectrum and mask recipes, which are input conventions.
@@ -31,12 +33,16 @@ except the spectrum and mask recipes, which are input conventions.
 from __future__ import annotations
 
 import math
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
 
+from . import _native
+
 __all__ = [
-    "hermitian_full", "validate_spectrum", "apply_power", "philox4x32_10",
+    "fft2", "ifft2", "fft_rows", "set_threads", "threads", "hermitian_full",
+    "validate_spectrum", "apply_power", "philox4x32_10",
     "uniform52", "white_noise", "draw", "project", "rhs", "apply_A",
     "apply_S", "pcg", "PcgResult", "realize", "Realization",
     "dft2_direct", "circulant_corr", "dense_matrix", "ml_dense_cov",
@@ -45,6 +51,49 @@ __all__ = [
     "ms_radii", "annulus_offsets", "ms_classes", "laplace_ms",
     "loss_masked_sq", "lanczos_tridiag",
 ]
+
+
+# ---------------------------------------------------------------------------
+# The oracle's own DFT (Sect. 4: exactly unitary on the periodic grid)
+# ---------------------------------------------------------------------------
+
+_THREADS = max(1, int(os.cpu_count() or 1))
+
+
+def set_threads(n: int) -> None:
+    """Host threads of the transforms (the results do not depend on it)."""
+    global _THREADS
+    _THREADS = max(1, int(n))
+
+
+def threads() -> int:
+    return _THREADS
+
+
+def _transform(x: np.ndarray, sign: int, rows_only: bool) -> np.ndarray:
+    a = np.array(x, dtype=np.complex128, order="C", copy=True)
+    if a.ndim != 2:
+        raise ValueError("expected a 2-D array")
+    fn = _native.lib().oracle_fft_rows if rows_only else _native.lib().oracle_fft2
+    nthr = _THREADS if a.size >= 65536 else 1     # small maps: threads cost more than they save
+    if fn(a.shape[0], a.shape[1], a.ctypes.data, sign, nthr) != 0:
+        raise MemoryError("oracle FFT: out of host memory")
+    return a
+
+
+def fft2(x: np.ndarray) -> np.ndarray:
+    """Unnormalised 2D DFT ``X(k) = sum_r x(r) exp(-2 pi i (ky y/ny + kx x/nx))``."""
+    return _transform(x, -1, False)
+
+
+def ifft2(X: np.ndarray) -> np.ndarray:
+    """Inverse 2D DFT, carrying the ``1/n``."""
+    return _transform(X, +1, False) / (X.shape[0] * X.shape[1])
+
+
+def fft_rows(x: np.ndarray) -> np.ndarray:
+    """Unnormalised 1D DFT of every row of a 2-D array."""
+    return _transform(x, -1, True)
 
 
 # ---------------------------------------------------------------------------
@@ -78,7 +127,7 @@ def validate_spectrum(P_half: np.ndarray, nx: int) -> None:
 
 def apply_power(x: np.ndarray, P_full: np.ndarray, s: float) -> np.ndarray:
     """``C^s x = F^-1 diag(P^s) F x`` for a real map ``x``."""
-    return np.real(np.fft.ifft2(np.fft.fft2(x) * P_full ** s))
+    return np.real(ifft2(fft2(x) * P_full ** s))
 
 
 # ---------------------------------------------------------------------------
@@ -369,9 +418,9 @@ def backward(P_half, observed, d, seed, real: Realization, bidx_half, sig_half,
     grad_d = np.where(obs, -Qlam, 0.0)
     h = np.where(masked, g, Qlam)
     w = np.where(obs, d - real.y, real.u)
-    xi_hat = np.fft.fft2(white_noise(ny, nx, seed))
-    dLdP = (np.real(np.conj(np.fft.fft2(h)) * xi_hat) / (2.0 * n * np.sqrt(P_full))
-            + np.real(np.conj(np.fft.fft2(lam)) * np.fft.fft2(w)) / (n * P_full ** 2))
+    xi_hat = fft2(white_noise(ny, nx, seed))
+    dLdP = (np.real(np.conj(fft2(h)) * xi_hat) / (2.0 * n * np.sqrt(P_full))
+            + np.real(np.conj(fft2(lam)) * fft2(w)) / (n * P_full ** 2))
     bfull = band_full(bidx_half, nx)
     sfull = hermitian_full(sig_half, nx)
     nb = int(bidx_half.max()) + 1
@@ -460,8 +509,7 @@ def subdivide(observed, delta, threshold=0.03):
     for dy, dx in offs:
         disc[dy % ny, dx % nx] = 1.0
     obs = observed.astype(bool)
-    count = np.rint(np.real(np.fft.ifft2(np.fft.fft2(obs.astype(np.float64)) *
-                                         np.fft.fft2(disc)))).astype(np.int64)
+    count = np.rint(np.real(ifft2(fft2(obs.astype(np.float64)) * fft2(disc)))).astype(np.int64)
     return (~obs) & (count * 100 > round(threshold * 100) * len(offs))
 
 
@@ -538,14 +586,14 @@ def laplace_ms(observed, d, radii, iters):
         offs = annulus_offsets(r_in, r_out)
         for dy, dx in offs:
             k[dy % ny, dx % nx] = 1.0 / len(offs)
-        spectra.append(np.fft.fft2(k))
+        spectra.append(fft2(k))
     x = np.where(obs, np.asarray(d, dtype=np.float64), 0.0)
     for _ in range(iters):
-        X = np.fft.fft2(x)
+        X = fft2(x)
         new = x.copy()
         for j, K in enumerate(spectra):
             sel = (~obs) & (cls == j)
             if sel.any():
-                new[sel] = np.real(np.fft.ifft2(X * K))[sel]
+                new[sel] = np.real(ifft2(X * K))[sel]
         x = new
     return x

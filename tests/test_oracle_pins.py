@@ -64,12 +64,60 @@ def test_white_noise_moments():
 
 # ----------------------------------------------------------------- transforms
 
-@pytest.mark.parametrize("ny,nx", [(8, 16), (15, 14), (21, 10)])
+@pytest.mark.parametrize("ny,nx", [(8, 16), (15, 14), (21, 10), (13, 17)])
 def test_fft_matches_direct_dft(ny, nx):
-    """Power-of-two and mixed-radix (3, 5, 7) grids."""
+    """The oracle's own transform against the DFT's definition (two dense
+    matrix products) on power-of-two, mixed-radix (3, 5, 7) and prime grids,
+    forward and inverse; NumPy's FFT is a second, independent check."""
     rng = np.random.default_rng(0)
-    x = rng.standard_normal((ny, nx))
-    assert np.allclose(np.fft.fft2(x), O.dft2_direct(x), rtol=0, atol=1e-12)
+    x = rng.standard_normal((ny, nx)) + 1j * rng.standard_normal((ny, nx))
+    X = O.fft2(x)
+    assert np.allclose(X, O.dft2_direct(x), rtol=0, atol=1e-12)
+    assert np.allclose(X, np.fft.fft2(x), rtol=0, atol=1e-12)
+    # inverse: F^-1 carries 1/n and conjugates the kernel
+    assert np.allclose(O.ifft2(X), x, rtol=0, atol=1e-13)
+    assert np.allclose(O.ifft2(x), np.conj(O.dft2_direct(np.conj(x))) / (ny * nx),
+                       rtol=0, atol=1e-13)
+
+
+def _dft_direct_1d(v):
+    """Length-n DFT of a vector by its definition, in row blocks; the phase
+    j k mod n is formed in integers so that the angle is exact."""
+    n = v.size
+    j = np.arange(n, dtype=np.int64)
+    out = np.empty(n, dtype=np.complex128)
+    for k0 in range(0, n, 500):
+        k = np.arange(k0, min(k0 + 500, n), dtype=np.int64)
+        ph = (k[:, None] * j[None, :]) % n
+        out[k0:k0 + k.size] = np.exp(-2j * math.pi * ph / n) @ v
+    return out
+
+
+def test_fft_rows_of_the_flat_sky_length():
+    """7000-point rows (2^3 5^3 7, the long side of the Sect. 3 maps) and
+    600-point columns (2^3 3 5^2) against the direct DFT."""
+    rng = np.random.default_rng(3)
+    for n in (7000, 600):
+        x = rng.standard_normal((2, n)) + 1j * rng.standard_normal((2, n))
+        X = O.fft_rows(x)
+        for r in range(2):
+            ref = _dft_direct_1d(x[r])
+            assert np.max(np.abs(X[r] - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_fft_independent_of_thread_count():
+    """Rows and columns are split over host threads; every element is the
+    same sequence of operations whatever the split."""
+    x = np.random.default_rng(4).standard_normal((96, 40))
+    n0 = O.threads()
+    try:
+        O.set_threads(1)
+        a = O.fft2(x)
+        O.set_threads(7)
+        b = O.fft2(x)
+    finally:
+        O.set_threads(n0)
+    assert np.array_equal(a, b)
 
 
 @pytest.mark.parametrize("ny,nx", [(8, 16), (15, 14), (12, 20)])
