@@ -52,10 +52,10 @@ typedef struct fill_plan fill_plan;
 
 typedef enum {
   FILL_OK = 0,
-  FILL_EINVAL = 1,      /* bad argument: size, spectrum, mask, pointer */
+  FILL_EINVAL = 1,      /* bad argument: size, spectrum, mask, pointer, non-finite data */
   FILL_ENOMEM = 2,      /* device or pinned host allocation failed */
   FILL_ENOTCONV = 3,    /* iteration limit reached before the tolerance */
-  FILL_EBREAKDOWN = 4,  /* p^T A p <= 0, r^T z <= 0 or a non-finite value */
+  FILL_EBREAKDOWN = 4,  /* p^T A p <= 0, r^T z <= 0 or a non-finite value inside the solve */
   FILL_ETIMEOUT = 5,    /* reserved: bounded device wait expired */
   FILL_ECUDA = 6        /* CUDA runtime error (message via fill_last_error) */
 } fill_status;
@@ -132,11 +132,50 @@ fill_status fill_init(fill_plan** plan, int ny, int nx, const double* P_half,
  * out:     device, batch contiguous maps of ny*nx (same type as d);
  *          out_U = d_U exactly, out_M = y_M + u.
  * stats:   host array of batch entries, or NULL.
- * Returns the worst per-realization status (FILL_ENOTCONV / FILL_EBREAKDOWN
- * leave the last iterate in out), or FILL_EINVAL / FILL_ECUDA.
+ * Data that are not finite on the observed pixels (NaN, Inf, or values so
+ * large that the right-hand side overflows) give that realization the status
+ * FILL_EINVAL: its solve stops before the first iteration, the call returns
+ * at once, and the plan stays usable.
+ * Returns the worst per-realization status -- FILL_EINVAL before
+ * FILL_EBREAKDOWN before FILL_ENOTCONV (the last two leave the last iterate
+ * in out) -- or FILL_EINVAL for bad arguments, or FILL_ECUDA.
  */
 fill_status fill_realize(fill_plan* plan, const void* d, long long d_stride,
                          const uint64_t* seeds, double tol, void* out, fill_stats* stats);
+
+/*
+ * fill_realize_batch -- constrained realizations (Sects. 2.1-2.4) for several
+ * plans in one call: masks, spectra and grid sizes may differ between plans.
+ * d[i]: device, one data map shared by plan i's batch; out[i]: device, plan
+ * i's batch maps; seeds: host, one per realization in plan order (plan 0's
+ * batch first); stats: host, one entry per realization, or NULL.  The result
+ * of each plan equals what fill_realize would give it.
+ * Plans of one mode (FP32 or FP64), one precond setting and one stream run as
+ * a group (see fill_group_init): plans of the same grid share every pass
+ * launch and the grid sizes run as concurrent branches of one graph per CG
+ * loop.  The first call with a given list of plans builds that group
+ * (device descriptors and the loop graph) and caches it in plans[0];
+ * later calls with the same list reuse it, and fill_destroy(plans[0]) frees
+ * it.  Any other list (mixed mode, or differing settings) runs the plans one
+ * after another.  Errors: as fill_realize.
+ */
+fill_status fill_realize_batch(fill_plan* const* plans, int count, const void* const* d,
+                               const uint64_t* seeds, double tol, void* const* out,
+                               fill_stats* stats);
+
+/*
+ * fill_set_spectrum -- replaces the plan's spectrum P(k) in place (for
+ * band-power updates: an optimisation over the amplitudes a_b of
+ * P = sum_b a_b T_b + N needs a new P at every step, Sects. 2.1, 4).  Same
+ * layout and validation as fill_init's P_half (host, float64, ny x (nx/2+1),
+ * finite, > 0, Hermitian-consistent); rebuilds the tables 1/(nP) and
+ * sqrt(P)/n of every precision the plan holds, the relaxation level
+ * max 1/P, and -- if fill_set_bands was called -- the band-gradient weights
+ * at the new P.  Allocates nothing; waits for the plan's stream first.  The
+ * realizations of earlier calls are not kept: fill_backward then needs a new
+ * fill_realize.  Errors: FILL_EINVAL (message via fill_last_error), FILL_ECUDA.
+ */
+fill_status fill_set_spectrum(fill_plan* plan, const double* P_half);
 
 /*
  * fill_ml -- maximum-likelihood fill (Sect. 2.1): x_M = -((C^-1)_MM)^-1 (C^-1)_MU d_U,
@@ -310,13 +349,14 @@ fill_status fill_autotune(fill_plan* plan, const char* cache_path);
 /*
  * Groups: many realizations over masks and grid sizes in one call.
  * fill_group_init collects plans (all FILL_MODE_FP32 or all FILL_MODE_FP64,
- * same precond and stream, power-of-two grids; each keeps its own mask,
- * spectrum and buffers).
+ * same precond and stream; power-of-two or mixed-radix grids; each keeps its
+ * own mask, spectrum and buffers).
  * Plans with the same grid form a size class whose instances share every pass
  * launch; the classes run concurrently as parallel branches of one captured
  * CUDA graph per chunk of CG iterations.  autotune != 0 tunes each class's
- * schedule (cached in cache_path if not NULL).  The plans must outlive the
- * group.  Errors: FILL_EINVAL, FILL_ENOMEM, FILL_ECUDA.
+ * schedule (cached in cache_path if not NULL; mixed-radix classes keep their
+ * fixed schedule).  The plans must outlive the group.  Errors: FILL_EINVAL,
+ * FILL_ENOMEM, FILL_ECUDA.
  */
 typedef struct fill_group fill_group;
 fill_status fill_group_init(fill_group** group, fill_plan* const* plans, int count,
@@ -327,7 +367,8 @@ fill_status fill_group_init(fill_group** group, fill_plan* const* plans, int cou
  * plan of the group.  d[i]: device, one data map shared by plan i's batch;
  * out[i]: device, plan i's batch maps; seeds: host, one per realization in
  * plan order (plan 0's batch first); stats: host, one per realization, or
- * NULL.  Returns the worst status.
+ * NULL.  Returns the worst per-realization status (ranked as in
+ * fill_realize).
  */
 fill_status fill_group_realize(fill_group* group, const void* const* d, const uint64_t* seeds,
                                double tol, void* const* out, fill_stats* stats);

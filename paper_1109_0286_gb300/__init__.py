@@ -7,8 +7,11 @@ kernels of ``libcgfill.so``.  There is no CPU fallback; using the library
 without the built extension or without a GPU raises.
 
 Low-level names mirror the C ABI (``fill_init``, ``fill_realize``,
-``fill_draw``, ``fill_apply``, ``fill_history``, ``fill_destroy``,
-``fill_strerror``, ``fill_version``); ``Plan`` wraps them for torch tensors.
+``fill_realize_batch``, ``fill_set_spectrum``, ``fill_draw``, ``fill_apply``,
+``fill_history``, ``fill_destroy``, ``fill_strerror``, ``fill_version``);
+``Plan`` wraps them for torch tensors, and ``FillRealize`` (a
+``torch.autograd.Function``) puts a realization into a torch graph with
+gradients for the data map and the band-power amplitudes of P(k).
 """
 from __future__ import annotations
 
@@ -26,7 +29,9 @@ __all__ = [
     "fill_lanczos", "fill_time_pass", "fill_set_bands", "fill_backward", "fill_autotune", "fill_group_init",
     "fill_group_realize", "fill_group_size", "fill_group_destroy", "Group", "fill_apply_static",
     "fill_masked_count", "fill_destroy", "fill_strerror", "fill_last_error",
-    "fill_version", "Plan", "MODES", "EXPORTED_SYMBOLS",
+    "fill_version", "fill_realize_batch", "fill_set_spectrum", "Plan", "MODES",
+    "EXPORTED_SYMBOLS", "BandPowerSpectrum", "FillRealize", "fill_realize_autograd",
+    "realize_batch",
 ]
 
 MODES = {"fp64": 0, "fp32": 1, "mixed": 2}
@@ -39,7 +44,7 @@ EXPORTED_SYMBOLS = [
     "fill_autotune",
     "fill_group_init", "fill_group_realize", "fill_group_size", "fill_group_destroy",
     "fill_apply_static", "fill_masked_count", "fill_destroy", "fill_strerror",
-    "fill_last_error", "fill_version",
+    "fill_last_error", "fill_version", "fill_realize_batch", "fill_set_spectrum",
 ]
 
 
@@ -66,7 +71,8 @@ class FillStats(ctypes.Structure):
 class FillError(RuntimeError):
     def __init__(self, status: int, where: str):
         msg = f"{where}: {STATUS.get(status, status)} ({fill_strerror(status)})"
-        if status == 6 or (status == 1 and where in ("fill_apply_static", "fill_subdivide")):
+        if status == 6 or (status == 1 and where in ("fill_apply_static", "fill_subdivide",
+                                                     "fill_set_spectrum")):
             msg += ": " + fill_last_error()
         super().__init__(msg)
         self.status = status
@@ -136,6 +142,11 @@ def load() -> ctypes.CDLL:
     lib.fill_group_destroy.restype = None
     lib.fill_apply_static.argtypes = [_ci, _ci, _vp, _vp, _ci, _vp, _vp, _vp]
     lib.fill_apply_static.restype = _ci
+    lib.fill_realize_batch.argtypes = [ctypes.POINTER(_vp), _ci, ctypes.POINTER(_vp), _vp, _cd,
+                                       ctypes.POINTER(_vp), ctypes.POINTER(FillStats)]
+    lib.fill_realize_batch.restype = _ci
+    lib.fill_set_spectrum.argtypes = [_vp, _vp]
+    lib.fill_set_spectrum.restype = _ci
     lib.fill_masked_count.argtypes = [_vp]
     lib.fill_masked_count.restype = _cll
     lib.fill_destroy.argtypes = [_vp]
@@ -329,6 +340,26 @@ def fill_apply_static(ny, nx, P_ptr, obs_ptr, which, in_ptr, out_ptr, stream=0):
         raise FillError(st, "fill_apply_static")
 
 
+def fill_realize_batch(plans, d_ptrs, seeds, tol, out_ptrs, total):
+    """Realizations for several plans in one call (one data map per plan)."""
+    s = np.ascontiguousarray(seeds, dtype=np.uint64)
+    pl = (_vp * len(plans))(*plans)
+    d = (_vp * len(d_ptrs))(*d_ptrs)
+    o = (_vp * len(out_ptrs))(*out_ptrs)
+    stats = (FillStats * total)()
+    st = load().fill_realize_batch(pl, len(plans), d, s.ctypes.data, _cd(tol), o, stats)
+    return st, [x.as_dict() for x in stats]
+
+
+def fill_set_spectrum(plan, P_half, ny, nx):
+    P = np.ascontiguousarray(P_half, dtype=np.float64)
+    if P.shape != (ny, nx // 2 + 1):
+        raise ValueError("P_half must be ny x (nx/2+1)")
+    st = load().fill_set_spectrum(_vp(plan), P.ctypes.data)
+    if st != 0:
+        raise FillError(st, "fill_set_spectrum")
+
+
 def fill_masked_count(plan) -> int:
     return int(load().fill_masked_count(_vp(plan)))
 
@@ -382,6 +413,7 @@ class Plan:
         o.update_delta = float(update_delta)
         o.host_loops = 1 if host_loops else 0
         self.nbands = 0
+        self.calls = 0          # compute calls so far (each may overwrite the device state)
         self.ny, self.nx = observed.shape
         self.batch = int(batch)
         self.mode = mode
@@ -401,6 +433,7 @@ class Plan:
     def realize(self, d, seeds, tol, out=None, check=True):
         """Constrained realizations of data ``d`` (one map shared by the batch,
         or ``batch`` maps).  Returns ``(out, stats)``."""
+        self.calls += 1
         import torch
         shared = d.numel() == self.ny * self.nx
         self._check(d, "d", 1 if shared else self.batch)
@@ -420,6 +453,7 @@ class Plan:
         """Maximum-likelihood fills x_M = -(Q_MM)^-1 Q_MU d_U of data ``d``
         (one map shared by the batch, or ``batch`` maps).  Returns
         ``(out, stats)``."""
+        self.calls += 1
         import torch
         shared = d.numel() == self.ny * self.nx
         self._check(d, "d", 1 if shared else self.batch)
@@ -435,6 +469,7 @@ class Plan:
     def relax(self, d, iters, out=None, check=True):
         """Kernel-relaxation sweeps (Sect. 5, eq. Algo) from x_M = 0: returns
         ``(out, stats)``."""
+        self.calls += 1
         import torch
         shared = d.numel() == self.ny * self.nx
         self._check(d, "d", 1 if shared else self.batch)
@@ -454,6 +489,7 @@ class Plan:
     def laplace_ms(self, d, iters, cls, out=None, check=True):
         """Sweeps of the kernel Laplace solver with per-pixel annulus index
         ``cls`` (device uint8 map).  Returns ``(out, stats)``."""
+        self.calls += 1
         import torch
         shared = d.numel() == self.ny * self.nx
         self._check(d, "d", 1 if shared else self.batch)
@@ -469,6 +505,12 @@ class Plan:
             raise FillError(st, "fill_laplace_ms")
         return out, stats
 
+    def set_spectrum(self, P_half):
+        """Replace P(k) in place (``fill_set_spectrum``): new tables, no
+        re-allocation; the mask, buffers and graphs are kept."""
+        self.calls += 1
+        fill_set_spectrum(self._plan, P_half, self.ny, self.nx)
+
     def set_bands(self, band_of_k, sig_half):
         """Band-power templates T_b(k) = 1[band(k) = b] S(k) for ``backward``."""
         self.nbands = fill_set_bands(self._plan, band_of_k, sig_half)
@@ -476,6 +518,7 @@ class Plan:
     def backward(self, d, grad_x, tol, grad_d=None, bands=True, check=True):
         """Adjoint gradients of L(x) through the last ``realize``: returns
         ``(dL/dd, dL/da_b or None, stats)``."""
+        self.calls += 1
         import torch
         shared = d.numel() == self.ny * self.nx
         self._check(d, "d", 1 if shared else self.batch)
@@ -491,6 +534,7 @@ class Plan:
         return grad_d, gb, stats
 
     def draw(self, seeds, out=None):
+        self.calls += 1
         import torch
         if out is None:
             out = torch.empty((self.batch, self.ny, self.nx), dtype=self.dtype, device=self.device)
@@ -500,6 +544,7 @@ class Plan:
 
     def apply(self, which, x):
         """0: C^-1 x, 1: C^{1/2} x, 2: P_x C^-1 P_x x, 3: P_x C^{1/2} P_x x."""
+        self.calls += 1
         import torch
         self._check(x, "x", 1)
         out = torch.empty_like(x)
@@ -508,12 +553,14 @@ class Plan:
 
     def time_pass(self, pass_id, precision=None, reps=20):
         """(ms per launch, algorithmic bytes per launch) of one hot-loop pass."""
+        self.calls += 1
         if precision is None:
             precision = 1 if self.mode == "fp64" else 0
         return fill_time_pass(self._plan, pass_id, precision, reps)
 
     def autotune(self, cache_path=None):
         """Time the valid launch schedules and keep the fastest."""
+        self.calls += 1
         fill_autotune(self._plan, cache_path)
 
     def history(self, inst=0):
@@ -578,3 +625,130 @@ class Group:
             self.close()
         except Exception:
             pass
+
+
+def realize_batch(plans, ds, seeds, tol, outs=None, check=True):
+    """``fill_realize_batch``: realizations for several plans (masks, spectra
+    and grid sizes may differ), one data map per plan.  Returns
+    ``(outs, stats)`` with one output tensor of ``batch`` maps per plan."""
+    import torch
+    if outs is None:
+        outs = [torch.empty((p.batch, p.ny, p.nx), dtype=p.dtype, device=p.device)
+                for p in plans]
+    for p, d, o in zip(plans, ds, outs):
+        p._check(d, "d", 1)
+        p._check(o, "out", p.batch)
+        p.calls += 1
+    total = sum(p.batch for p in plans)
+    seeds = np.asarray(seeds, dtype=np.uint64).reshape(-1)
+    if seeds.size != total:
+        raise ValueError("need one seed per realization")
+    st, stats = fill_realize_batch([p._plan for p in plans], [d.data_ptr() for d in ds], seeds,
+                                   tol, [o.data_ptr() for o in outs], total)
+    if check and st != 0:
+        raise FillError(st, "fill_realize_batch")
+    return outs, stats
+
+
+# ------------------------------------------------------------ autograd
+
+class BandPowerSpectrum:
+    """Band-power parameterisation of the spectrum:
+    ``P(k) = sum_b a_b 1[band(k) = b] S(k) + N(k)`` on the half plane
+    ``ny x (nx/2+1)``; ``band_of_k`` (int), ``sig_half`` (S) and ``noise``
+    (N, an array of that shape or a scalar) are host arrays.  The templates
+    ``T_b = 1[band = b] S`` are what ``fill_set_bands`` receives, so the
+    library's band gradient is dL/da_b."""
+
+    def __init__(self, band_of_k, sig_half, noise):
+        self.band_of_k = np.ascontiguousarray(band_of_k, dtype=np.int32)
+        self.sig_half = np.ascontiguousarray(sig_half, dtype=np.float64)
+        self.noise = noise
+        self.nbands = int(self.band_of_k.max()) + 1
+
+    def __call__(self, amps) -> np.ndarray:
+        a = np.asarray(amps, dtype=np.float64).reshape(-1)
+        if a.size != self.nbands:
+            raise ValueError(f"need {self.nbands} band amplitudes")
+        return a[self.band_of_k] * self.sig_half + self.noise
+
+
+def _make_autograd():
+    import torch
+
+    class _FillRealize(torch.autograd.Function):
+        """Constrained realizations as a differentiable torch operation.
+
+        ``x = FillRealize.apply(d, amps, plan, model, seeds, tol)``: ``d`` is
+        the data map (one map shared by the plan's batch, or ``batch`` maps),
+        ``amps`` the band amplitudes a_b (host or device float64 tensor) of
+        ``model`` (a ``BandPowerSpectrum``); the forward sets the plan's
+        spectrum to ``model(amps)`` (``fill_set_spectrum``) when it differs
+        from the current one and calls ``fill_realize``.  The backward calls
+        ``fill_backward`` with the incoming dL/dx: one adjoint solve with the
+        same operator and preconditioner gives dL/dd and dL/da_b (summed over
+        the batch when ``d`` or ``amps`` are shared).  The draw's noise is held
+        fixed by the seeds (a reparameterised gradient).  The plan needs
+        ``backward=True``.  If the plan ran other work between the forward
+        and the backward (another forward, a second backward), the backward
+        first re-runs the same forward -- realizations are reproducible bit
+        for bit from (d, P, seeds) -- so every backward sees its own
+        realization.
+        """
+
+        @staticmethod
+        def forward(ctx, d, amps, plan, model, seeds, tol):
+            a = amps.detach().to("cpu", torch.float64).numpy().copy()
+            _ensure_spectrum(plan, model, a)
+            x, stats = plan.realize(d.detach(), seeds, tol)
+            ctx.plan, ctx.model, ctx.seeds, ctx.tol, ctx.a = plan, model, seeds, tol, a
+            ctx.amps_meta = (amps.device, amps.dtype, amps.shape)
+            ctx.calls = plan.calls
+            ctx.stats = stats
+            ctx.save_for_backward(d)
+            return x
+
+        @staticmethod
+        def backward(ctx, gx):
+            (d,) = ctx.saved_tensors
+            plan = ctx.plan
+            if plan.calls != ctx.calls or not np.array_equal(plan._amps, ctx.a):
+                _ensure_spectrum(plan, ctx.model, ctx.a)
+                plan.realize(d.detach(), ctx.seeds, ctx.tol)
+            want_bands = ctx.needs_input_grad[1]
+            gx = gx.to(plan.dtype).contiguous()
+            gd, gb, _ = plan.backward(d.detach(), gx, ctx.tol, bands=want_bands)
+            grad_d = grad_a = None
+            if ctx.needs_input_grad[0]:
+                grad_d = gd.sum(0).reshape(d.shape) if d.numel() == plan.ny * plan.nx else \
+                    gd.reshape(d.shape)
+            if want_bands:
+                dev, dt, shape = ctx.amps_meta
+                grad_a = torch.from_numpy(gb.sum(0)).to(device=dev, dtype=dt).reshape(shape)
+            return grad_d, grad_a, None, None, None, None
+
+    return _FillRealize
+
+
+def _ensure_spectrum(plan, model, a):
+    """Give ``plan`` the spectrum ``model(a)`` and the band templates of
+    ``model`` (only what changed)."""
+    if getattr(plan, "_model", None) is not model:
+        plan.set_bands(model.band_of_k, model.sig_half)
+        plan._model = model
+        plan._amps = None
+    if getattr(plan, "_amps", None) is None or not np.array_equal(plan._amps, a):
+        plan.set_spectrum(model(a))
+        plan._amps = np.array(a, copy=True)
+
+
+def fill_realize_autograd(d, amps, plan, model, seeds, tol):
+    """Differentiable constrained realizations: ``FillRealize.apply``."""
+    return FillRealize.apply(d, amps, plan, model, seeds, tol)
+
+
+try:
+    import torch as _torch
+except ImportError:   # pragma: no cover
+    _torch = None
+FillRealize = _make_autograd() if _torch is not None else None

@@ -2,10 +2,13 @@
 
 Compiles the translation units in parallel with nvcc (one -gencode, static
 cudart) and links them into one shared library with a plain C ABI.  Skips the
-work when the library is newer than every source.
+work only when a SHA-256 of every source, the header, this file and the
+compiler flags, stored beside the library when it was built, matches the
+current one (a copied or stale binary with newer timestamps is rebuilt).
 """
 from __future__ import annotations
 
+import hashlib
 import os
 import shutil
 import subprocess
@@ -15,8 +18,11 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "_lib")
 LIBNAME = "libcgfill.so"
-SOURCES = ["cg_launch_f32.cu", "cg_launch_f64.cu", "cg_launch_df.cu", "cgfill.cu", "cg_static.cu",
-           "cg_subdivide.cu", "cg_generic.cu"]
+SOURCES = ["cg_launch_df_row0.cu", "cg_launch_df_row1.cu", "cg_launch_df_row2.cu",
+           "cg_launch_f32_row0.cu", "cg_launch_f32_row1.cu", "cg_launch_f64_row0.cu",
+           "cg_launch_f64_row1.cu", "cg_launch_df_col.cu", "cg_generic.cu", "cgfill.cu",
+           "cg_launch_f32_col.cu", "cg_launch_f64_col.cu", "cg_launch_f32_row.cu",
+           "cg_launch_f64_row.cu", "cg_launch_df_row.cu", "cg_static.cu", "cg_subdivide.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
@@ -33,14 +39,29 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libcgfill")
 
 
+def source_digest() -> str:
+    """SHA-256 over the sources, the header, this build script and the flags."""
+    h = hashlib.sha256()
+    deps = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC))
+    deps += [os.path.join(ROOT, "include", "cgfill.h"), os.path.abspath(__file__)]
+    for d in deps:
+        if os.path.isfile(d):
+            h.update(os.path.basename(d).encode())
+            with open(d, "rb") as f:
+                h.update(f.read())
+    h.update(" ".join(ARCH + FLAGS).encode())
+    return h.hexdigest()
+
+
+def _stamp(target: str) -> str:
+    return target + ".sha256"
+
+
 def _stale(target: str) -> bool:
-    if not os.path.exists(target):
+    if not (os.path.exists(target) and os.path.exists(_stamp(target))):
         return True
-    t = os.path.getmtime(target)
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
-    deps.append(os.path.join(ROOT, "include", "cgfill.h"))
-    deps.append(os.path.abspath(__file__))
-    return any(os.path.getmtime(d) > t for d in deps)
+    with open(_stamp(target)) as f:
+        return f.read().strip() != source_digest()
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -74,6 +95,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if res.returncode != 0:
         raise RuntimeError("link failed:\n" + res.stdout + res.stderr)
     os.replace(tmp, target)
+    with open(_stamp(target) + ".tmp", "w") as f:
+        f.write(source_digest())
+    os.replace(_stamp(target) + ".tmp", _stamp(target))
     return target
 
 

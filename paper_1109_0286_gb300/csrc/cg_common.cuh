@@ -241,7 +241,7 @@ __device__ __forceinline__ void scalar_update(int sop, CgState* st, double sum) 
       if (st->hist && st->hist_cap > 0) st->hist[0] = sum > 0.0 ? 1.0 : 0.0;
       if (!isfinite(sum)) {
         st->done = 1;
-        st->status = 4;  // NaN / Inf in the data
+        st->status = 1;  // FILL_EINVAL: NaN / Inf in the data (P is validated on the host)
       } else if (sum == 0.0) {
         st->done = 1;    // nothing to solve: u = 0
       }

@@ -116,12 +116,18 @@ cudaError_t Launch<T>::band_dot(const InstDesc<T>* d, int ninst, const DotArgs& 
 }
 
 template <typename T>
-cudaError_t Launch<T>::prepare() {
+cudaError_t Launch<T>::prepare_rows() {
   cudaError_t e = cudaSuccess;
 #define CGF_PREP_ROW(LL) if (e == cudaSuccess) e = detail::prep_row<T, LL>();
   CGF_PREP_ROW(4) CGF_PREP_ROW(5) CGF_PREP_ROW(6) CGF_PREP_ROW(7) CGF_PREP_ROW(8)
   CGF_PREP_ROW(9) CGF_PREP_ROW(10) CGF_PREP_ROW(11) CGF_PREP_ROW(12)
 #undef CGF_PREP_ROW
+  return e;
+}
+
+template <typename T>
+cudaError_t Launch<T>::prepare_cols() {
+  cudaError_t e = cudaSuccess;
 #define CGF_PREP_COL(LN)                                             \
   if (e == cudaSuccess) e = detail::allow_smem(k_col<T, LN>);        \
   if (e == cudaSuccess) e = detail::allow_smem(k_col<T, LN, true>);
@@ -130,5 +136,37 @@ cudaError_t Launch<T>::prepare() {
 #undef CGF_PREP_COL
   return e;
 }
+
+// Row-pass kernels of one transform length LL = log2(nx/2): explicit
+// instantiation (EXT empty) in the unit that compiles them, or an extern
+// declaration (EXT = extern) where they are only called, so that the lengths
+// can be spread over several translation units that compile in parallel.
+#define CGF_ROW_LL(EXT, T, LL)                                                              \
+  EXT template cudaError_t detail::row_ll<T, LL>(bool, bool, const InstDesc<T>*, int,       \
+                                                 const RowArgs&, const T*, cudaStream_t);   \
+  EXT template cudaError_t detail::prep_row<T, LL>();
+#define CGF_ROW_EXTERN_ALL(T)                                                               \
+  CGF_ROW_LL(extern, T, 4) CGF_ROW_LL(extern, T, 5) CGF_ROW_LL(extern, T, 6)                \
+  CGF_ROW_LL(extern, T, 7) CGF_ROW_LL(extern, T, 8) CGF_ROW_LL(extern, T, 9)                \
+  CGF_ROW_LL(extern, T, 10) CGF_ROW_LL(extern, T, 11) CGF_ROW_LL(extern, T, 12)
+
+// Explicit instantiation of one precision's row-pass dispatch or column-pass
+// members.
+#define CGF_INSTANTIATE_ROWS(T)                                                             \
+  CGF_ROW_EXTERN_ALL(T)                                                                     \
+  template cudaError_t Launch<T>::row(int, bool, bool, const InstDesc<T>*, int,             \
+                                      const RowArgs&, const T*, cudaStream_t);              \
+  template cudaError_t Launch<T>::prepare_rows();                                           \
+  template size_t Launch<T>::row_smem(int, int);
+#define CGF_INSTANTIATE_COLS(T)                                                             \
+  template cudaError_t Launch<T>::col(int, const InstDesc<T>*, int, const ColArgs&,         \
+                                      const T*, cudaStream_t);                              \
+  template cudaError_t Launch<T>::vec(const InstDesc<T>*, int, const VecArgs&, int,         \
+                                      cudaStream_t);                                        \
+  template cudaError_t Launch<T>::band_dot(const InstDesc<T>*, int, const DotArgs&,         \
+                                           cudaStream_t);                                   \
+  template cudaError_t Launch<T>::prepare_cols();                                           \
+  template size_t Launch<T>::col_smem(int, int);                                            \
+  template int Launch<T>::max_threads();
 
 }  // namespace cgf

@@ -1,5 +1,6 @@
 // Host-side launchers for the pass kernels, one instantiation set per
-// precision (cg_launch_f32.cu, cg_launch_f64.cu).
+// precision, each split into a row-pass and a column-pass translation unit
+// (cg_launch_{f32,f64,df}_{row,col}.cu) so that they compile in parallel.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -21,7 +22,12 @@ struct Launch {
   static size_t col_smem(int log_n, int ffts);
   static int max_threads();
   // Raise the dynamic shared-memory limit of every kernel once (not a stream op).
-  static cudaError_t prepare();
+  static cudaError_t prepare() {
+    cudaError_t e = prepare_rows();
+    return e == cudaSuccess ? prepare_cols() : e;
+  }
+  static cudaError_t prepare_rows();   // the row-pass kernels
+  static cudaError_t prepare_cols();   // the column-pass kernels
 };
 
 }  // namespace cgf

@@ -19,9 +19,11 @@
 
 #include <cmath>
 #include <mutex>
+#include <string>
 
 #include "../../include/cgfill.h"
 #include "cg_launch.h"
+#include "cg_schedule.h"
 #include "cg_types.h"
 
 namespace {
@@ -119,29 +121,54 @@ int pow2_log(int v) {
   return (1 << l) == v ? l : -1;
 }
 
+// Rejected call: records the reason for fill_last_error.
+fill_status reject(const char* why) {
+  cgf_set_last_error((std::string("fill_apply_static: ") + why).c_str());
+  return FILL_EINVAL;
+}
+
+fill_status cuda_error(cudaError_t e, const char* where) {
+  cgf_set_last_error((std::string("fill_apply_static: ") + where + ": " + cudaGetErrorString(e)).c_str());
+  return FILL_ECUDA;
+}
+
 }  // namespace
 
 extern "C" fill_status fill_apply_static(int ny, int nx, const double* P_half,
                                          const uint8_t* observed, int which, const float* in,
                                          float* out, void* stream) {
+  cgf_set_last_error("");
+  if (!P_half || !in || !out) return reject("null pointer");
+  if (in == out) return reject("in and out may not alias");
+  if (which < 0 || which > 3) return reject("which must be 0, 1, 2 or 3");
+  if (which >= 2 && !observed) return reject("which >= 2 needs the observed mask");
   const int log_l = pow2_log(nx / 2), log_n = pow2_log(ny);
-  if (!P_half || !in || !out || in == out || which < 0 || which > 3 || log_l < 4 || log_l > 12 ||
-      log_n < 4 || log_n > 13 || (which >= 2 && !observed))
-    return FILL_EINVAL;
+  if (log_l < 4 || log_l > 12 || log_n < 4 || log_n > 13)
+    return reject("grid must be powers of two with 32 <= nx <= 8192 and 16 <= ny <= 8192");
   const Layout L = layout(ny, nx);
-  if (L.total > kStaticScratchBytes) {
-    cgf_set_last_error("fill_apply_static: grid too large for the 8 MiB static scratch "
-                       "(at most about 1024 x 1024 pixels)");
-    return FILL_EINVAL;
-  }
+  if (L.total > kStaticScratchBytes)
+    return reject("grid too large for the 8 MiB static scratch (at most about 1024 x 1024 pixels)");
+  // the launch schedule of a plan with default options on this grid
+  const int rows = default_rows<float>(log_l, ny), ffts = default_ffts<float>(log_n, nx / 2 + 1);
+  if (!schedule_valid<float>(log_l, log_n, ny, rows, ffts))
+    return reject("no valid launch schedule for this grid");
+  // an error left pending by earlier, unrelated work would otherwise be
+  // reported by the launch checks below as if this call had caused it
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "a CUDA error was pending before this call");
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FILL_ECUDA;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return reject("device index beyond the supported 64");
   {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_scratch_addr[dev]) {
       void* ptr = nullptr;
-      if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || !ptr) return FILL_ECUDA;
-      if (Launch<float>::prepare() != cudaSuccess) return FILL_ECUDA;
+      e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+      if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress");
+      if (!ptr) return cuda_error(cudaErrorInvalidSymbol, "cudaGetSymbolAddress");
+      e = Launch<float>::prepare();
+      if (e != cudaSuccess) return cuda_error(e, "kernel attributes");
       g_scratch_addr[dev] = ptr;
     }
   }
@@ -150,22 +177,19 @@ extern "C" fill_status fill_apply_static(int ny, int nx, const double* P_half,
   const bool masked = which >= 2;
   k_static_setup<<<256, 256, 0, s>>>(base, L, ny, nx, P_half, masked ? observed : nullptr,
                                      (which == 1 || which == 3) ? 1 : 0, in, out);
-  if (cudaGetLastError() != cudaSuccess) return FILL_ECUDA;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "set-up kernel launch");
   const InstDesc<float>* desc = reinterpret_cast<const InstDesc<float>*>(base + L.desc);
   const float* tw = reinterpret_cast<const float*>(base + L.tw);
-  // same launch schedule as a plan's default for this grid
-  const int TT = (1 << log_l) / 16, TN = (1 << log_n) / 16;
-  int rows = TT >= 256 ? 4 : (TT >= 128 ? 4 : (TT >= 64 ? 8 : 16));
-  if (rows * TT < 256) rows = 256 / TT;
-  if (rows > ny) rows = ny;
-  int ffts = TN >= 256 ? 1 : 256 / TN;
-  if (ffts > nx / 2 + 1) ffts = nx / 2 + 1;
   const int lr = pow2_log(rows);
   RowArgs ra{ny, nx, rows, lr, masked ? OP_LOAD_W_MASK : OP_LOAD_W, SC_NONE, SKIP_NEVER, 0};
-  if (Launch<float>::row(log_l, false, true, desc, 1, ra, tw, s) != cudaSuccess) return FILL_ECUDA;
+  e = Launch<float>::row(log_l, false, true, desc, 1, ra, tw, s);
+  if (e != cudaSuccess) return cuda_error(e, "forward row pass");
   ColArgs ca{ny, nx / 2 + 1, ffts, 0, SKIP_NEVER, 0};
-  if (Launch<float>::col(log_n, desc, 1, ca, tw, s) != cudaSuccess) return FILL_ECUDA;
+  e = Launch<float>::col(log_n, desc, 1, ca, tw, s);
+  if (e != cudaSuccess) return cuda_error(e, "column pass");
   RowArgs rb{ny, nx, rows, lr, masked ? OP_STORE_Y_MASK : OP_STORE_Y, SC_NONE, SKIP_NEVER, 0};
-  if (Launch<float>::row(log_l, true, false, desc, 1, rb, tw, s) != cudaSuccess) return FILL_ECUDA;
+  e = Launch<float>::row(log_l, true, false, desc, 1, rb, tw, s);
+  if (e != cudaSuccess) return cuda_error(e, "inverse row pass");
   return FILL_OK;
 }

@@ -31,7 +31,7 @@ struct CgState {
   int iter;        // completed operator applications
   int max_iter;
   int done;        // 1 once converged / stopped; later passes skip the instance
-  int status;      // 0 ok, 3 not converged, 4 breakdown
+  int status;      // 0 ok, 1 invalid data (non-finite), 3 not converged, 4 breakdown
   int first;       // 1 before the first z: beta = 0
   int hist_cap;
   unsigned int ticket;  // last-CTA counter for the grid reductions

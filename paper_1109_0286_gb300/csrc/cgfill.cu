@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -22,6 +23,7 @@
 #include "cg_common.cuh"
 #include "cg_generic.h"
 #include "cg_launch.h"
+#include "cg_schedule.h"
 #include "cg_types.h"
 
 using namespace cgf;
@@ -115,6 +117,12 @@ struct fill_plan {
   uint2* mw = nullptr;           // mask words: observed bits, compact offset
   long long nv = 0;              // compact vector stride per instance (>= nmasked)
   std::vector<double> P_half;    // host copy of the spectrum
+  std::vector<int32_t> band_idx; // band templates of fill_set_bands (host copies), so
+  std::vector<double> band_sig;  // that fill_set_spectrum can rebuild the gradient weights
+  int nbands = 0;
+  struct fill_group* batch_group = nullptr;     // cached group of fill_realize_batch
+  std::vector<unsigned long long> batch_key;    // serials of its plans, in order
+  unsigned long long serial = 0;                // unique id of this plan
   long long launches = 0;        // kernels issued by the current call
   double relax_a = 0.0;          // max_k 1/P(k): white level of C^-1 (Sect. 5 relaxation)
   cudaGraphExec_t mixed_graph = nullptr;   // reliable-update mixed CG loop
@@ -128,6 +136,7 @@ struct fill_plan {
   std::vector<void*> dev;
   std::vector<void*> host;
   ~fill_plan() {
+    if (batch_group) fill_group_destroy(batch_group);
     if (mixed_graph) cudaGraphExecDestroy(mixed_graph);
     if (f.iter_graph) cudaGraphExecDestroy(f.iter_graph);
     if (g.iter_graph) cudaGraphExecDestroy(g.iter_graph);
@@ -160,28 +169,6 @@ struct fill_plan {
 };
 
 namespace {
-
-// ----------------------------------------------------------------- schedules
-// Default row-pass CTA: at least 16 rows or 256 threads, at most 512 threads
-// (two CTAs per SM) unless that would leave fewer than 4 rows per CTA.
-template <typename T>
-int default_rows(int log_l, int ny) {
-  const int TT = (1 << log_l) / 16;
-  int rows = std::max(16, 256 / TT);
-  const int cap = std::min(512, Launch<T>::max_threads());
-  rows = std::min(rows, std::max(cap / TT, std::min(4, Launch<T>::max_threads() / TT)));
-  while (rows > 1 && Launch<T>::row_smem(log_l, rows) > 210 * 1024) rows /= 2;
-  return std::min(rows, ny);
-}
-
-template <typename T>
-int default_ffts(int log_n, int nkx) {
-  const int TT = (1 << log_n) / 16;
-  int f = std::max(1, 256 / TT);
-  f = std::min(f, std::max(1, Launch<T>::max_threads() / TT));
-  while (f > 1 && Launch<T>::col_smem(log_n, f) > 100 * 1024) f /= 2;
-  return std::min(f, nkx);
-}
 
 // ----------------------------------------------------------------- small kernels
 template <typename T>
@@ -952,6 +939,55 @@ fill_status setup_generic(fill_plan* p) {
   return FILL_OK;
 }
 
+// P must be finite, > 0, and real-symmetric on the two self-conjugate columns
+// kx = 0 and kx = nx/2, so that C is a real symmetric operator (Sect. 4).
+bool spectrum_valid(int ny, int nx, const double* P_half) {
+  const int nkx = nx / 2 + 1;
+  for (long long i = 0; i < (long long)ny * nkx; ++i)
+    if (!(std::isfinite(P_half[i]) && P_half[i] > 0.0)) return false;
+  for (int col : {0, nx / 2})
+    for (int my = 0; my < ny; ++my) {
+      const double a = P_half[(size_t)my * nkx + col], b = P_half[(size_t)((ny - my) % ny) * nkx + col];
+      if (std::fabs(a - b) > 1e-12 * std::fabs(a)) return false;
+    }
+  return true;
+}
+
+// Spectral tables [kx][ky] with the inverse DFT's 1/n folded in: 1/(nP) for
+// C^-1 and sqrt(P)/n for C^{1/2} (Sects. 2.1, 2.3, 2.4); *relax_a = max 1/P,
+// the white level of C^-1 used by the relaxation of Sect. 5.
+void spectral_tables(int ny, int nx, const double* P_half, std::vector<double>& tinv,
+                     std::vector<double>& tsqrt, double* relax_a) {
+  const int nkx = nx / 2 + 1;
+  const double n = double(ny) * double(nx);
+  tinv.assign((size_t)nkx * ny, 0.0);
+  tsqrt.assign((size_t)nkx * ny, 0.0);
+  double a = 0.0;
+  for (int ky = 0; ky < ny; ++ky)
+    for (int kx = 0; kx < nkx; ++kx) {
+      const double P = P_half[(size_t)ky * nkx + kx];
+      a = std::max(a, 1.0 / P);
+      tinv[(size_t)kx * ny + ky] = 1.0 / (P * n);
+      tsqrt[(size_t)kx * ny + ky] = std::sqrt(P) / n;
+    }
+  *relax_a = a;
+}
+
+// Copies the tables into a precision's device buffers (synchronous).
+template <typename T>
+cudaError_t upload_tables(fill_plan* p, const std::vector<double>& tinv,
+                          const std::vector<double>& tsqrt) {
+  Precision<T>& P = prec<T>(p);
+  const size_t ntab = tinv.size();
+  std::vector<T> a(ntab), b(ntab);
+  for (size_t i = 0; i < ntab; ++i) {
+    a[i] = (T)tinv[i];
+    b[i] = (T)tsqrt[i];
+  }
+  CE(cudaMemcpy(P.t_inv, a.data(), ntab * sizeof(T), cudaMemcpyHostToDevice));
+  return cudaMemcpy(P.t_sqrt, b.data(), ntab * sizeof(T), cudaMemcpyHostToDevice);
+}
+
 template <typename T>
 fill_status setup_precision(fill_plan* p, const std::vector<double>& tinv,
                             const std::vector<double>& tsqrt, const std::vector<double>& tw) {
@@ -985,14 +1021,9 @@ fill_status setup_precision(fill_plan* p, const std::vector<double>& tinv,
     for (size_t i = 0; i < B; ++i) ptrs[i] = P.st + i;
     CK(cudaMemcpy(P.stp, ptrs.data(), B * sizeof(CgState*), cudaMemcpyHostToDevice));
   }
-  std::vector<T> a(ntab), b2(ntab), w(2 * size_t(kLmax));
-  for (size_t i = 0; i < ntab; ++i) {
-    a[i] = (T)tinv[i];
-    b2[i] = (T)tsqrt[i];
-  }
+  std::vector<T> w(2 * size_t(kLmax));
   for (size_t i = 0; i < w.size(); ++i) w[i] = (T)tw[i];
-  CK(cudaMemcpy(P.t_inv, a.data(), ntab * sizeof(T), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(P.t_sqrt, b2.data(), ntab * sizeof(T), cudaMemcpyHostToDevice));
+  CK(upload_tables<T>(p, tinv, tsqrt));
   CK(cudaMemcpy(P.tw, w.data(), w.size() * sizeof(T), cudaMemcpyHostToDevice));
   CK(cudaMemset(P.u, 0, B * nv * sizeof(T)));
   CK(cudaMemset(P.p, 0, B * nv * sizeof(T)));
@@ -1003,12 +1034,7 @@ fill_status setup_precision(fill_plan* p, const std::vector<double>& tinv,
     P.rows = p->o.rows_per_cta > 0 ? std::min(p->o.rows_per_cta, p->ny)
                                    : default_rows<T>(p->log_l, p->ny);
     P.ffts = p->o.ffts_per_cta > 0 ? p->o.ffts_per_cta : default_ffts<T>(p->log_n, p->nx / 2 + 1);
-    const int TT = (1 << p->log_l) / 16;
-    if (P.rows * TT > Launch<T>::max_threads() || p->ny % P.rows != 0 ||
-        p->ny / P.rows > kMaxPartials || Launch<T>::row_smem(p->log_l, P.rows) > 227 * 1024 ||
-        P.ffts * ((1 << p->log_n) / 16) > Launch<T>::max_threads() ||
-        Launch<T>::col_smem(p->log_n, P.ffts) > 227 * 1024)
-      return FILL_EINVAL;
+    if (!schedule_valid<T>(p->log_l, p->log_n, p->ny, P.rows, P.ffts)) return FILL_EINVAL;
   }
   CK(Launch<T>::prepare());
   for (size_t i = 0; i < B; ++i) {
@@ -1046,6 +1072,20 @@ cudaError_t init_states(fill_plan* p, double tol) {
   return cudaGetLastError();
 }
 
+// Severity of a per-realization status: invalid data outranks a breakdown,
+// which outranks a solve that ran out of iterations.
+int severity(int st) {
+  switch (st) {
+    case FILL_OK: return 0;
+    case FILL_ENOTCONV: return 1;
+    case FILL_EBREAKDOWN: return 2;
+    default: return 3;
+  }
+}
+void note_status(int st, fill_status* worst) {
+  if (severity(st) > severity(*worst)) *worst = (fill_status)st;
+}
+
 void collect_stats(fill_plan* p, fill_stats* stats, double ms, fill_status* worst) {
   const bool mixed = p->o.mode == FILL_MODE_MIXED;
   for (int i = 0; i < p->batch; ++i) {
@@ -1068,7 +1108,7 @@ void collect_stats(fill_plan* p, fill_stats* stats, double ms, fill_status* wors
     }
     st.ms = ms;
     st.launches = (int)p->launches;
-    if (st.status > *worst) *worst = (fill_status)st.status;
+    note_status(st.status, worst);
     if (stats) stats[i] = st;
   }
 }
@@ -1117,14 +1157,7 @@ fill_status fill_init(fill_plan** out, int ny, int nx, const double* P_half,
       !(o.update_delta < 1.0))
     return FILL_EINVAL;
   const int nkx = nx / 2 + 1;
-  // P: finite, positive, real-symmetric on the self-conjugate columns.
-  for (long long i = 0; i < (long long)ny * nkx; ++i)
-    if (!(std::isfinite(P_half[i]) && P_half[i] > 0.0)) return FILL_EINVAL;
-  for (int col : {0, nx / 2})
-    for (int my = 0; my < ny; ++my) {
-      const double a = P_half[(size_t)my * nkx + col], b = P_half[(size_t)((ny - my) % ny) * nkx + col];
-      if (std::fabs(a - b) > 1e-12 * std::fabs(a)) return FILL_EINVAL;
-    }
+  if (!spectrum_valid(ny, nx, P_half)) return FILL_EINVAL;
   const long long npix = (long long)ny * nx;
   long long nmasked = 0;
   std::vector<uint2> words((npix + 31) / 32, make_uint2(0u, 0u));
@@ -1156,6 +1189,10 @@ fill_status fill_init(fill_plan** out, int ny, int nx, const double* P_half,
   p->o = o;
   p->s = reinterpret_cast<cudaStream_t>(stream);
   p->P_half.assign(P_half, P_half + (size_t)ny * nkx);
+  {
+    static std::atomic<unsigned long long> next_serial{1};
+    p->serial = next_serial++;
+  }
   fill_status fs = FILL_OK;
   auto fail = [&](fill_status st) {
     delete p;
@@ -1169,15 +1206,8 @@ fill_status fill_init(fill_plan** out, int ny, int nx, const double* P_half,
     return fail(FILL_ENOMEM);
   e = cudaMemcpy(p->mw, words.data(), words.size() * sizeof(uint2), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return fail(cuda_fail(e, "upload mask"));
-  // Tables [kx][ky] with the inverse DFT's 1/n folded in.
-  std::vector<double> tinv((size_t)nkx * ny), tsqrt((size_t)nkx * ny), tw;
-  for (int ky = 0; ky < ny; ++ky)
-    for (int kx = 0; kx < nkx; ++kx) {
-      const double P = P_half[(size_t)ky * nkx + kx];
-      p->relax_a = std::max(p->relax_a, 1.0 / P);
-      tinv[(size_t)kx * ny + ky] = 1.0 / (P * double(npix));
-      tsqrt[(size_t)kx * ny + ky] = std::sqrt(P) / double(npix);
-    }
+  std::vector<double> tinv, tsqrt, tw;
+  spectral_tables(ny, nx, P_half, tinv, tsqrt, &p->relax_a);
   twiddles_host(tw);
   if (o.mode == FILL_MODE_FP32 || o.mode == FILL_MODE_MIXED) {
     fs = setup_precision<float>(p, tinv, tsqrt, tw);
@@ -1751,7 +1781,39 @@ fill_status fill_set_bands(fill_plan* p, int nbands, const int32_t* band_of_k,
   fill_status fs = set_bands_t<float>(p, nbands, band_of_k, sig_half);
   if (fs == FILL_OK) fs = set_bands_t<double>(p, nbands, band_of_k, sig_half);
   if (fs == FILL_OK) fs = set_bands_t<df>(p, nbands, band_of_k, sig_half);
+  if (fs == FILL_OK) {
+    p->band_idx.assign(band_of_k, band_of_k + nh);
+    p->band_sig.assign(sig_half, sig_half + nh);
+    p->nbands = nbands;
+  }
   return fs;
+}
+
+fill_status fill_set_spectrum(fill_plan* p, const double* P_half) {
+  if (!p || !P_half) return FILL_EINVAL;
+  if (!spectrum_valid(p->ny, p->nx, P_half)) {
+    cgf_set_last_error("fill_set_spectrum: P must be finite, > 0 and Hermitian-consistent");
+    return FILL_EINVAL;
+  }
+  // the plan's stream may still run work that reads the tables
+  CK(cudaStreamSynchronize(p->s));
+  std::vector<double> tinv, tsqrt;
+  double a = 0.0;
+  spectral_tables(p->ny, p->nx, P_half, tinv, tsqrt, &a);
+  if (p->f.used) CK(upload_tables<float>(p, tinv, tsqrt));
+  if (p->g.used) CK(upload_tables<double>(p, tinv, tsqrt));
+  if (p->h.used) CK(upload_tables<df>(p, tinv, tsqrt));
+  p->relax_a = a;
+  p->P_half.assign(P_half, P_half + (size_t)p->ny * (p->nx / 2 + 1));
+  // the band-power gradient weights depend on P
+  if (p->nbands > 0) {
+    fill_status fs = set_bands_t<float>(p, p->nbands, p->band_idx.data(), p->band_sig.data());
+    if (fs == FILL_OK) fs = set_bands_t<double>(p, p->nbands, p->band_idx.data(), p->band_sig.data());
+    if (fs == FILL_OK) fs = set_bands_t<df>(p, p->nbands, p->band_idx.data(), p->band_sig.data());
+    if (fs != FILL_OK) return fs;
+  }
+  CK(cudaDeviceSynchronize());
+  return FILL_OK;
 }
 
 fill_status fill_backward(fill_plan* p, const void* d, long long d_stride, const void* grad_x,
@@ -1986,8 +2048,16 @@ namespace {
 template <typename T>
 Ctx<T> gctx(fill_group* g, GroupClass& c) {
   fill_plan* p0 = g->plans[c.plans[0]];
-  return Ctx<T>{c.ny, c.nx, c.log_l, c.log_n, c.rows, c.ffts, c.ninst, g->precond, c.npix,
-                reinterpret_cast<const InstDesc<T>*>(c.desc), prec<T>(p0).tw, &g->launches};
+  Ctx<T> x{c.ny, c.nx, c.log_l, c.log_n, c.rows, c.ffts, c.ninst, g->precond, c.npix,
+           reinterpret_cast<const InstDesc<T>*>(c.desc), prec<T>(p0).tw, &g->launches};
+  if (p0->gen) {   // mixed-radix grid: the class shares the first plan's transforms
+    x.grow = &p0->grow;
+    x.gcol = &p0->gcol;
+    x.gwl = prec<T>(p0).gwl;
+    x.gwx = prec<T>(p0).gwx;
+    x.gwn = prec<T>(p0).gwn;
+  }
+  return x;
 }
 
 template <typename T>
@@ -2008,7 +2078,7 @@ fill_status group_setup(fill_group* g, int autotune, const char* path) {
     c.rows = prec<T>(p0).rows;
     c.ffts = prec<T>(p0).ffts;
     CK(cudaMemcpy(c.desc, c.hdesc, nb, cudaMemcpyHostToDevice));
-    if (autotune) {
+    if (autotune && !p0->gen) {   // mixed-radix classes keep their fixed schedule
       const int pr = prec_code<T>();
       if (!cache_lookup(path, pr, c.ny, c.nx, c.ninst, &c.rows, &c.ffts)) {
         Ctx<T> cx_ = gctx<T>(g, c);
@@ -2118,24 +2188,25 @@ fill_status group_realize_t(fill_group* g, const void* const* d, const uint64_t*
   if (fs != FILL_OK) return fs;
   CK(cudaStreamSynchronize(g->s));
   if (!g->host_loops) g->launches += 1 + (long long)(*g->hloop) * g->graph_kernels;
-  if (stats) {
-    for (auto& c : g->cls) {
-      int k = 0;
-      for (int pi : c.plans) {
-        fill_plan* p = g->plans[pi];
-        for (int i = 0; i < p->batch; ++i, ++k) {
-          const CgState& a = c.hst[k];
-          fill_stats st{};
-          st.iters = a.iter;
-          st.status = a.status;
-          st.rel_resid = a.bb > 0 ? std::sqrt(a.rr / a.bb) : 0.0;
-          st.true_rel_resid = -1.0;
-          stats[g->first[pi] + i] = st;
-        }
+  fill_status worst = FILL_OK;
+  for (auto& c : g->cls) {
+    int k = 0;
+    for (int pi : c.plans) {
+      fill_plan* p = g->plans[pi];
+      for (int i = 0; i < p->batch; ++i, ++k) {
+        const CgState& a = c.hst[k];
+        note_status(a.status, &worst);
+        if (!stats) continue;
+        fill_stats st{};
+        st.iters = a.iter;
+        st.status = a.status;
+        st.rel_resid = a.bb > 0 ? std::sqrt(a.rr / a.bb) : 0.0;
+        st.true_rel_resid = -1.0;
+        stats[g->first[pi] + i] = st;
       }
     }
   }
-  return FILL_OK;
+  return worst;
 }
 
 }  // namespace
@@ -2172,7 +2243,7 @@ fill_status fill_group_init(fill_group** out, fill_plan* const* plans, int count
   int flat = 0;
   for (int i = 0; i < count; ++i) {
     fill_plan* p = plans[i];
-    if (!p || p->gen || p->o.mode != mode || p->o.precond != g->precond || p->s != g->s)
+    if (!p || p->o.mode != mode || p->o.precond != g->precond || p->s != g->s)
       return fail(FILL_EINVAL);
     g->plans.push_back(p);
     g->first.push_back(flat);
@@ -2238,22 +2309,58 @@ fill_status fill_group_realize(fill_group* g, const void* const* d, const uint64
     if (!d[i] || !out[i]) return FILL_EINVAL;
   const auto t0 = std::chrono::steady_clock::now();
   g->launches = 0;
-  fill_status fs = g->mode == FILL_MODE_FP32
-                       ? group_realize_t<float>(g, d, seeds, tol, out, stats)
-                       : group_realize_t<double>(g, d, seeds, tol, out, stats);
-  if (fs != FILL_OK) return fs;
+  const fill_status worst = g->mode == FILL_MODE_FP32
+                                ? group_realize_t<float>(g, d, seeds, tol, out, stats)
+                                : group_realize_t<double>(g, d, seeds, tol, out, stats);
+  if (worst == FILL_ECUDA) return worst;
   const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  fill_status worst = FILL_OK;
   if (stats)
     for (int i = 0; i < g->ntot; ++i) {
       stats[i].ms = ms;
       stats[i].launches = (int)g->launches;
-      if (stats[i].status > worst) worst = (fill_status)stats[i].status;
     }
   return worst;
 }
 
 int fill_group_size(const fill_group* g) { return g ? g->ntot : -1; }
+
+fill_status fill_realize_batch(fill_plan* const* plans, int count, const void* const* d,
+                               const uint64_t* seeds, double tol, void* const* out,
+                               fill_stats* stats) {
+  if (!plans || count < 1 || !d || !seeds || !out || !(tol >= 0.0)) return FILL_EINVAL;
+  std::vector<unsigned long long> key(count);
+  bool groupable = true;
+  for (int i = 0; i < count; ++i) {
+    fill_plan* p = plans[i];
+    if (!p || !d[i] || !out[i]) return FILL_EINVAL;
+    key[i] = p->serial;
+    groupable = groupable && p->o.mode != FILL_MODE_MIXED && p->o.mode == plans[0]->o.mode &&
+                p->o.precond == plans[0]->o.precond && p->s == plans[0]->s;
+  }
+  if (!groupable) {
+    // one plan after another, each with its own data map shared by its batch
+    fill_status worst = FILL_OK;
+    int first = 0;
+    for (int i = 0; i < count; ++i) {
+      fill_status fs = fill_realize(plans[i], d[i], 0, seeds + first, tol, out[i],
+                                    stats ? stats + first : nullptr);
+      if (fs == FILL_ECUDA) return fs;
+      note_status(fs, &worst);
+      first += plans[i]->batch;
+    }
+    return worst;
+  }
+  fill_plan* p0 = plans[0];
+  if (!p0->batch_group || p0->batch_key != key) {
+    fill_group_destroy(p0->batch_group);
+    p0->batch_group = nullptr;
+    p0->batch_key.clear();
+    fill_status fs = fill_group_init(&p0->batch_group, plans, count, 0, nullptr);
+    if (fs != FILL_OK) return fs;
+    p0->batch_key = key;
+  }
+  return fill_group_realize(p0->batch_group, d, seeds, tol, out, stats);
+}
 
 void fill_group_destroy(fill_group* g) {
   if (!g) return;

@@ -151,3 +151,46 @@ def test_cufft_comparison_arm_computes_the_realization(ny, nx, precond):
     got = x[0].numpy()
     assert np.array_equal(got[~m], d[~m]) and it > 0
     assert np.linalg.norm(got[m] - ref.x[m]) <= 1e-9 * np.linalg.norm(ref.x[m])
+
+
+def test_static_apply_rejections_need_no_gpu(lib):
+    """fill_apply_static validates its arguments before any CUDA call and
+    records the reason (fill_last_error) on every rejection."""
+    P = np.ones((64, 33))
+    x = np.zeros((64, 64), np.float32)
+    y = np.zeros((64, 64), np.float32)
+    m = np.ones((64, 64), np.uint8)
+    cases = [
+        ((64, 64, P.ctypes.data, m.ctypes.data, 7, x.ctypes.data, y.ctypes.data, None), "which"),
+        ((64, 64, P.ctypes.data, None, 2, x.ctypes.data, y.ctypes.data, None), "mask"),
+        ((64, 64, P.ctypes.data, m.ctypes.data, 0, x.ctypes.data, x.ctypes.data, None), "alias"),
+        ((64, 60, P.ctypes.data, m.ctypes.data, 0, x.ctypes.data, y.ctypes.data, None), "powers of two"),
+        ((2048, 2048, P.ctypes.data, m.ctypes.data, 0, x.ctypes.data, y.ctypes.data, None), "too large"),
+        ((64, 64, None, m.ctypes.data, 0, x.ctypes.data, y.ctypes.data, None), "null"),
+    ]
+    for args, why in cases:
+        assert lib.fill_apply_static(*args) == 1
+        assert why in cg.fill_last_error(), (why, cg.fill_last_error())
+
+
+def test_new_entry_points_reject_bad_arguments_on_the_host(lib):
+    """fill_set_spectrum and fill_realize_batch check their arguments before
+    touching a plan or the device."""
+    P = np.ones((64, 33))
+    assert lib.fill_set_spectrum(None, P.ctypes.data) == 1
+    assert lib.fill_realize_batch(None, 1, None, None, 1e-6, None, None) == 1
+    plans = (ctypes.c_void_p * 1)(None)
+    assert lib.fill_realize_batch(plans, 0, None, None, 1e-6, None, None) == 1
+
+
+def test_band_power_spectrum_model():
+    """P(k) = sum_b a_b 1[band(k) = b] S(k) + N, the parameterisation the
+    autograd wrapper hands to fill_set_spectrum."""
+    k_lo = 2 * np.pi / 64
+    bidx, sig, noise = synth.band_templates_half(64, 64, k_lo, 8)
+    model = cg.BandPowerSpectrum(bidx, sig, noise)
+    a = np.linspace(0.5, 1.5, 8)
+    assert np.allclose(model(np.ones(8)), synth.spectrum_cmb_like(64, 64, k_lo), rtol=1e-14)
+    assert np.array_equal(model(a), a[bidx] * sig + noise)
+    with pytest.raises(ValueError):
+        model(np.ones(7))

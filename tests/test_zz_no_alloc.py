@@ -9,6 +9,7 @@ import math
 import numpy as np
 import pytest
 
+import oracle as O
 from workloads import synth
 
 torch = pytest.importorskip("torch")
@@ -32,9 +33,15 @@ def test_static_apply_matches_plan(ny, nx):
     P_dev = torch.from_numpy(P).cuda()
     obs_dev = torch.from_numpy(obs).cuda()
     stream = torch.cuda.current_stream().cuda_stream
+    Pf = O.hermitian_full(P, nx)
+    masked = obs == 0
     rng = np.random.default_rng(ny)
     for call in range(2):                       # two calls in a row reuse the scratch
-        x = torch.from_numpy(rng.standard_normal((ny, nx))).float().cuda()
+        xn = rng.standard_normal((ny, nx)).astype(np.float32)
+        x = torch.from_numpy(xn).cuda()
+        xd = xn.astype(np.float64)
+        oracle = [O.apply_power(xd, Pf, -1.0), O.apply_power(xd, Pf, 0.5),
+                  O.apply_A(xd, Pf, masked), O.apply_S(xd, Pf, masked)]
         for which in range(4):
             out = torch.empty_like(x)
             cg.fill_apply_static(ny, nx, P_dev.data_ptr(), obs_dev.data_ptr(), which,
@@ -42,6 +49,9 @@ def test_static_apply_matches_plan(ny, nx):
             torch.cuda.synchronize()
             ref = plan.apply(which, x)
             assert rel(out, ref) <= 2e-6, (call, which, rel(out, ref))
+            got = out.cpu().numpy().astype(np.float64)
+            err = np.linalg.norm(got - oracle[which]) / np.linalg.norm(oracle[which])
+            assert err <= 2e-6, (call, which, err)
 
 
 def test_static_apply_rejects_oversize():
