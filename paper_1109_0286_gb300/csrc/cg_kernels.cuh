@@ -595,24 +595,51 @@ k_vec(const InstDesc<T>* __restrict__ insts, VecArgs a) {
 // part[inst][cta][b] = sum over the CTA's half-plane modes k with band(k) = b
 // of coef(k) Re(conj(spec(k)) spec2(k)); both spectra are full 2D transforms
 // in the transposed layout, coef carries the Hermitian weight (1 on the two
-// self-conjugate columns, 2 elsewhere).
+// self-conjugate columns, 2 elsewhere).  The sums are reproducible bit for
+// bit: each warp takes fixed runs of 32 modes, the lanes of one band are
+// added in lane order by the band's lowest lane into the warp's own row of
+// partial sums, and the rows are added in warp order at the end.
+constexpr int kDotThreads = 256;
+
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kDotThreads)
 k_band_dot(const InstDesc<T>* __restrict__ insts, DotArgs a) {
-  __shared__ double hist[kMaxBands];
+  constexpr int NW = kDotThreads / 32;
+  __shared__ double hist[NW][kMaxBands];
+  __shared__ double vals[NW][32];
   const InstDesc<T>& I = insts[blockIdx.y];
-  for (int b = threadIdx.x; b < a.nbands; b += blockDim.x) hist[b] = 0.0;
-  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int b = lane; b < a.nbands; b += 32) hist[warp][b] = 0.0;
+  __syncwarp();
   const T* coef = reinterpret_cast<const T*>(a.coef);
-  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.nmodes;
-       m += (long long)gridDim.x * blockDim.x) {
-    const cx<T> x = ld_cx<T>(I.spec + 2 * m), z = ld_cx<T>(I.spec2 + 2 * m);
-    const double v = (double)((x.r * z.r + x.i * z.i) * ldg1(coef + m));
-    atomicAdd(&hist[__ldg(a.band + m)], v);
+  const long long stride = (long long)gridDim.x * NW * 32;
+  for (long long base = ((long long)blockIdx.x * NW + warp) * 32; base < a.nmodes; base += stride) {
+    const long long m = base + lane;
+    const bool valid = m < a.nmodes;
+    double v = 0.0;
+    int b = -1;
+    if (valid) {
+      const cx<T> x = ld_cx<T>(I.spec + 2 * m), z = ld_cx<T>(I.spec2 + 2 * m);
+      v = (double)((x.r * z.r + x.i * z.i) * ldg1(coef + m));
+      b = __ldg(a.band + m);
+    }
+    vals[warp][lane] = v;
+    const unsigned g = __match_any_sync(0xffffffffu, b);
+    __syncwarp();
+    if (valid && lane == __ffs(g) - 1) {
+      double sum = 0.0;
+      for (unsigned r = g; r; r &= r - 1) sum += vals[warp][__ffs(r) - 1];
+      hist[warp][b] += sum;
+    }
+    __syncwarp();
   }
   __syncthreads();
   double* out = a.part + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * a.nbands;
-  for (int b = threadIdx.x; b < a.nbands; b += blockDim.x) out[b] = hist[b];
+  for (int b = threadIdx.x; b < a.nbands; b += blockDim.x) {
+    double sum = 0.0;
+    for (int w = 0; w < NW; ++w) sum += hist[w][b];
+    out[b] = sum;
+  }
 }
 
 }  // namespace cgf

@@ -111,7 +111,7 @@ cudaError_t Launch<T>::vec(const InstDesc<T>* d, int ninst, const VecArgs& a, in
 
 template <typename T>
 cudaError_t Launch<T>::band_dot(const InstDesc<T>* d, int ninst, const DotArgs& a, cudaStream_t s) {
-  k_band_dot<T><<<dim3(kDotCtas, ninst), 256, 0, s>>>(d, a);
+  k_band_dot<T><<<dim3(kDotCtas, ninst), kDotThreads, 0, s>>>(d, a);
   return cudaGetLastError();
 }
 

@@ -255,8 +255,8 @@ def test_autograd_finite_differences_with_one_plan():
         L = (x[0] * x[0] * m).sum()
         if grad:
             L.backward()
-            return float(L), a.grad.numpy().copy()
-        return float(L)
+            return float(L.detach()), a.grad.numpy().copy()
+        return float(L.detach())
 
     _, g = loss(a0, grad=True)
     h = 1e-4
