@@ -34,10 +34,12 @@ if ROOT not in sys.path:
 
 METRIC = "constrained realizations/s at 4096^2 (rel err <= 1e-5; refined to 1e-10)"
 UNIT = "realizations/s"
-# FP64 PCG iterations for one realization of this workload at tol 1e-10
-# (measured by the FP64 GPU arm; used only to scale the oracle's per-iteration
-# CPU time to realizations/s in the reference / cpu_baseline legs).
-FP64_ITERS_WIDE4096 = 200
+# FP64 PCG iterations per realization of this workload at tol 1e-10, as the
+# FP64 GPU arm of this bench measures them (352.5 over seeds 100-107).  The
+# reference arm has no GPU run to measure them in, so it scales the oracle's
+# per-iteration time with this count; the GPU arm's cpu_baseline uses the
+# count measured in the same run.
+FP64_ITERS_WIDE4096 = 352.5
 
 # DRAM traffic (read + write bytes) of one launch of each hot-loop pass, from
 # the ncu captures summarised in profiles/k_*_fp32_4096x4096x2.md (2 instances
@@ -79,6 +81,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=0.0, help="CG tolerance (0: workload's)")
     ap.add_argument("--no-strips", action="store_true",
                     help="skip the Sect. 6 measurements (strip refinement, far-interior test)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other workloads (plain64, patch1024, batch_mixed, grad2048)")
     ap.add_argument("--update-delta", type=float, default=1e-2,
                     help="mixed mode: FP32 residual drop that triggers a true-residual update")
     ap.add_argument("--host-loops", action="store_true",
@@ -386,6 +390,127 @@ def act_measurement():
     return out, P, obs, d, spec
 
 
+def _events_ms(fn, reps):
+    """Average device time of fn() over `reps` calls (CUDA events on the
+    current stream, after one untimed call)."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = [fn() for _ in range(reps)]
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, out[-1]
+
+
+def configs_measurement():
+    """The other workloads of the benchmark's configuration list, each timed
+    by CUDA events (inputs resident, data drawn from P(k) by the library):
+
+    * plain64: the plain method in FP64 on 64^2, tol 1e-8, one realization;
+    * patch1024: 1024^2, FP32 operator with FP64-accurate reductions, tol 1e-6;
+    * batch_mixed: 256 realizations (128 x 256^2, 96 x 512^2, 32 x 1024^2),
+      each with its own mask, in ONE group call (fill_group_realize, the
+      machinery of fill_realize_batch; FP32, tol 1e-6, autotuned size
+      classes running as concurrent branches of one graph per CG loop);
+    * grad2048: 2048^2, FP32, 32 band powers: forward, adjoint (fill_backward
+      for dL/dd and dL/da_b of L = sum over M of x^2), fill_set_spectrum plus
+      forward, and the same through the torch.autograd.Function.
+    Returns the dict and the arrays the CPU legs re-check against the oracle."""
+    import math
+    import numpy as np
+    import torch
+    import paper_1109_0286_gb300 as cg
+    from workloads import synth, workload, WORKLOADS
+    out, keep = {}, {}
+
+    for name, reps in (("plain64", 20), ("patch1024", 5)):
+        P, obs, spec = workload(name)
+        mode = spec["precision"]
+        plan = cg.Plan(P, obs, mode=mode)
+        d = plan.draw([spec["data_seed"]])[0].clone()
+        seed, tol = spec["seeds"][0], spec["tol"]
+        ms, (x, st) = _events_ms(lambda: plan.realize(d, [seed], tol), reps)
+        out[name] = {"grid": list(obs.shape), "mode": mode, "tol": tol,
+                     "realizations_per_s": 1e3 / ms, "ms_per_realization": ms,
+                     "iters": st[0]["iters"], "cg_iters_per_s": st[0]["iters"] / (ms / 1e3),
+                     "status": st[0]["status"]}
+        keep[name] = (P, obs, d.double().cpu().numpy(), x[0].double().cpu().numpy(), seed, tol)
+        plan.close()
+
+    spec = WORKLOADS["batch_mixed"]
+    k_lo = 2 * math.pi / spec["k_lo_n"]
+    plans, ds, sizes = [], [], []
+    for n, count in spec["sizes"]:
+        P = synth.spectrum_cmb_like(n, n, k_lo)
+        first = None
+        for j in range(count):
+            obs = synth.mask_area_target(n, n, seed=spec["mask_seed"] * 100_000 + n * 1000 + j)
+            plans.append(cg.Plan(P, obs, mode="fp32"))
+            if first is None:
+                first = plans[-1].draw([spec["data_seed"]])[0].clone()
+            ds.append(first)
+            sizes.append(n)
+    g = cg.Group(plans, autotune=True)          # size classes with tuned schedules
+    seeds = [spec["seed0"] + i for i in range(len(plans))]
+    ms, (_, st) = _events_ms(lambda: g.realize(ds, seeds, spec["tol"]), 2)
+    g.close()
+    iters = sum(x["iters"] for x in st)
+    per_size = {}
+    for n in sorted(set(sizes)):
+        idx = [i for i, s_ in enumerate(sizes) if s_ == n]
+        pl = plans[idx[0]]
+        nbytes = sum(pl.time_pass(pid, reps=5)[1] * k for pid, k in ((0, 3), (1, 1), (2, 1), (3, 2), (4, 1)))
+        per_size[n] = {"count": len(idx), "iters_mean": sum(st[i]["iters"] for i in idx) / len(idx),
+                       "bytes_per_iter": nbytes}
+    moved = sum(per_size[sizes[i]]["bytes_per_iter"] * st[i]["iters"] for i in range(len(plans)))
+    out["batch_mixed"] = {"realizations": len(plans), "mode": "fp32", "tol": spec["tol"],
+                          "realizations_per_s": len(plans) / (ms / 1e3), "ms_per_call": ms,
+                          "cg_iters_per_s": iters / (ms / 1e3),
+                          "algorithmic_GB_per_s": moved / (ms / 1e3) / 1e9,
+                          "all_ok": all(x["status"] == 0 for x in st),
+                          "per_size": {str(k): v for k, v in per_size.items()},
+                          "note": "one fill_group_realize call; algorithmic bytes = "
+                                  "sum of iterations x the per-iteration pass bytes"}
+    for p_ in plans:
+        p_.close()
+    del plans, ds
+    torch.cuda.empty_cache()
+
+    P, obs, spec = workload("grad2048")
+    n = obs.shape[0]
+    bidx, sig, noise = synth.band_templates_half(n, n, spec["k_lo"], spec["nbands"])
+    model = cg.BandPowerSpectrum(bidx, sig, noise)
+    plan = cg.Plan(P, obs, mode="fp32", backward=True)
+    plan.set_bands(bidx, sig)
+    d = plan.draw([spec["data_seed"]])[0].clone()
+    seed, tol = spec["seeds"][0], spec["tol"]
+    m = torch.from_numpy(obs == 0).cuda()
+    ms_f, (x, _) = _events_ms(lambda: plan.realize(d, [seed], tol), 3)
+    gx = (2.0 * x * m).contiguous()
+    ms_b, (_, _, sb) = _events_ms(lambda: plan.backward(d, gx, tol), 3)
+    amps = np.linspace(0.9, 1.1, spec["nbands"])
+
+    def respectrum():
+        plan.set_spectrum(model(amps))
+        return plan.realize(d, [seed], tol)
+    ms_s, _ = _events_ms(respectrum, 3)
+    a = torch.ones(spec["nbands"], dtype=torch.float64, requires_grad=True)
+
+    def autograd_step():
+        xx = cg.FillRealize.apply(d, a, plan, model, [seed], tol)
+        (xx[0] * xx[0] * m).sum().backward()
+        return xx
+    ms_a, _ = _events_ms(autograd_step, 3)
+    out["grad2048"] = {"grid": [n, n], "mode": "fp32", "tol": tol, "nbands": spec["nbands"],
+                       "forward_ms": ms_f, "backward_ms": ms_b, "adjoint_iters": sb[0]["iters"],
+                       "set_spectrum_plus_forward_ms": ms_s,
+                       "autograd_forward_backward_ms": ms_a}
+    plan.close()
+    return out, keep
+
+
 def cufft_pcg_realize(P_half, masked, d, y, tol, precond=True, max_iter=5000, check_every=8):
     """Timed comparison only, never part of the library: the same constrained
     realization (Sects. 2.1-2.4) written with PyTorch's FFT (cuFFT on the GPU)
@@ -435,6 +560,79 @@ def cufft_pcg_realize(P_half, masked, d, y, tol, precond=True, max_iter=5000, ch
     return torch.where(masked, y + u, d), it
 
 
+def cufft_refined_realize(P_half, masked, d, y, tol, inner_tol=1e-5, max_outer=20):
+    """Timed comparison only: the same realization with PyTorch FFT (cuFFT)
+    in the library's mixed-precision scheme -- FP32 PCG solves of
+    A delta = r inside an FP64 iterative refinement (r = b - A u recomputed
+    with FP64 transforms) until ||r|| <= tol ||b||.  P_half, d, y: FP64
+    tensors; masked: bool.  Returns (x, inner iterations, outer steps)."""
+    import torch
+    ny, nx = masked.shape
+    m64 = masked.to(torch.float64)
+    Pinv64 = 1.0 / P_half
+
+    def A64(v):
+        return m64 * torch.fft.irfft2(torch.fft.rfft2(m64 * v) * Pinv64, s=(ny, nx))
+
+    b = -m64 * torch.fft.irfft2(torch.fft.rfft2((1.0 - m64) * (d - y)) * Pinv64, s=(ny, nx))
+    bn = torch.sqrt((b * b).sum(dim=(1, 2)))
+    u = torch.zeros_like(b)
+    P32, zeros32 = P_half.float(), torch.zeros_like(b, dtype=torch.float32)
+    inner = outer = 0
+    for outer in range(1, max_outer + 1):
+        r = b - A64(u)
+        if bool((torch.sqrt((r * r).sum(dim=(1, 2))) <= tol * bn).all()):
+            break
+        delta, it = cufft_pcg_solve(P32, masked, r.float(), inner_tol)
+        inner += it
+        u = u + delta.double()
+    return torch.where(masked, y + u, d), inner, outer
+
+
+def cufft_pcg_solve(P_half, masked, b, tol, precond=True, max_iter=5000, check_every=8):
+    """PCG with B = S S on A u = b (PyTorch FFT, the dtype of b) until
+    ||r|| <= tol ||b|| for every map.  Returns (u, iterations)."""
+    import torch
+    ny, nx = masked.shape
+    m = masked.to(b.dtype)
+    Pinv, Psq = 1.0 / P_half, torch.sqrt(P_half)
+
+    def apply(x, Ps):
+        return torch.fft.irfft2(torch.fft.rfft2(x) * Ps, s=(ny, nx))
+
+    def A(v):
+        return m * apply(m * v, Pinv)
+
+    def prec(v):
+        return m * apply(m * apply(m * v, Psq), Psq) if precond else v
+
+    def dot(a, c):
+        return (a * c).sum(dim=(1, 2))
+
+    u = torch.zeros_like(b)
+    r = b.clone()
+    z = prec(r)
+    p = z.clone()
+    rz = dot(r, z)
+    thr = tol * tol * dot(b, b)
+    it = 0
+    while it < max_iter:
+        q = A(p)
+        pq = dot(p, q)
+        alpha = torch.where(pq > 0, rz / pq, torch.zeros_like(pq))[:, None, None]
+        u += alpha * p
+        r -= alpha * q
+        it += 1
+        if it % check_every == 0 and bool((dot(r, r) <= thr).all()):
+            break
+        z = prec(r)
+        rz_new = dot(r, z)
+        beta = torch.where(rz > 0, rz_new / rz, torch.zeros_like(rz))[:, None, None]
+        rz = rz_new
+        p = z + beta * p
+    return u, it
+
+
 def cufft_arm(P, obs, d, batch, tol64):
     """cuFFT-based PCG timed beside the library (spec comparison):
     FP32 to 1e-5 on `batch` maps, FP64 to tol64 on one map; each timed
@@ -443,6 +641,33 @@ def cufft_arm(P, obs, d, batch, tol64):
     each, then one timed by CUDA events."""
     import torch
     out = {"note": "PyTorch FFT (cuFFT) + elementwise ops; comparison only"}
+    try:   # the library's own scheme with cuFFT: FP32 PCG inside FP64 refinement to tol64
+        dev = torch.device("cuda")
+        Ph = torch.as_tensor(P, dtype=torch.float64, device=dev)
+        masked = torch.as_tensor(obs == 0, device=dev)
+        dd = d.to(dtype=torch.float64)
+        ny, nx = masked.shape
+
+        def refined(seed):
+            g = torch.Generator(device=dev).manual_seed(seed)
+            xi = torch.randn((batch, ny, nx), generator=g, dtype=torch.float64, device=dev)
+            y = torch.fft.irfft2(torch.fft.rfft2(xi) * torch.sqrt(Ph), s=(ny, nx))
+            return cufft_refined_realize(Ph, masked, dd, y, tol64)
+
+        refined(1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, inner, outer = refined(2)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out["fp32_pcg_fp64_refined"] = {"realizations_per_s": batch / (ms / 1e3), "ms_per_step": ms,
+                                        "batch": batch, "tol": tol64, "inner_iters": inner,
+                                        "refinement_steps": outer, "inner_tol": 1e-5}
+    except Exception as e:   # comparison only: never fail the bench line
+        out["fp32_pcg_fp64_refined"] = {"error": repr(e)[:200]}
+    torch.cuda.empty_cache()
     for name, dt, B, tol in (("fp32", torch.float32, batch, 1e-5), ("fp64", torch.float64, 1, tol64)):
         try:
             dev = torch.device("cuda")
@@ -502,9 +727,33 @@ def oracle_sample(P, obs, d, seed, iters):
 
 
 def threads_used():
-    """Threads the oracle actually runs on: numpy.fft (pocketfft) and the
-    element-wise ufuncs it uses are single-threaded."""
-    return 1
+    """Host threads the oracle's transforms run on (its own C FFT splits rows
+    and columns over every host core; its element-wise NumPy steps run on
+    one)."""
+    import oracle as O
+    return O.threads()
+
+
+def oracle_check(P, obs, d_np, x_np, seed, tol):
+    """The error of one GPU realization against the FP64 oracle on the same
+    inputs: the oracle's draw y for the seed, its right-hand side b, and the
+    certificate ||b - A u|| / ||b|| of the GPU's correction u = x - y on the
+    masked pixels, with the oracle's own operator A (no solve needed at full
+    size); also the draw's relative error on M and whether the observed
+    pixels equal the data bit for bit."""
+    import numpy as np
+    import oracle as O
+    nx = obs.shape[1]
+    Pf = O.hermitian_full(P, nx)
+    m = obs == 0
+    t0 = time.perf_counter()
+    y = O.draw(Pf, seed)
+    b = O.rhs(Pf, obs, d_np, y)
+    u = np.where(m, x_np - y, 0.0)
+    r = b - O.apply_A(u, Pf, m)
+    return {"true_rel_resid_oracle": float(np.linalg.norm(r) / np.linalg.norm(b)),
+            "observed_bit_exact": bool(np.array_equal(x_np[~m], d_np[~m])),
+            "tol": tol, "seed": int(seed), "ms": (time.perf_counter() - t0) * 1e3}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -597,7 +846,7 @@ def run_gpu(args):
     with Clocks(local) as clk:
         e0.record(stream)
         for k in range(args.steps):
-            _, st = plan.realize(d, seeds(args.warmup + k), tol)
+            last_x, st = plan.realize(d, seeds(args.warmup + k), tol)
             iters += sum(s["iters"] for s in st)
             launches += st[0]["launches"]
             worst_resid = max([worst_resid] + [s["true_rel_resid"] if s["true_rel_resid"] >= 0
@@ -605,6 +854,8 @@ def run_gpu(args):
         e1.record(stream)
         torch.cuda.synchronize()
     barrier()
+    last_seed = seeds(args.warmup + args.steps - 1)[0]
+    last_x = last_x[0].clone()
     ms = e0.elapsed_time(e1)
     ms_max = max_over_ranks(ms, dist, "cuda")
     value = job_throughput(B, args.steps, world, ms_max)
@@ -722,19 +973,56 @@ def run_gpu(args):
                 "iters_per_realization": it64 / (B * args.fp64_steps)}
         p64.close()
 
-    # cuFFT-based PCG (timed comparison, not part of the library)
+    # cuFFT-based PCG (timed comparison, not part of the library), and the
+    # library's FP32 mode at the cuFFT FP32 arm's tolerance
     cufft = cufft_arm(P, obs, d, B, tol) if (rank == 0 and not args.no_fp64) else None
+    if cufft is not None:
+        p32 = cg.Plan(P, obs, mode="fp32", batch=B)
+        d32 = d.float().contiguous()
+        ms32, (_, st32) = _events_ms(lambda: p32.realize(d32, seeds(0), 1e-5), 1)
+        cufft["library_fp32_same_tol"] = {"realizations_per_s": B / (ms32 / 1e3), "ms_per_step": ms32,
+                                          "batch": B, "tol": 1e-5,
+                                          "iters_per_realization": sum(x["iters"] for x in st32) / B}
+        p32.close()
+        del d32
+        torch.cuda.empty_cache()
 
-    cpu = None
+    configs, keep = (None, None)
+    if rank == 0 and not args.no_configs:
+        configs, keep = configs_measurement()
+
+    cpu, oracle_err = None, None
     if rank == 0 and world == 1 and not args.no_cpu:
+        import numpy as np
+        import oracle as O
         dn = d.cpu().numpy().astype("float64")
-        setup, t_iter = oracle_sample(P, obs, dn, spec["seeds"][0], 1)
+        cpu_iters = 3
+        setup, t_iter = oracle_sample(P, obs, dn, spec["seeds"][0], cpu_iters)
         n_it = fp64["iters_per_realization"] if fp64 else FP64_ITERS_WIDE4096
         cpu = {"value": 1.0 / (setup + n_it * t_iter), "unit": UNIT, "cores": threads_used(),
                "kind": "oracle",
-               "sample": (f"NumPy FP64 oracle on the full {ny}x{nx} workload: draw + RHS "
-                          f"({setup:.1f} s) and 1 preconditioned CG iteration ({t_iter:.1f} s), "
-                          f"scaled to {n_it:.0f} iterations per realization")}
+               "sample": (f"FP64 oracle (own C FFT on {threads_used()} host threads, NumPy "
+                          f"element-wise) on the full {ny}x{nx} workload: draw + RHS "
+                          f"({setup:.1f} s) and {cpu_iters} preconditioned CG iterations "
+                          f"({t_iter:.2f} s each), scaled to the {n_it:.1f} iterations per "
+                          f"realization the FP64 GPU PCG needed in this run")}
+        # error of the headline's last realization against the oracle
+        x_last = last_x.double().cpu().numpy()
+        oracle_err = oracle_check(P, obs, dn, x_last, last_seed, tol)
+        # whole realizations on the host cores, checked against the GPU's
+        if keep is not None:
+            for name in ("plain64", "patch1024"):
+                Pk, obsk, dk, xk, seedk, tolk = keep[name]
+                t0 = time.perf_counter()
+                ref = O.realize(Pk, obsk, dk, seedk, tol=tolk)
+                sec = time.perf_counter() - t0
+                mk = obsk == 0
+                configs[name]["cpu_baseline"] = {
+                    "value": 1.0 / sec, "unit": UNIT, "cores": threads_used(), "kind": "oracle",
+                    "sample": f"one whole realization ({ref.pcg.iters} iterations)"}
+                configs[name]["rel_err_vs_oracle_same_tol"] = float(
+                    np.linalg.norm(xk[mk] - ref.x[mk]) / np.linalg.norm(ref.x[mk]))
+                configs[name]["observed_bit_exact"] = bool(np.array_equal(xk[~mk], dk[~mk]))
         if act is not None:   # the same oracle sample on the Sect. 3 map
             a_out, aP, aobs, ad, aspec = act
             setup, t_iter = oracle_sample(aP, aobs, ad.cpu().numpy().astype("float64"),
@@ -768,6 +1056,8 @@ def run_gpu(args):
                 "passes": pass_table, "lanczos": lanczos, "relax": relax, "strips": strip_meas,
                 "far_interior": far, "laplace_ms": lms,
                 "act7000x600": act[0] if act is not None else None,
+                "configs": configs,
+                "oracle_check": oracle_err,
                 "clocks": clk.summary(),
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)

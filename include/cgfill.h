@@ -56,7 +56,8 @@ typedef enum {
   FILL_ENOMEM = 2,      /* device or pinned host allocation failed */
   FILL_ENOTCONV = 3,    /* iteration limit reached before the tolerance */
   FILL_EBREAKDOWN = 4,  /* p^T A p <= 0, r^T z <= 0 or a non-finite value inside the solve */
-  FILL_ETIMEOUT = 5,    /* reserved: bounded device wait expired */
+  FILL_ETIMEOUT = 5,    /* a kernel's bounded wait for an asynchronous copy expired
+                           (reported by fill_realize, fill_backward or a group call) */
   FILL_ECUDA = 6        /* CUDA runtime error (message via fill_last_error) */
 } fill_status;
 
@@ -93,6 +94,11 @@ typedef struct {
                             the residual recomputed in double-float whenever the FP32
                             residual has fallen by this factor; default 1e-2.  0:
                             restarted iterative refinement (FP32 solves to inner_tol) */
+  int col_kernel;        /* column pass of the FP32 table passes (power-of-two grids):
+                            0 register-fed kernel (default); 1 persistent kernel fed by
+                            bulk copies (TMA) into a double-buffered shared-memory slot;
+                            the same arithmetic, so the results are identical.
+                            fill_autotune may switch it */
 } fill_opts;
 
 typedef struct {

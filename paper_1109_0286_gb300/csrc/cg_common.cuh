@@ -102,6 +102,45 @@ __device__ __forceinline__ void st_pair(T* p, T a, T b) {
   *reinterpret_cast<typename V2<T>::t*>(p) = v;
 }
 
+// Complex load of data read once by this kernel: no allocation in L1, so the
+// twiddle table cached there stays resident (coherent path: the kernel may
+// write the same address after reading it).
+template <typename T>
+__device__ __forceinline__ cx<T> ld_stream_cx(const T* p);
+template <>
+__device__ __forceinline__ cx<float> ld_stream_cx<float>(const float* p) {
+  float x, y;
+  asm volatile("ld.global.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(x), "=f"(y) : "l"(p));
+  return {x, y};
+}
+template <>
+__device__ __forceinline__ cx<double> ld_stream_cx<double>(const double* p) {
+  double x, y;
+  asm volatile("ld.global.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(x), "=d"(y) : "l"(p));
+  return {x, y};
+}
+template <>
+__device__ __forceinline__ cx<df> ld_stream_cx<df>(const df* p) {
+  float a, b, c, d;
+  asm volatile("ld.global.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(a), "=f"(b), "=f"(c), "=f"(d)
+               : "l"(p));
+  return {df(a, b), df(c, d)};
+}
+
+// Asks the copy engine to bring elements [c0, c1) of a vector into L2 (one
+// instruction for the whole range; rounded out to 16-byte boundaries, which
+// stay inside the vector's allocation since its length is padded to a
+// multiple of 64 elements).
+template <typename S>
+__device__ __forceinline__ void prefetch_l2(const S* v, long long c0, long long c1) {
+  if (!v || c1 <= c0) return;
+  const uintptr_t b = reinterpret_cast<uintptr_t>(v + c0) & ~uintptr_t(15);
+  const uintptr_t e = (reinterpret_cast<uintptr_t>(v + c1) + 15) & ~uintptr_t(15);
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b), "r"((uint32_t)(e - b))
+               : "memory");
+}
+
 // Pixel pairs of the caller's maps, converted to / from the pass element type.
 template <typename T>
 __device__ __forceinline__ void ld_map_pair(const typename MapOf<T>::type* p, T& a, T& b) {

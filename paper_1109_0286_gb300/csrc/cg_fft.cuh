@@ -63,6 +63,24 @@ struct XBuf<df> {   // same layout as FP64: split real / imaginary arrays of 8-b
   }
 };
 
+// Unpadded FP32 exchange area of one transform (L interleaved complex
+// elements): element i lives at i ^ ((i >> 4) & 15).  The XOR keeps every
+// access of fft_regs free of bank conflicts -- the contiguous stage reads,
+// the stride-16 writes after the first radix-16 stage, the stride-R0 writes
+// after a leading radix-2/4/8 stage -- without the padding of XBuf, so an
+// area that received a contiguous TMA copy can serve as the exchange area.
+struct XBufSw {
+  float2* c;
+  __device__ __forceinline__ explicit XBufSw(float2* base) : c(base) {}
+  __device__ __forceinline__ void st(int i, cx<float> v) const {
+    c[i ^ ((i >> 4) & 15)] = make_float2(v.r, v.i);
+  }
+  __device__ __forceinline__ cx<float> ld(int i) const {
+    const float2 t = c[i ^ ((i >> 4) & 15)];
+    return {t.x, t.y};
+  }
+};
+
 // a * (-i) for the forward transform, a * (+i) for the inverse.
 template <typename T, bool INV>
 __device__ __forceinline__ cx<T> mul_mi(cx<T> a) {
@@ -221,8 +239,8 @@ struct XBar {
   }
 };
 
-template <typename T, int LOG_L, bool INV>
-__device__ __forceinline__ void fft_regs(cx<T> (&v)[16], const XBuf<T>& xb, int tid,
+template <typename T, int LOG_L, bool INV, typename XB>
+__device__ __forceinline__ void fft_regs(cx<T> (&v)[16], const XB& xb, int tid,
                                          const T* __restrict__ tw, XBar first = XBar{0, 0},
                                          XBar bar = XBar{0, 0}) {
   constexpr int TT = (1 << LOG_L) / 16;

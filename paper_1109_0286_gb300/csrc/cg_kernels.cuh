@@ -10,6 +10,7 @@
 // projections P_x, the white-noise draw, the CG vector updates and the inner
 // products -- is fused into the row passes.
 #pragma once
+#include "cg_async.cuh"
 #include "cg_fft.cuh"
 
 namespace cgf {
@@ -66,6 +67,45 @@ template <typename T, typename S>
 __device__ __forceinline__ void stc(S* v, const PairIdx& q, T a0, T a1) {
   if (q.m0) v[q.i0] = (S)a0;
   if (q.m1) v[q.i1] = (S)a1;
+}
+
+// The compact CG-vector elements of a CTA's rows form one contiguous range
+// [c0, c1) (vectors are stored in row-major order of the masked pixels): its
+// first word's offset, and the last word's offset plus its masked count.
+// One thread asks the copy engine to bring the ranges the op will read into
+// L2, so that the per-pixel-pair gathers later in the pass hit L2 instead of
+// waiting on HBM one chunk after another.
+template <typename T>
+__device__ __forceinline__ void prefetch_compact(const InstDesc<T>& I, int op, const uint2* mws,
+                                                 int nwords) {
+  const uint2 w0 = mws[0], w1 = mws[nwords - 1];
+  const long long c0 = w0.y, c1 = (long long)w1.y + __popc(~w1.x);
+  switch (op) {
+    case OP_R_UPD:
+      prefetch_l2(I.r, c0, c1);
+      prefetch_l2(I.q, c0, c1);
+      prefetch_l2(I.u, c0, c1);
+      prefetch_l2(I.p, c0, c1);
+      break;
+    case OP_P_UPD_Z:
+      prefetch_l2(I.z, c0, c1);
+      prefetch_l2(I.p, c0, c1);
+      break;
+    case OP_P_UPD_R:
+      prefetch_l2(I.r, c0, c1);
+      prefetch_l2(I.p, c0, c1);
+      break;
+    case OP_LOAD_R: prefetch_l2(I.r, c0, c1); break;
+    case OP_LOAD_U: prefetch_l2(I.u, c0, c1); break;
+    case OP_U64_UPD:
+      prefetch_l2(I.u, c0, c1);
+      prefetch_l2(I.dlt, c0, c1);
+      break;
+    case OP_Q: prefetch_l2(I.p, c0, c1); break;
+    case OP_Z: prefetch_l2(I.r, c0, c1); break;
+    case OP_RES: prefetch_l2(I.b, c0, c1); break;
+    default: break;
+  }
 }
 
 // ----------------------------------------------------------------- sources
@@ -301,7 +341,7 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
     const T* spec = (a.spec_sel ? I.spec2 : I.spec) + 2 * ((size_t)kk * ny + y0 + rr);
     cx<T> t[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) t[i] = ldg_cx<T>(spec + i * tstep);
+    for (int i = 0; i < 16; ++i) t[i] = ld_stream_cx<T>(spec + i * tstep);
     cx<T> tn{};
     if (threadIdx.x < rows)
       tn = ldg_cx<T>((a.spec_sel ? I.spec2 : I.spec) + 2 * ((size_t)L * ny + y0 + threadIdx.x));
@@ -310,6 +350,7 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
     for (int i = 0; i < 16; ++i) tile[HOIST ? tb + i * ts : tix(kk + i * TT, rr)] = t[i];
     if (threadIdx.x < rows) tile[tix(L, threadIdx.x)] = tn;
     __syncthreads();
+    if (threadIdx.x == 0 && !OUT_SPEC) prefetch_compact(I, a.op, mws, rows * TT);
     // C2R: Z[k] = (X[k] + conj X[L-k]) + i e^{+2 pi i k / nx} (X[k] - conj X[L-k])
     const cx<T> wt = twiddle<T>(tw, tid * TWS);
     const int cb = tix(tid, row), cm = tix(L - tid, row);
@@ -360,6 +401,7 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
     }
   } else {
     __syncthreads();   // mask words
+    if (threadIdx.x == 0) prefetch_compact(I, a.op, mws, rows * TT);
     const T alpha = (T)I.st->alpha, beta = (T)I.st->beta;
     switch (a.op) {
       case OP_R_UPD: src_fill<T, TT, OP_R_UPD>(I, mwr, rowpix, tid, alpha, beta, v, acc); break;
@@ -447,7 +489,7 @@ k_col(const InstDesc<T>* __restrict__ insts, ColArgs a, const T* __restrict__ tw
   const T* src = PRE ? I.spec + 2 * (long long)(act ? kx : 0) * N : col;
   cx<T> v[16];
 #pragma unroll
-  for (int e = 0; e < 16; ++e) v[e] = act ? ld_cx<T>(src + 2 * (tid + e * TT)) : cx<T>{(T)0, (T)0};
+  for (int e = 0; e < 16; ++e) v[e] = act ? ld_stream_cx<T>(src + 2 * (tid + e * TT)) : cx<T>{(T)0, (T)0};
   if constexpr (!PRE) fft_regs<T, LOG_N, false>(v, xb, tid, tw, bar, bar);
   if (a.table >= 0) {
     const T* tab = (a.table >= 2 ? I.kt + (long long)(a.table - 2) * a.nkx * N
@@ -462,6 +504,126 @@ k_col(const InstDesc<T>* __restrict__ insts, ColArgs a, const T* __restrict__ tw
   if (act) {
 #pragma unroll
     for (int e = 0; e < 16; ++e) st_cx<T>(col + 2 * (tid + e * TT), v[e]);
+  }
+}
+
+// ----------------------------------------------------------------- column pass (TMA)
+// FP32 column pass of the CG loops (forward column FFT, x 1/(nP) or x sqrt(P)/n,
+// inverse FFT) as a persistent kernel fed by bulk copies.  A work item is a
+// block of F consecutive spectrum rows (kx .. kx+F-1) of one instance: F N
+// contiguous complex values and the matching F N table values.  CTA c takes
+// a contiguous run of items (kx-major, instance-minor, so an item's table
+// rows were usually just read by the previous item and come from L2).  While
+// item j is transformed, one thread has the copy engine bring item j+1 into
+// the other of two shared-memory slots (cp.async.bulk, completion on the
+// slot's mbarrier), so no thread waits on global loads.  The landing area of
+// each column is then its exchange area (XBufSw, unpadded), and the results
+// go to global memory straight from registers.  Items of instances that are
+// done are skipped.  Every wait is bounded: on a timeout the CTA sets
+// *a.err, waits (bounded) for the copies it issued, and returns.
+constexpr int kColTmaSlots = 2;
+
+__host__ __device__ __forceinline__ size_t col_tma_smem(int log_n, int ffts) {
+  const size_t fn = size_t(ffts) << log_n;
+  return kColTmaSlots * fn * (sizeof(float2) + sizeof(float)) + 2 * kColTmaSlots * sizeof(uint64_t);
+}
+
+template <int LOG_N>
+__global__ void __launch_bounds__(LOG_N >= 13 ? 512 : 256, LOG_N >= 13 ? 1 : 2)
+k_col_tma(const InstDesc<float>* __restrict__ insts, ColArgs a, const float* __restrict__ tw,
+          int ninst) {
+  constexpr int N = 1 << LOG_N, TT = N / 16;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int F = a.ffts;
+  const size_t fn = size_t(F) * N;
+  float2* slot0 = reinterpret_cast<float2*>(smem_raw);
+  float* tab0 = reinterpret_cast<float*>(smem_raw + kColTmaSlots * fn * sizeof(float2));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + kColTmaSlots * fn * (sizeof(float2) + sizeof(float)));
+  const int f = threadIdx.x / TT, tid = threadIdx.x - f * TT;
+  const XBar fbar = XBar::make(TT, F, f);
+  const int nkb = (a.nkx + F - 1) / F;
+  const long long total = (long long)nkb * ninst;
+  const long long per = (total + gridDim.x - 1) / gridDim.x;
+  const long long first = (long long)blockIdx.x * per;
+  const long long end = first + per < total ? first + per : total;
+
+  auto next_item = [&](long long i) {
+    while (i < end && skip_instance(a.check_done, insts[i % ninst].st)) ++i;
+    return i;
+  };
+  auto issue = [&](long long i, int sl) {   // one thread
+    const InstDesc<float>& I = insts[i % ninst];
+    const int kx0 = (int)(i / ninst) * F;
+    const int nc = a.nkx - kx0 < F ? a.nkx - kx0 : F;
+    const uint32_t bs = (uint32_t)nc * N * sizeof(float2), bt = (uint32_t)nc * N * sizeof(float);
+    mbar_arrive_expect(&bar[sl], bs + bt);
+    bulk_g2s(slot0 + sl * fn, I.spec + 2 * (long long)kx0 * N, bs, &bar[sl]);
+    bulk_g2s(tab0 + sl * fn, (a.table ? I.t_sqrt : I.t_inv) + (long long)kx0 * N, bt, &bar[sl]);
+  };
+
+  if (threadIdx.x == 0) {
+    for (int sl = 0; sl < kColTmaSlots; ++sl) mbar_init(&bar[sl], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  long long it = next_item(first);
+  if (threadIdx.x == 0 && it < end) issue(it, 0);
+  uint32_t phase = 0u;                   // bit sl: parity of slot sl's next completion
+  uint32_t pending = it < end ? 1u : 0u;  // bit sl: a copy into slot sl is in flight
+  int sl = 0;
+  while (it < end) {
+    const long long nxt = next_item(it + 1);
+    if (nxt < end) {
+      // the other slot's previous item is finished (CTA barrier at the end of
+      // the last iteration): hand it to the copy engine
+      if (threadIdx.x == 0) {
+        fence_proxy_async();
+        issue(nxt, sl ^ 1);
+      }
+      pending |= 1u << (sl ^ 1);
+    }
+    const bool ok = mbar_wait(&bar[sl], (phase >> sl) & 1u);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        if (a.err) atomicExch(a.err, 1);
+        for (int q = 0; q < kColTmaSlots; ++q)   // let the copies in flight land (bounded)
+          if (((pending >> q) & 1u) && !(q == sl && ok)) mbar_wait(&bar[q], (phase >> q) & 1u);
+      }
+      __syncthreads();
+      return;
+    }
+    pending &= ~(1u << sl);
+    phase ^= 1u << sl;
+
+    const InstDesc<float>& I = insts[it % ninst];
+    const int kx = (int)(it / ninst) * F + f;
+    const bool act = kx < a.nkx;
+    float2* buf = slot0 + sl * fn + size_t(f) * N;
+    const float* tb = tab0 + sl * fn + size_t(f) * N;
+    cx<float> v[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const float2 t = act ? buf[tid + e * TT] : make_float2(0.f, 0.f);
+      v[e] = cx<float>{t.x, t.y};
+    }
+    const XBufSw xb(buf);
+    fft_regs<float, LOG_N, false>(v, xb, tid, tw, fbar, fbar);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = scal(v[e], act ? tb[tid + e * TT] : 0.f);
+    // the inverse transform reloads its twiddles (an opaque copy of the table
+    // pointer): keeping the forward transform's alive across the table
+    // multiply would cost some 60 registers and spills
+    const float* tw_inv;
+    asm("mov.b64 %0, %1;" : "=l"(tw_inv) : "l"(tw));
+    fft_regs<float, LOG_N, true>(v, xb, tid, tw_inv, fbar, fbar);
+    if (act) {
+      float* col = I.spec + 2 * (long long)kx * N;
+#pragma unroll
+      for (int e = 0; e < 16; ++e) st_cx<float>(col + 2 * (tid + e * TT), v[e]);
+    }
+    __syncthreads();   // slot sl is free again
+    it = nxt;
+    sl ^= 1;
   }
 }
 

@@ -1,5 +1,7 @@
 // Size dispatch: runtime log2 sizes -> compile-time kernel instantiations.
 #pragma once
+#include <type_traits>
+
 #include "cg_kernels.cuh"
 #include "cg_launch.h"
 
@@ -54,9 +56,44 @@ cudaError_t row_ll(bool in_spec, bool out_spec, const InstDesc<T>* d, int ninst,
   return cudaGetLastError();
 }
 
+// Persistent CTAs of the TMA column pass (SMs x resident CTAs), per log2 N;
+// set by prepare_cols.
+static int g_col_tma_ctas[14] = {};
+
+// Column FFTs per item of the TMA column pass: F N = 4096 complex values
+// (256 threads) when N <= 4096, one 8192-point column otherwise.
+inline int col_tma_ffts(int log_n) { return log_n >= 12 ? 1 : (4096 >> log_n); }
+
+template <int LN>
+cudaError_t prep_col_tma() {
+  const int F = col_tma_ffts(LN), threads = F * ((1 << LN) / 16);
+  const size_t sm = col_tma_smem(LN, F);
+  cudaError_t e = cudaFuncSetAttribute(k_col_tma<LN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm);
+  int dev = 0, sms = 0, per = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_col_tma<LN>, threads, sm);
+  if (e == cudaSuccess) g_col_tma_ctas[LN] = sms * (per > 0 ? per : 1);
+  return e;
+}
+
 template <typename T, int LN>
 cudaError_t col_ln(const InstDesc<T>* d, int ninst, const ColArgs& a, const T* tw, cudaStream_t s) {
   constexpr int TT = (1 << LN) / 16;
+  if constexpr (std::is_same<T, float>::value) {
+    // the CG loops' table passes: persistent, bulk-copy fed
+    if (a.variant == 1 && (a.table == 0 || a.table == 1) && !a.pre && a.spec_sel == 0 &&
+        g_col_tma_ctas[LN] > 0) {
+      const int F = col_tma_ffts(LN);
+      ColArgs b = a;
+      b.ffts = F;
+      const long long items = (long long)((a.nkx + F - 1) / F) * ninst;
+      const int grid = (int)(items < g_col_tma_ctas[LN] ? items : g_col_tma_ctas[LN]);
+      k_col_tma<LN><<<grid, F * TT, col_tma_smem(LN, F), s>>>(d, b, tw, ninst);
+      return cudaGetLastError();
+    }
+  }
   dim3 grid(ninst, (a.nkx + a.ffts - 1) / a.ffts), block(a.ffts * TT);
   const size_t sm = Launch<T>::col_smem(LN, a.ffts);
   if (a.pre)
@@ -128,6 +165,12 @@ cudaError_t Launch<T>::prepare_rows() {
 template <typename T>
 cudaError_t Launch<T>::prepare_cols() {
   cudaError_t e = cudaSuccess;
+  if constexpr (std::is_same<T, float>::value) {
+#define CGF_PREP_TMA(LN) if (e == cudaSuccess) e = detail::prep_col_tma<LN>();
+    CGF_PREP_TMA(4) CGF_PREP_TMA(5) CGF_PREP_TMA(6) CGF_PREP_TMA(7) CGF_PREP_TMA(8)
+    CGF_PREP_TMA(9) CGF_PREP_TMA(10) CGF_PREP_TMA(11) CGF_PREP_TMA(12) CGF_PREP_TMA(13)
+#undef CGF_PREP_TMA
+  }
 #define CGF_PREP_COL(LN)                                             \
   if (e == cudaSuccess) e = detail::allow_smem(k_col<T, LN>);        \
   if (e == cudaSuccess) e = detail::allow_smem(k_col<T, LN, true>);

@@ -195,6 +195,9 @@ struct ColArgs {
   int spec_sel;     // 0: spec, 1: spec2
   int pre;          // 1: the input is spec, already column-transformed (table >= 0; the
                     // forward FFT is skipped and the result goes to spec_sel's buffer)
+  int* err;         // device error flag (set to 1 when a bounded wait gave up), or null
+  int variant;      // FP32 table passes: 0 register-fed kernel, 1 persistent bulk-copy-fed
+                    // kernel (chosen per grid by the autotuner)
 };
 
 // Band-binned spectral products for the band-power gradient.

@@ -97,6 +97,7 @@ struct Precision {
   InstDesc<T>* desc = nullptr;  // device, batch
   InstDesc<T>* hdesc = nullptr; // pinned
   int rows = 0, ffts = 0;
+  int col_variant = 0;          // column kernel of the table passes (ColArgs::variant)
   bool used = false;
   cudaGraphExec_t iter_graph = nullptr;   // CG loop graph (conditional WHILE node)
   long long iter_graph_kernels = 0;       // kernels per loop body
@@ -127,8 +128,9 @@ struct fill_plan {
   double relax_a = 0.0;          // max_k 1/P(k): white level of C^-1 (Sect. 5 relaxation)
   cudaGraphExec_t mixed_graph = nullptr;   // reliable-update mixed CG loop
   long long mixed_graph_kernels = 0;
+  int* dev_err = nullptr;        // device: set by a kernel whose bounded wait gave up
   int* loop_counter = nullptr;   // device [2]: loop bodies, IF bodies of the last loop graph
-  int* hloop = nullptr;          // pinned mirror
+  int* hloop = nullptr;          // pinned: loop counters [0..1], device error flag [2]
   long long if_kernels = 0;      // kernels inside the update IF node
   Precision<float> f;
   Precision<double> g;           // FP64 mode
@@ -241,10 +243,12 @@ Precision<df>& prec<df>(fill_plan* p) { return p->h; }
 template <typename T>
 struct Ctx {
   int ny, nx, log_l, log_n, rows, ffts, ninst, precond;
+  int col_variant;
   long long npix;
   const InstDesc<T>* desc;
   const T* tw;
   long long* launches;
+  int* err = nullptr;             // device error flag of bounded waits
   const GenLen* grow = nullptr;   // mixed-radix grids: transforms and twiddles
   const GenLen* gcol = nullptr;
   const T* gwl = nullptr;
@@ -256,7 +260,8 @@ template <typename T>
 Ctx<T> ctx(fill_plan* p, int ninst = -1) {
   Precision<T>& P = prec<T>(p);
   Ctx<T> c{p->ny, p->nx, p->log_l, p->log_n, P.rows, P.ffts,
-           ninst < 0 ? p->batch : ninst, p->o.precond, p->npix, P.desc, P.tw, &p->launches};
+           ninst < 0 ? p->batch : ninst, p->o.precond, P.col_variant, p->npix, P.desc, P.tw,
+           &p->launches, p->dev_err};
   if (p->gen) {
     c.grow = &p->grow;
     c.gcol = &p->gcol;
@@ -281,7 +286,7 @@ template <typename T>
 cudaError_t col(const Ctx<T>& c, cudaStream_t s, int table, int skip, int spec_sel = 0,
                 int pre = 0) {
   ++*c.launches;
-  ColArgs a{c.ny, c.nx / 2 + 1, c.ffts, table, skip, spec_sel, pre};
+  ColArgs a{c.ny, c.nx / 2 + 1, c.ffts, table, skip, spec_sel, pre, c.err, c.col_variant};
   if (c.gcol) return GenLaunch<T>::col(c.desc, c.ninst, a, *c.gcol, c.gwn, s);
   return Launch<T>::col(c.log_n, c.desc, c.ninst, a, c.tw, s);
 }
@@ -1035,6 +1040,7 @@ fill_status setup_precision(fill_plan* p, const std::vector<double>& tinv,
                                    : default_rows<T>(p->log_l, p->ny);
     P.ffts = p->o.ffts_per_cta > 0 ? p->o.ffts_per_cta : default_ffts<T>(p->log_n, p->nx / 2 + 1);
     if (!schedule_valid<T>(p->log_l, p->log_n, p->ny, P.rows, P.ffts)) return FILL_EINVAL;
+    P.col_variant = std::is_same<T, float>::value ? p->o.col_kernel : 0;
   }
   CK(Launch<T>::prepare());
   for (size_t i = 0; i < B; ++i) {
@@ -1113,6 +1119,23 @@ void collect_stats(fill_plan* p, fill_stats* stats, double ms, fill_status* wors
   }
 }
 
+// Queues the read-back of the device error flag on the plan's stream (before
+// the call's final synchronisation).
+cudaError_t queue_err_readback(fill_plan* p) {
+  return cudaMemcpyAsync(&p->hloop[2], p->dev_err, sizeof(int), cudaMemcpyDeviceToHost, p->s);
+}
+
+// After the final synchronisation: a kernel whose bounded wait gave up set
+// the flag; report it once (FILL_ETIMEOUT) and clear it.
+fill_status take_err(fill_plan* p) {
+  if (!p->hloop[2]) return FILL_OK;
+  p->hloop[2] = 0;
+  cudaMemsetAsync(p->dev_err, 0, sizeof(int), p->s);
+  cudaStreamSynchronize(p->s);
+  g_last_error = "a bounded device wait timed out (a kernel gave up waiting for a copy)";
+  return FILL_ETIMEOUT;
+}
+
 }  // namespace
 
 // =================================================================== C ABI
@@ -1154,7 +1177,7 @@ fill_status fill_init(fill_plan** out, int ny, int nx, const double* P_half,
   if (o.mode < 0 || o.mode > 2 || o.batch < 1 || o.batch > 65535 || o.max_iter < 1 ||
       o.max_refine < 1 || o.host_loops < 0 || o.host_loops > 1 || !(o.inner_tol > 0.0) || o.history_cap < 0 || o.rows_per_cta < 0 ||
       o.ffts_per_cta < 0 || o.backward < 0 || o.backward > 1 || !(o.update_delta >= 0.0) ||
-      !(o.update_delta < 1.0))
+      !(o.update_delta < 1.0) || o.col_kernel < 0 || o.col_kernel > 1)
     return FILL_EINVAL;
   const int nkx = nx / 2 + 1;
   if (!spectrum_valid(ny, nx, P_half)) return FILL_EINVAL;
@@ -1202,8 +1225,11 @@ fill_status fill_init(fill_plan** out, int ny, int nx, const double* P_half,
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap2, cudaStreamNonBlocking);
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaStreamCreate"));
   if (p->dalloc(&p->mw, words.size()) != cudaSuccess) return fail(FILL_ENOMEM);
-  if (p->dalloc(&p->loop_counter, 2) != cudaSuccess || p->halloc(&p->hloop, 2) != cudaSuccess)
+  if (p->dalloc(&p->loop_counter, 2) != cudaSuccess || p->halloc(&p->hloop, 3) != cudaSuccess ||
+      p->dalloc(&p->dev_err, 1) != cudaSuccess)
     return fail(FILL_ENOMEM);
+  e = cudaMemset(p->dev_err, 0, sizeof(int));
+  if (e != cudaSuccess) return fail(cuda_fail(e, "fill_init"));
   e = cudaMemcpy(p->mw, words.data(), words.size() * sizeof(uint2), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return fail(cuda_fail(e, "upload mask"));
   std::vector<double> tinv, tsqrt, tw;
@@ -1298,10 +1324,12 @@ fill_status realize_impl(fill_plan* p, const void* d, long long d_stride, const 
     CK(cudaMemcpyAsync(p->h.hst, p->h.st, sizeof(CgState) * B, cudaMemcpyDeviceToHost, p->s));
     CK(cudaMemcpyAsync(p->f.hst, p->f.st, sizeof(CgState) * B, cudaMemcpyDeviceToHost, p->s));
   }
+  CK(queue_err_readback(p));
   CK(cudaStreamSynchronize(p->s));
   const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   collect_stats(p, stats, ms, &worst);
-  return worst;
+  const fill_status te = take_err(p);
+  return te != FILL_OK ? te : worst;
 }
 }  // namespace
 
@@ -1837,11 +1865,13 @@ fill_status fill_backward(fill_plan* p, const void* d, long long d_stride, const
   } else {
     CK(cudaMemcpyAsync(p->g.hst, p->g.st, sizeof(CgState) * p->batch, cudaMemcpyDeviceToHost, p->s));
   }
+  CK(queue_err_readback(p));
   CK(cudaStreamSynchronize(p->s));
   const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   fill_status worst = FILL_OK;
   collect_stats(p, stats, ms, &worst);
-  return worst;
+  const fill_status te = take_err(p);
+  return te != FILL_OK ? te : worst;
 }
 
 long long fill_masked_count(const fill_plan* p) { return p ? p->nmasked : -1; }
@@ -1925,6 +1955,7 @@ cudaError_t autotune_ctx(Ctx<T> c, cudaStream_t s, int* best_rows, int* best_fft
     }
   }
   best = 1e30f;
+  c.col_variant = 0;
   for (int f = 1; f <= nkx && f <= 64; f *= 2) {
     if (f * TN > Launch<T>::max_threads() || Launch<T>::col_smem(c.log_n, f) > limit) continue;
     c.ffts = f;
@@ -1935,7 +1966,26 @@ cudaError_t autotune_ctx(Ctx<T> c, cudaStream_t s, int* best_rows, int* best_fft
       *best_ffts = f;
     }
   }
+  if (std::is_same<T, float>::value) {
+    // the persistent bulk-copy-fed column kernel (its own column blocking):
+    // recorded as ffts = -1
+    c.col_variant = 1;
+    float ms = 0.f;
+    CE(time_launches(s, 3, [&](cudaStream_t st) { return col<T>(c, st, 0, false); }, &ms));
+    if (ms < best) *best_ffts = -1;
+  }
   return cudaSuccess;
+}
+
+// Applies a tuned column choice: ffts > 0 register-fed kernel with that many
+// FFTs per CTA, ffts = -1 the bulk-copy-fed kernel (the CTA shape stays).
+void apply_col_choice(int tuned, int* ffts, int* variant) {
+  if (tuned < 0) {
+    *variant = 1;
+  } else {
+    *variant = 0;
+    *ffts = tuned;
+  }
 }
 
 // Autotune cache: lines "prec ny nx ninst rows ffts".
@@ -1974,7 +2024,7 @@ fill_status tune_plan_t(fill_plan* p, const char* path) {
   Precision<T>& P = prec<T>(p);
   if (!P.used) return FILL_OK;
   const int pr = prec_code<T>();
-  int rows = P.rows, ffts = P.ffts;
+  int rows = P.rows, ffts = P.col_variant ? -1 : P.ffts;
   if (!cache_lookup(path, pr, p->ny, p->nx, p->batch, &rows, &ffts)) {
     fill_desc<T>(p, nullptr, 0, nullptr, nullptr, nullptr);
     CK(upload_desc<T>(p));
@@ -1982,9 +2032,12 @@ fill_status tune_plan_t(fill_plan* p, const char* path) {
     CK(autotune_ctx<T>(ctx<T>(p), p->s, &rows, &ffts));
     cache_store(path, pr, p->ny, p->nx, p->batch, rows, ffts);
   }
-  if (rows != P.rows || ffts != P.ffts) {
+  int nf = P.ffts, nv = P.col_variant;
+  apply_col_choice(ffts, &nf, &nv);
+  if (rows != P.rows || nf != P.ffts || nv != P.col_variant) {
     P.rows = rows;
-    P.ffts = ffts;
+    P.ffts = nf;
+    P.col_variant = nv;
     if (P.iter_graph) {
       cudaGraphExecDestroy(P.iter_graph);
       P.iter_graph = nullptr;
@@ -2003,7 +2056,7 @@ fill_status tune_plan_t(fill_plan* p, const char* path) {
 namespace {
 
 struct GroupClass {
-  int ny = 0, nx = 0, log_l = 0, log_n = 0, rows = 0, ffts = 0, ninst = 0;
+  int ny = 0, nx = 0, log_l = 0, log_n = 0, rows = 0, ffts = 0, ninst = 0, col_variant = 0;
   long long npix = 0;
   std::vector<int> plans;       // group indices of the plans in this class
   void* desc = nullptr;         // device InstDesc<T>[ninst]
@@ -2048,8 +2101,9 @@ namespace {
 template <typename T>
 Ctx<T> gctx(fill_group* g, GroupClass& c) {
   fill_plan* p0 = g->plans[c.plans[0]];
-  Ctx<T> x{c.ny, c.nx, c.log_l, c.log_n, c.rows, c.ffts, c.ninst, g->precond, c.npix,
-           reinterpret_cast<const InstDesc<T>*>(c.desc), prec<T>(p0).tw, &g->launches};
+  Ctx<T> x{c.ny, c.nx, c.log_l, c.log_n, c.rows, c.ffts, c.ninst, g->precond, c.col_variant,
+           c.npix, reinterpret_cast<const InstDesc<T>*>(c.desc), prec<T>(p0).tw, &g->launches,
+           p0->dev_err};
   if (p0->gen) {   // mixed-radix grid: the class shares the first plan's transforms
     x.grow = &p0->grow;
     x.gcol = &p0->gcol;
@@ -2077,16 +2131,24 @@ fill_status group_setup(fill_group* g, int autotune, const char* path) {
     fill_plan* p0 = g->plans[c.plans[0]];
     c.rows = prec<T>(p0).rows;
     c.ffts = prec<T>(p0).ffts;
+    c.col_variant = prec<T>(p0).col_variant;
     CK(cudaMemcpy(c.desc, c.hdesc, nb, cudaMemcpyHostToDevice));
     if (autotune && !p0->gen) {   // mixed-radix classes keep their fixed schedule
       const int pr = prec_code<T>();
-      if (!cache_lookup(path, pr, c.ny, c.nx, c.ninst, &c.rows, &c.ffts)) {
+      int tuned = c.col_variant ? -1 : c.ffts;
+      if (cache_lookup(path, pr, c.ny, c.nx, c.ninst, &c.rows, &tuned)) {
+        apply_col_choice(tuned, &c.ffts, &c.col_variant);
+      } else {
         Ctx<T> cx_ = gctx<T>(g, c);
         k_state_init<T><<<(c.ninst + 127) / 128, 128, 0, g->s>>>(
             reinterpret_cast<const InstDesc<T>*>(c.desc), c.ninst, 0.0, 1, 1);
         CK(cudaGetLastError());
-        CK(autotune_ctx<T>(cx_, g->s, &c.rows, &c.ffts));
-        cache_store(path, pr, c.ny, c.nx, c.ninst, c.rows, c.ffts);
+        int rows = c.rows;
+        tuned = c.ffts;
+        CK(autotune_ctx<T>(cx_, g->s, &rows, &tuned));
+        cache_store(path, pr, c.ny, c.nx, c.ninst, rows, tuned);
+        c.rows = rows;
+        apply_col_choice(tuned, &c.ffts, &c.col_variant);
       }
     }
   }
@@ -2186,9 +2248,12 @@ fill_status group_realize_t(fill_group* g, const void* const* d, const uint64_t*
     return cudaMemcpyAsync(c.hst, c.st, sizeof(CgState) * c.ninst, cudaMemcpyDeviceToHost, c.cs);
   });
   if (fs != FILL_OK) return fs;
+  fill_plan* p0 = g->plans[0];   // its stream is the group's
+  CK(queue_err_readback(p0));
   CK(cudaStreamSynchronize(g->s));
   if (!g->host_loops) g->launches += 1 + (long long)(*g->hloop) * g->graph_kernels;
   fill_status worst = FILL_OK;
+  if (take_err(p0) != FILL_OK) return FILL_ETIMEOUT;
   for (auto& c : g->cls) {
     int k = 0;
     for (int pi : c.plans) {

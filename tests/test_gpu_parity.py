@@ -476,3 +476,27 @@ def test_wide4096_full_size_certificate():
         cert = np.linalg.norm(np.where(m, O.apply_power(w, Pf, -1.0), 0)) / np.linalg.norm(b)
         assert cert <= 3e-10, cert
         assert stats[i]["true_rel_resid"] <= spec["tol"]
+
+
+@pytest.mark.parametrize("ny,nx,batch", [(256, 256, 3), (64, 128, 2), (2048, 2048, 1)])
+def test_bulk_copy_column_kernel_gives_identical_results(ny, nx, batch):
+    """The persistent column kernel fed by bulk copies (col_kernel=1) runs
+    the same transforms as the register-fed one: FP32 realizations, the
+    mixed mode's FP32 iterations and the operators are equal bit for bit."""
+    P, obs = case(ny, nx, seed=ny + 3)
+    d = O.draw(O.hermitian_full(P, nx), 5)
+    seeds = list(range(11, 11 + batch))
+    for mode, tol in (("fp32", 1e-6), ("mixed", 1e-10)):
+        dt = torch.float32 if mode == "fp32" else torch.float64
+        outs = []
+        for ck in (0, 1):
+            plan = cg.Plan(P, obs, mode=mode, batch=batch, col_kernel=ck)
+            x, st = plan.realize(gpu_map(d, dt), seeds, tol)
+            outs.append((x, [s_["iters"] for s_ in st]))
+            if mode == "fp32":
+                xx = gpu_map(np.random.default_rng(1).standard_normal((ny, nx)), dt)
+                outs[-1] += (plan.apply(0, xx), plan.apply(3, xx))
+            plan.close()
+        assert torch.equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1], mode
+        if mode == "fp32":
+            assert torch.equal(outs[0][2], outs[1][2]) and torch.equal(outs[0][3], outs[1][3])

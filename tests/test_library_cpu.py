@@ -63,9 +63,28 @@ def test_host_only_calls(lib):
     lib.fill_destroy(None)
 
 
-def test_struct_layouts():
-    assert ctypes.sizeof(cg.FillOpts) == 56
-    assert ctypes.sizeof(cg.FillStats) == 40
+def test_struct_layouts(tmp_path):
+    """The ctypes mirrors have the sizes and field offsets the C compiler
+    gives the header's structs."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "sizes.c"
+    fields = [f for f, _ in cg.FillOpts._fields_]
+    src.write_text(
+        '#include <stddef.h>\n#include <stdio.h>\n#include "cgfill.h"\nint main(void) {\n'
+        '  printf("%zu %zu\\n", sizeof(fill_opts), sizeof(fill_stats));\n'
+        + "".join(f'  printf("%zu\\n", offsetof(fill_opts, {f}));\n' for f in fields)
+        + "  return 0;\n}\n")
+    exe = tmp_path / "sizes"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    assert int(out[0]) == ctypes.sizeof(cg.FillOpts)
+    assert int(out[1]) == ctypes.sizeof(cg.FillStats)
+    for f, off in zip(fields, out[2:]):
+        assert getattr(cg.FillOpts, f).offset == int(off), f
 
 
 def test_mask_generators():
