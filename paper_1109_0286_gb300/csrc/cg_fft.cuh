@@ -8,8 +8,10 @@
 // radix-16 stages.  On entry thread t holds x[t + e L/16] in v[e]; on exit it
 // holds X[t + e L/16] -- the same positions -- so a forward transform, a
 // diagonal multiply and an inverse transform chain without a shared-memory
-// round trip.  Between stages data goes through shared memory (XBuf).  A radix-16 stage needs W^(jm r),
-// r = 1..15: three table loads and at most four complex products each.
+// round trip.  Between stages data goes through shared memory (XBuf).  A
+// radix-16 stage needs W^(jm r), r = 1..15: fifteen loads from its own
+// table of correctly rounded values (stw_* in cg_types.h), or three master
+// table entries and complex products (TAB = false).
 #pragma once
 #include "cg_common.cuh"
 
@@ -239,7 +241,11 @@ struct XBar {
   }
 };
 
-template <typename T, int LOG_L, bool INV, typename XB>
+// TAB: twiddles from the per-stage tables (the row passes: 5-11% faster at
+// 4096^2), else from three entries of the master table and complex products
+// (the column passes: the tables' loads raise their register pressure into
+// spills, 21% slower).
+template <typename T, int LOG_L, bool INV, bool TAB = true, typename XB>
 __device__ __forceinline__ void fft_regs(cx<T> (&v)[16], const XB& xb, int tid,
                                          const T* __restrict__ tw, XBar first = XBar{0, 0},
                                          XBar bar = XBar{0, 0}) {
@@ -278,22 +284,43 @@ __device__ __forceinline__ void fft_regs(cx<T> (&v)[16], const XB& xb, int tid,
 #pragma unroll
       for (int e = 0; e < 16; ++e) v[e] = xb.ld(tid + e * TT);
       const int jm = tid & (ns - 1);
-      const int stride = kLmax / (ns * 16);
-      // W^(jm r) for r = 1..15 from three table entries (W^jm, W^4jm, W^8jm)
-      // and at most four complex products each (a few ulp).
-      cx<T> w[16];
-      w[1] = twiddle<T>(tw, jm * stride);
-      w[4] = twiddle<T>(tw, 4 * jm * stride);
-      w[8] = twiddle<T>(tw, 8 * jm * stride);
-      w[2] = cmul(w[1], w[1]);
-      w[3] = cmul(w[2], w[1]);
-      w[5] = cmul(w[4], w[1]);
-      w[6] = cmul(w[4], w[2]);
-      w[7] = cmul(w[4], w[3]);
+      // W_{16 ns}^(jm r), r = 1..15: correctly rounded entries of the stage's
+      // table ([r - 1][jm]; consecutive jm of a warp read consecutive entries)
+      if constexpr (TAB) {
+        // Loaded in three groups of five, each applied before the next group is
+        // issued (the empty asm with a memory clobber keeps the compiler from
+        // hoisting all fifteen loads, which would need 30 more registers).
+        const T* ts = tw + 2 * (kLmax + stw_base(LOG_L) + stw_stage_off(LOG_L, s) + jm);
 #pragma unroll
-      for (int r = 9; r < 16; ++r) w[r] = cmul(w[8], w[r - 8]);
+        for (int g = 0; g < 3; ++g) {
+          cx<T> w[5];
 #pragma unroll
-      for (int r = 1; r < 16; ++r) v[r] = INV ? cmulc(v[r], w[r]) : cmul(v[r], w[r]);
+          for (int k = 0; k < 5; ++k) w[k] = ldg_cx<T>(ts + 2 * (5 * g + k) * ns);
+#pragma unroll
+          for (int k = 0; k < 5; ++k) {
+            const int r = 5 * g + k + 1;
+            v[r] = INV ? cmulc(v[r], w[k]) : cmul(v[r], w[k]);
+          }
+          asm volatile("" ::: "memory");
+        }
+      } else {
+        // W^(jm r) from three master-table entries (W^jm, W^4jm, W^8jm) and at
+        // most four complex products each (a few ulp)
+        const int stride = kLmax / (ns * 16);
+        cx<T> w[16];
+        w[1] = twiddle<T>(tw, jm * stride);
+        w[4] = twiddle<T>(tw, 4 * jm * stride);
+        w[8] = twiddle<T>(tw, 8 * jm * stride);
+        w[2] = cmul(w[1], w[1]);
+        w[3] = cmul(w[2], w[1]);
+        w[5] = cmul(w[4], w[1]);
+        w[6] = cmul(w[4], w[2]);
+        w[7] = cmul(w[4], w[3]);
+#pragma unroll
+        for (int r = 9; r < 16; ++r) w[r] = cmul(w[8], w[r - 8]);
+#pragma unroll
+        for (int r = 1; r < 16; ++r) v[r] = INV ? cmulc(v[r], w[r]) : cmul(v[r], w[r]);
+      }
     }
     dft16<T, INV>(v);
     if (!last) {

@@ -56,7 +56,7 @@ Layout layout(int ny, int nx) {
   const size_t nkx = size_t(nx) / 2 + 1, npix = size_t(ny) * nx;
   Layout L{};
   size_t o = 0;
-  L.tw = o;   o = align256(o + 2 * sizeof(float) * kLmax);
+  L.tw = o;   o = align256(o + 2 * sizeof(float) * kTwEntries);
   L.tab = o;  o = align256(o + sizeof(float) * nkx * ny);
   L.spec = o; o = align256(o + 2 * sizeof(float) * nkx * ny);
   L.bits = o; o = align256(o + sizeof(uint2) * ((npix + 31) / 32));
@@ -67,7 +67,8 @@ Layout layout(int ny, int nx) {
   return L;
 }
 
-// Builds everything a call needs inside the scratch: twiddles W_8192^m, the
+// Builds everything a call needs inside the scratch: twiddles W_8192^m and
+// the FFT stage tables, the
 // table (1/(nP) or sqrt(P)/n in the transposed [kx][ky] layout), the mask
 // bits, a zeroed CG state and the instance descriptor.
 __global__ void k_static_setup(unsigned char* base, Layout L, int ny, int nx, const double* P,
@@ -85,6 +86,21 @@ __global__ void k_static_setup(unsigned char* base, Layout L, int ny, int nx, co
     sincospi(2.0 * double(m) / double(kLmax), &s, &c);
     tw[2 * m] = (float)c;
     tw[2 * m + 1] = (float)-s;
+  }
+  // the per-stage tables of every power-of-two length (layout in cg_types.h)
+  for (long long e = tid; e < kStwEntries; e += nthr) {
+    int l = 4;
+    while (l < 13 && e >= stw_base(l + 1)) ++l;
+    int rem = (int)(e - stw_base(l));
+    int st = stw_first(l);
+    while (st + 1 < l / 4 && rem >= stw_stage_off(l, st + 1)) ++st;
+    rem -= stw_stage_off(l, st);
+    const int ns = stw_ns(l, st);
+    const int r = 1 + rem / ns, jm = rem % ns;
+    double s, c;
+    sincospi(2.0 * double((long long)jm * r) / double(16LL * ns), &s, &c);
+    tw[2 * (kLmax + e)] = (float)c;
+    tw[2 * (kLmax + e) + 1] = (float)-s;
   }
   for (long long t = tid; t < (long long)nkx * ny; t += nthr) {
     const int kx = (int)(t / ny), ky = (int)(t % ny);

@@ -14,6 +14,12 @@
 #pragma once
 #include <cstdint>
 
+#ifdef __CUDACC__
+#define CGF_HD __host__ __device__
+#else
+#define CGF_HD
+#endif
+
 namespace cgf {
 
 // Scalar state of one CG solve (Sect. 2.4), kept on the device so the
@@ -44,11 +50,6 @@ struct CgState {
   double* coef;    // CG coefficients: alpha_j at [2j], beta_j at [2j+1], j < hist_cap
 };
 
-#ifdef __CUDACC__
-#define CGF_HD __host__ __device__
-#else
-#define CGF_HD
-#endif
 
 // Double-float number hi + lo (|lo| <= ulp(hi) / 2, about 48 significant
 // bits): the high-precision type of the mixed mode, whose arithmetic runs on
@@ -219,6 +220,37 @@ struct VecArgs {
 };
 
 constexpr int kLmax = 8192;        // twiddle master table: W_8192^m
+
+// Per-stage twiddle tables of the register-resident FFT (cg_fft.cuh), stored
+// after the master table.  A transform of length 2^log (4 <= log <= 13) has
+// one leading stage of radix 2^(log mod 4) (if nonzero) and log/4 radix-16
+// stages; the radix-16 stage s runs on sub-transforms of size
+// ns = 2^(log mod 4) 16^s and needs W_{16 ns}^(jm r), jm < ns, r = 1..15
+// (none for the very first stage, ns = 1).  Its table holds them as
+// [r - 1][jm], so that the threads of a warp (consecutive jm) read
+// consecutive entries.
+CGF_HD constexpr int stw_ns0(int log) { return (log % 4) ? (1 << (log % 4)) : 1; }
+CGF_HD constexpr int stw_first(int log) { return (log % 4) ? 0 : 1; }   // first twiddled stage
+CGF_HD constexpr int stw_ns(int log, int s) {
+  int ns = stw_ns0(log);
+  for (int t = 0; t < s; ++t) ns *= 16;
+  return ns;
+}
+// entries of the stages before s of length 2^log
+CGF_HD constexpr int stw_stage_off(int log, int s) {
+  int o = 0;
+  for (int t = stw_first(log); t < s; ++t) o += 15 * stw_ns(log, t);
+  return o;
+}
+CGF_HD constexpr int stw_size(int log) { return stw_stage_off(log, log / 4); }
+// entries of the lengths 2^4 .. 2^(log-1) (the tables of length 2^log start here)
+CGF_HD constexpr int stw_base(int log) {
+  int o = 0;
+  for (int l = 4; l < log; ++l) o += stw_size(l);
+  return o;
+}
+constexpr int kStwEntries = stw_base(14);   // all lengths 2^4 .. 2^13
+constexpr int kTwEntries = kLmax + kStwEntries;   // complex entries of a twiddle buffer
 constexpr int kMaxPartials = 4096; // CTAs per instance per reducing pass
 constexpr int kMaxBands = 64;      // band-power gradient bins
 constexpr int kDotCtas = 256;      // CTAs per instance of the band-binned product

@@ -56,10 +56,44 @@ int ilog2(int v) {
   return l;
 }
 
-// W_kLmax^m = exp(-2 pi i m / kLmax) from quadrant-reduced angles.
+// exp(-2 pi i num / den) in FP64 from an angle reduced to [0, pi/4]
+// (octant symmetry), so the result carries the full accuracy of cos / sin.
+void unit_root(long long num, long long den, double* re, double* im) {
+  const long long m = 8 * (((num % den) + den) % den);
+  const int o = (int)(m / den);                 // octant 0..7
+  const double f = double(m % den) / double(den);
+  const double th = (o & 1) ? (1.0 - f) * M_PI / 4.0 : f * M_PI / 4.0;
+  const double c0 = std::cos(th), s0 = std::sin(th);
+  double c, sn;
+  switch (o) {
+    case 0: c = c0; sn = s0; break;
+    case 1: c = s0; sn = c0; break;
+    case 2: c = -s0; sn = c0; break;
+    case 3: c = -c0; sn = s0; break;
+    case 4: c = -c0; sn = -s0; break;
+    case 5: c = -s0; sn = -c0; break;
+    case 6: c = s0; sn = -c0; break;
+    default: c = c0; sn = -s0; break;
+  }
+  *re = c;
+  *im = -sn;
+}
+
+// W_kLmax^m = exp(-2 pi i m / kLmax) from quadrant-reduced angles, followed
+// by the per-stage tables of every power-of-two length (stw_* in cg_types.h).
 void twiddles_host(std::vector<double>& tw) {
   const int N = kLmax, Q = N / 4;
-  tw.resize(2 * size_t(N));
+  tw.resize(2 * size_t(kTwEntries));
+  for (int l = 4; l <= 13; ++l)
+    for (int st = stw_first(l); st < l / 4; ++st) {
+      const int ns = stw_ns(l, st);
+      const size_t base = size_t(kLmax) + stw_base(l) + stw_stage_off(l, st);
+      for (int r = 1; r < 16; ++r)
+        for (int jm = 0; jm < ns; ++jm) {
+          const size_t e = base + size_t(r - 1) * ns + jm;
+          unit_root((long long)jm * r, 16LL * ns, &tw[2 * e], &tw[2 * e + 1]);
+        }
+    }
   for (int m = 0; m < N; ++m) {
     const int q = m / Q, r = m % Q;
     const double th = 2.0 * M_PI * double(r) / double(N);
@@ -1011,7 +1045,7 @@ fill_status setup_precision(fill_plan* p, const std::vector<double>& tinv,
   }
   const size_t ntab = size_t(p->nx / 2 + 1) * p->ny;
   if (p->dalloc(&P.t_inv, ntab) != cudaSuccess || p->dalloc(&P.t_sqrt, ntab) != cudaSuccess ||
-      p->dalloc(&P.tw, 2 * size_t(kLmax)) != cudaSuccess)
+      p->dalloc(&P.tw, 2 * size_t(kTwEntries)) != cudaSuccess)
     return FILL_ENOMEM;
   if (p->dalloc(&P.st, B) != cudaSuccess || p->halloc(&P.hst, B) != cudaSuccess ||
       p->dalloc(&P.partial, B * kMaxPartials) != cudaSuccess ||
@@ -1026,7 +1060,7 @@ fill_status setup_precision(fill_plan* p, const std::vector<double>& tinv,
     for (size_t i = 0; i < B; ++i) ptrs[i] = P.st + i;
     CK(cudaMemcpy(P.stp, ptrs.data(), B * sizeof(CgState*), cudaMemcpyHostToDevice));
   }
-  std::vector<T> w(2 * size_t(kLmax));
+  std::vector<T> w(2 * size_t(kTwEntries));
   for (size_t i = 0; i < w.size(); ++i) w[i] = (T)tw[i];
   CK(upload_tables<T>(p, tinv, tsqrt));
   CK(cudaMemcpy(P.tw, w.data(), w.size() * sizeof(T), cudaMemcpyHostToDevice));
