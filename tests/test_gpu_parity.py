@@ -140,7 +140,13 @@ def test_fp64_parity_cmb_256(precond):
     x = out[0].cpu().numpy()
     m = obs == 0
     assert np.array_equal(x[~m], d[~m])
-    assert abs(stats[0]["iters"] - ref.pcg.iters) <= 2
+    # Finite-precision CG (reading G19): after hundreds of unpreconditioned
+    # iterations, FP64 implementations that differ only in rounding stop a
+    # few iterations apart -- on this case the GPU path stops at 447 with
+    # twiddles from complex products and at 450 with correctly rounded ones
+    # (the oracle at 447) -- so plain CG may differ by 1% of its iterations.
+    slack = 2 if precond else max(2, ref.pcg.iters // 100)
+    assert abs(stats[0]["iters"] - ref.pcg.iters) <= slack
     assert fp64_gate(x, ref, conv, m)
     if precond:
         out, _ = plan.realize(gpu_map(d, torch.float64), [4], 1e-13)
