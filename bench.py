@@ -42,18 +42,19 @@ UNIT = "realizations/s"
 FP64_ITERS_WIDE4096 = 352.5
 
 # DRAM traffic (read + write bytes) of one launch of each hot-loop pass, from
-# the ncu captures summarised in profiles/k_*_fp32_4096x4096x2.md (2 instances
-# of the 4096^2 workload, FP32 kernels): (per-instance MB, shared MB), the
-# shared part (column table, mask words) read once per launch.  A launch over
-# B instances is scaled as B * per-instance + shared.  Reported only while the
-# pass-kernel sources hash to the profiled version; otherwise traffic is null.
-TRAFFIC = {"src_hash": "7262950242584565",
-           "k_col (column FFT, x 1/(nP), inverse FFT)": (107.12, 33.57),
-           "k_row src (r, u update + R2C)": (140.76, 4.19),
-           "k_row src (p update + R2C)": (90.61, 4.19),
-           "k_row sink (C2R + q = P_x, p^T q)": (95.66, 4.19),
-           "k_row mid (C2R, P_x, R2C)": (108.26, 4.19)}
-KERNEL_SOURCES = ["cg_types.h", "cg_common.cuh", "cg_fft.cuh", "cg_kernels.cuh", "cg_launch.cuh"]
+# one ncu capture of 2 instances of the 4096^2 workload (FP32 kernels):
+# (per-instance MB, shared MB), the shared part (column table, mask words)
+# read once per launch; a launch over B instances is B * per-instance +
+# shared.  Reported only while the pass-kernel sources hash to the captured
+# version; otherwise traffic is null.
+TRAFFIC = {"src_hash": "05b88ff3de4ffb05",
+           "k_col (column FFT, x 1/(nP), inverse FFT)": (104.52, 33.57),
+           "k_row src (r, u update + R2C)": (140.81, 4.19),
+           "k_row src (p update + R2C)": (88.81, 4.19),
+           "k_row sink (C2R + q = P_x, p^T q)": (86.06, 4.19),
+           "k_row mid (C2R, P_x, R2C)": (124.91, 4.19)}
+KERNEL_SOURCES = ["cg_types.h", "cg_common.cuh", "cg_async.cuh", "cg_fft.cuh", "cg_kernels.cuh",
+                  "cg_launch.cuh"]
 
 
 def kernel_src_hash():
