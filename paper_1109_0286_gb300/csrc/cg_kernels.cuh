@@ -278,26 +278,16 @@ __device__ __forceinline__ void mid_fill(const InstDesc<T>& I, const uint2* mwr,
 
 // ----------------------------------------------------------------- row pass
 // CTA = `rows` consecutive grid rows, L/16 threads per row; blockIdx.y is the
-// instance.  Shared memory: one region per row holding that row's part of
-// the transposed spectrum tile (L + 1 complex values, k = 0..L, row-major)
-// and serving afterwards as the row's padded FFT exchange area (XBuf,
-// PADL = L + L/16 + 1 values), then the rows' mask words (nx/32 = L/16 per
-// row: one per thread).  Since a row's exchange area overlaps only its own
-// tile entries, the transforms start after their row's barrier, not the
-// CTA's.  The row stride RS >= PADL is rounded up to RS = 32/rows (mod 16)
-// complex values, which staggers the rows across the banks so that the
-// (k, r) sweeps of the global loads and stores -- a warp covering 32/rows
-// consecutive k of every row -- hit each bank pair at most twice.
+// instance.  Shared memory: per-row FFT exchange areas, aliased with the
+// transposed tile [(L+1) x rows] used for the spectrum load / store,
+// then the rows' mask words (nx/32 = L/16 per row: one per thread).
 // XI: the source is the seed's white noise (kept out of the other source
 // kernels, whose register allocation it would otherwise burden).
-__host__ __device__ __forceinline__ int row_stride(int log_l, int rows) {
-  const int padl = (1 << log_l) + (1 << log_l) / 16 + 1;
-  const int stagger = (32 / rows) & 15;
-  return padl + (((stagger - padl) % 16) + 16) % 16;
-}
 template <typename T>
 __host__ __device__ __forceinline__ size_t row_main_bytes(int log_l, int rows) {
-  return (size_t(rows) * row_stride(log_l, rows) * 2 * sizeof(T) + 15) & ~size_t(15);
+  const size_t L = size_t(1) << log_l, padl = L + L / 16 + 1;
+  const size_t fft = size_t(rows) * 2 * padl, tile = 2 * (L + 1) * size_t(rows);
+  return ((fft > tile ? fft : tile) * sizeof(T) + 15) & ~size_t(15);
 }
 
 template <typename T, int LOG_L, bool IN_SPEC, bool OUT_SPEC, bool XI = false>
@@ -305,6 +295,7 @@ __global__ void __launch_bounds__(KCfg<T>::kMaxThreads)
 k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw) {
   constexpr int L = 1 << LOG_L, TT = L / 16, PADL = L + L / 16 + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
   __shared__ double red[32];
   const InstDesc<T>& I = insts[blockIdx.y];
   if (skip_instance(a.check_done, I.st)) return;
@@ -313,21 +304,28 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
   const int row = threadIdx.x / TT, tid = threadIdx.x - row * TT;
   const int y0 = blockIdx.x * rows, y = y0 + row;
   const int ny = a.ny;
-  const int RS = row_stride(LOG_L, rows);
-  // the tile: row r's entries k = 0..L at r RS + k
-  cx<T>* tile = reinterpret_cast<cx<T>*>(smem_raw);
-  cx<T>* trow = tile + row * RS;                 // this row's region
-  const XBuf<T> xb(reinterpret_cast<T*>(trow), PADL);   // ... as its exchange area
+  const XBuf<T> xb(sm + row * 2 * PADL, PADL);
+  // transposed tile [(L+1)][rows], aliases the FFT areas; column r of row k at
+  // k rows + (r ^ g(k)), g(k) = (k >> gs) & (rows - 1): both the
+  // consecutive-k accesses of one row and the (k, r) sweep of the global
+  // loads / stores are free of bank conflicts
+  cx<T>* tile = reinterpret_cast<cx<T>*>(sm);
+  const int gs = lr < 4 ? 4 - lr : 0;
+  auto tix = [&](int k, int r) { return (k << lr) + (r ^ ((k >> gs) & (rows - 1))); };
   uint2* mws = reinterpret_cast<uint2*>(smem_raw + row_main_bytes<T>(LOG_L, rows));
   const uint2* mwr = mws + row * TT;            // this row's mask words
   constexpr int TWS = kLmax / (2 * L);          // W_{nx}^k = table[k * TWS]
   const int rowpix = y * a.nx;
   // tile element (kk + i TT, rr) for i = 0..15 belongs to thread (kk, rr); the
-  // Nyquist entry k = L to threads 0..rows-1
+  // Nyquist row k = L to threads 0..rows-1
   const int rr = threadIdx.x & (rows - 1), kk = threadIdx.x >> lr;
   const size_t tstep = 2 * (size_t)TT * ny;
-  cx<T>* tcol = tile + rr * RS + kk;             // (kk, rr) in the tile
-  const XBar rbar = XBar::make(TT, rows, row);   // this row's barrier
+  // From L = 512 on, TT is a multiple of 2^max(lr, 4) (rows * TT <= 1024), so
+  // adding multiples of TT to k leaves the swizzle bits g(k) unchanged: a
+  // thread's tile indices for k0 + i TT are one base plus i (TT rows).
+  constexpr bool HOIST = LOG_L >= 9;
+  const int ts = TT << lr;
+  const XBar cta{0, 0}, rbar = XBar::make(TT, rows, row);   // CTA / this row's barrier
   cx<T> v[16];
   Acc<T> acc;
 
@@ -341,18 +339,20 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
     cx<T> tn{};
     if (threadIdx.x < rows)
       tn = ldg_cx<T>((a.spec_sel ? I.spec2 : I.spec) + 2 * ((size_t)L * ny + y0 + threadIdx.x));
+    const int tb = tix(kk, rr);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) tcol[i * TT] = t[i];
-    if (threadIdx.x < rows) tile[threadIdx.x * RS + L] = tn;
+    for (int i = 0; i < 16; ++i) tile[HOIST ? tb + i * ts : tix(kk + i * TT, rr)] = t[i];
+    if (threadIdx.x < rows) tile[tix(L, threadIdx.x)] = tn;
     __syncthreads();
     if (threadIdx.x == 0 && !OUT_SPEC) prefetch_compact(I, a.op, mws, rows * TT);
     // C2R: Z[k] = (X[k] + conj X[L-k]) + i e^{+2 pi i k / nx} (X[k] - conj X[L-k])
     const cx<T> wt = twiddle<T>(tw, tid * TWS);
+    const int cb = tix(tid, row), cm = tix(L - tid, row);
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       const int k = tid + e * TT;
-      cx<T> xk = trow[k];
-      cx<T> xc = conjx(trow[L - k]);
+      cx<T> xk = tile[HOIST ? cb + e * ts : tix(k, row)];
+      cx<T> xc = conjx(tile[HOIST ? cm - e * ts : tix(L - k, row)]);
       if (k == 0) {
         xk.i = (T)0;
         xc.i = (T)0;
@@ -362,8 +362,8 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
       const cx<T> dif = cmulc(xk - xc, w);  // (X - conj X') e^{+i...}
       v[e] = cx<T>{sum.r - dif.i, sum.i + dif.r};
     }
-    // the first exchange overwrites this row's tile entries only
-    fft_regs<T, LOG_L, true>(v, xb, tid, tw, rbar, rbar);
+    // the first exchange overwrites tile entries other rows still read
+    fft_regs<T, LOG_L, true>(v, xb, tid, tw, cta, rbar);
     // v[e] = x[2j] + i x[2j+1], j = tid + e TT
     if constexpr (OUT_SPEC) {
       if (a.op == OP_Y_W)
@@ -426,33 +426,30 @@ k_row(const InstDesc<T>* __restrict__ insts, RowArgs a, const T* __restrict__ tw
   }
 
   if constexpr (OUT_SPEC) {
-    // after an inverse transform (the middle passes) the forward one reloads
-    // its twiddles through an opaque copy of the table pointer: sharing the
-    // inverse transform's loads would keep them live across and spill
-    const T* tw_f = tw;
-    if constexpr (IN_SPEC) asm("mov.b64 %0, %1;" : "=l"(tw_f) : "l"(tw));
-    fft_regs<T, LOG_L, false>(v, xb, tid, tw_f, rbar, rbar);
-    // Z (the half-length transform) into this row's tile region; the threads
-    // of the global stores form X from Z[k] and Z[L-k] of their row:
+    fft_regs<T, LOG_L, false>(v, xb, tid, tw, rbar, rbar);
+    // Z (the half-length transform) into the transposed tile; the threads of
+    // the global stores form X from Z[k] and Z[L-k]:
     // R2C: X[k] = (Z[k] + conj Z[L-k]) / 2 - (i/2) e^{-2 pi i k/nx} (Z[k] - conj Z[L-k])
-    rbar.sync();   // the row's last exchange reads are done
+    __syncthreads();   // the tile overwrites other rows' exchange areas
+    const int cb = tix(tid, row);
 #pragma unroll
-    for (int e = 0; e < 16; ++e) trow[tid + e * TT] = v[e];
+    for (int e = 0; e < 16; ++e) tile[HOIST ? cb + e * ts : tix(tid + e * TT, row)] = v[e];
     __syncthreads();
     const cx<T> wt = twiddle<T>(tw, kk * TWS);
     T* spec = (a.spec_sel ? I.spec2 : I.spec) + 2 * ((size_t)kk * ny + y0 + rr);
-    const cx<T>* zr = tile + rr * RS;
+    const int tb = tix(kk, rr), tm = tix(L - kk, rr);   // L - kk: the Nyquist row when kk = 0
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
       const int k = kk + i * TT;
-      const cx<T> zk = zr[k];
-      const cx<T> zc = conjx(zr[(L - k) & (L - 1)]);
+      const cx<T> zk = tile[HOIST ? tb + i * ts : tix(k, rr)];
+      const int im = (i == 0 && kk == 0) ? tix(0, rr) : tm - i * ts;
+      const cx<T> zc = conjx(tile[HOIST ? im : tix((L - k) & (L - 1), rr)]);
       const cx<T> ev = scal(zk + zc, (T)0.5);
       const cx<T> od = scal(mul_mi<T, false>(zk - zc), (T)0.5);
       st_cx<T>(spec + i * tstep, ev + cmul(od, cmul(wt, w32<T>(i))));
     }
     if (threadIdx.x < rows) {   // Nyquist: X[L] = Re Z[0] - Im Z[0]
-      const cx<T> z0 = tile[threadIdx.x * RS];
+      const cx<T> z0 = tile[tix(0, threadIdx.x)];
       st_cx<T>((a.spec_sel ? I.spec2 : I.spec) + 2 * ((size_t)L * ny + y0 + threadIdx.x),
                cx<T>{z0.r - z0.i, (T)0});
     }
