@@ -201,6 +201,29 @@ def test_mixed_refinement_to_1e10(precond, delta):
           f"updates {[s['refine_steps'] for s in stats]}")
 
 
+def test_mixed_1024_elementwise_to_1e12():
+    """The headline's mixed mode on the wide-cut workload at 1024^2 (the
+    row transforms of 512 points), refined to a true relative residual of
+    1e-12, element by element against the converged FP64 oracle; the 4096^2
+    launch itself is checked by certificate (test_wide4096_full_size_certificate)."""
+    P, obs, spec = workload("wide4096", scale=4)
+    ny, nx = obs.shape
+    Pf = O.hermitian_full(P, nx)
+    d = O.draw(Pf, spec["data_seed"])
+    seed = spec["seeds"][0]
+    plan = cg.Plan(P, obs, mode="mixed", max_iter=4000)
+    out, stats = plan.realize(gpu_map(d, torch.float64), [seed], 1e-12)
+    conv = O.realize(P, obs, d, seed, tol=1e-13)
+    m = obs == 0
+    x = out[0].cpu().numpy()
+    assert np.array_equal(x[~m], d[~m])
+    assert stats[0]["true_rel_resid"] <= 1e-12
+    err = rel(x[m], conv.x[m])
+    print(f"mixed 1024^2 to 1e-12: iters {stats[0]['iters']} (oracle {conv.pcg.iters}), "
+          f"rel err {err:.2e}")
+    assert err <= 1e-9, err
+
+
 def test_batch_equals_singles():
     P, obs = case(128, 128, seed=8)
     d = O.draw(O.hermitian_full(P, 128), 3)
@@ -473,10 +496,14 @@ def test_wide4096_full_size_certificate():
     plan = cg.Plan(P, obs, mode="mixed", batch=len(seeds))
     out, stats = plan.realize(gpu_map(d, torch.float64), seeds, spec["tol"])
     m = obs == 0
+    ys = plan.draw(seeds)
+    rows = [0, 1, 777, ny // 2, ny - 1]
     for i in (0, len(seeds) - 1):
         x = out[i].cpu().numpy()
         assert np.array_equal(x[~m], d[~m])
         y = O.draw(Pf, seeds[i])
+        yg = ys[i][rows].cpu().numpy()
+        assert rel(yg, y[rows]) <= 1e-11, rel(yg, y[rows])
         w = np.where(m, x - y, d - y)
         b = O.rhs(Pf, obs, d, y)
         cert = np.linalg.norm(np.where(m, O.apply_power(w, Pf, -1.0), 0)) / np.linalg.norm(b)
