@@ -152,6 +152,8 @@ struct fill_plan {
   uint2* mw = nullptr;           // mask words: observed bits, compact offset
   long long nv = 0;              // compact vector stride per instance (>= nmasked)
   std::vector<double> P_half;    // host copy of the spectrum
+  double* P_dev = nullptr;       // device copy (fill_set_spectrum builds the tables from it)
+  double* sig_dev = nullptr;     // device copy of the band templates' S(k) (fill_set_bands)
   std::vector<int32_t> band_idx; // band templates of fill_set_bands (host copies), so
   std::vector<double> band_sig;  // that fill_set_spectrum can rebuild the gradient weights
   int nbands = 0;
@@ -260,6 +262,31 @@ __global__ void k_inner_collect(CgState* st32, CgState* st64, int n) {
   st64[i].total_iter += st32[i].iter;
   st32[i].last_iter = st32[i].iter;
   st32[i].iter = 0;
+}
+
+// Spectral tables of one precision from P on the device (fill_set_spectrum):
+// 1/(nP) and sqrt(P)/n in the transposed [kx][ky] layout and, with band
+// templates, the band-gradient weights wt S / (2 n sqrt P) and wt S / (n P^2)
+// (wt = 1 on the self-conjugate columns kx = 0, nx/2, else 2), in FP64 and
+// rounded to T once -- the values the host path computes.
+template <typename T>
+__global__ void k_spectral_tables(const double* P, const double* sig, int ny, int nkx, int nx,
+                                  T* t_inv, T* t_sqrt, T* c1, T* c2) {
+  const long long total = (long long)ny * nkx;
+  const double n = double(ny) * double(nx);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int kx = (int)(t / ny), ky = (int)(t % ny);
+    const long long h = (long long)ky * nkx + kx;
+    const double p = P[h];
+    t_inv[t] = (T)(1.0 / (p * n));
+    t_sqrt[t] = (T)(sqrt(p) / n);
+    if (c1) {
+      const double wt = (kx == 0 || kx == nx / 2) ? 1.0 : 2.0, sg = sig[h];
+      c1[t] = (T)(wt * sg / (2.0 * n * sqrt(p)));
+      c2[t] = (T)(wt * sg / (n * p * p));
+    }
+  }
 }
 
 // ----------------------------------------------------------------- pass helpers
@@ -1259,6 +1286,9 @@ fill_status fill_init(fill_plan** out, int ny, int nx, const double* P_half,
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap2, cudaStreamNonBlocking);
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaStreamCreate"));
   if (p->dalloc(&p->mw, words.size()) != cudaSuccess) return fail(FILL_ENOMEM);
+  if (p->dalloc(&p->P_dev, (size_t)ny * nkx) != cudaSuccess) return fail(FILL_ENOMEM);
+  e = cudaMemcpy(p->P_dev, P_half, (size_t)ny * nkx * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(cuda_fail(e, "upload spectrum"));
   if (p->dalloc(&p->loop_counter, 2) != cudaSuccess || p->halloc(&p->hloop, 3) != cudaSuccess ||
       p->dalloc(&p->dev_err, 1) != cudaSuccess)
     return fail(FILL_ENOMEM);
@@ -1847,6 +1877,8 @@ fill_status fill_set_bands(fill_plan* p, int nbands, const int32_t* band_of_k,
     p->band_idx.assign(band_of_k, band_of_k + nh);
     p->band_sig.assign(sig_half, sig_half + nh);
     p->nbands = nbands;
+    if (!p->sig_dev && p->dalloc(&p->sig_dev, nh) != cudaSuccess) return FILL_ENOMEM;
+    CK(cudaMemcpy(p->sig_dev, sig_half, nh * sizeof(double), cudaMemcpyHostToDevice));
   }
   return fs;
 }
@@ -1857,24 +1889,29 @@ fill_status fill_set_spectrum(fill_plan* p, const double* P_half) {
     cgf_set_last_error("fill_set_spectrum: P must be finite, > 0 and Hermitian-consistent");
     return FILL_EINVAL;
   }
+  const size_t nh = (size_t)p->ny * (p->nx / 2 + 1);
+  double a = 0.0;
+  for (size_t i = 0; i < nh; ++i) a = std::max(a, 1.0 / P_half[i]);
   // the plan's stream may still run work that reads the tables
   CK(cudaStreamSynchronize(p->s));
-  std::vector<double> tinv, tsqrt;
-  double a = 0.0;
-  spectral_tables(p->ny, p->nx, P_half, tinv, tsqrt, &a);
-  if (p->f.used) CK(upload_tables<float>(p, tinv, tsqrt));
-  if (p->g.used) CK(upload_tables<double>(p, tinv, tsqrt));
-  if (p->h.used) CK(upload_tables<df>(p, tinv, tsqrt));
+  CK(cudaMemcpyAsync(p->P_dev, P_half, nh * sizeof(double), cudaMemcpyHostToDevice, p->s));
+  // the tables of every precision the plan holds, and the band-gradient
+  // weights at the new P (they depend on it), built on the device
+  const int nkx = p->nx / 2 + 1, blocks = (int)std::min<size_t>((nh + 255) / 256, 4096);
+  const bool bands = p->nbands > 0;
+  if (p->f.used)
+    k_spectral_tables<float><<<blocks, 256, 0, p->s>>>(p->P_dev, p->sig_dev, p->ny, nkx, p->nx,
+        p->f.t_inv, p->f.t_sqrt, bands ? p->f.coef1 : nullptr, bands ? p->f.coef2 : nullptr);
+  if (p->g.used)
+    k_spectral_tables<double><<<blocks, 256, 0, p->s>>>(p->P_dev, p->sig_dev, p->ny, nkx, p->nx,
+        p->g.t_inv, p->g.t_sqrt, bands ? p->g.coef1 : nullptr, bands ? p->g.coef2 : nullptr);
+  if (p->h.used)
+    k_spectral_tables<df><<<blocks, 256, 0, p->s>>>(p->P_dev, p->sig_dev, p->ny, nkx, p->nx,
+        p->h.t_inv, p->h.t_sqrt, bands ? p->h.coef1 : nullptr, bands ? p->h.coef2 : nullptr);
+  CK(cudaGetLastError());
   p->relax_a = a;
-  p->P_half.assign(P_half, P_half + (size_t)p->ny * (p->nx / 2 + 1));
-  // the band-power gradient weights depend on P
-  if (p->nbands > 0) {
-    fill_status fs = set_bands_t<float>(p, p->nbands, p->band_idx.data(), p->band_sig.data());
-    if (fs == FILL_OK) fs = set_bands_t<double>(p, p->nbands, p->band_idx.data(), p->band_sig.data());
-    if (fs == FILL_OK) fs = set_bands_t<df>(p, p->nbands, p->band_idx.data(), p->band_sig.data());
-    if (fs != FILL_OK) return fs;
-  }
-  CK(cudaDeviceSynchronize());
+  p->P_half.assign(P_half, P_half + nh);
+  CK(cudaStreamSynchronize(p->s));
   return FILL_OK;
 }
 
