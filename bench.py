@@ -786,7 +786,8 @@ def run_reference(args):
     t_real = setup + FP64_ITERS_WIDE4096 * t_iter
     value = 1.0 / t_real
     cores = threads_used()
-    sample = (f"oracle (NumPy FP64) on {obs.shape[0]}x{obs.shape[1]}: draw + RHS once "
+    sample = (f"FP64 oracle (own C FFT on {cores} host threads, NumPy element-wise steps) "
+              f"on {obs.shape[0]}x{obs.shape[1]}: draw + RHS once "
               f"({setup:.1f} s) and 1 preconditioned CG iteration per step "
               f"({t_iter:.1f} s); realizations/s = 1/(setup + {FP64_ITERS_WIDE4096} iterations)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
