@@ -1,5 +1,5 @@
 // Instantiations of the mixed-radix pass kernels (FP32, FP64, double-float)
-// and the host-side factorisation of a transform length.
+// and the factorisation of a transform length with its twiddle layout.
 #include "cg_generic.cuh"
 
 namespace cgf {
@@ -21,6 +21,15 @@ bool gen_factor(int n, GenLen* g) {
   if (m != 1) return false;
   g->n = n;
   g->nst = k;
+  // stage s (sub-length ns, h = ns / R) holds h (R - 1) twiddles; the last
+  // stage (h = 1) none
+  int ns = n, off = 0;
+  for (int s = 0; s < k; ++s) {
+    const int h = ns / g->radix[s];
+    g->twoff[s] = off;
+    if (s < k - 1) off += h * (g->radix[s] - 1);
+    ns = h;
+  }
   return true;
 }
 

@@ -1,7 +1,8 @@
-// Mixed-radix pass kernels (radix 2, 3, 4, 5, 7) and their launchers; see
-// cg_generic.h.  The fused operations are those of cg_kernels.cuh, applied
-// per pixel pair; mask flags and compact indices come from the global mask
-// words (a row need not start on a word boundary here).
+// Mixed-radix pass kernels (radix 2, 3, 4, 5, 7, in-place DIF / DIT
+// transforms) and their launchers; see cg_generic.h.  The fused operations
+// are those of cg_kernels.cuh, applied per pixel pair; mask flags and compact
+// indices come from the global mask words (a row need not start on a word
+// boundary here).
 #pragma once
 #include "cg_generic.h"
 #include "cg_launch.cuh"
@@ -9,27 +10,59 @@
 namespace cgf {
 namespace gen {
 
-template <typename T>
-__device__ __forceinline__ cx<T> tw_at(const T* w, int t) {
-  return ldg_cx<T>(w + 2 * t);
+// The V values of one position of a thread group's transforms (one 16-byte
+// shared-memory access for two FP32 transforms).
+template <typename T, int V>
+__device__ __forceinline__ void ld_slot(const cx<T>* p, cx<T> (&v)[V]) {
+  if constexpr (V == 2 && std::is_same<T, float>::value) {
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    v[0] = cx<float>{a.x, a.y};
+    v[1] = cx<float>{a.z, a.w};
+  } else {
+#pragma unroll
+    for (int u = 0; u < V; ++u) v[u] = ld_cx<T>(reinterpret_cast<const T*>(p + u));
+  }
+}
+template <typename T, int V>
+__device__ __forceinline__ void st_slot(cx<T>* p, const cx<T> (&v)[V]) {
+  if constexpr (V == 2 && std::is_same<T, float>::value) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0].r, v[0].i, v[1].r, v[1].i);
+  } else {
+#pragma unroll
+    for (int u = 0; u < V; ++u) st_cx<T>(reinterpret_cast<T*>(p + u), v[u]);
+  }
 }
 
-// In-register DFT of R points, y_q = sum_m v_m W_R^{qm} (forward sign).  For
-// odd R the terms m and R - m pair up: with S_m = v_m + v_{R-m},
-// D_m = v_m - v_{R-m} (m = 1..H, H = (R-1)/2) and theta = 2 pi q m / R,
-//   y_q = v_0 + sum_m cos(theta) S_m - i sum_m sin(theta) D_m,
-//   y_{R-q} = the same with +i,
-// so each half-pair costs real-by-complex products only.  cs[j] = W_R^j
-// (j = 1..H) = (cos 2 pi j/R, -sin 2 pi j/R).
-template <typename T, int R>
-__device__ __forceinline__ void dft(cx<T> (&v)[R], const cx<T>* cs) {
+// cos and sin of 2 pi j / R for the odd radices (j = 1 .. (R-1)/2), each the
+// double nearest the exact value (from a 50-digit evaluation of the series).
+CGF_HD constexpr double radix_cos(int R, int j) {
+  return R == 3 ? -0.5
+       : R == 5 ? (j == 1 ? 0.30901699437494745 : -0.8090169943749475)
+       : (j == 1 ? 0.6234898018587335 : j == 2 ? -0.2225209339563144 : -0.9009688679024191);
+}
+CGF_HD constexpr double radix_sin(int R, int j) {
+  return R == 3 ? 0.8660254037844386
+       : R == 5 ? (j == 1 ? 0.9510565162951535 : 0.5877852522924731)
+       : (j == 1 ? 0.7818314824680298 : j == 2 ? 0.9749279121818236 : 0.4338837391175581);
+}
+
+// In-register DFT of R points, y_q = sum_m v_m W_R^{+-qm} (W_R = e^{-2 pi i/R};
+// the inverse takes the conjugate).  For odd R the terms m and R - m pair up:
+// with S_m = v_m + v_{R-m}, D_m = v_m - v_{R-m} (m = 1..H, H = (R-1)/2) and
+// theta = 2 pi q m / R,
+//   y_q = v_0 + sum_m cos(theta) S_m -+ i sum_m sin(theta) D_m,
+//   y_{R-q} = the same with the other sign,
+// so each half-pair costs real-by-complex products only, with the cosines
+// and sines compile-time constants.
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void dft(cx<T> (&v)[R]) {
   if constexpr (R == 2) {
     const cx<T> a = v[0], b = v[1];
     v[0] = a + b;
     v[1] = a - b;
   } else if constexpr (R == 4) {
     const cx<T> s02 = v[0] + v[2], d02 = v[0] - v[2];
-    const cx<T> s13 = v[1] + v[3], d13 = mul_mi<T, false>(v[1] - v[3]);
+    const cx<T> s13 = v[1] + v[3], d13 = mul_mi<T, INV>(v[1] - v[3]);
     v[0] = s02 + s13;
     v[2] = s02 - s13;
     v[1] = d02 + d13;
@@ -37,104 +70,231 @@ __device__ __forceinline__ void dft(cx<T> (&v)[R], const cx<T>* cs) {
   } else {
     constexpr int H = (R - 1) / 2;
     cx<T> S[H + 1], D[H + 1];
-    cx<T> y0 = v[0];
+    const cx<T> v0 = v[0];
+    cx<T> y0 = v0;
 #pragma unroll
     for (int m = 1; m <= H; ++m) {
       S[m] = v[m] + v[R - m];
       D[m] = v[m] - v[R - m];
       y0 = y0 + S[m];
     }
-    cx<T> y[R];
-    y[0] = y0;
+    v[0] = y0;
 #pragma unroll
     for (int q = 1; q <= H; ++q) {
-      cx<T> a = v[0], b{(T)0, (T)0};
+      cx<T> a = v0, b{(T)0, (T)0};
 #pragma unroll
       for (int m = 1; m <= H; ++m) {
         const int j = (q * m) % R, jj = j <= H ? j : R - j;
-        const T c = cs[jj].r, sn = j <= H ? -cs[jj].i : cs[jj].i;   // cos, sin of 2 pi j / R
+        const T c = T(radix_cos(R, jj));
+        const T sn = T(j <= H ? radix_sin(R, jj) : -radix_sin(R, jj));   // sin 2 pi j / R
         a = a + scal(S[m], c);
         b = b + scal(D[m], sn);
       }
-      y[q] = cx<T>{a.r + b.i, a.i - b.r};       // a - i b
-      y[R - q] = cx<T>{a.r - b.i, a.i + b.r};   // a + i b
+      const cx<T> mib{b.i, -b.r}, pib{-b.i, b.r};   // -i b, +i b
+      v[q] = INV ? a + pib : a + mib;
+      v[R - q] = INV ? a + mib : a + pib;
     }
-#pragma unroll
-    for (int q = 0; q < R; ++q) v[q] = y[q];
   }
 }
 
-// One self-sorting stage: butterfly b takes in[b + m n/R] (m < R), scales by
-// W_{ns R}^{m k} (k = b mod ns), transforms, and writes
-// out[(b - k) R + k + m ns].  cin / cout conjugate inputs / outputs (the
-// inverse transform as conj F conj).
-template <typename T, int R>
-__device__ __forceinline__ void stage(const cx<T>* in, cx<T>* out, int n, int ns, const T* w,
-                                      int t, int nt, bool cin, bool cout) {
-  const int nb = n / R, step = n / (ns * R);
-  cx<T> cs[R / 2 + 1];   // W_R^j, j = 1..(R-1)/2, for the odd radices
-  if constexpr (R % 2 == 1) {
-#pragma unroll
-    for (int j = 1; j <= R / 2; ++j) cs[j] = tw_at(w, j * nb);
-  }
-  // b = j ns + k, stepped by nt without a division per butterfly
-  int j = t / ns, k = t - j * ns;
-  const int dj = nt / ns, dk = nt - dj * ns, nsr = ns * R;
+// One stage of radix R over blocks of ns points (h = ns / R, nb = n / R
+// butterflies; butterfly b = blk h + j reads and writes positions
+// blk ns + j + m h).  Forward (DIF): DFT, then the twiddles W_ns^{q j} on the
+// outputs; inverse (transposed, conjugate): conjugate twiddles on the inputs,
+// then the inverse DFT.  `tws` is the stage's twiddle table (unused when
+// h = 1).  Thread t of nt takes butterflies t, t + nt, ...
+template <typename T, int V, int R, bool INV>
+__device__ __forceinline__ void stage(cx<T>* z, int ns, int h, int nb, const T* tws, int t,
+                                      int nt) {
+  const bool twd = h > 1;
+  const int hv = h * V;
+  int blk = t / h, j = t - blk * h;
+  const int dblk = nt / h, dj = nt - dblk * h;
   for (int b = t; b < nb; b += nt) {
-    cx<T> v[R];
+    cx<T>* p = z + (blk * ns + j) * V;
+    const T* wj = tws + 2 * (j * (R - 1));
+    cx<T> v[V][R];
 #pragma unroll
     for (int m = 0; m < R; ++m) {
-      v[m] = in[b + m * nb];
-      if (cin) v[m] = conjx(v[m]);
-    }
-    if (ns > 1) {
+      cx<T> sl[V];
+      ld_slot<T, V>(p + m * hv, sl);
 #pragma unroll
-      for (int m = 1; m < R; ++m) v[m] = cmul(v[m], tw_at(w, m * k * step));
+      for (int u = 0; u < V; ++u) v[u][m] = sl[u];
     }
-    dft<T, R>(v, cs);
-    const int base = j * nsr + k;   // (b - k) R + k
+    if constexpr (INV) {
+      if (twd) {
 #pragma unroll
-    for (int m = 0; m < R; ++m) out[base + m * ns] = cout ? conjx(v[m]) : v[m];
-    k += dk;
+        for (int m = 1; m < R; ++m) {
+          const cx<T> w = ldg_cx<T>(wj + 2 * (m - 1));
+#pragma unroll
+          for (int u = 0; u < V; ++u) v[u][m] = cmulc(v[u][m], w);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < V; ++u) dft<T, R, INV>(v[u]);
+    if constexpr (!INV) {
+      if (twd) {
+#pragma unroll
+        for (int m = 1; m < R; ++m) {
+          const cx<T> w = ldg_cx<T>(wj + 2 * (m - 1));
+#pragma unroll
+          for (int u = 0; u < V; ++u) v[u][m] = cmul(v[u][m], w);
+        }
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      cx<T> sl[V];
+#pragma unroll
+      for (int u = 0; u < V; ++u) sl[u] = v[u][m];
+      st_slot<T, V>(p + m * hv, sl);
+    }
     j += dj;
-    if (k >= ns) {
-      k -= ns;
-      ++j;
+    blk += dblk;
+    if (j >= h) {
+      j -= h;
+      ++blk;
     }
   }
 }
 
-// Unnormalised transform of the n values in `a` (forward: W_n = e^{-2 pi i/n};
-// inverse: the conjugate).  Every thread of the CTA calls it (CTA barriers);
-// threads t < nt of each transform share its butterflies.  Returns the buffer
-// that holds the result (a or b).
-template <typename T>
-__device__ cx<T>* fft(cx<T>* a, cx<T>* b, const GenLen& g, const T* w, int t, bool inv) {
-  int ns = 1;
-  for (int s = 0; s < g.nst; ++s) {
-    const int r = g.radix[s];
-    const bool cin = inv && s == 0, cout = inv && s == g.nst - 1;
-    switch (r) {
-      case 2: stage<T, 2>(a, b, g.n, ns, w, t, g.nt, cin, cout); break;
-      case 3: stage<T, 3>(a, b, g.n, ns, w, t, g.nt, cin, cout); break;
-      case 4: stage<T, 4>(a, b, g.n, ns, w, t, g.nt, cin, cout); break;
-      case 5: stage<T, 5>(a, b, g.n, ns, w, t, g.nt, cin, cout); break;
-      default: stage<T, 7>(a, b, g.n, ns, w, t, g.nt, cin, cout); break;
-    }
-    ns *= r;
-    __syncthreads();
-    cx<T>* c = a;
-    a = b;
-    b = c;
+template <typename T, int V, bool INV>
+__device__ __forceinline__ void stage_r(int R, cx<T>* z, int ns, int h, int nb, const T* tws,
+                                        int t, int nt) {
+  switch (R) {
+    case 2: stage<T, V, 2, INV>(z, ns, h, nb, tws, t, nt); break;
+    case 3: stage<T, V, 3, INV>(z, ns, h, nb, tws, t, nt); break;
+    case 4: stage<T, V, 4, INV>(z, ns, h, nb, tws, t, nt); break;
+    case 5: stage<T, V, 5, INV>(z, ns, h, nb, tws, t, nt); break;
+    default: stage<T, V, 7, INV>(z, ns, h, nb, tws, t, nt); break;
   }
-  return a;
+}
+
+// Forward stages 0 .. s_end - 1 of the transform in z (natural order in; after
+// all stages, digit-reversed order out).  Every thread of the CTA calls it: a
+// CTA barrier follows every stage.
+template <typename T, int V>
+__device__ void dif(cx<T>* z, const GenLen& g, const T* tw, int t, int s_end) {
+  int ns = g.n;
+  for (int s = 0; s < s_end; ++s) {
+    const int R = g.radix[s], h = ns / R;
+    stage_r<T, V, false>(R, z, ns, h, g.n / R, tw + 2 * g.twoff[s], t, g.nt);
+    __syncthreads();
+    ns = h;
+  }
+}
+
+// Inverse stages s_top - 1 down to 0 (digit-reversed order in, natural order
+// out after stage 0), with a CTA barrier after every stage.
+template <typename T, int V>
+__device__ void dit(cx<T>* z, const GenLen& g, const T* tw, int t, int s_top) {
+  int h = g.n;   // n_{s_top}: the points below stage s_top
+  for (int s = 0; s < s_top; ++s) h /= g.radix[s];
+  for (int s = s_top - 1; s >= 0; --s) {
+    const int R = g.radix[s], ns = h * R;
+    stage_r<T, V, true>(R, z, ns, h, g.n / R, tw + 2 * g.twoff[s], t, g.nt);
+    __syncthreads();
+    h = ns;
+  }
+}
+
+// Half spectrum -> digit-reversed complex row (C2R by a half-length FFT):
+// Z[k] = (X[k] + conj X[L-k]) + i e^{+2 pi i k/nx} (X[k] - conj X[L-k]) for
+// k < L, the imaginary parts of X[0] and X[L] dropped; stored at position
+// pos[k].  A thread takes k and L - k together (one load of each).  Rows at or
+// beyond ny (the padding row of an odd ny) read zeros.
+template <typename T>
+__device__ __forceinline__ cx<T> c2r_one(cx<T> xk, cx<T> xm, cx<T> w) {
+  const cx<T> xc = conjx(xm);
+  const cx<T> sum = xk + xc;
+  const cx<T> dif = cmulc(xk - xc, w);
+  return cx<T>{sum.r - dif.i, sum.i + dif.r};
+}
+template <typename T>
+__device__ __forceinline__ cx<T> r2c_one(cx<T> zk, cx<T> zm, cx<T> w) {
+  const cx<T> zc = conjx(zm);
+  const cx<T> ev = scal(zk + zc, (T)0.5);
+  const cx<T> od = scal(mul_mi<T, false>(zk - zc), (T)0.5);
+  return ev + cmul(od, w);
+}
+
+constexpr int kGenChunk = 4;
+
+template <typename T, int V>
+__device__ __forceinline__ void c2r(const T* spec, int ny, int y0, const GenLen& g, const T* wx,
+                                    cx<T>* z, int t, int nt) {
+  const int L = g.n, half = L / 2, nv = min(V, ny - y0);
+  constexpr int CH = 2;
+  for (int k0 = t; k0 <= half; k0 += CH * nt) {
+    cx<T> xa[CH][V], xb[CH][V], wa[CH], wb[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const int k = min(k0 + c * nt, half), kc = L - k;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const bool ok = v < nv;
+        xa[c][v] = ok ? ldg_cx<T>(spec + 2 * ((size_t)k * ny + y0 + v)) : cx<T>{(T)0, (T)0};
+        xb[c][v] = ok ? ldg_cx<T>(spec + 2 * ((size_t)kc * ny + y0 + v)) : cx<T>{(T)0, (T)0};
+      }
+      wa[c] = ldg_cx<T>(wx + 2 * k);
+      wb[c] = ldg_cx<T>(wx + 2 * kc);
+    }
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const int k = k0 + c * nt, kc = L - k;
+      if (k > half) break;
+      cx<T> za[V], zb[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        cx<T> p = xa[c][v], q = xb[c][v];
+        if (k == 0) {
+          p.i = (T)0;
+          q.i = (T)0;
+        }
+        za[v] = c2r_one(p, q, wa[c]);
+        zb[v] = c2r_one(q, p, wb[c]);
+      }
+      st_slot<T, V>(z + (int)g.pos[k] * V, za);
+      if (k > 0 && kc != k) st_slot<T, V>(z + (int)g.pos[kc] * V, zb);
+    }
+  }
+}
+
+// Digit-reversed complex row -> half spectrum (R2C):
+// X[k] = (Z[k] + conj Z[L-k]) / 2 - (i/2) e^{-2 pi i k/nx} (Z[k] - conj Z[L-k])
+// (Z[L] = Z[0]), X[L] = Re Z[0] - Im Z[0]; rows at or beyond ny are not stored.
+template <typename T, int V>
+__device__ __forceinline__ void r2c(T* spec, int ny, int y0, const GenLen& g, const T* wx,
+                                    const cx<T>* z, int t, int nt) {
+  const int L = g.n, half = L / 2, nv = min(V, ny - y0);
+  for (int k = t; k <= half; k += nt) {
+    const int kc = L - k;
+    cx<T> za[V], zb[V];
+    ld_slot<T, V>(z + (int)g.pos[k] * V, za);
+    if (k == 0) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) zb[v] = za[v];
+    } else {
+      ld_slot<T, V>(z + (int)g.pos[kc] * V, zb);
+    }
+    const cx<T> wa = ldg_cx<T>(wx + 2 * k), wb = ldg_cx<T>(wx + 2 * kc);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      if (v >= nv) break;
+      st_cx<T>(spec + 2 * ((size_t)k * ny + y0 + v), r2c_one(za[v], zb[v], wa));
+      if (k == 0)
+        st_cx<T>(spec + 2 * ((size_t)L * ny + y0 + v), cx<T>{za[v].r - za[v].i, (T)0});
+      else if (kc != k)
+        st_cx<T>(spec + 2 * ((size_t)kc * ny + y0 + v), r2c_one(zb[v], za[v], wb));
+    }
+  }
 }
 
 // ----------------------------------------------------------------- per-pair operations
 // Each row loop takes kGenChunk pixel pairs per thread at a time: their mask
 // words first, then every operand load, then the arithmetic and stores, so
 // the loads of a chunk are in flight together.
-constexpr int kGenChunk = 4;
 
 struct Opnd {   // one pixel pair: mask flags, compact indices, pixel index
   PairIdx q;
@@ -281,7 +441,7 @@ __device__ __forceinline__ void chunk_words(const uint2* mw, int rowpix, int j0,
   }
 }
 
-template <typename T, int OP>
+template <typename T, int OP, int V>
 __device__ __forceinline__ void src_row(const InstDesc<T>& I, int rowpix, cx<T>* z, int L, int t,
                                         int nt, T alpha, T beta, Acc<T>& acc) {
   constexpr bool W = !(OP == OP_LOAD_W || OP == OP_LOAD_Y);
@@ -294,11 +454,11 @@ __device__ __forceinline__ void src_row(const InstDesc<T>& I, int rowpix, cx<T>*
       if (o[u].ok) src_load<T, OP>(I, o[u], x[u]);
 #pragma unroll
     for (int u = 0; u < kGenChunk; ++u)
-      if (o[u].ok) z[j0 + u * nt] = src_op<T, OP>(I, o[u], x[u], alpha, beta, acc);
+      if (o[u].ok) z[(j0 + u * nt) * V] = src_op<T, OP>(I, o[u], x[u], alpha, beta, acc);
   }
 }
 
-template <typename T, int OP>
+template <typename T, int OP, int V>
 __device__ __forceinline__ void sink_row(const InstDesc<T>& I, int rowpix, const cx<T>* z, int L,
                                          int t, int nt, Acc<T>& acc, int param) {
   for (int j0 = t; j0 < L; j0 += kGenChunk * nt) {
@@ -310,11 +470,11 @@ __device__ __forceinline__ void sink_row(const InstDesc<T>& I, int rowpix, const
       if (o[u].ok) sink_load<T, OP>(I, o[u], x[u]);
 #pragma unroll
     for (int u = 0; u < kGenChunk; ++u)
-      if (o[u].ok) sink_op<T, OP>(I, o[u], x[u], z[j0 + u * nt], acc, param);
+      if (o[u].ok) sink_op<T, OP>(I, o[u], x[u], z[(j0 + u * nt) * V], acc, param);
   }
 }
 
-template <typename T, int OP>
+template <typename T, int OP, int V>
 __device__ __forceinline__ void mid_row(const InstDesc<T>& I, int rowpix, cx<T>* z, int L, int t,
                                         int nt) {
   for (int j0 = t; j0 < L; j0 += kGenChunk * nt) {
@@ -326,143 +486,128 @@ __device__ __forceinline__ void mid_row(const InstDesc<T>& I, int rowpix, cx<T>*
       if (o[u].ok && OP == OP_Y_W) ld_map_pair<T>(I.d + o[u].pix, d[u][0], d[u][1]);
 #pragma unroll
     for (int u = 0; u < kGenChunk; ++u)
-      if (o[u].ok) z[j0 + u * nt] = mid_op<T, OP>(I, o[u], d[u][0], d[u][1], z[j0 + u * nt]);
+      if (o[u].ok)
+        z[(j0 + u * nt) * V] = mid_op<T, OP>(I, o[u], d[u][0], d[u][1], z[(j0 + u * nt) * V]);
   }
 }
 
 }  // namespace gen
 
 // ----------------------------------------------------------------- row pass
-// CTA = `rows` consecutive grid rows, g.nt threads per row; blockIdx.y is the
-// instance.  Shared memory: two buffers of L + 1 complex values per row.
-template <typename T, bool IN_SPEC, bool OUT_SPEC, bool XI = false>
-__global__ void __launch_bounds__(KCfg<T>::kMaxThreads)
+// CTA = a.rows consecutive grid rows in groups of V (one group per g.nt
+// threads; blockIdx.y is the instance), rows at or beyond ny (odd ny) idle.
+// Shared memory: L complex values per row, interleaved [position][V] within a
+// group.
+template <typename T, int V, bool IN_SPEC, bool OUT_SPEC, bool XI = false>
+__global__ void __launch_bounds__(kGenThreads, gen_minb<T>())
 k_row_gen(const InstDesc<T>* __restrict__ insts, RowArgs a, GenLen g, const T* __restrict__ wl,
           const T* __restrict__ wx) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
   const InstDesc<T>& I = insts[blockIdx.y];
   if (skip_instance(a.check_done, I.st)) return;
-  const int L = g.n, nt = g.nt, rows = a.rows, ny = a.ny, stride = 2 * (L + 1);
-  const int row = threadIdx.x / nt, t = threadIdx.x - row * nt;
-  const int y0 = blockIdx.x * rows;
-  const int rowpix = (y0 + row) * a.nx;
-  cx<T>* base = reinterpret_cast<cx<T>*>(smem_raw);
-  cx<T>* A = base + row * stride;
-  cx<T>* B = A + (L + 1);
-  cx<T>* Z = A;   // the buffer holding the row's values
+  const int L = g.n, nt = g.nt, ny = a.ny;
+  const int grp = threadIdx.x / nt, t = threadIdx.x - grp * nt;
+  const int y0 = blockIdx.x * a.rows + grp * V;
+  const int nv = min(V, ny - y0);   // rows of this group inside the grid
+  cx<T>* Z = reinterpret_cast<cx<T>*>(smem_raw) + grp * L * V;
   Acc<T> acc;
 
   if constexpr (IN_SPEC) {
-    const T* spec = a.spec_sel ? I.spec2 : I.spec;
-    // X[k] of the `rows` rows: consecutive threads take consecutive rows of one k
-    const int total = (L + 1) * rows;
-    for (int f0 = threadIdx.x; f0 < total; f0 += gen::kGenChunk * blockDim.x) {
-      cx<T> tv[gen::kGenChunk];
-#pragma unroll
-      for (int u = 0; u < gen::kGenChunk; ++u) {
-        const int f = f0 + u * blockDim.x;
-        if (f < total)
-          tv[u] = ldg_cx<T>(spec + 2 * ((size_t)(f >> a.log_rows) * ny + y0 + (f & (rows - 1))));
-      }
-#pragma unroll
-      for (int u = 0; u < gen::kGenChunk; ++u) {
-        const int f = f0 + u * blockDim.x;
-        if (f < total) base[(f & (rows - 1)) * stride + (f >> a.log_rows)] = tv[u];
-      }
-    }
+    gen::c2r<T, V>(a.spec_sel ? I.spec2 : I.spec, ny, y0, g, wx, Z, t, nt);
     __syncthreads();
-    // C2R: Z[k] = (X[k] + conj X[L-k]) + i e^{+2 pi i k/nx} (X[k] - conj X[L-k])
-    for (int k = t; k < L; k += nt) {
-      cx<T> xk = A[k], xc = conjx(A[L - k]);
-      if (k == 0) {
-        xk.i = (T)0;
-        xc.i = (T)0;
-      }
-      const cx<T> sum = xk + xc;
-      const cx<T> dif = cmulc(xk - xc, gen::tw_at(wx, k));
-      B[k] = cx<T>{sum.r - dif.i, sum.i + dif.r};
-    }
-    __syncthreads();
-    Z = gen::fft<T>(B, A, g, wl, t, true);   // Z[j] = x[2j] + i x[2j+1] (scaled)
-    if constexpr (OUT_SPEC) {
-      if (a.op == OP_Y_W)
-        gen::mid_row<T, OP_Y_W>(I, rowpix, Z, L, t, nt);
-      else
-        gen::mid_row<T, OP_MASK>(I, rowpix, Z, L, t, nt);
-    } else {
-      switch (a.op) {
-        case OP_Q: gen::sink_row<T, OP_Q>(I, rowpix, Z, L, t, nt, acc, 0); break;
-        case OP_Z: gen::sink_row<T, OP_Z>(I, rowpix, Z, L, t, nt, acc, 0); break;
-        case OP_B: gen::sink_row<T, OP_B>(I, rowpix, Z, L, t, nt, acc, 0); break;
-        case OP_RES: gen::sink_row<T, OP_RES>(I, rowpix, Z, L, t, nt, acc, 0); break;
-        case OP_GRAD: gen::sink_row<T, OP_GRAD>(I, rowpix, Z, L, t, nt, acc, 0); break;
-        case OP_RELAX: gen::sink_row<T, OP_RELAX>(I, rowpix, Z, L, t, nt, acc, 0); break;
-        case OP_KSEL: gen::sink_row<T, OP_KSEL>(I, rowpix, Z, L, t, nt, acc, a.param); break;
-        case OP_STORE_Y: gen::sink_row<T, OP_STORE_Y>(I, rowpix, Z, L, t, nt, acc, 0); break;
-        case OP_STORE_Y_MASK:
-          gen::sink_row<T, OP_STORE_Y_MASK>(I, rowpix, Z, L, t, nt, acc, 0);
-          break;
-        default: break;
+    gen::dit<T, V>(Z, g, wl, t, g.nst);   // Z[j] = x[2j] + i x[2j+1] (scaled)
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      if (v >= nv) break;
+      const int rowpix = (y0 + v) * a.nx;
+      cx<T>* zv = Z + v;
+      if constexpr (OUT_SPEC) {
+        if (a.op == OP_Y_W)
+          gen::mid_row<T, OP_Y_W, V>(I, rowpix, zv, L, t, nt);
+        else
+          gen::mid_row<T, OP_MASK, V>(I, rowpix, zv, L, t, nt);
+      } else {
+        switch (a.op) {
+          case OP_Q: gen::sink_row<T, OP_Q, V>(I, rowpix, zv, L, t, nt, acc, 0); break;
+          case OP_Z: gen::sink_row<T, OP_Z, V>(I, rowpix, zv, L, t, nt, acc, 0); break;
+          case OP_B: gen::sink_row<T, OP_B, V>(I, rowpix, zv, L, t, nt, acc, 0); break;
+          case OP_RES: gen::sink_row<T, OP_RES, V>(I, rowpix, zv, L, t, nt, acc, 0); break;
+          case OP_GRAD: gen::sink_row<T, OP_GRAD, V>(I, rowpix, zv, L, t, nt, acc, 0); break;
+          case OP_RELAX: gen::sink_row<T, OP_RELAX, V>(I, rowpix, zv, L, t, nt, acc, 0); break;
+          case OP_KSEL:
+            gen::sink_row<T, OP_KSEL, V>(I, rowpix, zv, L, t, nt, acc, a.param);
+            break;
+          case OP_STORE_Y: gen::sink_row<T, OP_STORE_Y, V>(I, rowpix, zv, L, t, nt, acc, 0); break;
+          case OP_STORE_Y_MASK:
+            gen::sink_row<T, OP_STORE_Y_MASK, V>(I, rowpix, zv, L, t, nt, acc, 0);
+            break;
+          default: break;
+        }
       }
     }
   } else if constexpr (XI) {
-    for (int j = t; j < L; j += nt) {
-      double x0, x1;
-      normal_pair(I.seed, (uint32_t)((rowpix >> 1) + j), x0, x1);
-      A[j] = cx<T>{(T)x0, (T)x1};
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const int rowpix = (y0 + (v < nv ? v : 0)) * a.nx;
+      for (int j = t; j < L; j += nt) {
+        double x0 = 0.0, x1 = 0.0;
+        if (v < nv) normal_pair(I.seed, (uint32_t)((rowpix >> 1) + j), x0, x1);
+        Z[j * V + v] = cx<T>{(T)x0, (T)x1};
+      }
     }
   } else {
     const T alpha = (T)I.st->alpha, beta = (T)I.st->beta;
-    switch (a.op) {
-      case OP_R_UPD: gen::src_row<T, OP_R_UPD>(I, rowpix, A, L, t, nt, alpha, beta, acc); break;
-      case OP_P_UPD_Z:
-        gen::src_row<T, OP_P_UPD_Z>(I, rowpix, A, L, t, nt, alpha, beta, acc);
-        break;
-      case OP_P_UPD_R:
-        gen::src_row<T, OP_P_UPD_R>(I, rowpix, A, L, t, nt, alpha, beta, acc);
-        break;
-      case OP_LOAD_R: gen::src_row<T, OP_LOAD_R>(I, rowpix, A, L, t, nt, alpha, beta, acc); break;
-      case OP_LOAD_U: gen::src_row<T, OP_LOAD_U>(I, rowpix, A, L, t, nt, alpha, beta, acc); break;
-      case OP_LOAD_Y: gen::src_row<T, OP_LOAD_Y>(I, rowpix, A, L, t, nt, alpha, beta, acc); break;
-      case OP_LOAD_W: gen::src_row<T, OP_LOAD_W>(I, rowpix, A, L, t, nt, alpha, beta, acc); break;
-      case OP_LOAD_W_MASK:
-        gen::src_row<T, OP_LOAD_W_MASK>(I, rowpix, A, L, t, nt, alpha, beta, acc);
-        break;
-      case OP_LOAD_D_U:
-        gen::src_row<T, OP_LOAD_D_U>(I, rowpix, A, L, t, nt, alpha, beta, acc);
-        break;
-      case OP_U64_UPD:
-        gen::src_row<T, OP_U64_UPD>(I, rowpix, A, L, t, nt, alpha, beta, acc);
-        break;
-      default:
-        for (int j = t; j < L; j += nt) A[j] = cx<T>{(T)0, (T)0};
-        break;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      cx<T>* zv = Z + v;
+      if (v >= nv) {   // padding row: zeros
+        for (int j = t; j < L; j += nt) zv[j * V] = cx<T>{(T)0, (T)0};
+        continue;
+      }
+      const int rowpix = (y0 + v) * a.nx;
+      switch (a.op) {
+        case OP_R_UPD:
+          gen::src_row<T, OP_R_UPD, V>(I, rowpix, zv, L, t, nt, alpha, beta, acc);
+          break;
+        case OP_P_UPD_Z:
+          gen::src_row<T, OP_P_UPD_Z, V>(I, rowpix, zv, L, t, nt, alpha, beta, acc);
+          break;
+        case OP_P_UPD_R:
+          gen::src_row<T, OP_P_UPD_R, V>(I, rowpix, zv, L, t, nt, alpha, beta, acc);
+          break;
+        case OP_LOAD_R:
+          gen::src_row<T, OP_LOAD_R, V>(I, rowpix, zv, L, t, nt, alpha, beta, acc);
+          break;
+        case OP_LOAD_U:
+          gen::src_row<T, OP_LOAD_U, V>(I, rowpix, zv, L, t, nt, alpha, beta, acc);
+          break;
+        case OP_LOAD_Y:
+          gen::src_row<T, OP_LOAD_Y, V>(I, rowpix, zv, L, t, nt, alpha, beta, acc);
+          break;
+        case OP_LOAD_W:
+          gen::src_row<T, OP_LOAD_W, V>(I, rowpix, zv, L, t, nt, alpha, beta, acc);
+          break;
+        case OP_LOAD_W_MASK:
+          gen::src_row<T, OP_LOAD_W_MASK, V>(I, rowpix, zv, L, t, nt, alpha, beta, acc);
+          break;
+        case OP_LOAD_D_U:
+          gen::src_row<T, OP_LOAD_D_U, V>(I, rowpix, zv, L, t, nt, alpha, beta, acc);
+          break;
+        case OP_U64_UPD:
+          gen::src_row<T, OP_U64_UPD, V>(I, rowpix, zv, L, t, nt, alpha, beta, acc);
+          break;
+        default:
+          for (int j = t; j < L; j += nt) zv[j * V] = cx<T>{(T)0, (T)0};
+          break;
+      }
     }
   }
 
   if constexpr (OUT_SPEC) {
     __syncthreads();
-    Z = gen::fft<T>(Z, Z == A ? B : A, g, wl, t, false);
-    const int off = (Z == A) ? 0 : L + 1;   // the same buffer in every row
-    // R2C: X[k] = (Z[k] + conj Z[L-k]) / 2 - (i/2) e^{-2 pi i k/nx} (Z[k] - conj Z[L-k]),
-    // X[L] = Re Z[0] - Im Z[0]; stored transposed, consecutive threads on consecutive rows
-    T* spec = a.spec_sel ? I.spec2 : I.spec;
-    for (int f = threadIdx.x; f < (L + 1) * rows; f += blockDim.x) {
-      const int k = f >> a.log_rows, r = f & (rows - 1);
-      const cx<T>* Zr = base + r * stride + off;
-      cx<T> X;
-      if (k < L) {
-        const cx<T> zk = Zr[k], zc = conjx(Zr[k == 0 ? 0 : L - k]);
-        const cx<T> ev = scal(zk + zc, (T)0.5);
-        const cx<T> od = scal(mul_mi<T, false>(zk - zc), (T)0.5);
-        X = ev + cmul(od, gen::tw_at(wx, k));
-      } else {
-        const cx<T> z0 = Zr[0];
-        X = cx<T>{z0.r - z0.i, (T)0};
-      }
-      st_cx<T>(spec + 2 * ((size_t)k * ny + y0 + r), X);
-    }
+    gen::dif<T, V>(Z, g, wl, t, g.nst);
+    gen::r2c<T, V>(a.spec_sel ? I.spec2 : I.spec, ny, y0, g, wx, Z, t, nt);
   }
 
   if (a.sop != SC_NONE)
@@ -470,90 +615,185 @@ k_row_gen(const InstDesc<T>* __restrict__ insts, RowArgs a, GenLen g, const T* _
 }
 
 // ----------------------------------------------------------------- column pass
-// CTA = `ffts` spectrum rows (one kx each), g.nt threads per column; forward
-// FFT, x table, inverse FFT, in place (table < 0: forward only; PRE: input
-// already transformed in spec, output to spec_sel's buffer).  Shared memory:
-// two buffers of ny complex values per column.
-template <typename T, bool PRE = false>
-__global__ void __launch_bounds__(KCfg<T>::kMaxThreads)
+// CTA = a.ffts spectrum rows (one kx each) in groups of V; forward FFT (all
+// stages but the last), then per butterfly of the last stage: its forward
+// DFT, the table at the butterfly's frequencies k0 + q n/R, the inverse DFT;
+// then the remaining inverse stages and the store, in natural order
+// (table < 0: forward only, the last stage's outputs stored at their
+// frequencies; PRE: the input is spec, already transformed, gathered at the
+// same frequencies, and the output goes to spec_sel's buffer).  Shared
+// memory: ny complex values per column.
+namespace gen {
+
+template <typename T, int V, int R, bool PRE>
+__device__ __forceinline__ void col_middle(cx<T>* z, const GenLen& g, const T* tab0,
+                                           long long tstride, const T* src0, T* dst0,
+                                           long long cstride, int nv, int table, int t, int nt) {
+  const int N = g.n, nb = N / R;   // the last stage's butterflies; k = k0 + q nb
+  for (int blk = t; blk < nb; blk += nt) {
+    const int k0 = g.rev[blk * R];
+    cx<T> v[V][R];
+    if constexpr (PRE) {
+#pragma unroll
+      for (int u = 0; u < V; ++u)
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+          v[u][q] = u < nv ? ld_cx<T>(src0 + u * cstride + 2 * (k0 + q * nb)) : cx<T>{(T)0, (T)0};
+    } else {
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        cx<T> sl[V];
+        ld_slot<T, V>(z + (blk * R + q) * V, sl);
+#pragma unroll
+        for (int u = 0; u < V; ++u) v[u][q] = sl[u];
+      }
+#pragma unroll
+      for (int u = 0; u < V; ++u) dft<T, R, false>(v[u]);
+    }
+    if (table < 0) {
+#pragma unroll
+      for (int u = 0; u < V; ++u)
+        if (u < nv)
+#pragma unroll
+          for (int q = 0; q < R; ++q) st_cx<T>(dst0 + u * cstride + 2 * (k0 + q * nb), v[u][q]);
+      continue;
+    }
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+#pragma unroll
+      for (int q = 0; q < R; ++q)
+        v[u][q] = scal(v[u][q], u < nv ? ldg1(tab0 + u * tstride + k0 + q * nb) : (T)0);
+      dft<T, R, true>(v[u]);
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      cx<T> sl[V];
+#pragma unroll
+      for (int u = 0; u < V; ++u) sl[u] = v[u][q];
+      st_slot<T, V>(z + (blk * R + q) * V, sl);
+    }
+  }
+}
+
+}  // namespace gen
+
+template <typename T, int V, bool PRE = false>
+__global__ void __launch_bounds__(kGenThreads, gen_minb<T>())
 k_col_gen(const InstDesc<T>* __restrict__ insts, ColArgs a, GenLen g, const T* __restrict__ wn) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const InstDesc<T>& I = insts[blockIdx.x];
   if (skip_instance(a.check_done, I.st)) return;
-  const int N = g.n;
-  const int f = threadIdx.x / g.nt, t = threadIdx.x - f * g.nt;
-  const int kx = blockIdx.y * a.ffts + f;
-  const bool act = kx < a.nkx;
-  cx<T>* A = reinterpret_cast<cx<T>*>(smem_raw) + f * 2 * N;
-  cx<T>* B = A + N;
-  T* col = (a.spec_sel ? I.spec2 : I.spec) + 2 * (long long)(act ? kx : 0) * N;
-  const T* srcp = PRE ? I.spec + 2 * (long long)(act ? kx : 0) * N : col;
-  for (int j = t; j < N; j += g.nt) A[j] = act ? ld_cx<T>(srcp + 2 * j) : cx<T>{(T)0, (T)0};
-  __syncthreads();
-  cx<T>* Z = A;
-  if constexpr (!PRE) Z = gen::fft<T>(A, B, g, wn, t, false);
-  if (a.table >= 0) {
-    const T* tab = (a.table >= 2 ? I.kt + (long long)(a.table - 2) * a.nkx * N
-                    : a.table ? I.t_sqrt : I.t_inv) + (long long)(act ? kx : 0) * N;
-    for (int j = t; j < N; j += g.nt) Z[j] = scal(Z[j], act ? ldg1(tab + j) : (T)0);
+  const int N = g.n, nt = g.nt;
+  const int grp = threadIdx.x / nt, t = threadIdx.x - grp * nt;
+  const int kx0 = blockIdx.y * a.ffts + grp * V;
+  const int nv = max(0, min(V, a.nkx - kx0));   // columns of this group inside the spectrum
+  const int kxa = nv > 0 ? kx0 : 0;
+  cx<T>* Z = reinterpret_cast<cx<T>*>(smem_raw) + grp * N * V;
+  const long long cstride = 2LL * N;   // T elements between consecutive columns
+  T* col = (a.spec_sel ? I.spec2 : I.spec) + cstride * kxa;
+  const T* srcp = PRE ? I.spec + cstride * kxa : col;
+  const int S = g.nst, R = g.radix[S - 1];
+
+  if constexpr (!PRE) {
+    for (int y0 = t; y0 < N; y0 += gen::kGenChunk * nt) {
+      cx<T> x[gen::kGenChunk][V];
+#pragma unroll
+      for (int c = 0; c < gen::kGenChunk; ++c) {
+        const int y = min(y0 + c * nt, N - 1);
+#pragma unroll
+        for (int u = 0; u < V; ++u)
+          x[c][u] = u < nv ? ld_stream_cx<T>(srcp + u * cstride + 2 * y) : cx<T>{(T)0, (T)0};
+      }
+#pragma unroll
+      for (int c = 0; c < gen::kGenChunk; ++c)
+        if (y0 + c * nt < N) gen::st_slot<T, V>(Z + (y0 + c * nt) * V, x[c]);
+    }
     __syncthreads();
-    Z = gen::fft<T>(Z, Z == A ? B : A, g, wn, t, true);
+    gen::dif<T, V>(Z, g, wn, t, S - 1);
   }
-  if (act)
-    for (int j = t; j < N; j += g.nt) st_cx<T>(col + 2 * j, Z[j]);
+  const T* tab0 = nullptr;
+  long long tstride = N;
+  if (a.table >= 0)
+    tab0 = (a.table >= 2 ? I.kt + (long long)(a.table - 2) * a.nkx * N
+            : a.table ? I.t_sqrt : I.t_inv) + (long long)kxa * N;
+  switch (R) {
+    case 2: gen::col_middle<T, V, 2, PRE>(Z, g, tab0, tstride, srcp, col, cstride, nv, a.table, t, nt); break;
+    case 3: gen::col_middle<T, V, 3, PRE>(Z, g, tab0, tstride, srcp, col, cstride, nv, a.table, t, nt); break;
+    case 4: gen::col_middle<T, V, 4, PRE>(Z, g, tab0, tstride, srcp, col, cstride, nv, a.table, t, nt); break;
+    case 5: gen::col_middle<T, V, 5, PRE>(Z, g, tab0, tstride, srcp, col, cstride, nv, a.table, t, nt); break;
+    default: gen::col_middle<T, V, 7, PRE>(Z, g, tab0, tstride, srcp, col, cstride, nv, a.table, t, nt); break;
+  }
+  if (a.table < 0) return;
+  __syncthreads();
+  gen::dit<T, V>(Z, g, wn, t, S - 1);
+  for (int y0 = t; y0 < N; y0 += gen::kGenChunk * nt) {
+#pragma unroll
+    for (int c = 0; c < gen::kGenChunk; ++c) {
+      const int y = y0 + c * nt;
+      if (y >= N) break;
+      cx<T> x[V];
+      gen::ld_slot<T, V>(Z + y * V, x);
+#pragma unroll
+      for (int u = 0; u < V; ++u)
+        if (u < nv) st_cx<T>(col + u * cstride + 2 * y, x[u]);
+    }
+  }
 }
 
 // ----------------------------------------------------------------- launchers
 template <typename T>
 size_t GenLaunch<T>::row_smem(int L, int rows) {
-  return size_t(rows) * 2 * (L + 1) * sizeof(cx<T>);
+  return size_t(rows) * L * sizeof(cx<T>);
 }
 
 template <typename T>
 size_t GenLaunch<T>::col_smem(int ny, int ffts) {
-  return size_t(ffts) * 2 * ny * sizeof(cx<T>);
+  return size_t(ffts) * ny * sizeof(cx<T>);
 }
 
 template <typename T>
-int GenLaunch<T>::max_threads() { return KCfg<T>::kMaxThreads; }
+int GenLaunch<T>::max_threads() { return kGenThreads; }
 
 template <typename T>
 cudaError_t GenLaunch<T>::row(bool in_spec, bool out_spec, const InstDesc<T>* d, int ninst,
                               const RowArgs& a, const GenLen& g, const T* wl, const T* wx,
                               cudaStream_t s) {
-  const dim3 grid(a.ny / a.rows, ninst), block(a.rows * g.nt);
+  constexpr int V = gen_v<T>();
+  const dim3 grid((a.ny + a.rows - 1) / a.rows, ninst), block(a.rows / V * g.nt);
   const size_t sm = row_smem(g.n, a.rows);
   if (in_spec && out_spec)
-    k_row_gen<T, true, true><<<grid, block, sm, s>>>(d, a, g, wl, wx);
+    k_row_gen<T, V, true, true><<<grid, block, sm, s>>>(d, a, g, wl, wx);
   else if (in_spec)
-    k_row_gen<T, true, false><<<grid, block, sm, s>>>(d, a, g, wl, wx);
+    k_row_gen<T, V, true, false><<<grid, block, sm, s>>>(d, a, g, wl, wx);
   else if (a.op == OP_XI)
-    k_row_gen<T, false, true, true><<<grid, block, sm, s>>>(d, a, g, wl, wx);
+    k_row_gen<T, V, false, true, true><<<grid, block, sm, s>>>(d, a, g, wl, wx);
   else
-    k_row_gen<T, false, true><<<grid, block, sm, s>>>(d, a, g, wl, wx);
+    k_row_gen<T, V, false, true><<<grid, block, sm, s>>>(d, a, g, wl, wx);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t GenLaunch<T>::col(const InstDesc<T>* d, int ninst, const ColArgs& a, const GenLen& g,
                               const T* wn, cudaStream_t s) {
-  const dim3 grid(ninst, (a.nkx + a.ffts - 1) / a.ffts), block(a.ffts * g.nt);
+  constexpr int V = gen_v<T>();
+  const dim3 grid(ninst, (a.nkx + a.ffts - 1) / a.ffts), block(a.ffts / V * g.nt);
   const size_t sm = col_smem(g.n, a.ffts);
   if (a.pre)
-    k_col_gen<T, true><<<grid, block, sm, s>>>(d, a, g, wn);
+    k_col_gen<T, V, true><<<grid, block, sm, s>>>(d, a, g, wn);
   else
-    k_col_gen<T><<<grid, block, sm, s>>>(d, a, g, wn);
+    k_col_gen<T, V><<<grid, block, sm, s>>>(d, a, g, wn);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t GenLaunch<T>::prepare() {
-  cudaError_t e = detail::allow_smem(k_row_gen<T, true, true>);
-  if (e == cudaSuccess) e = detail::allow_smem(k_row_gen<T, true, false>);
-  if (e == cudaSuccess) e = detail::allow_smem(k_row_gen<T, false, true>);
-  if (e == cudaSuccess) e = detail::allow_smem(k_row_gen<T, false, true, true>);
-  if (e == cudaSuccess) e = detail::allow_smem(k_col_gen<T>);
-  if (e == cudaSuccess) e = detail::allow_smem(k_col_gen<T, true>);
+  constexpr int V = gen_v<T>();
+  cudaError_t e = detail::allow_smem(k_row_gen<T, V, true, true>);
+  if (e == cudaSuccess) e = detail::allow_smem(k_row_gen<T, V, true, false>);
+  if (e == cudaSuccess) e = detail::allow_smem(k_row_gen<T, V, false, true>);
+  if (e == cudaSuccess) e = detail::allow_smem(k_row_gen<T, V, false, true, true>);
+  if (e == cudaSuccess) e = detail::allow_smem(k_col_gen<T, V>);
+  if (e == cudaSuccess) e = detail::allow_smem(k_col_gen<T, V, true>);
   return e;
 }
 

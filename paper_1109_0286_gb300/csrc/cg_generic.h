@@ -7,36 +7,80 @@
 // same helpers): a ROW pass (real row <-> half spectrum, R2C / C2R by a
 // half-length complex FFT, the elementwise operation of the pass fused in),
 // a COLUMN pass (forward FFT, x real table, inverse FFT) and the inverse ROW
-// pass.  The transforms are self-sorting (Stockham) mixed-radix FFTs in shared
-// memory: stages of radix 4, 2, 3, 5, 7, each thread taking whole butterflies,
-// two buffers ping-ponged between stages, twiddles W_n^t from a table built in
-// FP64 on the host.
+// pass.
+//
+// The transforms run in place in shared memory.  The forward transform is a
+// decimation-in-frequency (Gentleman-Sande) factorisation n = R_0 R_1 ...
+// R_{S-1}: stage s splits every block of n_s = R_s ... R_{S-1} points into R_s
+// interleaved sub-blocks with butterflies of radix R_s, each thread reading
+// and writing the same R_s positions, so no second buffer is needed.  Its
+// output sits in digit-reversed order: position p = sum_s q_s h_s
+// (h_s = n_{s+1}) holds frequency k = sum_s q_s R_0 ... R_{s-1}.  The inverse
+// is the transposed factorisation (decimation in time, stages in reverse
+// order, conjugate twiddles), which takes digit-reversed input to natural
+// output.  The column pass chains the two with the spectral table applied at
+// the digit-reversed positions, fusing the last forward stage, the table and
+// the first inverse stage into one step; the row passes permute once, when
+// they read or write the half spectrum (frequency k <-> position pos[k]).
+//
+// A thread group of g.nt threads works on V transforms at once (V rows, or V
+// columns), their values interleaved in shared memory as [position][V]: a
+// butterfly's index arithmetic and twiddles serve all V, and a position's V
+// values move as one 16-byte access in FP32.
 #pragma once
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "cg_types.h"
 
 namespace cgf {
 
-constexpr int kGenMaxStages = 24;
+constexpr int kGenMaxStages = 16;
 constexpr int kGenMaxLen = 4096;   // nx / 2 and ny at most 4096
 
-// One transform length: its stage radices (applied in this order) and the
-// threads that share one transform.
+// One transform length: its stage radices (applied in this order by the
+// forward transform), the offsets of the stages' twiddles in its table, the
+// threads that share one group of V transforms, and the digit-reversal maps.
 struct GenLen {
   int n;
   int nst;
   int nt;
   int radix[kGenMaxStages];
+  // Stage s < nst - 1: twiddles W_{n_s}^{q j} (j < h_s, q = 1 .. R_s - 1) at
+  // complex entry twoff[s] + j (R_s - 1) + q - 1 of the table.  The last stage
+  // (h = 1) has none.
+  int twoff[kGenMaxStages];
+  const unsigned short* rev;   // device, n entries: position -> frequency
+  const unsigned short* pos;   // device, n entries: frequency -> position
 };
 
-// Factor n into radix-4, 2, 3, 5, 7 stages; false if n has another prime factor.
+// Factor n into radix-4, 2, 3, 5, 7 stages and lay out the stage twiddles;
+// false if n has another prime factor.  (The tables themselves and the
+// digit-reversal maps are built with the plan.)
 bool gen_factor(int n, GenLen* g);
+
+// Transforms per thread group: 2 in FP32, 1 in FP64 and double-float (their
+// butterflies already hold twice the registers).
+template <typename T>
+constexpr int gen_v() { return std::is_same<T, float>::value ? 2 : 1; }
+#ifndef CGF_GEN_THREADS
+#define CGF_GEN_THREADS 256
+#endif
+#ifndef CGF_GEN_MINB
+#define CGF_GEN_MINB 3
+#endif
+constexpr int kGenThreads = CGF_GEN_THREADS;   // most threads in one CTA
+// CTAs per SM the kernels are compiled for (registers per thread
+// 65536 / (kGenThreads x this)): FP32, then FP64 and double-float.
+template <typename T>
+constexpr int gen_minb() { return std::is_same<T, float>::value ? CGF_GEN_MINB : 2; }
 
 template <typename T>
 struct GenLaunch {
-  // wl: W_L^t (t < L), wx: W_nx^k (k <= L), wn: W_ny^t (t < ny); complex, interleaved.
-  // The white-noise source (op OP_XI) runs its own instantiation.
+  // wl: table of nx / 2, wx: W_nx^k (k <= nx / 2), wn: table of ny.  Rows per
+  // CTA (RowArgs::rows) and columns per CTA (ColArgs::ffts) are multiples of
+  // gen_v<T>().  The white-noise source (op OP_XI) runs its own instantiation.
   static cudaError_t row(bool in_spec, bool out_spec, const InstDesc<T>* d, int ninst,
                          const RowArgs& a, const GenLen& g, const T* wl, const T* wx,
                          cudaStream_t s);

@@ -922,19 +922,58 @@ void twiddles_len(int n, int count, std::vector<double>& w) {
   }
 }
 
-// Threads per mixed-radix transform (a multiple of 32, at most 512).  A stage
-// of radix R has n/R butterflies, shared round-robin by the transform's
-// threads; the last round leaves threads idle.  Among the candidates, take the
-// one with the best product of stage efficiency (butterflies / thread slots
-// over all stages) and SM occupancy (transforms resident per SM by shared
-// memory -- `slots` complex values each -- times threads, against the
-// threads the registers allow: 1024 at 64 per thread for FP32, 512 at 128
-// for FP64 and double-float).
-void gen_threads(GenLen* g, size_t slots, bool wide) {
-  const double tmax = wide ? 512.0 : 1024.0;
-  const size_t bytes = slots * (wide ? 16 : 8), per_sm = size_t(225) * 1024 / bytes;
+// The table of a factored mixed-radix length (complex entries, interleaved,
+// FP64: the stage twiddles in the layout of GenLen::twoff; at least one entry)
+// and its digit-reversal maps.
+void gen_tables(const GenLen& g, std::vector<double>& tw, std::vector<unsigned short>& rev,
+                std::vector<unsigned short>& pos) {
+  const int n = g.n, S = g.nst;
+  std::vector<double> w;   // W_n^t, t < n
+  twiddles_len(n, n, w);
+  tw.clear();
+  auto push = [&](const std::vector<double>& src, int t) {
+    tw.push_back(src[2 * size_t(t)]);
+    tw.push_back(src[2 * size_t(t) + 1]);
+  };
+  // W_ns^{q j} = W_n^{q j (n / ns)}
+  int ns = n;
+  for (int s = 0; s < S - 1; ++s) {
+    const int R = g.radix[s], h = ns / R, step = n / ns;
+    for (int j = 0; j < h; ++j)
+      for (int q = 1; q < R; ++q) push(w, (int)(((long long)q * j * step) % n));
+    ns = h;
+  }
+  // position p = sum_s q_s h_s holds frequency k = sum_s q_s R_0 ... R_{s-1}
+  rev.assign(n, 0);
+  pos.assign(n, 0);
+  for (int p = 0; p < n; ++p) {
+    int rem = p, k = 0, wgt = 1, nss = n;
+    for (int s = 0; s < S; ++s) {
+      const int h = nss / g.radix[s], q = rem / h;
+      rem -= q * h;
+      k += q * wgt;
+      wgt *= g.radix[s];
+      nss = h;
+    }
+    rev[p] = (unsigned short)k;
+    pos[k] = (unsigned short)p;
+  }
+}
+
+// Threads per group of V mixed-radix transforms (a multiple of 32, at most
+// 512).  A stage of radix R has n/R butterflies, shared round-robin by the
+// group's threads; the last round leaves threads idle.  Among the
+// candidates, take the one with the best product of stage efficiency
+// (butterflies / thread slots over all stages) and SM occupancy (groups
+// resident per SM by shared memory -- V n complex values each -- times
+// threads, against the threads an SM runs at the kernels' register counts:
+// kGenThreads x gen_minb).
+void gen_threads(GenLen* g, int V, bool wide) {
+  const double tmax = double(kGenThreads) * (wide ? gen_minb<double>() : gen_minb<float>());
+  const size_t bytes = size_t(V) * g->n * (wide ? 16 : 8);
+  const size_t per_sm = std::max<size_t>(1, size_t(225) * 1024 / bytes);
   double best = -1.0;
-  for (int nt = 32; nt <= 512; nt += 32) {
+  for (int nt = 32; nt <= kGenThreads; nt += 32) {
     long long slots_used = 0, work = 0;
     for (int s = 0; s < g->nst; ++s) {
       const int nb = g->n / g->radix[s];
@@ -952,45 +991,46 @@ void gen_threads(GenLen* g, size_t slots, bool wide) {
 }
 
 // Mixed-radix schedule and twiddle tables of one precision: rows per CTA
-// (4, 2 or 1, dividing ny, within the thread and shared-memory limits) and
-// column FFTs per CTA, unless the options fix them.
+// and column FFTs per CTA (multiples of the group width V = gen_v<T>(), one
+// or two groups of g.nt threads, within the shared-memory limit), unless the
+// options fix them; the digit-reversal maps once per plan.
 template <typename T>
 fill_status setup_generic(fill_plan* p) {
   Precision<T>& P = prec<T>(p);
+  constexpr int V = gen_v<T>();
   const int L = p->nx / 2, ny = p->ny, maxt = GenLaunch<T>::max_threads();
   const size_t smax = 200 * 1024;
   auto row_ok = [&](int r) {
-    return r >= 1 && pow2(r) && ny % r == 0 && r * p->grow.nt <= maxt && ny / r <= kMaxPartials &&
-           GenLaunch<T>::row_smem(L, r) <= smax;
+    return r >= V && r % V == 0 && pow2(r / V) && (r / V) * p->grow.nt <= maxt &&
+           (ny + r - 1) / r <= kMaxPartials && GenLaunch<T>::row_smem(L, r) <= smax;
   };
   auto col_ok = [&](int f) {
-    return f >= 1 && f * p->gcol.nt <= maxt && GenLaunch<T>::col_smem(ny, f) <= smax;
+    return f >= V && f % V == 0 && (f / V) * p->gcol.nt <= maxt &&
+           GenLaunch<T>::col_smem(ny, f) <= smax;
   };
-  // defaults: CTAs of at most 512 threads and 113 KB, so that two fit an SM
-  const size_t half = 113 * 1024;
+  // defaults: as many groups as kGenThreads threads hold, in at most 75 KB of
+  // shared memory (three CTAs on an SM)
+  const size_t third = 75 * 1024;
   if (p->o.rows_per_cta > 0) {
     P.rows = p->o.rows_per_cta;
   } else {
-    P.rows = 1;
-    for (int r : {4, 2})
-      if (row_ok(r) && r * p->grow.nt <= 512 && GenLaunch<T>::row_smem(L, r) <= half) {
-        P.rows = r;
-        break;
-      }
+    P.rows = V;
+    if (row_ok(2 * V) && GenLaunch<T>::row_smem(L, 2 * V) <= third) P.rows = 2 * V;
   }
   if (p->o.ffts_per_cta > 0) {
     P.ffts = p->o.ffts_per_cta;
   } else {
-    P.ffts = 1;
-    while (col_ok(2 * P.ffts) && 2 * P.ffts * p->gcol.nt <= 512 &&
-           GenLaunch<T>::col_smem(ny, 2 * P.ffts) <= half && 2 * P.ffts <= 16)
+    P.ffts = V;
+    while (col_ok(2 * P.ffts) && GenLaunch<T>::col_smem(ny, 2 * P.ffts) <= third &&
+           2 * P.ffts <= 16)
       P.ffts *= 2;
   }
   if (!row_ok(P.rows) || !col_ok(P.ffts)) return FILL_EINVAL;
   std::vector<double> wl, wx, wn;
-  twiddles_len(L, L, wl);
+  std::vector<unsigned short> revl, posl, revn, posn;
+  gen_tables(p->grow, wl, revl, posl);
   twiddles_len(p->nx, L + 1, wx);
-  twiddles_len(ny, ny, wn);
+  gen_tables(p->gcol, wn, revn, posn);
   auto upload = [&](T** dst, const std::vector<double>& src) -> cudaError_t {
     std::vector<T> h(src.size());
     for (size_t i = 0; i < src.size(); ++i) h[i] = (T)src[i];
@@ -1001,6 +1041,20 @@ fill_status setup_generic(fill_plan* p) {
   CK(upload(&P.gwl, wl));
   CK(upload(&P.gwx, wx));
   CK(upload(&P.gwn, wn));
+  auto upload_map = [&](const unsigned short** dst, const std::vector<unsigned short>& src) {
+    unsigned short* d = nullptr;
+    cudaError_t e = p->dalloc(&d, src.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(d, src.data(), src.size() * sizeof(unsigned short), cudaMemcpyHostToDevice);
+    *dst = d;
+    return e;
+  };
+  if (!p->grow.rev) {
+    CK(upload_map(&p->grow.rev, revl));
+    CK(upload_map(&p->grow.pos, posl));
+    CK(upload_map(&p->gcol.rev, revn));
+    CK(upload_map(&p->gcol.pos, posn));
+  }
   CK(GenLaunch<T>::prepare());
   return FILL_OK;
 }
@@ -1227,8 +1281,8 @@ fill_status fill_init(fill_plan** out, int ny, int nx, const double* P_half,
       return FILL_EINVAL;
     // threads per transform, for the precision that carries the CG loop
     const bool wide = opts && opts->mode == FILL_MODE_FP64;
-    gen_threads(&grow, size_t(2) * (nx / 2 + 1), wide);
-    gen_threads(&gcol, size_t(2) * ny, wide);
+    gen_threads(&grow, wide ? 1 : 2, wide);
+    gen_threads(&gcol, wide ? 1 : 2, wide);
   }
   fill_opts o;
   if (opts)
