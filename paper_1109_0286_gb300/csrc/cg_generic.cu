@@ -13,6 +13,7 @@ bool gen_factor(int n, GenLen* g) {
       m /= r;
     }
   };
+  take(8);
   take(4);
   take(2);
   take(3);

@@ -1,4 +1,4 @@
-// Mixed-radix pass kernels (radix 2, 3, 4, 5, 7, in-place DIF / DIT
+// Mixed-radix pass kernels (radix 2, 3, 4, 5, 7, 8, in-place DIF / DIT
 // transforms) and their launchers; see cg_generic.h.  The fused operations
 // are those of cg_kernels.cuh, applied per pixel pair; mask flags and compact
 // indices come from the global mask words (a row need not start on a word
@@ -67,6 +67,27 @@ __device__ __forceinline__ void dft(cx<T> (&v)[R]) {
     v[2] = s02 - s13;
     v[1] = d02 + d13;
     v[3] = d02 - d13;
+  } else if constexpr (R == 8) {
+    // two 4-point DFTs (even, odd inputs), then y_q = E_q + W_8^q O_q and
+    // y_{q+4} = E_q - W_8^q O_q
+    cx<T> e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+    dft<T, 4, INV>(e);
+    dft<T, 4, INV>(o);
+    const T h = T(0.70710678118654752);   // 1 / sqrt 2
+    // W_8 = (1 - i) / sqrt 2, W_8^3 = (-1 - i) / sqrt 2 (conjugates for the inverse)
+    const cx<T> o1 = INV ? cx<T>{(o[1].r - o[1].i) * h, (o[1].i + o[1].r) * h}
+                         : cx<T>{(o[1].r + o[1].i) * h, (o[1].i - o[1].r) * h};
+    const cx<T> o2 = mul_mi<T, INV>(o[2]);
+    const cx<T> o3 = INV ? cx<T>{-(o[3].r + o[3].i) * h, (o[3].r - o[3].i) * h}
+                         : cx<T>{(o[3].i - o[3].r) * h, -(o[3].r + o[3].i) * h};
+    v[0] = e[0] + o[0];
+    v[4] = e[0] - o[0];
+    v[1] = e[1] + o1;
+    v[5] = e[1] - o1;
+    v[2] = e[2] + o2;
+    v[6] = e[2] - o2;
+    v[3] = e[3] + o3;
+    v[7] = e[3] - o3;
   } else {
     constexpr int H = (R - 1) / 2;
     cx<T> S[H + 1], D[H + 1];
@@ -167,6 +188,7 @@ __device__ __forceinline__ void stage_r(int R, cx<T>* z, int ns, int h, int nb, 
     case 3: stage<T, V, 3, INV>(z, ns, h, nb, tws, t, nt); break;
     case 4: stage<T, V, 4, INV>(z, ns, h, nb, tws, t, nt); break;
     case 5: stage<T, V, 5, INV>(z, ns, h, nb, tws, t, nt); break;
+    case 8: stage<T, V, 8, INV>(z, ns, h, nb, tws, t, nt); break;
     default: stage<T, V, 7, INV>(z, ns, h, nb, tws, t, nt); break;
   }
 }
@@ -221,22 +243,49 @@ __device__ __forceinline__ cx<T> r2c_one(cx<T> zk, cx<T> zm, cx<T> w) {
 
 constexpr int kGenChunk = 4;
 
+// Rows y0 .. y0 + V - 1 of half-spectrum row k (element offset off = k ny + y0):
+// one 16-byte access for two FP32 rows when ny is even (off is then even);
+// rows at or beyond ny (nv < V) read zeros and are not written.
+template <typename T, int V>
+__device__ __forceinline__ void ld_spec(const T* spec, size_t off, int nv, bool vec,
+                                        cx<T> (&x)[V]) {
+  if constexpr (V == 2 && std::is_same<T, float>::value) {
+    if (vec) {
+      const float4 a = __ldg(reinterpret_cast<const float4*>(spec + 2 * off));
+      x[0] = cx<float>{a.x, a.y};
+      x[1] = cx<float>{a.z, a.w};
+      return;
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < V; ++v) x[v] = v < nv ? ldg_cx<T>(spec + 2 * (off + v)) : cx<T>{(T)0, (T)0};
+}
+template <typename T, int V>
+__device__ __forceinline__ void st_spec(T* spec, size_t off, int nv, bool vec, const cx<T> (&x)[V]) {
+  if constexpr (V == 2 && std::is_same<T, float>::value) {
+    if (vec) {
+      *reinterpret_cast<float4*>(spec + 2 * off) = make_float4(x[0].r, x[0].i, x[1].r, x[1].i);
+      return;
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < V; ++v)
+    if (v < nv) st_cx<T>(spec + 2 * (off + v), x[v]);
+}
+
 template <typename T, int V>
 __device__ __forceinline__ void c2r(const T* spec, int ny, int y0, const GenLen& g, const T* wx,
                                     cx<T>* z, int t, int nt) {
   const int L = g.n, half = L / 2, nv = min(V, ny - y0);
+  const bool vec = (ny & 1) == 0;
   constexpr int CH = 2;
   for (int k0 = t; k0 <= half; k0 += CH * nt) {
     cx<T> xa[CH][V], xb[CH][V], wa[CH], wb[CH];
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
       const int k = min(k0 + c * nt, half), kc = L - k;
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        const bool ok = v < nv;
-        xa[c][v] = ok ? ldg_cx<T>(spec + 2 * ((size_t)k * ny + y0 + v)) : cx<T>{(T)0, (T)0};
-        xb[c][v] = ok ? ldg_cx<T>(spec + 2 * ((size_t)kc * ny + y0 + v)) : cx<T>{(T)0, (T)0};
-      }
+      ld_spec<T, V>(spec, (size_t)k * ny + y0, nv, vec, xa[c]);
+      ld_spec<T, V>(spec, (size_t)kc * ny + y0, nv, vec, xb[c]);
       wa[c] = ldg_cx<T>(wx + 2 * k);
       wb[c] = ldg_cx<T>(wx + 2 * kc);
     }
@@ -268,6 +317,7 @@ template <typename T, int V>
 __device__ __forceinline__ void r2c(T* spec, int ny, int y0, const GenLen& g, const T* wx,
                                     const cx<T>* z, int t, int nt) {
   const int L = g.n, half = L / 2, nv = min(V, ny - y0);
+  const bool vec = (ny & 1) == 0;
   for (int k = t; k <= half; k += nt) {
     const int kc = L - k;
     cx<T> za[V], zb[V];
@@ -279,15 +329,14 @@ __device__ __forceinline__ void r2c(T* spec, int ny, int y0, const GenLen& g, co
       ld_slot<T, V>(z + (int)g.pos[kc] * V, zb);
     }
     const cx<T> wa = ldg_cx<T>(wx + 2 * k), wb = ldg_cx<T>(wx + 2 * kc);
+    cx<T> xa[V], xb[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      if (v >= nv) break;
-      st_cx<T>(spec + 2 * ((size_t)k * ny + y0 + v), r2c_one(za[v], zb[v], wa));
-      if (k == 0)
-        st_cx<T>(spec + 2 * ((size_t)L * ny + y0 + v), cx<T>{za[v].r - za[v].i, (T)0});
-      else if (kc != k)
-        st_cx<T>(spec + 2 * ((size_t)kc * ny + y0 + v), r2c_one(zb[v], za[v], wb));
+      xa[v] = r2c_one(za[v], zb[v], wa);
+      xb[v] = k == 0 ? cx<T>{za[v].r - za[v].i, (T)0} : r2c_one(zb[v], za[v], wb);
     }
+    st_spec<T, V>(spec, (size_t)k * ny + y0, nv, vec, xa);
+    if (k == 0 || kc != k) st_spec<T, V>(spec, (size_t)kc * ny + y0, nv, vec, xb);
   }
 }
 
@@ -441,29 +490,49 @@ __device__ __forceinline__ void chunk_words(const uint2* mw, int rowpix, int j0,
   }
 }
 
+// Operations whose inputs and outputs are all compact CG vectors: a pixel
+// pair without a masked pixel reads nothing, writes nothing, adds nothing to
+// the reduction and (sources) contributes zeros to the transform.
+template <int OP>
+struct CompactOnly {
+  static constexpr bool value = OP == OP_R_UPD || OP == OP_P_UPD_Z || OP == OP_P_UPD_R ||
+                                OP == OP_LOAD_R || OP == OP_LOAD_U || OP == OP_U64_UPD ||
+                                OP == OP_LOAD_W_MASK || OP == OP_Q || OP == OP_Z ||
+                                OP == OP_B || OP == OP_RES || OP == OP_KSEL;
+};
+
 template <typename T, int OP, int V>
 __device__ __forceinline__ void src_row(const InstDesc<T>& I, int rowpix, cx<T>* z, int L, int t,
                                         int nt, T alpha, T beta, Acc<T>& acc) {
   constexpr bool W = !(OP == OP_LOAD_W || OP == OP_LOAD_Y);
+  constexpr bool C = CompactOnly<OP>::value;
   for (int j0 = t; j0 < L; j0 += kGenChunk * nt) {
     Opnd o[kGenChunk];
     chunk_words<W>(I.mw, rowpix, j0, nt, L, o);
     T x[kGenChunk][8];
 #pragma unroll
     for (int u = 0; u < kGenChunk; ++u)
-      if (o[u].ok) src_load<T, OP>(I, o[u], x[u]);
+      if (o[u].ok && (!C || o[u].q.m0 || o[u].q.m1)) src_load<T, OP>(I, o[u], x[u]);
 #pragma unroll
-    for (int u = 0; u < kGenChunk; ++u)
-      if (o[u].ok) z[(j0 + u * nt) * V] = src_op<T, OP>(I, o[u], x[u], alpha, beta, acc);
+    for (int u = 0; u < kGenChunk; ++u) {
+      if (!o[u].ok) continue;
+      cx<T> zz{(T)0, (T)0};
+      if (!C || o[u].q.m0 || o[u].q.m1) zz = src_op<T, OP>(I, o[u], x[u], alpha, beta, acc);
+      z[(j0 + u * nt) * V] = zz;
+    }
   }
 }
 
 template <typename T, int OP, int V>
 __device__ __forceinline__ void sink_row(const InstDesc<T>& I, int rowpix, const cx<T>* z, int L,
                                          int t, int nt, Acc<T>& acc, int param) {
+  constexpr bool C = CompactOnly<OP>::value;
   for (int j0 = t; j0 < L; j0 += kGenChunk * nt) {
     Opnd o[kGenChunk];
     chunk_words<1>(I.mw, rowpix, j0, nt, L, o);
+#pragma unroll
+    for (int u = 0; u < kGenChunk; ++u)
+      if (C) o[u].ok = o[u].ok && (o[u].q.m0 || o[u].q.m1);
     T x[kGenChunk][2];
 #pragma unroll
     for (int u = 0; u < kGenChunk; ++u)
@@ -720,6 +789,7 @@ k_col_gen(const InstDesc<T>* __restrict__ insts, ColArgs a, GenLen g, const T* _
     case 2: gen::col_middle<T, V, 2, PRE>(Z, g, tab0, tstride, srcp, col, cstride, nv, a.table, t, nt); break;
     case 3: gen::col_middle<T, V, 3, PRE>(Z, g, tab0, tstride, srcp, col, cstride, nv, a.table, t, nt); break;
     case 4: gen::col_middle<T, V, 4, PRE>(Z, g, tab0, tstride, srcp, col, cstride, nv, a.table, t, nt); break;
+    case 8: gen::col_middle<T, V, 8, PRE>(Z, g, tab0, tstride, srcp, col, cstride, nv, a.table, t, nt); break;
     case 5: gen::col_middle<T, V, 5, PRE>(Z, g, tab0, tstride, srcp, col, cstride, nv, a.table, t, nt); break;
     default: gen::col_middle<T, V, 7, PRE>(Z, g, tab0, tstride, srcp, col, cstride, nv, a.table, t, nt); break;
   }

@@ -55,7 +55,7 @@ struct GenLen {
   const unsigned short* pos;   // device, n entries: frequency -> position
 };
 
-// Factor n into radix-4, 2, 3, 5, 7 stages and lay out the stage twiddles;
+// Factor n into radix-8, 4, 2, 3, 5, 7 stages and lay out the stage twiddles;
 // false if n has another prime factor.  (The tables themselves and the
 // digit-reversal maps are built with the plan.)
 bool gen_factor(int n, GenLen* g);
