@@ -477,19 +477,6 @@ __device__ __forceinline__ cx<T> mid_op(const InstDesc<T>& I, const Opnd& o, T d
   }
 }
 
-// Operands of the chunk's pixel pairs j = j0 + u nt: mask words first.
-template <int OP_NEEDS_WORD>
-__device__ __forceinline__ void chunk_words(const uint2* mw, int rowpix, int j0, int nt, int L,
-                                            Opnd (&o)[kGenChunk]) {
-#pragma unroll
-  for (int u = 0; u < kGenChunk; ++u) {
-    const int j = j0 + u * nt;
-    o[u].ok = j < L;
-    o[u].pix = rowpix + 2 * (o[u].ok ? j : 0);
-    if (OP_NEEDS_WORD) o[u].q = pair_index(mw, o[u].pix);
-  }
-}
-
 // Operations whose inputs and outputs are all compact CG vectors: a pixel
 // pair without a masked pixel reads nothing, writes nothing, adds nothing to
 // the reduction and (sources) contributes zeros to the transform.
@@ -501,62 +488,120 @@ struct CompactOnly {
                                 OP == OP_B || OP == OP_RES || OP == OP_KSEL;
 };
 
+// The elementwise loops take pixel pair j of all V rows of the group in one
+// thread (one shared-memory slot), CH = kGenChunk / V pairs at a time: mask
+// words first, then every operand load, then the arithmetic and stores.
+// Operands of pairs j = j0 + c nt of the group's rows (row v starts at pixel
+// pix0 + v nx); rows at or beyond ny (v >= nv) are not ok and read the mask
+// word of pixel 0.
+template <int V, int CH, bool WORD>
+__device__ __forceinline__ void chunk_words(const uint2* mw, int pix0, int nx, int nv, int j0,
+                                            int nt, int L, Opnd (&o)[CH][V]) {
+#pragma unroll
+  for (int c = 0; c < CH; ++c)
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const int j = j0 + c * nt;
+      o[c][v].ok = j < L && v < nv;
+      o[c][v].pix = o[c][v].ok ? pix0 + v * nx + 2 * j : 0;   // pixel 0: a valid dummy
+      if (WORD) o[c][v].q = pair_index(mw, o[c][v].pix);
+    }
+}
+
 template <typename T, int OP, int V>
-__device__ __forceinline__ void src_row(const InstDesc<T>& I, int rowpix, cx<T>* z, int L, int t,
-                                        int nt, T alpha, T beta, Acc<T>& acc) {
+__device__ __forceinline__ void src_rows(const InstDesc<T>& I, int pix0, int nx, int nv, cx<T>* z,
+                                         int L, int t, int nt, T alpha, T beta, Acc<T>& acc) {
   constexpr bool W = !(OP == OP_LOAD_W || OP == OP_LOAD_Y);
   constexpr bool C = CompactOnly<OP>::value;
-  for (int j0 = t; j0 < L; j0 += kGenChunk * nt) {
-    Opnd o[kGenChunk];
-    chunk_words<W>(I.mw, rowpix, j0, nt, L, o);
-    T x[kGenChunk][8];
+  constexpr int CH = kGenChunk / V;
+  for (int j0 = t; j0 < L; j0 += CH * nt) {
+    Opnd o[CH][V];
+    chunk_words<V, CH, W>(I.mw, pix0, nx, nv, j0, nt, L, o);
 #pragma unroll
-    for (int u = 0; u < kGenChunk; ++u)
-      if (o[u].ok && (!C || o[u].q.m0 || o[u].q.m1)) src_load<T, OP>(I, o[u], x[u]);
+    for (int c = 0; c < CH; ++c)
 #pragma unroll
-    for (int u = 0; u < kGenChunk; ++u) {
-      if (!o[u].ok) continue;
-      cx<T> zz{(T)0, (T)0};
-      if (!C || o[u].q.m0 || o[u].q.m1) zz = src_op<T, OP>(I, o[u], x[u], alpha, beta, acc);
-      z[(j0 + u * nt) * V] = zz;
+      for (int v = 0; v < V; ++v)
+        if (C) o[c][v].ok = o[c][v].ok && (o[c][v].q.m0 || o[c][v].q.m1);
+    T x[CH][V][8];
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+        if (o[c][v].ok) src_load<T, OP>(I, o[c][v], x[c][v]);
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const int j = j0 + c * nt;
+      if (j >= L) break;
+      cx<T> zz[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        zz[v] = cx<T>{(T)0, (T)0};
+        if (o[c][v].ok) zz[v] = src_op<T, OP>(I, o[c][v], x[c][v], alpha, beta, acc);
+      }
+      st_slot<T, V>(z + j * V, zz);
     }
   }
 }
 
 template <typename T, int OP, int V>
-__device__ __forceinline__ void sink_row(const InstDesc<T>& I, int rowpix, const cx<T>* z, int L,
-                                         int t, int nt, Acc<T>& acc, int param) {
+__device__ __forceinline__ void sink_rows(const InstDesc<T>& I, int pix0, int nx, int nv,
+                                          const cx<T>* z, int L, int t, int nt, Acc<T>& acc,
+                                          int param) {
   constexpr bool C = CompactOnly<OP>::value;
-  for (int j0 = t; j0 < L; j0 += kGenChunk * nt) {
-    Opnd o[kGenChunk];
-    chunk_words<1>(I.mw, rowpix, j0, nt, L, o);
+  constexpr int CH = kGenChunk / V;
+  for (int j0 = t; j0 < L; j0 += CH * nt) {
+    Opnd o[CH][V];
+    chunk_words<V, CH, true>(I.mw, pix0, nx, nv, j0, nt, L, o);
 #pragma unroll
-    for (int u = 0; u < kGenChunk; ++u)
-      if (C) o[u].ok = o[u].ok && (o[u].q.m0 || o[u].q.m1);
-    T x[kGenChunk][2];
+    for (int c = 0; c < CH; ++c)
 #pragma unroll
-    for (int u = 0; u < kGenChunk; ++u)
-      if (o[u].ok) sink_load<T, OP>(I, o[u], x[u]);
+      for (int v = 0; v < V; ++v)
+        if (C) o[c][v].ok = o[c][v].ok && (o[c][v].q.m0 || o[c][v].q.m1);
+    T x[CH][V][2];
 #pragma unroll
-    for (int u = 0; u < kGenChunk; ++u)
-      if (o[u].ok) sink_op<T, OP>(I, o[u], x[u], z[(j0 + u * nt) * V], acc, param);
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+        if (o[c][v].ok) sink_load<T, OP>(I, o[c][v], x[c][v]);
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      bool any = false;
+#pragma unroll
+      for (int v = 0; v < V; ++v) any = any || o[c][v].ok;
+      if (!any) continue;
+      cx<T> zz[V];
+      ld_slot<T, V>(z + (j0 + c * nt) * V, zz);
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+        if (o[c][v].ok) sink_op<T, OP>(I, o[c][v], x[c][v], zz[v], acc, param);
+    }
   }
 }
 
 template <typename T, int OP, int V>
-__device__ __forceinline__ void mid_row(const InstDesc<T>& I, int rowpix, cx<T>* z, int L, int t,
-                                        int nt) {
-  for (int j0 = t; j0 < L; j0 += kGenChunk * nt) {
-    Opnd o[kGenChunk];
-    chunk_words<1>(I.mw, rowpix, j0, nt, L, o);
-    T d[kGenChunk][2];
+__device__ __forceinline__ void mid_rows(const InstDesc<T>& I, int pix0, int nx, int nv, cx<T>* z,
+                                         int L, int t, int nt) {
+  constexpr int CH = kGenChunk / V;
+  for (int j0 = t; j0 < L; j0 += CH * nt) {
+    Opnd o[CH][V];
+    chunk_words<V, CH, true>(I.mw, pix0, nx, nv, j0, nt, L, o);
+    T d[CH][V][2];
 #pragma unroll
-    for (int u = 0; u < kGenChunk; ++u)
-      if (o[u].ok && OP == OP_Y_W) ld_map_pair<T>(I.d + o[u].pix, d[u][0], d[u][1]);
+    for (int c = 0; c < CH; ++c)
 #pragma unroll
-    for (int u = 0; u < kGenChunk; ++u)
-      if (o[u].ok)
-        z[(j0 + u * nt) * V] = mid_op<T, OP>(I, o[u], d[u][0], d[u][1], z[(j0 + u * nt) * V]);
+      for (int v = 0; v < V; ++v)
+        if (o[c][v].ok && OP == OP_Y_W) ld_map_pair<T>(I.d + o[c][v].pix, d[c][v][0], d[c][v][1]);
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const int j = j0 + c * nt;
+      if (j >= L) break;
+      cx<T> zz[V];
+      ld_slot<T, V>(z + j * V, zz);
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+        if (o[c][v].ok) zz[v] = mid_op<T, OP>(I, o[c][v], d[c][v][0], d[c][v][1], zz[v]);
+      st_slot<T, V>(z + j * V, zz);
+    }
   }
 }
 
@@ -582,39 +627,33 @@ k_row_gen(const InstDesc<T>* __restrict__ insts, RowArgs a, GenLen g, const T* _
   cx<T>* Z = reinterpret_cast<cx<T>*>(smem_raw) + grp * L * V;
   Acc<T> acc;
 
+  const int pix0 = y0 * a.nx;
   if constexpr (IN_SPEC) {
     gen::c2r<T, V>(a.spec_sel ? I.spec2 : I.spec, ny, y0, g, wx, Z, t, nt);
     __syncthreads();
     gen::dit<T, V>(Z, g, wl, t, g.nst);   // Z[j] = x[2j] + i x[2j+1] (scaled)
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      if (v >= nv) break;
-      const int rowpix = (y0 + v) * a.nx;
-      cx<T>* zv = Z + v;
-      if constexpr (OUT_SPEC) {
-        if (a.op == OP_Y_W)
-          gen::mid_row<T, OP_Y_W, V>(I, rowpix, zv, L, t, nt);
-        else
-          gen::mid_row<T, OP_MASK, V>(I, rowpix, zv, L, t, nt);
-      } else {
-        switch (a.op) {
-          case OP_Q: gen::sink_row<T, OP_Q, V>(I, rowpix, zv, L, t, nt, acc, 0); break;
-          case OP_Z: gen::sink_row<T, OP_Z, V>(I, rowpix, zv, L, t, nt, acc, 0); break;
-          case OP_B: gen::sink_row<T, OP_B, V>(I, rowpix, zv, L, t, nt, acc, 0); break;
-          case OP_RES: gen::sink_row<T, OP_RES, V>(I, rowpix, zv, L, t, nt, acc, 0); break;
-          case OP_GRAD: gen::sink_row<T, OP_GRAD, V>(I, rowpix, zv, L, t, nt, acc, 0); break;
-          case OP_RELAX: gen::sink_row<T, OP_RELAX, V>(I, rowpix, zv, L, t, nt, acc, 0); break;
-          case OP_KSEL:
-            gen::sink_row<T, OP_KSEL, V>(I, rowpix, zv, L, t, nt, acc, a.param);
-            break;
-          case OP_STORE_Y: gen::sink_row<T, OP_STORE_Y, V>(I, rowpix, zv, L, t, nt, acc, 0); break;
-          case OP_STORE_Y_MASK:
-            gen::sink_row<T, OP_STORE_Y_MASK, V>(I, rowpix, zv, L, t, nt, acc, 0);
-            break;
-          default: break;
-        }
+#define CGF_SINK(OPC, PARAM) \
+  gen::sink_rows<T, OPC, V>(I, pix0, a.nx, nv, Z, L, t, nt, acc, PARAM)
+    if constexpr (OUT_SPEC) {
+      if (a.op == OP_Y_W)
+        gen::mid_rows<T, OP_Y_W, V>(I, pix0, a.nx, nv, Z, L, t, nt);
+      else
+        gen::mid_rows<T, OP_MASK, V>(I, pix0, a.nx, nv, Z, L, t, nt);
+    } else {
+      switch (a.op) {
+        case OP_Q: CGF_SINK(OP_Q, 0); break;
+        case OP_Z: CGF_SINK(OP_Z, 0); break;
+        case OP_B: CGF_SINK(OP_B, 0); break;
+        case OP_RES: CGF_SINK(OP_RES, 0); break;
+        case OP_GRAD: CGF_SINK(OP_GRAD, 0); break;
+        case OP_RELAX: CGF_SINK(OP_RELAX, 0); break;
+        case OP_KSEL: CGF_SINK(OP_KSEL, a.param); break;
+        case OP_STORE_Y: CGF_SINK(OP_STORE_Y, 0); break;
+        case OP_STORE_Y_MASK: CGF_SINK(OP_STORE_Y_MASK, 0); break;
+        default: break;
       }
     }
+#undef CGF_SINK
   } else if constexpr (XI) {
 #pragma unroll
     for (int v = 0; v < V; ++v) {
@@ -627,50 +666,23 @@ k_row_gen(const InstDesc<T>* __restrict__ insts, RowArgs a, GenLen g, const T* _
     }
   } else {
     const T alpha = (T)I.st->alpha, beta = (T)I.st->beta;
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      cx<T>* zv = Z + v;
-      if (v >= nv) {   // padding row: zeros
-        for (int j = t; j < L; j += nt) zv[j * V] = cx<T>{(T)0, (T)0};
-        continue;
-      }
-      const int rowpix = (y0 + v) * a.nx;
-      switch (a.op) {
-        case OP_R_UPD:
-          gen::src_row<T, OP_R_UPD, V>(I, rowpix, zv, L, t, nt, alpha, beta, acc);
-          break;
-        case OP_P_UPD_Z:
-          gen::src_row<T, OP_P_UPD_Z, V>(I, rowpix, zv, L, t, nt, alpha, beta, acc);
-          break;
-        case OP_P_UPD_R:
-          gen::src_row<T, OP_P_UPD_R, V>(I, rowpix, zv, L, t, nt, alpha, beta, acc);
-          break;
-        case OP_LOAD_R:
-          gen::src_row<T, OP_LOAD_R, V>(I, rowpix, zv, L, t, nt, alpha, beta, acc);
-          break;
-        case OP_LOAD_U:
-          gen::src_row<T, OP_LOAD_U, V>(I, rowpix, zv, L, t, nt, alpha, beta, acc);
-          break;
-        case OP_LOAD_Y:
-          gen::src_row<T, OP_LOAD_Y, V>(I, rowpix, zv, L, t, nt, alpha, beta, acc);
-          break;
-        case OP_LOAD_W:
-          gen::src_row<T, OP_LOAD_W, V>(I, rowpix, zv, L, t, nt, alpha, beta, acc);
-          break;
-        case OP_LOAD_W_MASK:
-          gen::src_row<T, OP_LOAD_W_MASK, V>(I, rowpix, zv, L, t, nt, alpha, beta, acc);
-          break;
-        case OP_LOAD_D_U:
-          gen::src_row<T, OP_LOAD_D_U, V>(I, rowpix, zv, L, t, nt, alpha, beta, acc);
-          break;
-        case OP_U64_UPD:
-          gen::src_row<T, OP_U64_UPD, V>(I, rowpix, zv, L, t, nt, alpha, beta, acc);
-          break;
-        default:
-          for (int j = t; j < L; j += nt) zv[j * V] = cx<T>{(T)0, (T)0};
-          break;
-      }
+#define CGF_SRC(OPC) gen::src_rows<T, OPC, V>(I, pix0, a.nx, nv, Z, L, t, nt, alpha, beta, acc)
+    switch (a.op) {
+      case OP_R_UPD: CGF_SRC(OP_R_UPD); break;
+      case OP_P_UPD_Z: CGF_SRC(OP_P_UPD_Z); break;
+      case OP_P_UPD_R: CGF_SRC(OP_P_UPD_R); break;
+      case OP_LOAD_R: CGF_SRC(OP_LOAD_R); break;
+      case OP_LOAD_U: CGF_SRC(OP_LOAD_U); break;
+      case OP_LOAD_Y: CGF_SRC(OP_LOAD_Y); break;
+      case OP_LOAD_W: CGF_SRC(OP_LOAD_W); break;
+      case OP_LOAD_W_MASK: CGF_SRC(OP_LOAD_W_MASK); break;
+      case OP_LOAD_D_U: CGF_SRC(OP_LOAD_D_U); break;
+      case OP_U64_UPD: CGF_SRC(OP_U64_UPD); break;
+      default:
+        for (int j = t; j < L * V; j += nt) Z[j] = cx<T>{(T)0, (T)0};
+        break;
     }
+#undef CGF_SRC
   }
 
   if constexpr (OUT_SPEC) {
@@ -747,7 +759,7 @@ __device__ __forceinline__ void col_middle(cx<T>* z, const GenLen& g, const T* t
 }  // namespace gen
 
 template <typename T, int V, bool PRE = false>
-__global__ void __launch_bounds__(kGenThreads, gen_minb<T>())
+__global__ void __launch_bounds__(kGenThreads, gen_col_minb<T>())
 k_col_gen(const InstDesc<T>* __restrict__ insts, ColArgs a, GenLen g, const T* __restrict__ wn) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const InstDesc<T>& I = insts[blockIdx.x];

@@ -70,11 +70,17 @@ constexpr int gen_v() { return std::is_same<T, float>::value ? 2 : 1; }
 #ifndef CGF_GEN_MINB
 #define CGF_GEN_MINB 3
 #endif
+#ifndef CGF_GEN_COL_MINB
+#define CGF_GEN_COL_MINB CGF_GEN_MINB
+#endif
 constexpr int kGenThreads = CGF_GEN_THREADS;   // most threads in one CTA
-// CTAs per SM the kernels are compiled for (registers per thread
-// 65536 / (kGenThreads x this)): FP32, then FP64 and double-float.
+// CTAs per SM the row kernels are compiled for (registers per thread
+// 65536 / (kGenThreads x this)): FP32, then FP64 and double-float; and the
+// column kernels.
 template <typename T>
 constexpr int gen_minb() { return std::is_same<T, float>::value ? CGF_GEN_MINB : 2; }
+template <typename T>
+constexpr int gen_col_minb() { return std::is_same<T, float>::value ? CGF_GEN_COL_MINB : 2; }
 
 template <typename T>
 struct GenLaunch {
