@@ -344,11 +344,16 @@ fill_status fill_backward(fill_plan* plan, const void* d, long long d_stride,
 
 /*
  * fill_autotune -- chooses the plan's launch schedule (grid rows per CTA of
- * the row passes, column FFTs per CTA of the column pass) by timing every
- * valid candidate on the device; results are cached as text lines in
- * cache_path (NULL: no cache).  Call after fill_init, before fill_realize.
- * Mixed-radix grids keep their fixed schedule (returns FILL_OK at once).
- * Errors: FILL_EINVAL, FILL_ECUDA.
+ * the row passes, column FFTs per CTA of the column pass, and which column
+ * kernel) by timing every valid candidate on the device; results are cached
+ * as text lines in cache_path (NULL: no cache).  Mixed-radix grids also
+ * choose the radix schedule of each transform length (radix-8 stages or
+ * radix 4 and 2 only; odd radices ascending or descending), timed on the
+ * precision of the CG loop and applied to every precision of the plan, with
+ * new tables (graphs and groups built earlier keep the tables they were
+ * built with).  Results differ from the default schedule's by rounding only.
+ * Call after fill_init, before fill_realize.  Errors: FILL_EINVAL (also for a
+ * cached schedule that is not valid for the plan), FILL_ENOMEM, FILL_ECUDA.
  */
 fill_status fill_autotune(fill_plan* plan, const char* cache_path);
 

@@ -560,7 +560,8 @@ class Plan:
         return fill_time_pass(self._plan, pass_id, precision, reps)
 
     def autotune(self, cache_path=None):
-        """Time the valid launch schedules and keep the fastest."""
+        """Time the valid launch schedules (and, on mixed-radix grids, radix
+        schedules) and keep the fastest."""
         self.calls += 1
         fill_autotune(self._plan, cache_path)
 

@@ -4,7 +4,7 @@
 
 namespace cgf {
 
-bool gen_factor(int n, GenLen* g) {
+bool gen_factor(int n, GenLen* g, int code) {
   if (n < 2 || n > kGenMaxLen) return false;
   int m = n, k = 0;
   auto take = [&](int r) {
@@ -13,15 +13,22 @@ bool gen_factor(int n, GenLen* g) {
       m /= r;
     }
   };
-  take(8);
+  if (!(code & 1)) take(8);
   take(4);
   take(2);
-  take(3);
-  take(5);
-  take(7);
+  if (code & 2) {
+    take(7);
+    take(5);
+    take(3);
+  } else {
+    take(3);
+    take(5);
+    take(7);
+  }
   if (m != 1) return false;
   g->n = n;
   g->nst = k;
+  g->code = code;
   // stage s (sub-length ns, h = ns / R) holds h (R - 1) twiddles; the last
   // stage (h = 1) none
   int ns = n, off = 0;

@@ -46,6 +46,7 @@ struct GenLen {
   int n;
   int nst;
   int nt;
+  int code;   // radix schedule (gen_factor)
   int radix[kGenMaxStages];
   // Stage s < nst - 1: twiddles W_{n_s}^{q j} (j < h_s, q = 1 .. R_s - 1) at
   // complex entry twoff[s] + j (R_s - 1) + q - 1 of the table.  The last stage
@@ -55,10 +56,13 @@ struct GenLen {
   const unsigned short* pos;   // device, n entries: frequency -> position
 };
 
-// Factor n into radix-8, 4, 2, 3, 5, 7 stages and lay out the stage twiddles;
-// false if n has another prime factor.  (The tables themselves and the
-// digit-reversal maps are built with the plan.)
-bool gen_factor(int n, GenLen* g);
+// Factor n into stages and lay out the stage twiddles; false if n has a prime
+// factor above 7.  The radix schedule `code`: radix-8 stages first unless bit
+// 0 is set, then 4, 2, and the odd radices ascending (3, 5, 7), or descending
+// with bit 1.  (The tables themselves and the digit-reversal maps are built
+// with the plan; the threads per group, nt, are left as they are.)
+bool gen_factor(int n, GenLen* g, int code = 0);
+constexpr int kGenCodes = 4;
 
 // Transforms per thread group: 2 in FP32, 1 in FP64 and double-float (their
 // butterflies already hold twice the registers).

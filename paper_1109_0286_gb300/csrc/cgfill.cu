@@ -990,49 +990,37 @@ void gen_threads(GenLen* g, int V, bool wide) {
   }
 }
 
-// Mixed-radix schedule and twiddle tables of one precision: rows per CTA
-// and column FFTs per CTA (multiples of the group width V = gen_v<T>(), one
-// or two groups of g.nt threads, within the shared-memory limit), unless the
-// options fix them; the digit-reversal maps once per plan.
+// Validity of a mixed-radix CTA shape for precision T: rows per CTA and
+// column FFTs per CTA are multiples of the group width V = gen_v<T>(), the
+// row groups a power of two, within kGenThreads threads, the partial-sum slots
+// and 200 KB of shared memory.
 template <typename T>
-fill_status setup_generic(fill_plan* p) {
-  Precision<T>& P = prec<T>(p);
+bool gen_row_ok(const fill_plan* p, int r) {
   constexpr int V = gen_v<T>();
-  const int L = p->nx / 2, ny = p->ny, maxt = GenLaunch<T>::max_threads();
-  const size_t smax = 200 * 1024;
-  auto row_ok = [&](int r) {
-    return r >= V && r % V == 0 && pow2(r / V) && (r / V) * p->grow.nt <= maxt &&
-           (ny + r - 1) / r <= kMaxPartials && GenLaunch<T>::row_smem(L, r) <= smax;
-  };
-  auto col_ok = [&](int f) {
-    return f >= V && f % V == 0 && (f / V) * p->gcol.nt <= maxt &&
-           GenLaunch<T>::col_smem(ny, f) <= smax;
-  };
-  // defaults: as many groups as kGenThreads threads hold, in at most 75 KB of
-  // shared memory (three CTAs on an SM)
-  const size_t third = 75 * 1024;
-  if (p->o.rows_per_cta > 0) {
-    P.rows = p->o.rows_per_cta;
-  } else {
-    P.rows = V;
-    if (row_ok(2 * V) && GenLaunch<T>::row_smem(L, 2 * V) <= third) P.rows = 2 * V;
-  }
-  if (p->o.ffts_per_cta > 0) {
-    P.ffts = p->o.ffts_per_cta;
-  } else {
-    P.ffts = V;
-    while (col_ok(2 * P.ffts) && GenLaunch<T>::col_smem(ny, 2 * P.ffts) <= third &&
-           2 * P.ffts <= 16)
-      P.ffts *= 2;
-  }
-  if (!row_ok(P.rows) || !col_ok(P.ffts)) return FILL_EINVAL;
+  return r >= V && r % V == 0 && pow2(r / V) && (r / V) * p->grow.nt <= GenLaunch<T>::max_threads() &&
+         (p->ny + r - 1) / r <= kMaxPartials && GenLaunch<T>::row_smem(p->nx / 2, r) <= 200 * 1024;
+}
+template <typename T>
+bool gen_col_ok(const fill_plan* p, int f) {
+  constexpr int V = gen_v<T>();
+  return f >= V && f % V == 0 && (f / V) * p->gcol.nt <= GenLaunch<T>::max_threads() &&
+         GenLaunch<T>::col_smem(p->ny, f) <= 200 * 1024;
+}
+
+// Twiddle tables of precision T for the plan's current radix schedules, in
+// fresh device buffers (launch graphs captured earlier keep the buffers they
+// were built with).
+template <typename T>
+fill_status gen_upload(fill_plan* p) {
+  Precision<T>& P = prec<T>(p);
+  const int L = p->nx / 2;
   std::vector<double> wl, wx, wn;
-  std::vector<unsigned short> revl, posl, revn, posn;
-  gen_tables(p->grow, wl, revl, posl);
+  std::vector<unsigned short> rev, pos;
+  gen_tables(p->grow, wl, rev, pos);
   twiddles_len(p->nx, L + 1, wx);
-  gen_tables(p->gcol, wn, revn, posn);
+  gen_tables(p->gcol, wn, rev, pos);
   auto upload = [&](T** dst, const std::vector<double>& src) -> cudaError_t {
-    std::vector<T> h(src.size());
+    std::vector<T> h(std::max<size_t>(src.size(), 2));
     for (size_t i = 0; i < src.size(); ++i) h[i] = (T)src[i];
     cudaError_t e = p->dalloc(dst, h.size());
     if (e == cudaSuccess) e = cudaMemcpy(*dst, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
@@ -1041,6 +1029,11 @@ fill_status setup_generic(fill_plan* p) {
   CK(upload(&P.gwl, wl));
   CK(upload(&P.gwx, wx));
   CK(upload(&P.gwn, wn));
+  return FILL_OK;
+}
+
+// Digit-reversal maps of the current radix schedules (fresh device buffers).
+fill_status gen_upload_maps(fill_plan* p) {
   auto upload_map = [&](const unsigned short** dst, const std::vector<unsigned short>& src) {
     unsigned short* d = nullptr;
     cudaError_t e = p->dalloc(&d, src.size());
@@ -1049,11 +1042,46 @@ fill_status setup_generic(fill_plan* p) {
     *dst = d;
     return e;
   };
+  std::vector<double> tw;
+  std::vector<unsigned short> rev, pos;
+  gen_tables(p->grow, tw, rev, pos);
+  CK(upload_map(&p->grow.rev, rev));
+  CK(upload_map(&p->grow.pos, pos));
+  gen_tables(p->gcol, tw, rev, pos);
+  CK(upload_map(&p->gcol.rev, rev));
+  CK(upload_map(&p->gcol.pos, pos));
+  return FILL_OK;
+}
+
+// Mixed-radix schedule and twiddle tables of one precision: rows per CTA
+// and column FFTs per CTA (one or two groups of g.nt threads, within 75 KB of
+// shared memory so that three CTAs share an SM), unless the options fix them;
+// the digit-reversal maps once per plan.
+template <typename T>
+fill_status setup_generic(fill_plan* p) {
+  Precision<T>& P = prec<T>(p);
+  constexpr int V = gen_v<T>();
+  const size_t third = 75 * 1024;
+  if (p->o.rows_per_cta > 0) {
+    P.rows = p->o.rows_per_cta;
+  } else {
+    P.rows = V;
+    if (gen_row_ok<T>(p, 2 * V) && GenLaunch<T>::row_smem(p->nx / 2, 2 * V) <= third) P.rows = 2 * V;
+  }
+  if (p->o.ffts_per_cta > 0) {
+    P.ffts = p->o.ffts_per_cta;
+  } else {
+    P.ffts = V;
+    while (gen_col_ok<T>(p, 2 * P.ffts) && GenLaunch<T>::col_smem(p->ny, 2 * P.ffts) <= third &&
+           2 * P.ffts <= 16)
+      P.ffts *= 2;
+  }
+  if (!gen_row_ok<T>(p, P.rows) || !gen_col_ok<T>(p, P.ffts)) return FILL_EINVAL;
+  fill_status fs = gen_upload<T>(p);
+  if (fs != FILL_OK) return fs;
   if (!p->grow.rev) {
-    CK(upload_map(&p->grow.rev, revl));
-    CK(upload_map(&p->grow.pos, posl));
-    CK(upload_map(&p->gcol.rev, revn));
-    CK(upload_map(&p->gcol.pos, posn));
+    fs = gen_upload_maps(p);
+    if (fs != FILL_OK) return fs;
   }
   CK(GenLaunch<T>::prepare());
   return FILL_OK;
@@ -2124,10 +2152,12 @@ bool cache_lookup(const char* path, int prec, int ny, int nx, int ninst, int* ro
   if (!path) return false;
   FILE* f = std::fopen(path, "r");
   if (!f) return false;
+  char line[256];
   int a, b, c, d, r, q;
   bool found = false;
-  while (std::fscanf(f, "%d %d %d %d %d %d", &a, &b, &c, &d, &r, &q) == 6)
-    if (a == prec && b == ny && c == nx && d == ninst) {
+  while (std::fgets(line, sizeof line, f))
+    if (std::sscanf(line, "%d %d %d %d %d %d", &a, &b, &c, &d, &r, &q) == 6 && a == prec &&
+        b == ny && c == nx && d == ninst) {
       *rows = r;
       *ffts = q;
       found = true;
@@ -2141,6 +2171,38 @@ void cache_store(const char* path, int prec, int ny, int nx, int ninst, int rows
   FILE* f = std::fopen(path, "a");
   if (!f) return;
   std::fprintf(f, "%d %d %d %d %d %d\n", prec, ny, nx, ninst, rows, ffts);
+  std::fclose(f);
+}
+
+// Mixed-radix plans: lines "g prec ny nx ninst rows ffts row_code col_code".
+bool cache_lookup_gen(const char* path, int prec, int ny, int nx, int ninst, int* rows, int* ffts,
+                      int* rcode, int* ccode) {
+  if (!path) return false;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  char line[256];
+  int a, b, c, d, r, q, x, y;
+  bool found = false;
+  while (std::fgets(line, sizeof line, f))
+    if (std::sscanf(line, "g %d %d %d %d %d %d %d %d", &a, &b, &c, &d, &r, &q, &x, &y) == 8 &&
+        a == prec && b == ny && c == nx && d == ninst && x >= 0 && x < kGenCodes && y >= 0 &&
+        y < kGenCodes) {
+      *rows = r;
+      *ffts = q;
+      *rcode = x;
+      *ccode = y;
+      found = true;
+    }
+  std::fclose(f);
+  return found;
+}
+
+void cache_store_gen(const char* path, int prec, int ny, int nx, int ninst, int rows, int ffts,
+                     int rcode, int ccode) {
+  if (!path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "g %d %d %d %d %d %d %d %d\n", prec, ny, nx, ninst, rows, ffts, rcode, ccode);
   std::fclose(f);
 }
 
@@ -2172,6 +2234,111 @@ fill_status tune_plan_t(fill_plan* p, const char* path) {
       p->mixed_graph = nullptr;
     }
   }
+  return FILL_OK;
+}
+
+// Destroys the plan's captured CG-loop graphs (after a schedule change).
+void drop_graphs(fill_plan* p) {
+  auto drop = [](cudaGraphExec_t& g) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+  };
+  drop(p->f.iter_graph);
+  drop(p->g.iter_graph);
+  drop(p->h.iter_graph);
+  drop(p->mixed_graph);
+}
+
+// Switches one transform length (rows: nx / 2, else ny) of a mixed-radix plan
+// to radix schedule `code`: new tables for every precision in use and new
+// digit-reversal maps; the threads per group stay, so every CTA shape stays
+// valid.
+fill_status apply_gen_code(fill_plan* p, bool rows, int code) {
+  GenLen& g = rows ? p->grow : p->gcol;
+  if (g.code == code) return FILL_OK;
+  GenLen t = g;
+  if (!gen_factor(g.n, &t, code)) return FILL_EINVAL;
+  g = t;
+  fill_status fs = FILL_OK;
+  if (p->f.used) fs = gen_upload<float>(p);
+  if (fs == FILL_OK && p->g.used) fs = gen_upload<double>(p);
+  if (fs == FILL_OK && p->h.used) fs = gen_upload<df>(p);
+  if (fs == FILL_OK) fs = gen_upload_maps(p);
+  return fs;
+}
+
+// The radix schedules of a length that differ from one another.
+std::vector<int> gen_candidates(int n) {
+  std::vector<int> out;
+  std::vector<std::vector<int>> seen;
+  for (int code = 0; code < kGenCodes; ++code) {
+    GenLen g{};
+    if (!gen_factor(n, &g, code)) continue;
+    std::vector<int> r(g.radix, g.radix + g.nst);
+    if (std::find(seen.begin(), seen.end(), r) == seen.end()) {
+      seen.push_back(r);
+      out.push_back(code);
+    }
+  }
+  return out;
+}
+
+// Mixed-radix plans: the radix schedule of each transform length and the CTA
+// shapes, timed on the precision T that carries the CG loop; the other
+// precisions follow the chosen schedules and keep their CTA shapes.
+template <typename T>
+fill_status tune_gen_t(fill_plan* p, const char* path) {
+  Precision<T>& P = prec<T>(p);
+  constexpr int V = gen_v<T>();
+  const int pr = prec_code<T>();
+  int rows = P.rows, ffts = P.ffts, rcode = p->grow.code, ccode = p->gcol.code;
+  if (!cache_lookup_gen(path, pr, p->ny, p->nx, p->batch, &rows, &ffts, &rcode, &ccode)) {
+    fill_desc<T>(p, nullptr, 0, nullptr, nullptr, nullptr);
+    CK(upload_desc<T>(p));
+    CK(init_states<T>(p, 0.0));
+    float best = 1e30f;
+    for (int code : gen_candidates(p->grow.n)) {
+      fill_status fs = apply_gen_code(p, true, code);
+      if (fs != FILL_OK) return fs;
+      for (int r = V; r <= 4 * V; r *= 2) {
+        if (!gen_row_ok<T>(p, r)) continue;
+        Ctx<T> c = ctx<T>(p);
+        c.rows = r;
+        float ms = 0.f;
+        CK(time_launches(p->s, 3, [&](cudaStream_t st) { return tune_rows_once<T>(c, st); }, &ms));
+        if (ms < best) {
+          best = ms;
+          rows = r;
+          rcode = code;
+        }
+      }
+    }
+    best = 1e30f;
+    for (int code : gen_candidates(p->gcol.n)) {
+      fill_status fs = apply_gen_code(p, false, code);
+      if (fs != FILL_OK) return fs;
+      for (int f = V; f <= 16; f *= 2) {
+        if (!gen_col_ok<T>(p, f)) continue;
+        Ctx<T> c = ctx<T>(p);
+        c.ffts = f;
+        float ms = 0.f;
+        CK(time_launches(p->s, 3, [&](cudaStream_t st) { return col<T>(c, st, 0, false); }, &ms));
+        if (ms < best) {
+          best = ms;
+          ffts = f;
+          ccode = code;
+        }
+      }
+    }
+    cache_store_gen(path, pr, p->ny, p->nx, p->batch, rows, ffts, rcode, ccode);
+  }
+  if (!gen_row_ok<T>(p, rows) || !gen_col_ok<T>(p, ffts)) return FILL_EINVAL;
+  fill_status fs = apply_gen_code(p, true, rcode);
+  if (fs == FILL_OK) fs = apply_gen_code(p, false, ccode);
+  if (fs != FILL_OK) return fs;
+  P.rows = rows;
+  P.ffts = ffts;
+  drop_graphs(p);
   return FILL_OK;
 }
 
@@ -2405,7 +2572,12 @@ extern "C" {
 
 fill_status fill_autotune(fill_plan* p, const char* cache_path) {
   if (!p) return FILL_EINVAL;
-  if (p->gen) return FILL_OK;   // mixed-radix grids keep their fixed schedule
+  if (p->gen) {   // mixed-radix grids: radix schedules and CTA shapes
+    fill_status fs = p->o.mode == FILL_MODE_FP64 ? tune_gen_t<double>(p, cache_path)
+                                                 : tune_gen_t<float>(p, cache_path);
+    if (fs == FILL_OK) CK(cudaStreamSynchronize(p->s));
+    return fs;
+  }
   fill_status fs = tune_plan_t<float>(p, cache_path);
   if (fs == FILL_OK) fs = tune_plan_t<double>(p, cache_path);
   if (fs == FILL_OK) fs = tune_plan_t<df>(p, cache_path);

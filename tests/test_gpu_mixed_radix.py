@@ -167,8 +167,45 @@ def test_mixed_radix_sizes_rejected_where_unsupported():
         with pytest.raises((cg.FillError, ValueError)):
             cg.Plan(Pb, ob, mode="fp64")
     # groups take mixed-radix plans (tests/test_gpu_boundary.py checks their
-    # results); the autotuner leaves their fixed schedule alone
+    # results), also after the autotuner has changed the plan's schedule
     plan = cg.Plan(P, obs, mode="fp32")
     plan.autotune()
     g = cg.Group([plan])
     assert g.size == 1
+
+
+@pytest.mark.parametrize("mode,bound", [("fp64", 1e-9), ("mixed", 1e-8)])
+def test_every_radix_schedule_matches_oracle(tmp_path, mode, bound):
+    """Every radix schedule the autotuner can choose (radix-8 stages or not;
+    odd radices ascending or descending), forced through a cache line, gives
+    the oracle's converged realization; the autotuner's own choice is written
+    to its cache and, served again from there, reproduces itself bit for bit.
+    120 x 840: nx/2 = 420 = 4 3 5 7, ny = 120 = 8 3 5."""
+    ny, nx = 120, 840
+    P, obs = case(ny, nx)
+    d = O.draw(O.hermitian_full(P, nx), 9)
+    ref = O.realize(P, obs, d, 5, tol=1e-12)
+    m = obs == 0
+    prec, v = (1, 1) if mode == "fp64" else (0, 2)
+    dd = gpu_map(d, torch.float64)
+    for rcode in range(4):
+        for ccode in range(4):
+            cache = tmp_path / f"forced_{mode}_{rcode}{ccode}.txt"
+            cache.write_text(f"g {prec} {ny} {nx} 1 {v} {v} {rcode} {ccode}\n")
+            plan = cg.Plan(P, obs, mode=mode)
+            plan.autotune(str(cache))
+            out, st = plan.realize(dd, [5], 1e-10)
+            x = out[0].cpu().numpy()
+            assert st[0]["status"] == 0
+            assert np.array_equal(x[~m], d[~m])
+            assert rel(x[m], ref.x[m]) <= bound, (rcode, ccode, rel(x[m], ref.x[m]))
+    cache = str(tmp_path / f"tuned_{mode}.txt")
+    a = cg.Plan(P, obs, mode=mode)
+    a.autotune(cache)
+    assert any(line.startswith("g ") for line in open(cache))
+    xa, _ = a.realize(dd, [5], 1e-10)
+    assert rel(xa[0].cpu().numpy()[m], ref.x[m]) <= bound
+    b = cg.Plan(P, obs, mode=mode)
+    b.autotune(cache)   # served from the cache
+    xb, _ = b.realize(dd, [5], 1e-10)
+    assert torch.equal(xa, xb)
