@@ -21,9 +21,9 @@
  *   - Grid ny x nx, row-major, periodic; either nx and ny powers of two
  *     with 32 <= nx <= 8192 and 16 <= ny <= 8192 (register-resident FFT
  *     passes), or a mixed-radix grid: nx even, nx/2 and ny products of
- *     2, 3, 5 and 7 with 8 <= nx/2 <= 4096 and 8 <= ny <= 4096 (shared-memory
- *     Stockham passes of radix 2, 3, 4, 5, 7; the flat-sky workloads of
- *     Sect. 3 such as 7000 x 600 = 2^3 5^3 7 x 2^3 3 5^2).
+ *     2, 3, 5 and 7 with 8 <= nx/2 <= 4096 and 8 <= ny <= 4096 (in-place
+ *     shared-memory passes of radix 2, 3, 4, 5, 7, 8; the flat-sky workloads
+ *     of Sect. 3 such as 7000 x 600 = 2^3 5^3 7 x 2^3 3 5^2).
  *   - DFT: F x(k) = sum_r x(r) exp(-i k.r), F^-1 carries 1/n, n = ny*nx,
  *     k = 2 pi m / N with m in [-N/2, N/2).
  *   - P_half: host, float64, ny x (nx/2+1) row-major (the half plane of a
