@@ -206,6 +206,10 @@ __device__ __forceinline__ void sink_fill(const InstDesc<T>& I, const uint2* mwr
     for (int e = 0; e < CK; ++e) {
       const int j = tid + (h + e) * TT;
       const bool m0 = q[e].m0, m1 = q[e].m1;   // masked = not observed
+      // compact-vector ops: nothing to store or add (exactly) for a pair
+      // without a masked pixel
+      constexpr bool C = OP == OP_Q || OP == OP_Z || OP == OP_B || OP == OP_RES || OP == OP_KSEL;
+      if (C && !(m0 || m1)) continue;
       T a0 = v[h + e].r, a1 = v[h + e].i;
       if constexpr (OP == OP_Q || OP == OP_Z) {
         a0 = m0 ? a0 : (T)0;
