@@ -2,7 +2,8 @@
 FP64 oracle, whose transforms are numpy's for any length.
 
 Sizes cover every radix in both transforms, odd ny, a power-of-two row with
-a mixed-radix column, and the 7000 x 600 flat-sky workload of Sect. 3 (its
+a mixed-radix column, the longest transforms (4096 = 8^4 points, in rows and
+in columns), and the 7000 x 600 flat-sky workload of Sect. 3 (its
 scaled-down versions element by element, the full size by the certificate).
 """
 import math
@@ -22,7 +23,8 @@ if not torch.cuda.is_available():  # pragma: no cover
 import paper_1109_0286_gb300 as cg  # noqa: E402
 from paper_1109_0286_gb300 import laplace  # noqa: E402
 
-SIZES = [(60, 84), (45, 70), (27, 32), (48, 64), (600, 350), (8, 4200), (49, 16)]
+SIZES = [(60, 84), (45, 70), (27, 32), (48, 64), (600, 350), (8, 4200), (49, 16),
+         (24, 8192), (4096, 24)]   # the last two: 4096-point rows, 4096-point columns
 
 
 def rel(a, b):
