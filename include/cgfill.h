@@ -156,13 +156,14 @@ fill_status fill_realize(fill_plan* plan, const void* d, long long d_stride,
  * i's batch maps; seeds: host, one per realization in plan order (plan 0's
  * batch first); stats: host, one entry per realization, or NULL.  The result
  * of each plan equals what fill_realize would give it.
- * Plans of one mode (FP32 or FP64), one precond setting and one stream run as
- * a group (see fill_group_init): plans of the same grid share every pass
- * launch and the grid sizes run as concurrent branches of one graph per CG
- * loop.  The first call with a given list of plans builds that group
- * (device descriptors and the loop graph) and caches it in plans[0];
- * later calls with the same list reuse it, and fill_destroy(plans[0]) frees
- * it.  Any other list (mixed mode, or differing settings) runs the plans one
+ * Plans of one mode (FP32, FP64, or mixed with one update_delta > 0), one
+ * precond setting and one stream run as a group (see fill_group_init): plans
+ * of the same grid share every pass launch and the grid sizes run as
+ * concurrent branches of one graph per CG loop.  The first call with a given
+ * list of plans builds that group (device descriptors and the loop graph)
+ * and caches it in plans[0]; later calls with the same list reuse it, and
+ * fill_destroy(plans[0]) frees it.  Any other list (differing settings, or
+ * mixed mode with restarted refinement, update_delta = 0) runs the plans one
  * after another.  Errors: as fill_realize.
  */
 fill_status fill_realize_batch(fill_plan* const* plans, int count, const void* const* d,
@@ -359,15 +360,18 @@ fill_status fill_autotune(fill_plan* plan, const char* cache_path);
 
 /*
  * Groups: many realizations over masks and grid sizes in one call.
- * fill_group_init collects plans (all FILL_MODE_FP32 or all FILL_MODE_FP64,
+ * fill_group_init collects plans (all of one mode -- FILL_MODE_FP32,
+ * FILL_MODE_FP64, or FILL_MODE_MIXED with one update_delta > 0 for all --,
  * same precond and stream; power-of-two or mixed-radix grids; each keeps its
  * own mask, spectrum and buffers).
  * Plans with the same grid form a size class whose instances share every pass
  * launch; the classes run concurrently as parallel branches of one captured
- * CUDA graph per chunk of CG iterations.  autotune != 0 tunes each class's
- * schedule (cached in cache_path if not NULL; mixed-radix classes keep their
- * fixed schedule).  The plans must outlive the group.  Errors: FILL_EINVAL,
- * FILL_ENOMEM, FILL_ECUDA.
+ * CUDA graph per CG loop (mixed mode: the reliable-update loop of
+ * fill_realize, double-float draw, right-hand side and residual updates per
+ * class, an update IF node per class).  autotune != 0 tunes each class's
+ * schedule of the CG loop's precision (cached in cache_path if not NULL;
+ * mixed-radix classes keep their plans' schedules).  The plans must outlive
+ * the group.  Errors: FILL_EINVAL, FILL_ENOMEM, FILL_ECUDA.
  */
 typedef struct fill_group fill_group;
 fill_status fill_group_init(fill_group** group, fill_plan* const* plans, int count,

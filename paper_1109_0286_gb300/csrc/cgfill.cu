@@ -233,12 +233,14 @@ __global__ void k_gather_states(const InstDesc<T>* desc, int n, CgState* out) {
 // Prepares the FP32 inner solve of a refinement step: accumulate the finished
 // solve's iteration count, skip converged instances, and set the inner
 // tolerance to what the outer target still needs (floored by inner_tol).
-__global__ void k_inner_reset(CgState* st32, CgState* st64, int n, double tol, double floor_tol,
-                              int max_iter) {
+// (States reached through the FP32 and double-float descriptors of the same
+// instances, which need not be contiguous: a group's class spans plans.)
+__global__ void k_inner_reset(const InstDesc<float>* lo, const InstDesc<df>* hi, int n,
+                              double tol, double floor_tol, int max_iter) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  CgState& a = st32[i];
-  CgState& g = st64[i];
+  CgState& a = *lo[i].st;
+  CgState& g = *hi[i].st;
   g.total_iter += a.iter;
   a.iter = 0;
   a.status = 0;
@@ -256,12 +258,13 @@ __global__ void k_inner_reset(CgState* st32, CgState* st64, int n, double tol, d
   a.done = 0;
 }
 
-__global__ void k_inner_collect(CgState* st32, CgState* st64, int n) {
+__global__ void k_inner_collect(const InstDesc<float>* lo, const InstDesc<df>* hi, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  st64[i].total_iter += st32[i].iter;
-  st32[i].last_iter = st32[i].iter;
-  st32[i].iter = 0;
+  CgState& a = *lo[i].st;
+  hi[i].st->total_iter += a.iter;
+  a.last_iter = a.iter;
+  a.iter = 0;
 }
 
 // Spectral tables of one precision from P on the device (fill_set_spectrum):
@@ -600,7 +603,7 @@ fill_status mixed_refine(fill_plan* p, double tol) {
   const int nb = (B + 127) / 128;
   for (int outer = 0; outer < p->o.max_refine; ++outer) {
     ++p->launches;
-    k_inner_reset<<<nb, 128, 0, p->s>>>(p->f.st, p->h.st, B, tol, p->o.inner_tol, p->o.max_iter);
+    k_inner_reset<<<nb, 128, 0, p->s>>>(p->f.desc, p->h.desc, B, tol, p->o.inner_tol, p->o.max_iter);
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(p->f.u, 0, B * p->nv * sizeof(float), p->s));
     CK(cudaMemsetAsync(p->f.p, 0, B * p->nv * sizeof(float), p->s));
@@ -617,20 +620,23 @@ fill_status mixed_refine(fill_plan* p, double tol) {
     if (all) break;
   }
   ++p->launches;
-  k_inner_collect<<<nb, 128, 0, p->s>>>(p->f.st, p->h.st, B);
+  k_inner_collect<<<nb, 128, 0, p->s>>>(p->f.desc, p->h.desc, B);
   CK(cudaGetLastError());
   return FILL_OK;
 }
 
 // Links the FP32 and high-precision states of each instance and sets the reliable-update
 // threshold on the FP32 state.
-__global__ void k_link_states(CgState* st32, CgState* st64, int n, double delta2) {
+__global__ void k_link_states(const InstDesc<float>* lo, const InstDesc<df>* hi, int n,
+                              double delta2) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  st32[i].peer = st64 + i;
-  st64[i].peer = st32 + i;
-  st32[i].delta2 = delta2;
-  st32[i].tol2 = st64[i].tol2;
+  CgState* a = lo[i].st;
+  CgState* g = hi[i].st;
+  a->peer = g;
+  g->peer = a;
+  a->delta2 = delta2;
+  a->tol2 = g->tol2;
 }
 
 // Sets an IF condition to 1 iff some instance's state has an update due.
@@ -680,112 +686,136 @@ cudaError_t capture_if(cudaStream_t s, cudaStream_t s2, cudaGraphConditionalHand
 // the true residual r = b - A u in double-float, restart the FP32 residual from it and
 // keep the search direction; then the preconditioned residual.  The update
 // passes skip every instance without a pending update.
-// The update passes sit in an IF node that runs only when some instance has
-// an update due (kernels inside still skip the instances without one).
-cudaError_t mixed_update_passes(fill_plan* p, cudaStream_t s) {
-  CE(row<df>(p, s, OP_U64_UPD, SC_NONE, false, true, SKIP_UNLESS_UPD));
-  CE(col<df>(p, s, 0, SKIP_UNLESS_UPD));
-  CE(row<df>(p, s, OP_RES, SC_RES_UPD, true, false, SKIP_UNLESS_UPD));
-  return row<float>(p, s, OP_LOAD_R, SC_CLEAR_UPD, false, true, SKIP_UNLESS_UPD);
+// The update passes sit in an IF node that runs only when some instance of
+// the contexts has an update due (kernels inside still skip the instances
+// without one).  The contexts lo (FP32) and hi (double-float) cover the same
+// instances: a plan's batch, or a size class of a group.
+
+// What a mixed loop body needs beyond its two launch contexts.
+struct MixedLoop {
+  CgState* const* st_hi;   // device: the high-precision state of every instance
+  int n;
+  int* counter;            // device loop counters ([1]: IF bodies run)
+  cudaStream_t cap2;       // stream that captures the IF bodies
+  bool host_loops;
+  long long* if_kernels;   // kernels inside one IF body
+};
+
+cudaError_t mixed_update_passes(const Ctx<float>& lo, const Ctx<df>& hi, cudaStream_t s,
+                                bool reload) {
+  CE(row<df>(hi, s, OP_U64_UPD, SC_NONE, false, true, SKIP_UNLESS_UPD));
+  CE(col<df>(hi, s, 0, SKIP_UNLESS_UPD));
+  CE(row<df>(hi, s, OP_RES, SC_RES_UPD, true, false, SKIP_UNLESS_UPD));
+  if (!reload) return cudaSuccess;
+  return row<float>(lo, s, OP_LOAD_R, SC_CLEAR_UPD, false, true, SKIP_UNLESS_UPD);
 }
 
-cudaError_t update_if(fill_plan* p, cudaStream_t s, bool reload) {
-  if (p->o.host_loops) {
-    // no graph: the update passes run every iteration and skip the instances
-    // without an update due
-    if (reload) return mixed_update_passes(p, s);
-    CE(row<df>(p, s, OP_U64_UPD, SC_NONE, false, true, SKIP_UNLESS_UPD));
-    CE(col<df>(p, s, 0, SKIP_UNLESS_UPD));
-    return row<df>(p, s, OP_RES, SC_RES_UPD, true, false, SKIP_UNLESS_UPD);
-  }
+cudaError_t update_if(const Ctx<float>& lo, const Ctx<df>& hi, cudaStream_t s, bool reload,
+                      const MixedLoop& m) {
+  // no graph: the update passes run every iteration and skip the instances
+  // without an update due
+  if (m.host_loops) return mixed_update_passes(lo, hi, s, reload);
   cudaStreamCaptureStatus st;
   cudaGraph_t g = nullptr;
   CE(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr));
   cudaGraphConditionalHandle h;
   CE(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
-  ++p->launches;
-  k_if_any_upd<<<1, 256, 0, s>>>(h, p->h.stp, p->batch, p->loop_counter);
+  ++*lo.launches;
+  k_if_any_upd<<<1, 256, 0, s>>>(h, m.st_hi, m.n, m.counter);
   CE(cudaGetLastError());
-  const long long before = p->launches;
-  cudaError_t e = capture_if(s, p->cap2, h, [&](cudaStream_t s2) -> cudaError_t {
-    if (reload) return mixed_update_passes(p, s2);
-    CE(row<df>(p, s2, OP_U64_UPD, SC_NONE, false, true, SKIP_UNLESS_UPD));
-    CE(col<df>(p, s2, 0, SKIP_UNLESS_UPD));
-    return row<df>(p, s2, OP_RES, SC_RES_UPD, true, false, SKIP_UNLESS_UPD);
+  const long long before = *lo.launches;
+  cudaError_t e = capture_if(s, m.cap2, h, [&](cudaStream_t s2) -> cudaError_t {
+    return mixed_update_passes(lo, hi, s2, reload);
   });
-  p->if_kernels = p->launches - before;
+  *m.if_kernels = *lo.launches - before;
   return e;
 }
 
-cudaError_t mixed_iter(fill_plan* p, cudaStream_t s) {
-  CE(row<float>(p, s, OP_P_UPD_Z, SC_NONE, false, true, SKIP_DONE));
-  CE(col<float>(p, s, 0, SKIP_DONE));
-  CE(row<float>(p, s, OP_Q, SC_ALPHA, true, false, SKIP_DONE));
-  CE(row<float>(p, s, OP_R_UPD, SC_RCHECK_UPD, false, true, SKIP_DONE));
-  CE(update_if(p, s, true));
-  CE(col<float>(p, s, 1, SKIP_DONE));
-  CE(row<float>(p, s, OP_MASK, SC_NONE, true, true, SKIP_DONE));
-  CE(col<float>(p, s, 1, SKIP_DONE));
-  return row<float>(p, s, OP_Z, SC_BETA, true, false, SKIP_DONE);
+cudaError_t mixed_iter(const Ctx<float>& lo, const Ctx<df>& hi, cudaStream_t s,
+                       const MixedLoop& m) {
+  if (!lo.precond) {
+    CE(row<float>(lo, s, OP_P_UPD_R, SC_NONE, false, true, SKIP_DONE));
+    CE(col<float>(lo, s, 0, SKIP_DONE));
+    CE(row<float>(lo, s, OP_Q, SC_ALPHA, true, false, SKIP_DONE));
+    CE(vec<float>(lo, s, VOP_UPDATE, SC_RCHECK_UPD, SKIP_DONE));
+    CE(update_if(lo, hi, s, false, m));
+    // plain CG: z = r, so beta = r^T r / rho (the reload pass also reduces ||r||^2)
+    return row<float>(lo, s, OP_LOAD_R, SC_BETA, false, true, SKIP_DONE);
+  }
+  CE(row<float>(lo, s, OP_P_UPD_Z, SC_NONE, false, true, SKIP_DONE));
+  CE(col<float>(lo, s, 0, SKIP_DONE));
+  CE(row<float>(lo, s, OP_Q, SC_ALPHA, true, false, SKIP_DONE));
+  CE(row<float>(lo, s, OP_R_UPD, SC_RCHECK_UPD, false, true, SKIP_DONE));
+  CE(update_if(lo, hi, s, true, m));
+  CE(col<float>(lo, s, 1, SKIP_DONE));
+  CE(row<float>(lo, s, OP_MASK, SC_NONE, true, true, SKIP_DONE));
+  CE(col<float>(lo, s, 1, SKIP_DONE));
+  return row<float>(lo, s, OP_Z, SC_BETA, true, false, SKIP_DONE);
 }
 
-cudaError_t mixed_iter_plain(fill_plan* p, cudaStream_t s) {
-  CE(row<float>(p, s, OP_P_UPD_R, SC_NONE, false, true, SKIP_DONE));
-  CE(col<float>(p, s, 0, SKIP_DONE));
-  CE(row<float>(p, s, OP_Q, SC_ALPHA, true, false, SKIP_DONE));
-  CE(vec<float>(p, s, VOP_UPDATE, SC_RCHECK_UPD, SKIP_DONE));
-  CE(update_if(p, s, false));
-  // plain CG: z = r, so beta = r^T r / rho (the reload pass also reduces ||r||^2)
-  return row<float>(p, s, OP_LOAD_R, SC_BETA, false, true, SKIP_DONE);
+// Before a mixed loop (b, r and r32 set, the high-precision states holding
+// ||b||^2, u = 0 in double-float): link the two precisions' states, set the
+// reliable-update threshold, mirror the instances already done (b = 0) into
+// the FP32 states, and start the FP32 PCG from r32.
+cudaError_t mixed_start(const Ctx<float>& lo, const Ctx<df>& hi, cudaStream_t s, double tol,
+                        double delta, int max_iter) {
+  const int nb = (lo.ninst + 127) / 128;
+  ++*lo.launches;
+  k_link_states<<<nb, 128, 0, s>>>(lo.desc, hi.desc, lo.ninst, delta * delta);
+  CE(cudaGetLastError());
+  CE(vec<float>(lo, s, VOP_ZERO_UP, SC_NONE, false));
+  ++*lo.launches;
+  k_inner_reset<<<nb, 128, 0, s>>>(lo.desc, hi.desc, lo.ninst, tol, 0.0, max_iter);
+  CE(cudaGetLastError());
+  ++*lo.launches;
+  k_link_states<<<nb, 128, 0, s>>>(lo.desc, hi.desc, lo.ninst, delta * delta);
+  CE(cudaGetLastError());
+  return pcg_start<float>(lo, s, SC_BB);
+}
+
+// After a mixed loop: fold anything left (breakdown / limits), report the
+// true residual, and add the FP32 iterations to the high-precision counts.
+cudaError_t mixed_finish(const Ctx<float>& lo, const Ctx<df>& hi, cudaStream_t s) {
+  CE(row<df>(hi, s, OP_U64_UPD, SC_NONE, false, true, SKIP_DONE));
+  CE(col<df>(hi, s, 0, SKIP_DONE));
+  CE(row<df>(hi, s, OP_RES, SC_RES, true, false, SKIP_DONE));
+  ++*lo.launches;
+  k_inner_collect<<<(lo.ninst + 127) / 128, 128, 0, s>>>(lo.desc, hi.desc, lo.ninst);
+  return cudaGetLastError();
+}
+
+MixedLoop mixed_loop(fill_plan* p) {
+  return MixedLoop{p->h.stp, p->batch, p->loop_counter, p->cap2, p->o.host_loops != 0,
+                   &p->if_kernels};
+}
+
+cudaError_t mixed_iter(fill_plan* p, cudaStream_t s) {
+  return mixed_iter(ctx<float>(p), ctx<df>(p), s, mixed_loop(p));
 }
 
 fill_status build_mixed_graph(fill_plan* p) {
   if (p->mixed_graph) return FILL_OK;
   return build_loop_graph(
-      p->cap,
-      [&](cudaStream_t s) { return p->o.precond ? mixed_iter(p, s) : mixed_iter_plain(p, s); },
-      p->f.stp, p->batch, p->loop_counter, p->o.max_iter + 4, &p->launches, &p->mixed_graph,
-      &p->mixed_graph_kernels);
+      p->cap, [&](cudaStream_t s) { return mixed_iter(p, s); }, p->f.stp, p->batch,
+      p->loop_counter, p->o.max_iter + 4, &p->launches, &p->mixed_graph, &p->mixed_graph_kernels);
 }
 
 // Mixed-precision solve with reliable updates (b, r, r32 and the high-precision state
 // with ||b||^2 are set; u64 = 0).
 fill_status mixed_reliable(fill_plan* p, double tol) {
-  const int B = p->batch;
-  const int nb = (B + 127) / 128;
-  const double d = p->o.update_delta;
-  ++p->launches;
-  k_link_states<<<nb, 128, 0, p->s>>>(p->f.st, p->h.st, B, d * d);
-  CK(cudaGetLastError());
-  CK(cudaMemsetAsync(p->f.u, 0, B * p->nv * sizeof(float), p->s));
-  CK(cudaMemsetAsync(p->f.p, 0, B * p->nv * sizeof(float), p->s));
-  // instances with b = 0 are done in the high-precision state: mirror that to FP32
-  ++p->launches;
-  k_inner_reset<<<nb, 128, 0, p->s>>>(p->f.st, p->h.st, B, tol, 0.0, p->o.max_iter);
-  CK(cudaGetLastError());
-  ++p->launches;
-  k_link_states<<<nb, 128, 0, p->s>>>(p->f.st, p->h.st, B, d * d);
-  CK(cudaGetLastError());
-  CK(pcg_start<float>(p, p->s, SC_BB));
+  CK(mixed_start(ctx<float>(p), ctx<df>(p), p->s, tol, p->o.update_delta, p->o.max_iter));
   fill_status fs;
   if (p->o.host_loops) {
     fs = run_loop_host(
-        p->s,
-        [&](cudaStream_t s) { return p->o.precond ? mixed_iter(p, s) : mixed_iter_plain(p, s); },
-        p->f.stp, p->batch, p->loop_counter, p->hloop, p->o.max_iter + 4, &p->launches);
+        p->s, [&](cudaStream_t s) { return mixed_iter(p, s); }, p->f.stp, p->batch,
+        p->loop_counter, p->hloop, p->o.max_iter + 4, &p->launches);
   } else {
     fs = build_mixed_graph(p);
     if (fs != FILL_OK) return fs;
     fs = run_loop_graph(p, p->mixed_graph, p->mixed_graph_kernels, p->if_kernels);
   }
   if (fs != FILL_OK) return fs;
-  // fold anything left (breakdown / limits) and report the true residual
-  CK(row<df>(p, p->s, OP_U64_UPD, SC_NONE, false, true, SKIP_DONE));
-  CK(col<df>(p, p->s, 0, SKIP_DONE));
-  CK(row<df>(p, p->s, OP_RES, SC_RES, true, false, SKIP_DONE));
-  ++p->launches;
-  k_inner_collect<<<nb, 128, 0, p->s>>>(p->f.st, p->h.st, B);
-  CK(cudaGetLastError());
+  CK(mixed_finish(ctx<float>(p), ctx<df>(p), p->s));
   return FILL_OK;
 }
 
@@ -2351,12 +2381,20 @@ struct GroupClass {
   int ny = 0, nx = 0, log_l = 0, log_n = 0, rows = 0, ffts = 0, ninst = 0, col_variant = 0;
   long long npix = 0;
   std::vector<int> plans;       // group indices of the plans in this class
-  void* desc = nullptr;         // device InstDesc<T>[ninst]
+  void* desc = nullptr;         // device InstDesc<T>[ninst] (T: FP32 in mixed mode)
   void* hdesc = nullptr;        // pinned mirror
   CgState* st = nullptr;        // device gather buffer
   CgState* hst = nullptr;       // pinned
   cudaStream_t cs = nullptr;    // class stream
   cudaEvent_t join = nullptr;
+  // mixed mode: the double-float descriptors, schedule and states of the
+  // same instances
+  void* desc_hi = nullptr;
+  void* hdesc_hi = nullptr;
+  int rows_hi = 0, ffts_hi = 0, col_variant_hi = 0;
+  CgState* st_hi = nullptr;
+  CgState* hst_hi = nullptr;
+  CgState** stp_hi = nullptr;   // device: the double-float state of every instance
 };
 
 }  // namespace
@@ -2366,7 +2404,9 @@ struct fill_group {
   std::vector<int> first;       // first flat instance of each plan
   std::vector<GroupClass> cls;
   int mode = 1, precond = 1, max_iter = 10000, ntot = 0, host_loops = 0;
-  cudaStream_t s = nullptr, cap = nullptr;
+  double update_delta = 1e-2;   // mixed mode (reliable updates)
+  long long if_kernels = 0;     // mixed mode: kernels inside one update IF body
+  cudaStream_t s = nullptr, cap = nullptr, cap2 = nullptr;
   cudaEvent_t fork = nullptr, fork_cap = nullptr;
   CgState** stp = nullptr;      // device: state pointer of every instance
   int* counter = nullptr;       // device: loop bodies run by the last launch
@@ -2376,6 +2416,7 @@ struct fill_group {
   std::vector<void*> dev, host;
   ~fill_group() {
     if (graph) cudaGraphExecDestroy(graph);
+    if (cap2) cudaStreamDestroy(cap2);
     for (auto& c : cls) {
       if (c.cs) cudaStreamDestroy(c.cs);
       if (c.join) cudaEventDestroy(c.join);
@@ -2390,12 +2431,15 @@ struct fill_group {
 
 namespace {
 
+// Launch context of a size class (hi: the double-float side of a mixed
+// group).
 template <typename T>
-Ctx<T> gctx(fill_group* g, GroupClass& c) {
+Ctx<T> gctx(fill_group* g, GroupClass& c, bool hi = false) {
   fill_plan* p0 = g->plans[c.plans[0]];
-  Ctx<T> x{c.ny, c.nx, c.log_l, c.log_n, c.rows, c.ffts, c.ninst, g->precond, c.col_variant,
-           c.npix, reinterpret_cast<const InstDesc<T>*>(c.desc), prec<T>(p0).tw, &g->launches,
-           p0->dev_err};
+  Ctx<T> x{c.ny, c.nx, c.log_l, c.log_n, hi ? c.rows_hi : c.rows, hi ? c.ffts_hi : c.ffts,
+           c.ninst, g->precond, hi ? c.col_variant_hi : c.col_variant, c.npix,
+           reinterpret_cast<const InstDesc<T>*>(hi ? c.desc_hi : c.desc), prec<T>(p0).tw,
+           &g->launches, p0->dev_err};
   if (p0->gen) {   // mixed-radix grid: the class shares the first plan's transforms
     x.grow = &p0->grow;
     x.gcol = &p0->gcol;
@@ -2447,6 +2491,58 @@ fill_status group_setup(fill_group* g, int autotune, const char* path) {
   return FILL_OK;
 }
 
+// Mixed groups: the double-float descriptors (each plan's, copied per
+// class), their schedule (the first plan's) and the state buffers.
+fill_status group_setup_hi(fill_group* g) {
+  for (auto& c : g->cls) {
+    const size_t nb = sizeof(InstDesc<df>) * c.ninst;
+    if (cudaMalloc(&c.desc_hi, nb) != cudaSuccess) return FILL_ENOMEM;
+    g->dev.push_back(c.desc_hi);
+    if (cudaMallocHost(&c.hdesc_hi, nb) != cudaSuccess) return FILL_ENOMEM;
+    g->host.push_back(c.hdesc_hi);
+    if (cudaMalloc(&c.st_hi, sizeof(CgState) * c.ninst) != cudaSuccess) return FILL_ENOMEM;
+    g->dev.push_back(c.st_hi);
+    if (cudaMallocHost(&c.hst_hi, sizeof(CgState) * c.ninst) != cudaSuccess) return FILL_ENOMEM;
+    g->host.push_back(c.hst_hi);
+    if (cudaMalloc(&c.stp_hi, sizeof(CgState*) * c.ninst) != cudaSuccess) return FILL_ENOMEM;
+    g->dev.push_back(c.stp_hi);
+    InstDesc<df>* h = reinterpret_cast<InstDesc<df>*>(c.hdesc_hi);
+    std::vector<CgState*> ptrs;
+    int k = 0;
+    for (int pi : c.plans) {
+      fill_plan* p = g->plans[pi];
+      for (int i = 0; i < p->batch; ++i) {
+        h[k++] = p->h.hdesc[i];
+        ptrs.push_back(p->h.st + i);
+      }
+    }
+    fill_plan* p0 = g->plans[c.plans[0]];
+    c.rows_hi = p0->h.rows;
+    c.ffts_hi = p0->h.ffts;
+    c.col_variant_hi = p0->h.col_variant;
+    CK(cudaMemcpy(c.desc_hi, c.hdesc_hi, nb, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c.stp_hi, ptrs.data(), sizeof(CgState*) * ptrs.size(), cudaMemcpyHostToDevice));
+  }
+  return FILL_OK;
+}
+
+MixedLoop group_mixed_loop(fill_group* g, GroupClass& c, bool host_loops) {
+  return MixedLoop{c.stp_hi, c.ninst, g->counter, g->cap2, host_loops, &g->if_kernels};
+}
+
+// One iteration of every class of a mixed group (class streams forked from
+// and joined back to s).
+cudaError_t group_mixed_iter(fill_group* g, cudaStream_t s, cudaEvent_t fork, bool host_loops) {
+  CE(cudaEventRecord(fork, s));
+  for (auto& c : g->cls) {
+    CE(cudaStreamWaitEvent(c.cs, fork, 0));
+    CE(mixed_iter(gctx<float>(g, c), gctx<df>(g, c, true), c.cs, group_mixed_loop(g, c, host_loops)));
+    CE(cudaEventRecord(c.join, c.cs));
+    CE(cudaStreamWaitEvent(s, c.join, 0));
+  }
+  return cudaSuccess;
+}
+
 // The group's CG loop graph: every loop body forks the size classes onto
 // their streams (parallel branches), runs one iteration of each, and joins.
 template <typename T>
@@ -2464,6 +2560,15 @@ fill_status group_build_graph(fill_group* g) {
         }
         return cudaSuccess;
       },
+      g->stp, g->ntot, g->counter, g->max_iter + 4, &g->launches, &g->graph, &g->graph_kernels);
+}
+
+// The same for a mixed group: each class's body is the reliable-update
+// iteration, with its own update IF node.
+fill_status group_build_mixed_graph(fill_group* g) {
+  if (g->graph) return FILL_OK;
+  return build_loop_graph(
+      g->cap, [&](cudaStream_t cap) { return group_mixed_iter(g, cap, g->fork_cap, false); },
       g->stp, g->ntot, g->counter, g->max_iter + 4, &g->launches, &g->graph, &g->graph_kernels);
 }
 
@@ -2566,6 +2671,105 @@ fill_status group_realize_t(fill_group* g, const void* const* d, const uint64_t*
   return worst;
 }
 
+// Mixed groups (Sects. 2.1-2.4 as in a mixed plan): the double-float draw and
+// right-hand side per class, one FP32 PCG loop with reliable updates over all
+// classes (one graph, classes as parallel branches, an update IF node per
+// class), then per class the final fold, true residual and assembly.
+fill_status group_realize_mixed(fill_group* g, const void* const* d, const uint64_t* seeds,
+                                double tol, void* const* out, fill_stats* stats) {
+  for (auto& c : g->cls) {
+    InstDesc<df>* h = reinterpret_cast<InstDesc<df>*>(c.hdesc_hi);
+    InstDesc<float>* f = reinterpret_cast<InstDesc<float>*>(c.hdesc);
+    int k = 0;
+    for (int pi : c.plans) {
+      fill_plan* p = g->plans[pi];
+      for (int i = 0; i < p->batch; ++i, ++k) {
+        const unsigned long long seed = (unsigned long long)seeds[g->first[pi] + i];
+        h[k].d = reinterpret_cast<const double*>(d[pi]);
+        h[k].out = reinterpret_cast<double*>(out[pi]) + size_t(i) * p->npix;
+        h[k].seed = seed;
+        f[k].d = nullptr;
+        f[k].out = nullptr;
+        f[k].seed = seed;
+      }
+    }
+    CK(cudaMemcpyAsync(c.desc_hi, c.hdesc_hi, sizeof(InstDesc<df>) * c.ninst,
+                       cudaMemcpyHostToDevice, g->s));
+    CK(cudaMemcpyAsync(c.desc, c.hdesc, sizeof(InstDesc<float>) * c.ninst,
+                       cudaMemcpyHostToDevice, g->s));
+  }
+  fill_status fs = group_fork_join<df>(g, [&](GroupClass& c) -> cudaError_t {
+    const Ctx<float> lo = gctx<float>(g, c);
+    const Ctx<df> hi = gctx<df>(g, c, true);
+    const int nb = (c.ninst + 127) / 128;
+    g->launches += 2;
+    k_state_init<df><<<nb, 128, 0, c.cs>>>(hi.desc, c.ninst, tol * tol, g->max_iter, 1);
+    CE(cudaGetLastError());
+    k_state_init<float><<<nb, 128, 0, c.cs>>>(lo.desc, c.ninst, 0.0, g->max_iter, 1);
+    CE(cudaGetLastError());
+    CE(vec<df>(hi, c.cs, VOP_ZERO_UP, SC_NONE, false));
+    CE(draw_and_rhs<df>(hi, c.cs, false));
+    return mixed_start(lo, hi, c.cs, tol, g->update_delta, g->max_iter);
+  });
+  if (fs != FILL_OK) return fs;
+  if (g->host_loops) {
+    fs = run_loop_host(
+        g->s, [&](cudaStream_t s) { return group_mixed_iter(g, s, g->fork, true); }, g->stp,
+        g->ntot, g->counter, g->hloop, g->max_iter + 4, &g->launches);
+    if (fs != FILL_OK) return fs;
+  } else {
+    fs = group_build_mixed_graph(g);
+    if (fs != FILL_OK) return fs;
+    CK(cudaGraphLaunch(g->graph, g->s));
+    CK(cudaMemcpyAsync(g->hloop, g->counter, 2 * sizeof(int), cudaMemcpyDeviceToHost, g->s));
+  }
+  fs = group_fork_join<df>(g, [&](GroupClass& c) -> cudaError_t {
+    const Ctx<float> lo = gctx<float>(g, c);
+    const Ctx<df> hi = gctx<df>(g, c, true);
+    CE(mixed_finish(lo, hi, c.cs));
+    CE(vec<df>(hi, c.cs, VOP_ASSEMBLE, SC_NONE, false));
+    const int nb = (c.ninst + 127) / 128;
+    g->launches += 2;
+    k_gather_states<df><<<nb, 128, 0, c.cs>>>(hi.desc, c.ninst, c.st_hi);
+    CE(cudaGetLastError());
+    k_gather_states<float><<<nb, 128, 0, c.cs>>>(lo.desc, c.ninst, c.st);
+    CE(cudaGetLastError());
+    CE(cudaMemcpyAsync(c.hst_hi, c.st_hi, sizeof(CgState) * c.ninst, cudaMemcpyDeviceToHost, c.cs));
+    return cudaMemcpyAsync(c.hst, c.st, sizeof(CgState) * c.ninst, cudaMemcpyDeviceToHost, c.cs);
+  });
+  if (fs != FILL_OK) return fs;
+  fill_plan* p0 = g->plans[0];   // its stream is the group's
+  CK(queue_err_readback(p0));
+  CK(cudaStreamSynchronize(g->s));
+  if (!g->host_loops) {
+    const long long ifk = g->if_kernels, ncls = (long long)g->cls.size();
+    g->launches += 1 + (long long)g->hloop[0] * (g->graph_kernels - ncls * ifk) +
+                   (long long)g->hloop[1] * ifk;
+  }
+  fill_status worst = FILL_OK;
+  if (take_err(p0) != FILL_OK) return FILL_ETIMEOUT;
+  for (auto& c : g->cls) {
+    int k = 0;
+    for (int pi : c.plans) {
+      fill_plan* p = g->plans[pi];
+      for (int i = 0; i < p->batch; ++i, ++k) {
+        const CgState& a = c.hst[k];
+        const CgState& h = c.hst_hi[k];
+        fill_stats st{};
+        st.iters = h.total_iter;
+        st.refine_steps = h.refine;
+        const bool conv = h.rr <= h.tol2 * h.bb;
+        st.status = h.status ? h.status : (conv ? FILL_OK : FILL_ENOTCONV);
+        st.rel_resid = a.bb > 0 ? std::sqrt(a.rr / a.bb) : 0.0;
+        st.true_rel_resid = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
+        note_status(st.status, &worst);
+        if (stats) stats[g->first[pi] + i] = st;
+      }
+    }
+  }
+  return worst;
+}
+
 }  // namespace
 
 extern "C" {
@@ -2590,7 +2794,8 @@ fill_status fill_group_init(fill_group** out, fill_plan* const* plans, int count
   if (!out || !plans || count < 1) return FILL_EINVAL;
   *out = nullptr;
   const int mode = plans[0] ? plans[0]->o.mode : -1;
-  if (mode != FILL_MODE_FP32 && mode != FILL_MODE_FP64) return FILL_EINVAL;
+  if (mode != FILL_MODE_FP32 && mode != FILL_MODE_FP64 && mode != FILL_MODE_MIXED)
+    return FILL_EINVAL;
   fill_group* g = new (std::nothrow) fill_group();
   if (!g) return FILL_ENOMEM;
   auto fail = [&](fill_status st) {
@@ -2601,11 +2806,16 @@ fill_status fill_group_init(fill_group** out, fill_plan* const* plans, int count
   g->precond = plans[0]->o.precond;
   g->max_iter = plans[0]->o.max_iter;
   g->host_loops = plans[0]->o.host_loops;
+  g->update_delta = plans[0]->o.update_delta;
   g->s = plans[0]->s;
   int flat = 0;
   for (int i = 0; i < count; ++i) {
     fill_plan* p = plans[i];
     if (!p || p->o.mode != mode || p->o.precond != g->precond || p->s != g->s)
+      return fail(FILL_EINVAL);
+    // mixed groups run the reliable-update loop (update_delta > 0), one
+    // threshold for all
+    if (mode == FILL_MODE_MIXED && (!(p->o.update_delta > 0.0) || p->o.update_delta != g->update_delta))
       return fail(FILL_EINVAL);
     g->plans.push_back(p);
     g->first.push_back(flat);
@@ -2628,6 +2838,8 @@ fill_status fill_group_init(fill_group** out, fill_plan* const* plans, int count
   }
   g->ntot = flat;
   cudaError_t e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess && mode == FILL_MODE_MIXED)
+    e = cudaStreamCreateWithFlags(&g->cap2, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->fork_cap, cudaEventDisableTiming);
   for (auto& c : g->cls) {
@@ -2640,7 +2852,7 @@ fill_status fill_group_init(fill_group** out, fill_plan* const* plans, int count
   }
   if (e == cudaSuccess) e = cudaMalloc(&g->counter, 2 * sizeof(int));
   if (e == cudaSuccess) g->dev.push_back(g->counter);
-  if (e == cudaSuccess) e = cudaMallocHost(&g->hloop, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&g->hloop, 2 * sizeof(int));
   if (e == cudaSuccess) g->host.push_back(g->hloop);
   if (e == cudaSuccess) e = cudaMalloc(&g->stp, sizeof(CgState*) * g->ntot);
   if (e == cudaSuccess) g->dev.push_back(g->stp);
@@ -2649,14 +2861,15 @@ fill_status fill_group_init(fill_group** out, fill_plan* const* plans, int count
     for (auto& c : g->cls)
       for (int pi : c.plans) {
         fill_plan* p = g->plans[pi];
-        CgState* st = mode == FILL_MODE_FP32 ? p->f.st : p->g.st;
+        CgState* st = mode == FILL_MODE_FP64 ? p->g.st : p->f.st;   // the CG loop's states
         for (int i = 0; i < p->batch; ++i) ptrs.push_back(st + i);
       }
     e = cudaMemcpy(g->stp, ptrs.data(), sizeof(CgState*) * ptrs.size(), cudaMemcpyHostToDevice);
   }
   if (e != cudaSuccess) return fail(cuda_fail(e, "fill_group_init"));
-  fill_status fs = mode == FILL_MODE_FP32 ? group_setup<float>(g, autotune, cache_path)
-                                          : group_setup<double>(g, autotune, cache_path);
+  fill_status fs = mode == FILL_MODE_FP64 ? group_setup<double>(g, autotune, cache_path)
+                                          : group_setup<float>(g, autotune, cache_path);
+  if (fs == FILL_OK && mode == FILL_MODE_MIXED) fs = group_setup_hi(g);
   if (fs != FILL_OK) return fail(fs);
   e = cudaStreamSynchronize(g->s);
   if (e != cudaSuccess) return fail(cuda_fail(e, "fill_group_init"));
@@ -2671,9 +2884,10 @@ fill_status fill_group_realize(fill_group* g, const void* const* d, const uint64
     if (!d[i] || !out[i]) return FILL_EINVAL;
   const auto t0 = std::chrono::steady_clock::now();
   g->launches = 0;
-  const fill_status worst = g->mode == FILL_MODE_FP32
-                                ? group_realize_t<float>(g, d, seeds, tol, out, stats)
-                                : group_realize_t<double>(g, d, seeds, tol, out, stats);
+  const fill_status worst =
+      g->mode == FILL_MODE_MIXED  ? group_realize_mixed(g, d, seeds, tol, out, stats)
+      : g->mode == FILL_MODE_FP32 ? group_realize_t<float>(g, d, seeds, tol, out, stats)
+                                  : group_realize_t<double>(g, d, seeds, tol, out, stats);
   if (worst == FILL_ECUDA) return worst;
   const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (stats)
@@ -2696,8 +2910,10 @@ fill_status fill_realize_batch(fill_plan* const* plans, int count, const void* c
     fill_plan* p = plans[i];
     if (!p || !d[i] || !out[i]) return FILL_EINVAL;
     key[i] = p->serial;
-    groupable = groupable && p->o.mode != FILL_MODE_MIXED && p->o.mode == plans[0]->o.mode &&
-                p->o.precond == plans[0]->o.precond && p->s == plans[0]->s;
+    groupable = groupable && p->o.mode == plans[0]->o.mode &&
+                p->o.precond == plans[0]->o.precond && p->s == plans[0]->s &&
+                (p->o.mode != FILL_MODE_MIXED ||
+                 (p->o.update_delta > 0.0 && p->o.update_delta == plans[0]->o.update_delta));
   }
   if (!groupable) {
     // one plan after another, each with its own data map shared by its batch
