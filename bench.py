@@ -415,6 +415,7 @@ def configs_measurement():
       each with its own mask, in ONE group call (fill_group_realize, the
       machinery of fill_realize_batch; FP32, tol 1e-6, autotuned size
       classes running as concurrent branches of one graph per CG loop);
+      and the same batch in mixed precision to 1e-10 (batch_mixed_refined);
     * grad2048: 2048^2, FP32, 32 band powers: forward, adjoint (fill_backward
       for dL/dd and dL/da_b of L = sum over M of x^2), fill_set_spectrum plus
       forward, and the same through the torch.autograd.Function.
@@ -474,6 +475,34 @@ def configs_measurement():
                           "per_size": {str(k): v for k, v in per_size.items()},
                           "note": "one fill_group_realize call; algorithmic bytes = "
                                   "sum of iterations x the per-iteration pass bytes"}
+    for p_ in plans:
+        p_.close()
+    del plans, ds
+    torch.cuda.empty_cache()
+
+    # the same 256 realizations in mixed precision (FP32 operator, double-float
+    # draw, right-hand side and reliable updates) to 1e-10, one group call
+    plans, ds = [], []
+    for n, count in spec["sizes"]:
+        P = synth.spectrum_cmb_like(n, n, k_lo)
+        first = None
+        for j in range(count):
+            obs = synth.mask_area_target(n, n, seed=spec["mask_seed"] * 100_000 + n * 1000 + j)
+            plans.append(cg.Plan(P, obs, mode="mixed"))
+            if first is None:
+                first = plans[-1].draw([spec["data_seed"]])[0].clone()
+            ds.append(first)
+    g = cg.Group(plans, autotune=True)
+    ms, (_, st) = _events_ms(lambda: g.realize(ds, seeds, 1e-10), 2)
+    g.close()
+    out["batch_mixed_refined"] = {
+        "realizations": len(plans), "mode": "mixed", "tol": 1e-10,
+        "realizations_per_s": len(plans) / (ms / 1e3), "ms_per_call": ms,
+        "cg_iters_per_s": sum(x["iters"] for x in st) / (ms / 1e3),
+        "worst_true_rel_resid": max(x["true_rel_resid"] for x in st),
+        "all_ok": all(x["status"] == 0 for x in st),
+        "note": "one fill_group_realize call in mixed precision (not the configuration's FP32 "
+                "mode): the batching pattern at the precision target of the 4096^2 workload"}
     for p_ in plans:
         p_.close()
     del plans, ds
