@@ -99,6 +99,12 @@ typedef struct {
                             bulk copies (TMA) into a double-buffered shared-memory slot;
                             the same arithmetic, so the results are identical.
                             fill_autotune may switch it */
+  int lanes;             /* the CG loops run the batch as this many sub-batches, each a
+                            parallel branch of the loop graph (one launch per pass and
+                            lane; the GPU fills one lane's gaps with another's work);
+                            results are identical for any value.  0 = automatic: 2 for
+                            batch >= 2 on grids of at least 2^20 pixels, else 1; at
+                            most 8 */
 } fill_opts;
 
 typedef struct {

@@ -55,7 +55,8 @@ class FillOpts(ctypes.Structure):
                 ("inner_tol", ctypes.c_double),
                 ("history_cap", ctypes.c_int), ("rows_per_cta", ctypes.c_int),
                 ("ffts_per_cta", ctypes.c_int), ("backward", ctypes.c_int),
-                ("update_delta", ctypes.c_double), ("col_kernel", ctypes.c_int)]
+                ("update_delta", ctypes.c_double), ("col_kernel", ctypes.c_int),
+                ("lanes", ctypes.c_int)]
 
 
 class FillStats(ctypes.Structure):
@@ -395,7 +396,7 @@ class Plan:
     def __init__(self, P_half, observed, mode="mixed", precond=True, batch=1,
                  max_iter=10000, max_refine=10, inner_tol=1e-6, history_cap=0,
                  rows_per_cta=0, ffts_per_cta=0, backward=False, update_delta=1e-2,
-                 host_loops=False, col_kernel=0, stream=None):
+                 host_loops=False, col_kernel=0, lanes=0, stream=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("paper_1109_0286_gb300 needs a CUDA GPU; no CPU fallback exists")
@@ -413,6 +414,7 @@ class Plan:
         o.update_delta = float(update_delta)
         o.host_loops = 1 if host_loops else 0
         o.col_kernel = int(col_kernel)
+        o.lanes = int(lanes)
         self.nbands = 0
         self.calls = 0          # compute calls so far (each may overwrite the device state)
         self.ny, self.nx = observed.shape

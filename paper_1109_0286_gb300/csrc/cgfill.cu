@@ -140,6 +140,8 @@ struct Precision {
 
 }  // namespace
 
+constexpr int kMaxLanes = 8;   // CG-loop lanes of a plan (fill_opts::lanes)
+
 struct fill_plan {
   int ny = 0, nx = 0, log_l = 0, log_n = 0, batch = 1;
   bool gen = false;              // mixed-radix grid (cg_generic.h kernels)
@@ -149,6 +151,10 @@ struct fill_plan {
   cudaStream_t s = nullptr;      // caller's stream
   cudaStream_t cap = nullptr;    // plan-owned stream for graph capture
   cudaStream_t cap2 = nullptr;   // second capture stream (conditional bodies)
+  int nlanes = 1;                // CG-loop lanes (fill_opts::lanes)
+  cudaStream_t lane_s[kMaxLanes] = {};
+  cudaEvent_t lane_join[kMaxLanes] = {};
+  cudaEvent_t lane_fork = nullptr, lane_fork_cap = nullptr;
   uint2* mw = nullptr;           // mask words: observed bits, compact offset
   long long nv = 0;              // compact vector stride per instance (>= nmasked)
   std::vector<double> P_half;    // host copy of the spectrum
@@ -183,6 +189,12 @@ struct fill_plan {
     for (void* p : host) cudaFreeHost(p);
     if (cap) cudaStreamDestroy(cap);
     if (cap2) cudaStreamDestroy(cap2);
+    for (int l = 0; l < kMaxLanes; ++l) {
+      if (lane_s[l]) cudaStreamDestroy(lane_s[l]);
+      if (lane_join[l]) cudaEventDestroy(lane_join[l]);
+    }
+    if (lane_fork) cudaEventDestroy(lane_fork);
+    if (lane_fork_cap) cudaEventDestroy(lane_fork_cap);
   }
   template <typename X>
   cudaError_t dalloc(X** p, size_t count) {
@@ -447,9 +459,48 @@ template <typename T>
 cudaError_t pcg_start(fill_plan* p, cudaStream_t s, int load_sop) {
   return pcg_start<T>(ctx<T>(p), s, load_sop);
 }
+// Lanes: a plan's CG loops run its batch as nlanes sub-batches of
+// consecutive instances, each on its own stream (parallel branches of the
+// loop graph when captured).  Every pass computes each instance on its own,
+// so the results do not depend on the lanes.
 template <typename T>
-cudaError_t pcg_iter(fill_plan* p, cudaStream_t s) {
-  return pcg_iter<T>(ctx<T>(p), s);
+Ctx<T> lane_ctx(fill_plan* p, int first, int count) {
+  Ctx<T> c = ctx<T>(p);
+  c.desc += first;
+  c.ninst = count;
+  return c;
+}
+
+// body(first, count, stream) for each lane: on s itself with one lane, else
+// on the lane streams forked from s and joined back to it.
+template <typename F>
+cudaError_t on_lanes(fill_plan* p, cudaStream_t s, bool capturing, F body) {
+  if (p->nlanes <= 1) return body(0, p->batch, s);
+  const cudaEvent_t fork = capturing ? p->lane_fork_cap : p->lane_fork;
+  CE(cudaEventRecord(fork, s));
+  const int per = (p->batch + p->nlanes - 1) / p->nlanes;
+  for (int l = 0; l < p->nlanes; ++l) {
+    const int first = l * per, count = std::min(per, p->batch - first);
+    if (count <= 0) break;
+    CE(cudaStreamWaitEvent(p->lane_s[l], fork, 0));
+    CE(body(first, count, p->lane_s[l]));
+    CE(cudaEventRecord(p->lane_join[l], p->lane_s[l]));
+    CE(cudaStreamWaitEvent(s, p->lane_join[l], 0));
+  }
+  return cudaSuccess;
+}
+
+// Lanes that hold instances (the IF nodes of a mixed loop body).
+int active_lanes(const fill_plan* p) {
+  const int per = (p->batch + p->nlanes - 1) / p->nlanes;
+  return (p->batch + per - 1) / per;
+}
+
+template <typename T>
+cudaError_t pcg_iter(fill_plan* p, cudaStream_t s, bool capturing = false) {
+  return on_lanes(p, s, capturing, [&](int first, int count, cudaStream_t ls) {
+    return pcg_iter<T>(lane_ctx<T>(p, first, count), ls);
+  });
 }
 
 // ----------------------------------------------------------------- device-side CG loop
@@ -530,11 +581,11 @@ fill_status build_loop_graph(cudaStream_t cap, Body body, CgState* const* sts, i
 // Launches a loop graph on the plan's stream and accounts for its kernels
 // (if_kernels of each body run only when its IF node fires).
 fill_status run_loop_graph(fill_plan* p, cudaGraphExec_t exec, long long body_kernels,
-                           long long if_kernels = 0) {
+                           long long if_kernels = 0, int n_if = 1) {
   CK(cudaGraphLaunch(exec, p->s));
   CK(cudaMemcpyAsync(p->hloop, p->loop_counter, 2 * sizeof(int), cudaMemcpyDeviceToHost, p->s));
   CK(cudaStreamSynchronize(p->s));
-  p->launches += 1 + (long long)p->hloop[0] * (body_kernels - if_kernels) +
+  p->launches += 1 + (long long)p->hloop[0] * (body_kernels - n_if * if_kernels) +
                  (long long)p->hloop[1] * if_kernels;
   return FILL_OK;
 }
@@ -576,7 +627,7 @@ fill_status build_iter_graph(fill_plan* p) {
   Precision<T>& P = prec<T>(p);
   if (P.iter_graph) return FILL_OK;
   return build_loop_graph(
-      p->cap, [&](cudaStream_t s) { return pcg_iter<T>(p, s); }, P.stp, p->batch,
+      p->cap, [&](cudaStream_t s) { return pcg_iter<T>(p, s, true); }, P.stp, p->batch,
       p->loop_counter, p->o.max_iter + 4, &p->launches, &P.iter_graph, &P.iter_graph_kernels);
 }
 
@@ -784,19 +835,18 @@ cudaError_t mixed_finish(const Ctx<float>& lo, const Ctx<df>& hi, cudaStream_t s
   return cudaGetLastError();
 }
 
-MixedLoop mixed_loop(fill_plan* p) {
-  return MixedLoop{p->h.stp, p->batch, p->loop_counter, p->cap2, p->o.host_loops != 0,
-                   &p->if_kernels};
-}
-
-cudaError_t mixed_iter(fill_plan* p, cudaStream_t s) {
-  return mixed_iter(ctx<float>(p), ctx<df>(p), s, mixed_loop(p));
+cudaError_t mixed_iter(fill_plan* p, cudaStream_t s, bool capturing) {
+  return on_lanes(p, s, capturing, [&](int first, int count, cudaStream_t ls) {
+    const MixedLoop m{p->h.stp + first, count, p->loop_counter, p->cap2, p->o.host_loops != 0,
+                      &p->if_kernels};
+    return mixed_iter(lane_ctx<float>(p, first, count), lane_ctx<df>(p, first, count), ls, m);
+  });
 }
 
 fill_status build_mixed_graph(fill_plan* p) {
   if (p->mixed_graph) return FILL_OK;
   return build_loop_graph(
-      p->cap, [&](cudaStream_t s) { return mixed_iter(p, s); }, p->f.stp, p->batch,
+      p->cap, [&](cudaStream_t s) { return mixed_iter(p, s, true); }, p->f.stp, p->batch,
       p->loop_counter, p->o.max_iter + 4, &p->launches, &p->mixed_graph, &p->mixed_graph_kernels);
 }
 
@@ -807,12 +857,13 @@ fill_status mixed_reliable(fill_plan* p, double tol) {
   fill_status fs;
   if (p->o.host_loops) {
     fs = run_loop_host(
-        p->s, [&](cudaStream_t s) { return mixed_iter(p, s); }, p->f.stp, p->batch,
+        p->s, [&](cudaStream_t s) { return mixed_iter(p, s, false); }, p->f.stp, p->batch,
         p->loop_counter, p->hloop, p->o.max_iter + 4, &p->launches);
   } else {
     fs = build_mixed_graph(p);
     if (fs != FILL_OK) return fs;
-    fs = run_loop_graph(p, p->mixed_graph, p->mixed_graph_kernels, p->if_kernels);
+    fs = run_loop_graph(p, p->mixed_graph, p->mixed_graph_kernels, p->if_kernels,
+                        active_lanes(p));
   }
   if (fs != FILL_OK) return fs;
   CK(mixed_finish(ctx<float>(p), ctx<df>(p), p->s));
@@ -1350,7 +1401,8 @@ fill_status fill_init(fill_plan** out, int ny, int nx, const double* P_half,
   if (o.mode < 0 || o.mode > 2 || o.batch < 1 || o.batch > 65535 || o.max_iter < 1 ||
       o.max_refine < 1 || o.host_loops < 0 || o.host_loops > 1 || !(o.inner_tol > 0.0) || o.history_cap < 0 || o.rows_per_cta < 0 ||
       o.ffts_per_cta < 0 || o.backward < 0 || o.backward > 1 || !(o.update_delta >= 0.0) ||
-      !(o.update_delta < 1.0) || o.col_kernel < 0 || o.col_kernel > 1)
+      !(o.update_delta < 1.0) || o.col_kernel < 0 || o.col_kernel > 1 || o.lanes < 0 ||
+      o.lanes > kMaxLanes)
     return FILL_EINVAL;
   const int nkx = nx / 2 + 1;
   if (!spectrum_valid(ny, nx, P_half)) return FILL_EINVAL;
@@ -1396,6 +1448,16 @@ fill_status fill_init(fill_plan** out, int ny, int nx, const double* P_half,
   };
   cudaError_t e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap2, cudaStreamNonBlocking);
+  p->nlanes = o.lanes > 0 ? std::min(o.lanes, o.batch)
+                          : (o.batch >= 2 && npix >= (1LL << 20) ? 2 : 1);
+  if (p->nlanes > 1) {
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->lane_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->lane_fork_cap, cudaEventDisableTiming);
+    for (int l = 0; l < p->nlanes && e == cudaSuccess; ++l) {
+      e = cudaStreamCreateWithFlags(&p->lane_s[l], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->lane_join[l], cudaEventDisableTiming);
+    }
+  }
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaStreamCreate"));
   if (p->dalloc(&p->mw, words.size()) != cudaSuccess) return fail(FILL_ENOMEM);
   if (p->dalloc(&p->P_dev, (size_t)ny * nkx) != cudaSuccess) return fail(FILL_ENOMEM);

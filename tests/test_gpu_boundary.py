@@ -301,3 +301,46 @@ def test_autograd_backward_after_other_work_reruns_its_forward():
         x = cg.FillRealize.apply(d, aa, qp, q, [s], 1e-12)
         (x[0] * x[0] * m).sum().backward()
         assert torch.equal(a.grad, aa.grad)
+
+
+# ------------------------------------------------------------------ lanes
+
+@pytest.mark.parametrize("host_loops", [False, True])
+@pytest.mark.parametrize("mode", ["fp32", "fp64", "mixed"])
+def test_lanes_do_not_change_results(mode, host_loops):
+    """The CG loops' lanes (sub-batches run as parallel branches of the loop
+    graph, an update IF node per lane in mixed mode) leave every realization
+    and its iteration count bit for bit unchanged: 1, 2 and 3 lanes over a
+    batch of 5 (lanes of 3 + 2 and 2 + 2 + 1 instances)."""
+    n = 128
+    P = synth.spectrum_cmb_like(n, n, 2 * math.pi / n)
+    obs = synth.mask_area_target(n, n, seed=31)
+    d = torch.from_numpy(O.draw(O.hermitian_full(P, n), 4)).to(DT[mode]).cuda()
+    tol = 1e-6 if mode == "fp32" else 1e-10
+    res = []
+    for lanes in (1, 2, 3):
+        plan = cg.Plan(P, obs, mode=mode, batch=5, lanes=lanes, host_loops=host_loops)
+        x, st = plan.realize(d, [10, 11, 12, 13, 14], tol)
+        assert all(s["status"] == 0 for s in st)
+        res.append((x, [s["iters"] for s in st]))
+    for x, it in res[1:]:
+        assert torch.equal(x, res[0][0]) and it == res[0][1]
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_lanes_do_not_change_the_adjoint(mode):
+    """fill_backward's adjoint solve runs on the same lanes: dL/dd and the
+    band gradients are bit for bit those of a one-lane plan."""
+    bidx, sig, noise, obs = band_case(64, nbands=8)
+    model = cg.BandPowerSpectrum(bidx, sig, noise)
+    d = torch.from_numpy(O.draw(O.hermitian_full(model(np.ones(8)), 64), 6)).cuda()
+    m = torch.from_numpy(obs == 0).cuda()
+    outs = []
+    for lanes in (1, 2):
+        plan = cg.Plan(model(np.ones(8)), obs, mode=mode, backward=True, batch=2, lanes=lanes)
+        plan.set_bands(bidx, sig)
+        x, _ = plan.realize(d, [3, 4], 1e-10)
+        gd, gb, _ = plan.backward(d, (2.0 * x * m).contiguous(), 1e-10)
+        outs.append((gd, gb))
+    assert torch.equal(outs[0][0], outs[1][0])
+    assert np.array_equal(np.asarray(outs[0][1]), np.asarray(outs[1][1]))
