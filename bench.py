@@ -180,9 +180,12 @@ def job_throughput(batch, steps, world, ms_max):
 
 
 def workload_config(name, grid, batch, tol, mode, masked_fraction, world, **extra):
+    npix = int(grid[0]) * int(grid[1])
     cfg = {"workload": name, "grid": list(grid), "batch": batch, "tol": tol, "mode": mode,
            "precond": "sqrtC", "masked_fraction": round(float(masked_fraction), 4),
-           "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (no flush)"}
+           "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (no flush)",
+           # CG-loop lanes of the library's automatic setting (fill_opts.lanes = 0)
+           "lanes": 2 if batch >= 2 and npix >= 1 << 20 else 1}
     cfg.update(extra)
     return cfg
 
