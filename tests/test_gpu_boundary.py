@@ -305,17 +305,19 @@ def test_autograd_backward_after_other_work_reruns_its_forward():
 
 # ------------------------------------------------------------------ lanes
 
+@pytest.mark.parametrize("ny,nx", [(128, 128), (60, 140)])
 @pytest.mark.parametrize("host_loops", [False, True])
 @pytest.mark.parametrize("mode", ["fp32", "fp64", "mixed"])
-def test_lanes_do_not_change_results(mode, host_loops):
+def test_lanes_do_not_change_results(mode, host_loops, ny, nx):
     """The CG loops' lanes (sub-batches run as parallel branches of the loop
     graph, an update IF node per lane in mixed mode) leave every realization
     and its iteration count bit for bit unchanged: 1, 2 and 3 lanes over a
-    batch of 5 (lanes of 3 + 2 and 2 + 2 + 1 instances)."""
-    n = 128
-    P = synth.spectrum_cmb_like(n, n, 2 * math.pi / n)
-    obs = synth.mask_area_target(n, n, seed=31)
-    d = torch.from_numpy(O.draw(O.hermitian_full(P, n), 4)).to(DT[mode]).cuda()
+    batch of 5 (lanes of 3 + 2 and 2 + 2 + 1 instances), on a power-of-two
+    and a mixed-radix grid."""
+    P = synth.spectrum_cmb_like(ny, nx, 2 * math.pi / max(ny, nx))
+    obs = synth.mask_area_target(ny, nx, seed=31) if ny == nx else \
+        synth.mask_band_discs(ny, nx, 6, 5, 2.0, 5.0, 31)
+    d = torch.from_numpy(O.draw(O.hermitian_full(P, nx), 4)).to(DT[mode]).cuda()
     tol = 1e-6 if mode == "fp32" else 1e-10
     res = []
     for lanes in (1, 2, 3):
