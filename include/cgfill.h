@@ -86,8 +86,10 @@ typedef struct {
   double inner_tol;      /* relative tolerance floor of the FP32 inner solves
                             (mixed mode); default 1e-6 */
   int history_cap;       /* residual-history entries kept per realization; default 0 */
-  int rows_per_cta;      /* row-pass CTA height, 0 = default schedule */
-  int ffts_per_cta;      /* column FFTs per CTA, 0 = default schedule */
+  int rows_per_cta;      /* row-pass CTA height, 0 = default schedule (the CG loop's
+                            precision; the mixed mode's double-float passes keep
+                            their defaults) */
+  int ffts_per_cta;      /* column FFTs per CTA, 0 = default schedule (as rows_per_cta) */
   int backward;          /* 1: allocate the buffers fill_backward needs; default 0 */
   double update_delta;   /* mixed mode: one FP32 PCG with reliable updates -- the FP32
                             correction is folded into the double-float solution and

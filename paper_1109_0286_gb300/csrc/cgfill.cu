@@ -1071,6 +1071,15 @@ void gen_threads(GenLen* g, int V, bool wide) {
   }
 }
 
+// Whether precision T carries the plan's CG loop (FP64 in FP64 mode, FP32
+// otherwise): the schedule options rows_per_cta / ffts_per_cta set its CTA
+// shapes; the double-float passes of the mixed mode keep their defaults.
+template <typename T>
+bool loop_precision(const fill_plan* p) {
+  return p->o.mode == FILL_MODE_FP64 ? std::is_same<T, double>::value
+                                     : std::is_same<T, float>::value;
+}
+
 // Validity of a mixed-radix CTA shape for precision T: rows per CTA and
 // column FFTs per CTA are multiples of the group width V = gen_v<T>(), the
 // row groups a power of two, within kGenThreads threads, the partial-sum slots
@@ -1143,13 +1152,14 @@ fill_status setup_generic(fill_plan* p) {
   Precision<T>& P = prec<T>(p);
   constexpr int V = gen_v<T>();
   const size_t third = 75 * 1024;
-  if (p->o.rows_per_cta > 0) {
+  const bool user = loop_precision<T>(p);
+  if (user && p->o.rows_per_cta > 0) {
     P.rows = p->o.rows_per_cta;
   } else {
     P.rows = V;
     if (gen_row_ok<T>(p, 2 * V) && GenLaunch<T>::row_smem(p->nx / 2, 2 * V) <= third) P.rows = 2 * V;
   }
-  if (p->o.ffts_per_cta > 0) {
+  if (user && p->o.ffts_per_cta > 0) {
     P.ffts = p->o.ffts_per_cta;
   } else {
     P.ffts = V;
@@ -1260,9 +1270,11 @@ fill_status setup_precision(fill_plan* p, const std::vector<double>& tinv,
     fill_status gs = setup_generic<T>(p);
     if (gs != FILL_OK) return gs;
   } else {
-    P.rows = p->o.rows_per_cta > 0 ? std::min(p->o.rows_per_cta, p->ny)
-                                   : default_rows<T>(p->log_l, p->ny);
-    P.ffts = p->o.ffts_per_cta > 0 ? p->o.ffts_per_cta : default_ffts<T>(p->log_n, p->nx / 2 + 1);
+    const bool user = loop_precision<T>(p);
+    P.rows = user && p->o.rows_per_cta > 0 ? std::min(p->o.rows_per_cta, p->ny)
+                                           : default_rows<T>(p->log_l, p->ny);
+    P.ffts = user && p->o.ffts_per_cta > 0 ? p->o.ffts_per_cta
+                                           : default_ffts<T>(p->log_n, p->nx / 2 + 1);
     if (!schedule_valid<T>(p->log_l, p->log_n, p->ny, P.rows, P.ffts)) return FILL_EINVAL;
     P.col_variant = std::is_same<T, float>::value ? p->o.col_kernel : 0;
   }

@@ -211,3 +211,21 @@ def test_every_radix_schedule_matches_oracle(tmp_path, mode, bound):
     b.autotune(cache)   # served from the cache
     xb, _ = b.realize(dd, [5], 1e-10)
     assert torch.equal(xa, xb)
+
+
+def test_schedule_options_set_the_loop_precision():
+    """rows_per_cta / ffts_per_cta set the CTA shapes of the CG loop's
+    precision; the double-float passes of the mixed mode keep their own
+    defaults (on the 7000 x 600 grid their 256-thread groups could not take
+    two rows per CTA).  The realization converges like the default plan's."""
+    P, obs, spec = workload("act7000x600")
+    ny, nx = obs.shape
+    d = gpu_map(O.draw(O.hermitian_full(P, nx), spec["data_seed"]), torch.float64)
+    outs = []
+    for opts in ({}, {"rows_per_cta": 2, "ffts_per_cta": 4}):
+        plan = cg.Plan(P, obs, mode="mixed", **opts)
+        x, st = plan.realize(d, [spec["seeds"][0]], 1e-10)
+        assert st[0]["status"] == 0 and st[0]["true_rel_resid"] <= 1e-10
+        outs.append(x[0].cpu().numpy())
+    m = obs == 0
+    assert rel(outs[1][m], outs[0][m]) <= 1e-8
