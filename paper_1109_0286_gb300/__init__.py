@@ -388,9 +388,12 @@ class Plan:
     """A fill-in plan for one grid, spectrum and mask, fed with torch tensors.
 
     ``mode`` is ``"fp64"`` (plain FP64 PCG), ``"fp32"`` (FP32 operator,
-    FP64-accurate inner products) or ``"mixed"`` (FP32 inner PCG with FP64
-    residuals and iterative refinement).  Maps are float32 in fp32 mode and
-    float64 otherwise, on the current CUDA device.
+    FP64-accurate inner products) or ``"mixed"`` (FP32 inner PCG with
+    double-float residuals and reliable updates).  Maps are float32 in fp32
+    mode and float64 otherwise, on the current CUDA device.  The remaining
+    keywords mirror ``fill_opts`` (``lanes``: sub-batches of the CG loops run
+    as parallel graph branches, 0 = automatic; ``rows_per_cta`` /
+    ``ffts_per_cta``: the CG loop precision's CTA shapes, 0 = default).
     """
 
     def __init__(self, P_half, observed, mode="mixed", precond=True, batch=1,
