@@ -14,10 +14,13 @@ namespace gen {
 // shared-memory access for two FP32 transforms).
 template <typename T, int V>
 __device__ __forceinline__ void ld_slot(const cx<T>* p, cx<T> (&v)[V]) {
-  if constexpr (V == 2 && std::is_same<T, float>::value) {
-    const float4 a = *reinterpret_cast<const float4*>(p);
-    v[0] = cx<float>{a.x, a.y};
-    v[1] = cx<float>{a.z, a.w};
+  if constexpr (V % 2 == 0 && std::is_same<T, float>::value) {
+#pragma unroll
+    for (int h = 0; h < V; h += 2) {
+      const float4 a = *reinterpret_cast<const float4*>(p + h);
+      v[h] = cx<float>{a.x, a.y};
+      v[h + 1] = cx<float>{a.z, a.w};
+    }
   } else {
 #pragma unroll
     for (int u = 0; u < V; ++u) v[u] = ld_cx<T>(reinterpret_cast<const T*>(p + u));
@@ -25,8 +28,10 @@ __device__ __forceinline__ void ld_slot(const cx<T>* p, cx<T> (&v)[V]) {
 }
 template <typename T, int V>
 __device__ __forceinline__ void st_slot(cx<T>* p, const cx<T> (&v)[V]) {
-  if constexpr (V == 2 && std::is_same<T, float>::value) {
-    *reinterpret_cast<float4*>(p) = make_float4(v[0].r, v[0].i, v[1].r, v[1].i);
+  if constexpr (V % 2 == 0 && std::is_same<T, float>::value) {
+#pragma unroll
+    for (int h = 0; h < V; h += 2)
+      *reinterpret_cast<float4*>(p + h) = make_float4(v[h].r, v[h].i, v[h + 1].r, v[h + 1].i);
   } else {
 #pragma unroll
     for (int u = 0; u < V; ++u) st_cx<T>(reinterpret_cast<T*>(p + u), v[u]);
@@ -244,16 +249,20 @@ __device__ __forceinline__ cx<T> r2c_one(cx<T> zk, cx<T> zm, cx<T> w) {
 constexpr int kGenChunk = 4;
 
 // Rows y0 .. y0 + V - 1 of half-spectrum row k (element offset off = k ny + y0):
-// one 16-byte access for two FP32 rows when ny is even (off is then even);
-// rows at or beyond ny (nv < V) read zeros and are not written.
+// one 16-byte access per two FP32 rows when ny is even (off is then even) and
+// the group lies inside the grid; rows at or beyond ny (nv < V) read zeros
+// and are not written.
 template <typename T, int V>
 __device__ __forceinline__ void ld_spec(const T* spec, size_t off, int nv, bool vec,
                                         cx<T> (&x)[V]) {
-  if constexpr (V == 2 && std::is_same<T, float>::value) {
-    if (vec) {
-      const float4 a = __ldg(reinterpret_cast<const float4*>(spec + 2 * off));
-      x[0] = cx<float>{a.x, a.y};
-      x[1] = cx<float>{a.z, a.w};
+  if constexpr (V % 2 == 0 && std::is_same<T, float>::value) {
+    if (vec && nv == V) {
+#pragma unroll
+      for (int h = 0; h < V; h += 2) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(spec + 2 * (off + h)));
+        x[h] = cx<float>{a.x, a.y};
+        x[h + 1] = cx<float>{a.z, a.w};
+      }
       return;
     }
   }
@@ -262,9 +271,12 @@ __device__ __forceinline__ void ld_spec(const T* spec, size_t off, int nv, bool 
 }
 template <typename T, int V>
 __device__ __forceinline__ void st_spec(T* spec, size_t off, int nv, bool vec, const cx<T> (&x)[V]) {
-  if constexpr (V == 2 && std::is_same<T, float>::value) {
-    if (vec) {
-      *reinterpret_cast<float4*>(spec + 2 * off) = make_float4(x[0].r, x[0].i, x[1].r, x[1].i);
+  if constexpr (V % 2 == 0 && std::is_same<T, float>::value) {
+    if (vec && nv == V) {
+#pragma unroll
+      for (int h = 0; h < V; h += 2)
+        *reinterpret_cast<float4*>(spec + 2 * (off + h)) =
+            make_float4(x[h].r, x[h].i, x[h + 1].r, x[h + 1].i);
       return;
     }
   }
@@ -840,7 +852,7 @@ template <typename T>
 cudaError_t GenLaunch<T>::row(bool in_spec, bool out_spec, const InstDesc<T>* d, int ninst,
                               const RowArgs& a, const GenLen& g, const T* wl, const T* wx,
                               cudaStream_t s) {
-  constexpr int V = gen_v<T>();
+  constexpr int V = gen_vrow<T>();
   const dim3 grid((a.ny + a.rows - 1) / a.rows, ninst), block(a.rows / V * g.nt);
   const size_t sm = row_smem(g.n, a.rows);
   if (in_spec && out_spec)
@@ -869,11 +881,11 @@ cudaError_t GenLaunch<T>::col(const InstDesc<T>* d, int ninst, const ColArgs& a,
 
 template <typename T>
 cudaError_t GenLaunch<T>::prepare() {
-  constexpr int V = gen_v<T>();
-  cudaError_t e = detail::allow_smem(k_row_gen<T, V, true, true>);
-  if (e == cudaSuccess) e = detail::allow_smem(k_row_gen<T, V, true, false>);
-  if (e == cudaSuccess) e = detail::allow_smem(k_row_gen<T, V, false, true>);
-  if (e == cudaSuccess) e = detail::allow_smem(k_row_gen<T, V, false, true, true>);
+  constexpr int V = gen_v<T>(), VR = gen_vrow<T>();
+  cudaError_t e = detail::allow_smem(k_row_gen<T, VR, true, true>);
+  if (e == cudaSuccess) e = detail::allow_smem(k_row_gen<T, VR, true, false>);
+  if (e == cudaSuccess) e = detail::allow_smem(k_row_gen<T, VR, false, true>);
+  if (e == cudaSuccess) e = detail::allow_smem(k_row_gen<T, VR, false, true, true>);
   if (e == cudaSuccess) e = detail::allow_smem(k_col_gen<T, V>);
   if (e == cudaSuccess) e = detail::allow_smem(k_col_gen<T, V, true>);
   return e;

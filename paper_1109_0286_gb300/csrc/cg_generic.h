@@ -68,6 +68,12 @@ constexpr int kGenCodes = 4;
 // butterflies already hold twice the registers).
 template <typename T>
 constexpr int gen_v() { return std::is_same<T, float>::value ? 2 : 1; }
+// Rows per thread group of the row passes (FP32; FP64 and double-float 1).
+#ifndef CGF_GEN_VROW
+#define CGF_GEN_VROW 2
+#endif
+template <typename T>
+constexpr int gen_vrow() { return std::is_same<T, float>::value ? CGF_GEN_VROW : 1; }
 #ifndef CGF_GEN_THREADS
 #define CGF_GEN_THREADS 256
 #endif
@@ -89,8 +95,9 @@ constexpr int gen_col_minb() { return std::is_same<T, float>::value ? CGF_GEN_CO
 template <typename T>
 struct GenLaunch {
   // wl: table of nx / 2, wx: W_nx^k (k <= nx / 2), wn: table of ny.  Rows per
-  // CTA (RowArgs::rows) and columns per CTA (ColArgs::ffts) are multiples of
-  // gen_v<T>().  The white-noise source (op OP_XI) runs its own instantiation.
+  // CTA (RowArgs::rows) are multiples of gen_vrow<T>(), columns per CTA
+  // (ColArgs::ffts) of gen_v<T>().  The white-noise source (op OP_XI) runs its
+  // own instantiation.
   static cudaError_t row(bool in_spec, bool out_spec, const InstDesc<T>* d, int ninst,
                          const RowArgs& a, const GenLen& g, const T* wl, const T* wx,
                          cudaStream_t s);

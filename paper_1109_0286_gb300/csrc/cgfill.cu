@@ -1086,7 +1086,7 @@ bool loop_precision(const fill_plan* p) {
 // and 200 KB of shared memory.
 template <typename T>
 bool gen_row_ok(const fill_plan* p, int r) {
-  constexpr int V = gen_v<T>();
+  constexpr int V = gen_vrow<T>();
   return r >= V && r % V == 0 && pow2(r / V) && (r / V) * p->grow.nt <= GenLaunch<T>::max_threads() &&
          (p->ny + r - 1) / r <= kMaxPartials && GenLaunch<T>::row_smem(p->nx / 2, r) <= 200 * 1024;
 }
@@ -1150,14 +1150,15 @@ fill_status gen_upload_maps(fill_plan* p) {
 template <typename T>
 fill_status setup_generic(fill_plan* p) {
   Precision<T>& P = prec<T>(p);
-  constexpr int V = gen_v<T>();
+  constexpr int V = gen_v<T>(), VR = gen_vrow<T>();
   const size_t third = 75 * 1024;
   const bool user = loop_precision<T>(p);
   if (user && p->o.rows_per_cta > 0) {
     P.rows = p->o.rows_per_cta;
   } else {
-    P.rows = V;
-    if (gen_row_ok<T>(p, 2 * V) && GenLaunch<T>::row_smem(p->nx / 2, 2 * V) <= third) P.rows = 2 * V;
+    P.rows = VR;
+    if (gen_row_ok<T>(p, 2 * VR) && GenLaunch<T>::row_smem(p->nx / 2, 2 * VR) <= third)
+      P.rows = 2 * VR;
   }
   if (user && p->o.ffts_per_cta > 0) {
     P.ffts = p->o.ffts_per_cta;
@@ -1402,8 +1403,8 @@ fill_status fill_init(fill_plan** out, int ny, int nx, const double* P_half,
       return FILL_EINVAL;
     // threads per transform, for the precision that carries the CG loop
     const bool wide = opts && opts->mode == FILL_MODE_FP64;
-    gen_threads(&grow, wide ? 1 : 2, wide);
-    gen_threads(&gcol, wide ? 1 : 2, wide);
+    gen_threads(&grow, wide ? 1 : gen_vrow<float>(), wide);
+    gen_threads(&gcol, wide ? 1 : gen_v<float>(), wide);
   }
   fill_opts o;
   if (opts)
@@ -2404,7 +2405,7 @@ fill_status tune_gen_t(fill_plan* p, const char* path) {
     for (int code : gen_candidates(p->grow.n)) {
       fill_status fs = apply_gen_code(p, true, code);
       if (fs != FILL_OK) return fs;
-      for (int r = V; r <= 4 * V; r *= 2) {
+      for (int r = gen_vrow<T>(); r <= 4 * gen_vrow<T>(); r *= 2) {
         if (!gen_row_ok<T>(p, r)) continue;
         Ctx<T> c = ctx<T>(p);
         c.rows = r;
