@@ -60,6 +60,14 @@ def test_host_only_calls(lib):
                            ctypes.byref(o), None)
         assert st == 1 and not plan.value, (ny, nx)
     assert lib.fill_realize(None, None, 0, None, 1e-6, None, None) == 1
+    # option ranges are checked before any device work (lanes: 0..8)
+    Pv, mv = np.ones((64, 33)), np.ones((64, 64), np.uint8)
+    for field, bad in (("lanes", 9), ("lanes", -1), ("col_kernel", 2), ("host_loops", 2)):
+        ob = cg.fill_opts_default()
+        setattr(ob, field, bad)
+        st = lib.fill_init(ctypes.byref(plan), 64, 64, Pv.ctypes.data, mv.ctypes.data,
+                           ctypes.byref(ob), None)
+        assert st == 1 and not plan.value, field
     lib.fill_destroy(None)
 
 
