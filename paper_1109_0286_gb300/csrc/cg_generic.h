@@ -64,10 +64,14 @@ struct GenLen {
 bool gen_factor(int n, GenLen* g, int code = 0);
 constexpr int kGenCodes = 4;
 
-// Transforms per thread group: 2 in FP32, 1 in FP64 and double-float (their
-// butterflies already hold twice the registers).
+// Columns per thread group of the column pass: 2 in FP32 (a build-time
+// width), 1 in FP64 and double-float (their butterflies already hold twice
+// the registers).
+#ifndef CGF_GEN_VCOL
+#define CGF_GEN_VCOL 2
+#endif
 template <typename T>
-constexpr int gen_v() { return std::is_same<T, float>::value ? 2 : 1; }
+constexpr int gen_v() { return std::is_same<T, float>::value ? CGF_GEN_VCOL : 1; }
 // Rows per thread group of the row passes (FP32; FP64 and double-float 1).
 #ifndef CGF_GEN_VROW
 #define CGF_GEN_VROW 2
